@@ -1,0 +1,358 @@
+"""Pins of the FP64 oracle against facts the paper and mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: brute force,
+closed forms, invariants the paper states, special cases that reduce to a
+textbook routine, and the structures printed in Fig. 1a, Fig. 2 and Table 1.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import cp_oracle as co
+from oracle import mlp_oracle as mo
+from tests.conftest import golden
+
+# ----------------------------------------------------------------------------- generator
+
+
+def test_philox_known_answers():
+    for line in open(golden("philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        out = synth.philox4x32_10(*w[:6])
+        assert [int(x) for x in out] == w[6:]
+
+
+def test_uniform_range_and_moments():
+    u = synth.uniform(7, 3, 200001)
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 3e-3 and abs(u.var() - 1 / 12) < 2e-3
+    # element i does not depend on how many are drawn
+    assert np.array_equal(synth.uniform(7, 3, 11), u[:11])
+
+
+def test_collinear_factors_exact_gram():
+    C = 0.9
+    F = synth.collinear_factors(11, [20, 17, 16], 16, C)
+    K = (1 - C) * np.eye(16) + C * np.ones((16, 16))
+    for A in F:
+        assert np.abs(A.T @ A - K).max() < 1e-12
+
+
+def test_noise_ratio_exact():
+    F = synth.uniform_factors(5, [6, 7, 8], 3)
+    T = synth.cp_full(F)
+    Tn = synth.add_noise(T, 1e-2, 5, 64)
+    ratio = np.linalg.norm((Tn - T).ravel()) / np.linalg.norm(T.ravel())
+    assert abs(ratio - 1e-2) < 1e-12
+
+
+# ----------------------------------------------------------------------------- MTTKRP
+
+
+@pytest.mark.parametrize("dims", [(3, 4, 5), (2, 3, 4, 3), (2, 2, 3, 2, 3)])
+def test_mttkrp_definition_matches_bruteforce(dims):
+    R = 3
+    T = synth.normal(1, 0, int(np.prod(dims))).reshape(dims)
+    A = synth.gaussian_factors(2, dims, R)
+    for n in range(len(dims)):
+        Mb = co.mttkrp_bruteforce(T, A, n)
+        M = co.mttkrp(T, A, n)
+        assert np.abs(M - Mb).max() <= 1e-12 * max(1.0, np.abs(Mb).max())
+
+
+def test_mttkrp_order2_is_matrix_product():
+    """N = 2: M^(1) = T A(2) and M^(2) = T^T A(1), a plain matrix product."""
+    T = synth.normal(3, 0, 7 * 5).reshape(7, 5)
+    A = synth.gaussian_factors(4, (7, 5), 4)
+    assert np.allclose(co.mttkrp(T, A, 0), T @ A[1], rtol=0, atol=1e-13)
+    assert np.allclose(co.mttkrp(T, A, 1), T.T @ A[0], rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("dims", [(4, 5, 6), (3, 4, 3, 5), (3, 2, 3, 2, 3)])
+@pytest.mark.parametrize("route", ["dt", "msdt"])
+def test_tree_mttkrps_equal_definition(dims, route):
+    """Each tree-built M^(n) equals the definition with the factors current at that moment."""
+    N = len(dims)
+    A = synth.uniform_factors(5, dims, 4)
+    T = synth.normal(6, 0, int(np.prod(dims))).reshape(dims)
+    gen = co.dt_updates(T, A) if route == "dt" else co.msdt_updates(T, A, 3 * N)
+    count = 0
+    for n, M in gen:
+        ref = co.mttkrp(T, A, n)
+        assert np.abs(M - ref).max() <= 1e-12 * np.abs(ref).max()
+        # perturb A[n] like an update would, so later nodes must see the new factor
+        A[n] = A[n] * 0.5 + 0.1 * synth.uniform(7, count, A[n].size).reshape(A[n].shape)
+        count += 1
+    assert count == (N if route == "dt" else 3 * N)
+
+
+def _edges_1based(edges):
+    out = []
+    for parent, child in edges:
+        p = "T" if parent == "T" else ",".join(str(m + 1) for m in parent)
+        out.append((p, ",".join(str(m + 1) for m in child)))
+    return out
+
+
+def _read_edges(name):
+    out = []
+    for line in open(golden(name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        p, c = [x.strip() for x in line.split("->")]
+        out.append((p, c))
+    return out
+
+
+def test_dt_tree_is_fig1a():
+    dims = (3, 3, 3, 3)
+    A = synth.uniform_factors(1, dims, 2)
+    T = synth.normal(1, 0, 81).reshape(dims)
+    ctr = co.Counters()
+    for n, M in co.dt_updates(T, A, ctr):
+        pass
+    assert sorted(_edges_1based(ctr.edges)) == sorted(_read_edges("dt_tree_n4_fig1a.txt"))
+    assert ctr.ttm_modes == [3, 0]
+
+
+def test_msdt_tree_is_fig2():
+    dims = (3, 3, 3, 3)
+    A = synth.uniform_factors(1, dims, 2)
+    T = synth.normal(1, 0, 81).reshape(dims)
+    ctr = co.Counters()
+    for n, M in co.msdt_updates(T, A, 12, ctr):
+        pass
+    assert sorted(_edges_1based(ctr.edges)) == sorted(_read_edges("msdt_tree_n4_fig2.txt"))
+    assert ctr.ttm_modes == [3, 2, 1, 0]
+
+
+def test_first_level_ttm_counts_table1():
+    for line in open(golden("cost_table1.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        N, sweeps, dt_ttms, msdt_ttms = map(int, line.split())
+        dims = (2,) * N
+        T = synth.normal(2, 0, 2 ** N).reshape(dims)
+        r_dt = co.cp_als(T, synth.uniform_factors(3, dims, 2), sweeps, route="dt")
+        r_ms = co.cp_als(T, synth.uniform_factors(3, dims, 2), sweeps, route="msdt")
+        assert r_dt.counters.ttm == dt_ttms
+        assert r_ms.counters.ttm == msdt_ttms
+        s = 2
+        assert r_ms.counters.ttm_flops == pytest.approx(2 * N / (N - 1) * s ** N * 2 * sweeps)
+        assert r_dt.counters.ttm_flops == pytest.approx(4 * s ** N * 2 * sweeps)
+
+
+# ----------------------------------------------------------------------------- solve / residual
+
+
+def test_cholesky_solve_equals_pinv_and_lstsq():
+    A = synth.gaussian_factors(8, (30, 30), 6)
+    G = (A[0].T @ A[0]) * (A[1].T @ A[1])
+    M = synth.normal(9, 0, 12 * 6).reshape(12, 6)
+    X = co.solve_normal(M, G)
+    assert np.abs(X @ G - M).max() < 1e-10 * np.abs(M).max()
+    assert np.abs(X - M @ np.linalg.pinv(G)).max() < 1e-12 * np.abs(X).max()
+    # rank-deficient Gamma: the pseudo-inverse branch = minimum-norm least squares
+    B = synth.normal(10, 0, 6 * 3).reshape(6, 3)
+    Gd = B @ B.T                                   # rank 3, PSD, Cholesky fails
+    Xd = co.solve_normal(M, Gd)
+    ref = np.linalg.lstsq(Gd, M.T, rcond=None)[0].T
+    assert np.abs(Xd - ref).max() < 1e-8 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dims", [(5, 6, 7), (4, 3, 5, 4)])
+def test_residual_formula_equals_direct(dims):
+    R = 3
+    A = synth.uniform_factors(12, dims, R)
+    T = synth.normal(13, 0, int(np.prod(dims))).reshape(dims) + synth.cp_full(A)
+    N = len(dims)
+    S = [co.gram(a) for a in A]
+    G = co.hadamard_except(S, N - 1)
+    M = co.mttkrp(T, A, N - 1)
+    r1 = co.residual_formula(float(np.sum(T * T)), G, A[N - 1], M)
+    assert abs(r1 - co.residual_direct(T, A)) < 1e-10
+
+
+def test_cp_full_matches_generator_rank_one_sum():
+    A = synth.gaussian_factors(14, (3, 4, 2), 2)
+    T = co.cp_full(A)
+    i, j, k = 2, 1, 1
+    assert T[i, j, k] == pytest.approx(sum(A[0][i, r] * A[1][j, r] * A[2][k, r] for r in range(2)))
+    assert np.abs(T - synth.cp_full(A)).max() < 1e-13
+
+
+# ----------------------------------------------------------------------------- CP-ALS
+
+
+def test_als_direct_residual_monotone():
+    """ALS decreases the residual monotonically (Sec. I)."""
+    dims, R = (8, 9, 10), 4
+    T, F, A0 = synth.make_problem(20, dims, R, eta=0.05)
+    A = [a.copy() for a in A0]
+    prev = co.residual_direct(T, A)
+    for _ in range(15):
+        A = co.cp_als(T, A, 1).A
+        r = co.residual_direct(T, A)
+        assert r <= prev + 1e-13
+        prev = r
+
+
+def test_als_exact_recovery_noiseless():
+    """Noiseless rank-R tensors with well-conditioned factors are recovered (fit -> 1)."""
+    ok = 0
+    for seed in range(10):
+        dims, R = (10, 11, 12), 3
+        T, F, A0 = synth.make_problem(100 + seed, dims, R, law="gaussian")
+        res = co.cp_als(T, A0, 500, delta=1e-13)
+        if co.residual_direct(T, res.A) < 1e-8:
+            ok += 1
+    assert ok >= 8
+
+
+def test_als_order2_reaches_eckart_young():
+    """N = 2: the ALS fixed point is the best rank-R approximation (Eckart-Young)."""
+    s1, s2, R = 12, 9, 3
+    U, _ = np.linalg.qr(synth.normal(30, 0, s1 * s1).reshape(s1, s1))
+    V, _ = np.linalg.qr(synth.normal(30, 1, s2 * s2).reshape(s2, s2))
+    sig = np.array([10.0, 8.0, 6.0, 2.0, 1.5, 1.0, 0.5, 0.3, 0.1])
+    T = (U[:, :s2] * sig) @ V.T
+    res = co.cp_als(T, synth.uniform_factors(31, (s1, s2), R), 300)
+    opt = math.sqrt(np.sum(sig[R:] ** 2)) / math.sqrt(np.sum(sig ** 2))
+    assert abs(co.residual_direct(T, res.A) - opt) < 1e-10
+    assert abs(res.resid[-1] - opt) < 1e-8
+
+
+@pytest.mark.parametrize("dims", [(6, 7, 8), (4, 5, 4, 5)])
+def test_dt_msdt_naive_trajectories_identical(dims):
+    """MSDT gives exactly the results of the standard dimension tree (Sec. I, III)."""
+    T, F, A0 = synth.make_problem(40, dims, 3, eta=0.1)
+    a = co.cp_als(T, A0, 10, route="naive")
+    b = co.cp_als(T, A0, 10, route="dt")
+    c = co.cp_als(T, A0, 10, route="msdt")
+    for n in range(len(dims)):
+        sc = np.abs(a.A[n]).max()
+        assert np.abs(a.A[n] - b.A[n]).max() < 1e-10 * sc
+        assert np.abs(a.A[n] - c.A[n]).max() < 1e-10 * sc
+    assert np.allclose(a.resid, c.resid, rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- PP
+
+
+def _pp_setup(dims, R, seed, t, T=None, only=None):
+    Ap = synth.uniform_factors(seed, dims, R)
+    D = synth.gaussian_factors(seed + 1, dims, R)
+    A = [Ap[i] + (t * D[i] if (only is None or i == only) else 0.0) for i in range(len(dims))]
+    if T is None:
+        T = synth.normal(seed + 2, 0, int(np.prod(dims))).reshape(dims)
+    return T, Ap, A
+
+
+def _pp_err(T, Ap, A, n):
+    pairs, Mp = co.pp_operators(T, Ap)
+    dA = [A[i] - Ap[i] for i in range(len(A))]
+    S = [co.gram(a) for a in A]
+    Mt = co.pp_mttkrp(pairs, Mp, A, dA, S, n)
+    M = co.mttkrp(T, A, n)
+    return np.abs(Mt - M).max() / np.abs(M).max(), Mt, M
+
+
+@pytest.mark.parametrize("dims", [(5, 6, 7), (4, 5, 3, 4)])
+def test_pp_zero_perturbation_is_exact(dims):
+    T, Ap, A = _pp_setup(dims, 3, 50, 0.0)
+    for n in range(len(dims)):
+        e, Mt, M = _pp_err(T, Ap, A, n)
+        assert e < 1e-13
+
+
+@pytest.mark.parametrize("dims", [(5, 6, 7), (4, 5, 3, 4)])
+def test_pp_single_factor_perturbation_is_exact(dims):
+    """Multilinearity: with one dA(i) != 0 the first-order term is the whole change."""
+    for only in range(len(dims)):
+        T, Ap, A = _pp_setup(dims, 3, 60, 0.3, only=only)
+        for n in range(len(dims)):
+            e, _, _ = _pp_err(T, Ap, A, n)
+            assert e < 1e-12
+
+
+def test_pp_order3_exact_on_cp_tensor():
+    """N = 3, T = [[A]] with the current factors: V equals the second-order term exactly."""
+    dims = (5, 6, 7)
+    _, Ap, A = _pp_setup(dims, 3, 70, 0.2)
+    T = co.cp_full(A)
+    for n in range(3):
+        e, _, _ = _pp_err(T, Ap, A, n)
+        assert e < 1e-12
+
+
+def _slope(ts, errs):
+    return np.polyfit(np.log(ts), np.log(errs), 1)[0]
+
+
+def test_pp_error_order():
+    """||M~ - M|| ~ t^2 for N = 3 with a general T; ~ t^3 for N = 4 with T = [[A]]."""
+    ts = np.array([1e-1, 5e-2, 2.5e-2, 1.25e-2])
+    e3 = [_pp_err(*_pp_setup((5, 6, 7), 3, 80, t), 0)[0] for t in ts]
+    assert abs(_slope(ts, e3) - 2.0) < 0.1
+    e4 = []
+    for t in ts:
+        _, Ap, A = _pp_setup((4, 5, 4, 5), 3, 90, t)
+        e4.append(_pp_err(co.cp_full(A), Ap, A, 1)[0])
+    assert abs(_slope(ts, e4) - 3.0) < 0.1
+
+
+def test_pp_loop_tiny_eps_is_plain_als():
+    T, F, A0 = synth.make_problem(95, (6, 7, 8), 3, eta=0.05)
+    a = co.cp_als(T, A0, 8)
+    b = co.pp_cp_als(T, A0, 8, eps=1e-12)
+    assert b.kinds == ["als"] * 8 and b.n_pp_init == 0
+    assert np.allclose(a.resid, b.resid, rtol=0, atol=1e-14)
+
+
+def test_pp_loop_enters_and_tracks_als():
+    """With eps = 0.1 PP is entered near convergence and the fit follows exact ALS closely."""
+    T, F, A0 = synth.make_problem(96, (12, 13, 14), 4, eta=1e-3)
+    a = co.cp_als(T, A0, 40)
+    b = co.pp_cp_als(T, A0, 40, eps=0.1)
+    assert b.n_pp_init >= 1 and "pp" in b.kinds
+    assert b.kinds[0] == "als"                       # dA <- A initially: first sweep is exact
+    assert abs(b.resid[-1] - a.resid[-1]) < 1e-3
+
+
+# ----------------------------------------------------------------------------- MLP
+
+
+def test_mlp_param_count_and_fd_gradient():
+    assert mo.N_PARAMS == 4801
+    theta = mo.init_params(synth.uniform(200, 0, mo.N_PARAMS))
+    X = synth.normal(201, 0, 16 * 8).reshape(16, 8)
+    y = (synth.uniform(202, 0, 16) < 0.5).astype(float)
+    L, g = mo.grad(theta, X, y)
+    assert L == pytest.approx(mo.loss(theta, X, y), abs=1e-14)
+    idx = np.linspace(0, mo.N_PARAMS - 1, 97).astype(int)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros(mo.N_PARAMS)
+        e[i] = h
+        fd = (mo.loss(theta + e, X, y) - mo.loss(theta - e, X, y)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-9
+
+
+def test_mlp_loss_closed_forms():
+    """Zero weights: p = 1/2 and the loss is log 2; a single sample gives dL/db3 = p - y."""
+    theta = np.zeros(mo.N_PARAMS)
+    X = synth.normal(203, 0, 5 * 8).reshape(5, 8)
+    assert mo.loss(theta, X, np.ones(5)) == pytest.approx(math.log(2.0), abs=1e-15)
+    L, g = mo.grad(theta, X[:1], np.array([1.0]))
+    assert g[-1] == pytest.approx(0.5 - 1.0, abs=1e-15)
+
+
+def test_adam_first_step_is_signed_lr():
+    """With bias correction the first Adam step is -lr * g / (|g| + eps), about lr * sign(g)."""
+    g = np.array([3.0, -0.5, 1e-3])
+    th, m, v = mo.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.01, eps=1e-8)
+    assert np.allclose(th, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
