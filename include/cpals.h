@@ -1,0 +1,224 @@
+/*
+ * cpals.h - C ABI of the GB300 CP-ALS engine (dimension tree, multi-sweep
+ * dimension tree, pairwise perturbation) for dense order-N tensors.
+ *
+ * Problem (Sec. II-B, Alg. 1): given a dense tensor T of size s_1 x ... x s_N
+ * and a rank R, find factors A(n) (s_n x R) minimising
+ * 1/2 ||T - [[A(1), ..., A(N)]]||_F^2 by alternating least squares: each update
+ * solves A(n) Gamma(n) = M(n) with the MTTKRP M(n) = T_(n) P(n) and
+ * Gamma(n) = *_{k != n} A(k)^T A(k) (Eq. gram).
+ *
+ * Conventions shared by every call:
+ *  - Modes are 0-based (the paper's mode n is n-1 here).
+ *  - The tensor is C order (last index fastest), contiguous, on the device.
+ *  - Factors are s_n x R row-major (r fastest), FP64 on the host side of the
+ *    ABI; the library keeps FP64 masters plus FP32 / split-bf16 operand copies.
+ *  - Every call is enqueued on the CUDA stream given to cp_init (a
+ *    cudaStream_t passed as void*; NULL = legacy default stream).  Calls that
+ *    return host values (cp_fit, cp_get_*, cp_sweep_pp's regime tests)
+ *    synchronise that stream.
+ *  - Errors are returned, never raised by abort().  After CP_ECUDA or
+ *    CP_ETIMEOUT the context is poisoned and every later call returns
+ *    CP_ESTATE; cp_last_error() describes the first failure.
+ *  - The library owns every buffer it allocates (factors, tree intermediates,
+ *    PP operators, traces) and frees them in cp_free.  It never writes T.
+ */
+#ifndef CPALS_H
+#define CPALS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cp_ctx cp_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    CP_OK = 0,
+    CP_EINVAL = 1,    /* bad argument (sizes, mode, eps, NULL pointer)          */
+    CP_ENOMEM = 2,    /* device or host allocation failed                       */
+    CP_ECUDA = 3,     /* a CUDA call failed; context poisoned                   */
+    CP_ENOTSPD = 4,   /* Gamma(n) not positive definite even after the shift    */
+    CP_ENUMERIC = 5,  /* NaN or Inf in a factor or in the fit                   */
+    CP_ETIMEOUT = 6,  /* a bounded device wait ran out; context poisoned        */
+    CP_ESTATE = 7     /* context poisoned by an earlier failure, or wrong state */
+} cp_status;
+
+/* Arithmetic of the first-level TTM T x_m A(m) (Sec. II-C), the dominant
+ * contraction.  All variants accumulate in FP32; mTTVs run in FP32 and the
+ * Gram / Hadamard / Cholesky / residual terms in FP64 whatever is chosen. */
+typedef enum {
+    CP_FP32_SIMT = 0, /* FP32 FMA on the CUDA cores                              */
+    CP_TF32 = 1,      /* tcgen05 kind::tf32 on the raw FP32 tensor (10-bit mant.) */
+    CP_BF16X3 = 2,    /* tcgen05 kind::f16: x = hi + lo in bf16, hi*hi+hi*lo+lo*hi */
+    CP_BF16 = 3       /* tcgen05 kind::f16 on bf16(x) only (reported, low accuracy) */
+} cp_prec;
+
+typedef struct {
+    int prec;         /* cp_prec of the first-level TTM                           */
+    double pp_eps;    /* PP tolerance epsilon of Alg. 2 (0 < eps < 1)             */
+    double delta;     /* stopping tolerance on |r - r_old| (Alg. 1); <= 0: never  */
+    int max_sweeps;   /* cap used by cp_run (<= 0: no cap)                        */
+    int judge_every;  /* policy mode: direct residual every k sweeps (0 = off)    */
+    int use_policy;   /* reserved: the policy is passed to cp_sweep_pp            */
+    uint64_t seed;    /* Philox4x32-10 seed of the default U[0,1) initial factors */
+} cp_config;
+
+/* Fill *cfg with defaults: bf16x3 TTM, eps 0.1, delta 0, judge every 5 sweeps. */
+void cp_config_default(cp_config *cfg);
+
+/*
+ * cp_init - create a decomposition context (Alg. 1, line 2; Alg. 2, line 2).
+ *   N        tensor order, 3 <= N <= 8
+ *   dims     N mode sizes, each >= 1; host array, copied
+ *   R        rank, 1 <= R <= 256
+ *   T_dev    device pointer to the tensor, C order, contiguous.  dtype 0: FP32,
+ *            borrowed (must outlive the context, never written); dtype 1: FP64,
+ *            converted once into a library-owned FP32 copy.
+ *   A0_host  NULL, or N host blocks (s_n x R row-major FP64, concatenated in mode
+ *            order) of initial factors.  NULL draws U[0,1) entries (Alg. 1) from
+ *            Philox4x32-10 with key = cfg->seed, counter = (j, 0, n, 0) for
+ *            mode n, two doubles per block j, ((w0<<32|w1)>>11)*2^-53.
+ *   cfg      NULL for defaults; copied.
+ *   stream   cudaStream_t (as void*) every later call is enqueued on.
+ * Computes ||T||_F^2 and the Grams S(n) = A(n)^T A(n).  Sets dA(n) = A(n), so the
+ * first PP test fails and the first sweep is a regular one (Alg. 2, line 2).
+ * Returns CP_EINVAL on bad sizes, CP_ENOMEM if the workspace (about
+ * prod(dims)/min(dims) * R * 4 bytes per tree level, plus PP operators on first
+ * use) does not fit, CP_ECUDA on a CUDA failure.  *out is NULL on failure.
+ */
+cp_status cp_init(cp_ctx **out, int N, const int64_t *dims, int R, const void *T_dev,
+                  int dtype, const double *A0_host, const cp_config *cfg, void *stream);
+
+/*
+ * cp_mttkrp - exact MTTKRP M(mode) = T_(mode) P(mode) with the current factors
+ * (Sec. II-B), built down a dimension tree (first-level TTM, then mTTVs).
+ *   M_dev  device buffer of s_mode x R floats, row-major; written.
+ */
+cp_status cp_mttkrp(cp_ctx *ctx, int mode, float *M_dev);
+
+/*
+ * cp_ttm - first-level contraction X = T x_mode A(mode) (Sec. II-C) with the
+ * current factor.  X_dev: device buffer of prod_{k != mode} s_k x R floats, laid
+ * out with the remaining modes in increasing order then r fastest.
+ */
+cp_status cp_ttm(cp_ctx *ctx, int mode, float *X_dev);
+
+/*
+ * cp_sweep_dt - nsweeps CP-ALS sweeps (Alg. 1), each updating A(0..N-1) in order
+ * with MTTKRPs from the standard binary dimension tree (Sec. II-C, Fig. 1a): two
+ * first-level TTMs per sweep.  After each sweep the relative residual is
+ * evaluated with Eq. (residual) and recorded in the trace.
+ */
+cp_status cp_sweep_dt(cp_ctx *ctx, int nsweeps);
+
+/*
+ * cp_sweep_msdt - nsweeps sweeps with the multi-sweep dimension tree (Sec. III,
+ * Fig. 2): root T x_m A(m) right after A(m) is updated, serving the next N-1
+ * updates; roots cycle m = N-1, N-2, ..., 0.  The root persists across calls
+ * (the cross-sweep cache) while its factor is unchanged.
+ */
+cp_status cp_sweep_msdt(cp_ctx *ctx, int nsweeps);
+
+/*
+ * cp_sweep_pp - nsweeps sweeps of PP-CP-ALS (Alg. 2).  While every
+ * ||dA(i)||_F < eps ||A(i)||_F the sweep is approximated (Eq. ppupdate) from PP
+ * operators M_p(i,j), M_p(n) built at the PP initialization (not counted as a
+ * sweep); otherwise a regular MSDT sweep runs and dA(i) is that sweep's change.
+ *   eps     PP tolerance, 0 < eps < 1.
+ *   policy  NULL: the rule above.  Otherwise a cp_policy from cp_policy_create:
+ *           its network decides, before each sweep, between an approximated
+ *           sweep, a rebuild of the operators, and a regular sweep; a direct
+ *           residual every cfg.judge_every sweeps rolls back any sweep that
+ *           raised it.
+ */
+typedef struct cp_policy cp_policy;
+cp_status cp_sweep_pp(cp_ctx *ctx, int nsweeps, double eps, cp_policy *policy);
+
+/*
+ * cp_pp_init / cp_pp_mttkrp - the two PP steps exposed separately.  cp_pp_init
+ * sets A_p = A, dA = 0 and builds every M_p(i,j) (i < j) and M_p(n) with the PP
+ * dimension tree (Fig. 1b).  cp_pp_mttkrp writes the approximated MTTKRP of Eq.
+ * ppupdate for `mode` with the current A, dA = A - A_p and S (s_mode x R floats,
+ * device) without updating anything.  CP_ESTATE if no operators were built.
+ */
+cp_status cp_pp_init(cp_ctx *ctx);
+cp_status cp_pp_mttkrp(cp_ctx *ctx, int mode, float *M_dev);
+
+/*
+ * cp_fit - relative residual r and fitness f = 1 - r (Sec. V-C).
+ *   exact 0: Eq. (residual) from the amortized terms of the last update
+ *            (||T||^2 + <Gamma(N), S(N)> - 2 <M(N), A(N)>, radicand clamped at 0)
+ *   exact 1: directly, ||T - [[A]]||_F / ||T||_F (Eq. residual-def), one
+ *            streaming pass over T.
+ * Either output pointer may be NULL.  Synchronises the stream.
+ */
+cp_status cp_fit(cp_ctx *ctx, int exact, double *fit, double *resid);
+
+/* Copy factor `mode` out (host, s_mode x R FP64) or replace it (and its Gram). */
+cp_status cp_get_factor(cp_ctx *ctx, int mode, double *A_host);
+cp_status cp_set_factor(cp_ctx *ctx, int mode, const double *A_host);
+
+/* Per-sweep trace record, appended by every sweep call. */
+typedef struct {
+    int32_t sweep;        /* 0-based sweep index since cp_init                    */
+    int32_t kind;         /* 0 DT, 1 MSDT, 2 PP approximated, 3 PP regular (MSDT) */
+    int32_t pp_init;      /* 1 if PP operators were (re)built before this sweep   */
+    int32_t rolled_back;  /* 1 if the policy's judge undid this sweep             */
+    double resid;         /* Eq. (residual) after the sweep                       */
+    double max_rel_step;  /* max_i ||A(i)_after - A(i)_before||_F / ||A(i)||_F    */
+    double max_rel_dAp;   /* max_i ||A(i) - A_p(i)||_F / ||A(i)||_F (0 if no ops)  */
+    double v_share;       /* ||V(N-1)||_F / ||M~(N-1)||_F in PP sweeps, else 0    */
+    double ms;            /* device time of the sweep (CUDA events)               */
+} cp_trace_rec;
+
+/* Copy up to *len records into buf (may be NULL); *len returns the total count. */
+cp_status cp_get_trace(cp_ctx *ctx, cp_trace_rec *buf, size_t *len);
+
+/* Work counters since cp_init. */
+typedef struct {
+    int64_t ttm;            /* first-level TTMs (2 s^N R flops each)          */
+    int64_t mttv;           /* multi-TTV launches                             */
+    int64_t pp_init;        /* PP operator builds                             */
+    int64_t sweeps_exact;   /* DT/MSDT/regular sweeps                         */
+    int64_t sweeps_pp;      /* approximated sweeps                            */
+    int64_t launches;       /* kernel launches issued by the library          */
+    double ttm_flops;       /* algorithmic flops of the first-level TTMs      */
+    double mttv_flops;      /* 2 x entries read, summed over mTTVs            */
+    double pp_flops;        /* U + V flops of approximated MTTKRPs            */
+    double ttm_bytes;       /* algorithmic HBM bytes of the TTMs (read+write) */
+    double mttv_bytes;      /* algorithmic bytes of the mTTVs                 */
+} cp_stats;
+cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
+
+/* Description of the first failure of this context ("" if none); never NULL. */
+const char *cp_last_error(const cp_ctx *ctx);
+
+/* Release everything the context owns.  NULL-safe; T is not freed. */
+void cp_free(cp_ctx *ctx);
+
+/*
+ * Learned PP policy (no counterpart in the paper; Alg. 2's eps rule is the
+ * fallback).  A small MLP 8 -> 64 -> 64 -> 1 (tanh, tanh, sigmoid; 4801 FP32
+ * parameters, order W1, b1, W2, b2, w3, b3) scores from 8 trace features how
+ * safe an approximated sweep is.  Training and inference run in the library's
+ * own CUDA kernels on the stream given here.
+ */
+cp_status cp_policy_create(cp_policy **out, const float *theta_host, void *stream);
+cp_status cp_policy_get(cp_policy *p, float *theta_host);
+/* Forward pass: X_dev (B x 8 floats) -> prob_dev (B floats). */
+cp_status cp_policy_forward(cp_policy *p, const float *X_dev, int B, float *prob_dev);
+/* Mean binary cross-entropy and its gradient (4801 floats) on a batch. */
+cp_status cp_policy_grad(cp_policy *p, const float *X_dev, const float *y_dev, int B,
+                         float *loss_dev, float *grad_dev);
+/* `steps` Adam steps (Kingma and Ba 2015) over one batch, lr given. */
+cp_status cp_policy_train(cp_policy *p, const float *X_dev, const float *y_dev, int B,
+                          int steps, float lr);
+void cp_policy_free(cp_policy *p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPALS_H */

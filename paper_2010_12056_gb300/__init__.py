@@ -1,0 +1,299 @@
+"""GB300 CP-ALS engine: Python binding of libcpals.so (argument marshalling only).
+
+Every step of the decomposition runs in the library's CUDA kernels behind the C
+ABI declared in include/cpals.h; this module converts arguments, keeps the
+borrowed tensor alive and turns status codes into exceptions.  There is no CPU
+fallback: if libcpals.so is missing or fails to load, every call raises.
+
+PyTorch supplies device memory (the input tensor, output buffers) and the CUDA
+stream the library enqueues on (the current torch stream at construction).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcpals.so")
+_lib = None
+
+PREC = {"fp32": 0, "tf32": 1, "bf16x3": 2, "bf16": 3}
+STATUS = {0: "CP_OK", 1: "CP_EINVAL", 2: "CP_ENOMEM", 3: "CP_ECUDA", 4: "CP_ENOTSPD",
+          5: "CP_ENUMERIC", 6: "CP_ETIMEOUT", 7: "CP_ESTATE"}
+KINDS = {0: "dt", 1: "msdt", 2: "pp", 3: "pp-regular"}
+N_POLICY_PARAMS = 4801
+
+
+class CPError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("pp_eps", ctypes.c_double), ("delta", ctypes.c_double),
+                ("max_sweeps", ctypes.c_int), ("judge_every", ctypes.c_int),
+                ("use_policy", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class TraceRec(ctypes.Structure):
+    _fields_ = [("sweep", ctypes.c_int32), ("kind", ctypes.c_int32), ("pp_init", ctypes.c_int32),
+                ("rolled_back", ctypes.c_int32), ("resid", ctypes.c_double),
+                ("max_rel_step", ctypes.c_double), ("max_rel_dAp", ctypes.c_double),
+                ("v_share", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("ttm", ctypes.c_int64), ("mttv", ctypes.c_int64), ("pp_init", ctypes.c_int64),
+                ("sweeps_exact", ctypes.c_int64), ("sweeps_pp", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("ttm_flops", ctypes.c_double),
+                ("mttv_flops", ctypes.c_double), ("pp_flops", ctypes.c_double),
+                ("ttm_bytes", ctypes.c_double), ("mttv_bytes", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "cp_config_default": (None, [ctypes.POINTER(Config)]),
+    "cp_init": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(ctypes.c_int64), _I, _P, _I,
+                     ctypes.POINTER(_D), ctypes.POINTER(Config), _P]),
+    "cp_mttkrp": (_I, [_P, _I, _P]),
+    "cp_ttm": (_I, [_P, _I, _P]),
+    "cp_sweep_dt": (_I, [_P, _I]),
+    "cp_sweep_msdt": (_I, [_P, _I]),
+    "cp_sweep_pp": (_I, [_P, _I, _D, _P]),
+    "cp_pp_init": (_I, [_P]),
+    "cp_pp_mttkrp": (_I, [_P, _I, _P]),
+    "cp_fit": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "cp_get_factor": (_I, [_P, _I, ctypes.POINTER(_D)]),
+    "cp_set_factor": (_I, [_P, _I, ctypes.POINTER(_D)]),
+    "cp_get_trace": (_I, [_P, ctypes.POINTER(TraceRec), ctypes.POINTER(ctypes.c_size_t)]),
+    "cp_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
+    "cp_last_error": (ctypes.c_char_p, [_P]),
+    "cp_free": (None, [_P]),
+    "cp_policy_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_float), _P]),
+    "cp_policy_get": (_I, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "cp_policy_forward": (_I, [_P, _P, _I, _P]),
+    "cp_policy_grad": (_I, [_P, _P, _P, _I, _P, _P]),
+    "cp_policy_train": (_I, [_P, _P, _P, _I, _I, ctypes.c_float]),
+    "cp_policy_free": (None, [_P]),
+}
+
+
+def lib():
+    """Load libcpals.so (built by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class CPContext:
+    """One decomposition of a dense CUDA tensor (float32 borrowed, float64 copied once)."""
+
+    def __init__(self, T, R, A0=None, prec="bf16x3", seed=20101205, pp_eps=0.1, judge_every=5,
+                 stream=None):
+        import torch
+        if not (isinstance(T, torch.Tensor) and T.is_cuda and T.is_contiguous()):
+            raise ValueError("T must be a contiguous CUDA tensor")
+        if T.dtype not in (torch.float32, torch.float64):
+            raise ValueError("T must be float32 or float64")
+        self._L = lib()
+        self.T = T
+        self.dims = [int(d) for d in T.shape]
+        self.N = len(self.dims)
+        self.R = int(R)
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        cfg = Config()
+        self._L.cp_config_default(ctypes.byref(cfg))
+        cfg.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        cfg.seed = int(seed)
+        cfg.pp_eps = float(pp_eps)
+        cfg.judge_every = int(judge_every)
+        dims = (ctypes.c_int64 * self.N)(*self.dims)
+        a0p = None
+        if A0 is not None:
+            flat = np.ascontiguousarray(np.concatenate([np.asarray(a, np.float64).ravel() for a in A0]))
+            expect = sum(d * self.R for d in self.dims)
+            if flat.size != expect:
+                raise ValueError("A0 sizes do not match dims x R")
+            self._a0 = flat
+            a0p = flat.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        h = ctypes.c_void_p()
+        st = self._L.cp_init(ctypes.byref(h), self.N, dims, self.R, _dptr(T),
+                             1 if T.dtype == torch.float64 else 0, a0p, ctypes.byref(cfg),
+                             _stream_ptr(self._stream))
+        if st != 0:
+            raise CPError(st, "cp_init failed")
+        self._h = h
+
+    # -- helpers
+    def _ck(self, st):
+        if st != 0:
+            msg = self._L.cp_last_error(self._h)
+            raise CPError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.cp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls
+    def mttkrp(self, mode, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.dims[mode], self.R, dtype=torch.float32, device=self.T.device)
+        self._ck(self._L.cp_mttkrp(self._h, int(mode), _dptr(out)))
+        return out
+
+    def ttm(self, mode, out=None):
+        import torch
+        if out is None:
+            shape = [d for k, d in enumerate(self.dims) if k != mode] + [self.R]
+            out = torch.empty(shape, dtype=torch.float32, device=self.T.device)
+        self._ck(self._L.cp_ttm(self._h, int(mode), _dptr(out)))
+        return out
+
+    def sweep_dt(self, n=1):
+        self._ck(self._L.cp_sweep_dt(self._h, int(n)))
+
+    def sweep_msdt(self, n=1):
+        self._ck(self._L.cp_sweep_msdt(self._h, int(n)))
+
+    def sweep_pp(self, n=1, eps=0.1, policy=None):
+        self._ck(self._L.cp_sweep_pp(self._h, int(n), float(eps), policy._h if policy else None))
+
+    def pp_init(self):
+        self._ck(self._L.cp_pp_init(self._h))
+
+    def pp_mttkrp(self, mode, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.dims[mode], self.R, dtype=torch.float32, device=self.T.device)
+        self._ck(self._L.cp_pp_mttkrp(self._h, int(mode), _dptr(out)))
+        return out
+
+    def fit(self, exact=False):
+        f, r = ctypes.c_double(), ctypes.c_double()
+        self._ck(self._L.cp_fit(self._h, 1 if exact else 0, ctypes.byref(f), ctypes.byref(r)))
+        return f.value, r.value
+
+    def get_factor(self, mode):
+        out = np.empty((self.dims[mode], self.R), dtype=np.float64)
+        self._ck(self._L.cp_get_factor(self._h, int(mode), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def factors(self):
+        return [self.get_factor(n) for n in range(self.N)]
+
+    def set_factor(self, mode, A):
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        if A.shape != (self.dims[mode], self.R):
+            raise ValueError("bad factor shape")
+        self._ck(self._L.cp_set_factor(self._h, int(mode), A.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def trace(self):
+        n = ctypes.c_size_t(0)
+        self._ck(self._L.cp_get_trace(self._h, None, ctypes.byref(n)))
+        buf = (TraceRec * max(1, n.value))()
+        self._ck(self._L.cp_get_trace(self._h, buf, ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            r = buf[i]
+            out.append({"sweep": r.sweep, "kind": KINDS.get(r.kind, r.kind), "pp_init": r.pp_init,
+                        "rolled_back": r.rolled_back, "resid": r.resid,
+                        "max_rel_step": r.max_rel_step, "max_rel_dAp": r.max_rel_dAp,
+                        "v_share": r.v_share, "ms": r.ms})
+        return out
+
+    def stats(self):
+        s = Stats()
+        self._ck(self._L.cp_get_stats(self._h, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+
+class Policy:
+    """The learned PP-regime scorer (FP32 MLP 8 -> 64 -> 64 -> 1) on the device."""
+
+    def __init__(self, theta, stream=None):
+        import torch
+        self._L = lib()
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        if th.size != N_POLICY_PARAMS:
+            raise ValueError("theta must hold 4801 parameters")
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = self._L.cp_policy_create(ctypes.byref(h), th.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                      _stream_ptr(self._stream))
+        if st != 0:
+            raise CPError(st, "cp_policy_create failed")
+        self._h = h
+
+    def _ck(self, st):
+        if st != 0:
+            raise CPError(st, "policy call failed")
+
+    def get(self):
+        out = np.empty(N_POLICY_PARAMS, dtype=np.float32)
+        self._ck(self._L.cp_policy_get(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def forward(self, X):
+        import torch
+        X = X.contiguous()
+        out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        self._ck(self._L.cp_policy_forward(self._h, _dptr(X), int(X.shape[0]), _dptr(out)))
+        return out
+
+    def grad(self, X, y):
+        import torch
+        X, y = X.contiguous(), y.contiguous()
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        g = torch.empty(N_POLICY_PARAMS, dtype=torch.float32, device=X.device)
+        self._ck(self._L.cp_policy_grad(self._h, _dptr(X), _dptr(y), int(X.shape[0]), _dptr(loss), _dptr(g)))
+        return loss, g
+
+    def train(self, X, y, steps, lr=1e-3):
+        X, y = X.contiguous(), y.contiguous()
+        self._ck(self._L.cp_policy_train(self._h, _dptr(X), _dptr(y), int(X.shape[0]), int(steps), float(lr)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.cp_policy_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

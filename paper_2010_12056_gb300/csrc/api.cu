@@ -1,0 +1,984 @@
+// Host driver and C ABI of the CP-ALS engine.
+//
+// Schedules (Sec. II-C, III, Alg. 1-2) are expressed as contraction paths: the
+// MTTKRP of mode u is reached from T by contracting the other modes one at a
+// time, and each prefix of that sequence is a dimension-tree intermediate
+// M^(kept modes) (Eq. tensors-cp).  Intermediates live in one device buffer per
+// number of kept modes ("slot") and carry the version of every factor they were
+// contracted with, so a node is reused exactly when its contents would be
+// identical.  With the standard tree's paths this executes the dimension tree of
+// Fig. 1a (two first-level TTMs per sweep); with the multi-sweep paths it
+// executes Fig. 2, whose root survives across sweep and call boundaries.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "cpals_internal.h"
+
+namespace {
+
+struct Slot {
+    float* buf = nullptr;
+    size_t cap = 0;            // floats
+    bool valid = false;
+    uint32_t contracted = 0;   // bitmask of contracted modes
+    int ver[CP_MAXN] = {0};
+};
+
+}  // namespace
+
+struct cp_policy {
+    float* theta = nullptr;  // device, 4801
+    float* m = nullptr;
+    float* v = nullptr;
+    float* grad = nullptr;
+    float* scratch = nullptr;
+    float* loss = nullptr;
+    int t = 0;
+    cudaStream_t st = nullptr;
+};
+
+struct cp_ctx {
+    int N = 0, R = 0, Rpad = 0;
+    int64_t dims[CP_MAXN] = {0};
+    int Kpad[CP_MAXN] = {0};
+    int64_t numel = 0;
+    int smax = 0;
+    const float* T = nullptr;
+    float* T_owned = nullptr;
+    cudaStream_t st = nullptr;
+    cp_config cfg;
+    int num_sms = 148;
+
+    double* A64[CP_MAXN] = {0};
+    float* A32[CP_MAXN] = {0};
+    uint16_t* bhi[CP_MAXN] = {0};
+    uint16_t* blo[CP_MAXN] = {0};
+    float* bt32[CP_MAXN] = {0};
+    double* S[CP_MAXN] = {0};
+    double* dS[CP_MAXN] = {0};
+    double* Ap64[CP_MAXN] = {0};
+    float* dA32[CP_MAXN] = {0};
+    double* dA64[CP_MAXN] = {0};
+    int ver[CP_MAXN] = {0};
+    double** d_Slist = nullptr;
+    double** d_dSlist = nullptr;
+
+    double *Gamma = nullptr, *L = nullptr, *invd = nullptr, *W = nullptr;
+    double* gram_part = nullptr;
+    int nchunk = 1;
+    double* scal_part = nullptr;
+    double* scal_hist = nullptr;   // [cap][N][CP_NSCAL]
+    int scal_hist_cap = 0;
+    double* red_part = nullptr;
+    double* d_red_out = nullptr;
+    unsigned* dev_err = nullptr;
+    double normT2 = 0.0;
+
+    Slot slot[CP_MAXN + 1];
+
+    // PP state
+    bool pp_alloc = false, pp_valid = false;
+    float* pair[CP_MAXN][CP_MAXN] = {{0}};
+    float* Mp[CP_MAXN] = {0};
+    float* Mt = nullptr;
+    double dA_rel[CP_MAXN];  // ||dA(i)|| / ||A(i)|| as Alg. 2 tests it
+
+    int64_t t_msdt = 0;
+    int sweeps_done = 0;
+    bool have_last = false;
+    double last_resid = 1.0;
+
+    std::vector<cp_trace_rec> trace;
+    std::vector<double> last_hist;   // host copy of the last harvested scalars
+    std::vector<cudaEvent_t> events;
+    cp_stats stats;
+    std::string err;
+    bool poisoned = false;
+};
+
+namespace {
+
+// ------------------------------------------------------------------ errors
+cp_status fail(cp_ctx* c, cp_status s, const std::string& msg) {
+    if (c && c->err.empty()) c->err = msg;
+    if (c && (s == CP_ECUDA || s == CP_ETIMEOUT)) c->poisoned = true;
+    return s;
+}
+
+#define CKCUDA(ctx, expr)                                                                  \
+    do {                                                                                   \
+        cudaError_t e__ = (expr);                                                          \
+        if (e__ != cudaSuccess)                                                            \
+            return fail(ctx, CP_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+#define CKST(expr)                     \
+    do {                               \
+        cp_status s__ = (expr);        \
+        if (s__ != CP_OK) return s__;  \
+    } while (0)
+
+#define LAUNCH(ctx, expr)          \
+    do {                           \
+        (ctx)->stats.launches++;   \
+        CKCUDA(ctx, (expr));       \
+    } while (0)
+
+template <class Tp>
+cp_status dalloc(cp_ctx* c, Tp** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(Tp));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, CP_ENOMEM, "cudaMalloc of " + std::to_string(n * sizeof(Tp)) + " bytes failed");
+    }
+    return CP_OK;
+}
+
+// ------------------------------------------------------------------ Philox4x32-10 (host)
+// Salmon et al., SC'11: ten rounds; multipliers 0xD2511F53, 0xCD9E8D57; key
+// increments 0x9E3779B9, 0xBB67AE85 between rounds.
+void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+        const uint32_t n1 = (uint32_t)p1;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+        const uint32_t n3 = (uint32_t)p0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+    }
+}
+
+void philox_uniform(uint64_t seed, uint32_t stream, size_t n, double* out) {
+    for (size_t j = 0; 2 * j < n; ++j) {
+        uint32_t c[4] = {(uint32_t)j, (uint32_t)((uint64_t)j >> 32), stream, 0u};
+        philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+        const uint64_t a = (((uint64_t)c[0] << 32) | c[1]) >> 11;
+        const uint64_t b = (((uint64_t)c[2] << 32) | c[3]) >> 11;
+        out[2 * j] = (double)a * 0x1.0p-53;
+        if (2 * j + 1 < n) out[2 * j + 1] = (double)b * 0x1.0p-53;
+    }
+}
+
+// ------------------------------------------------------------------ contraction helpers
+// kept modes of a node = all modes minus `contracted`, in increasing order
+void contract_dims(const cp_ctx* c, uint32_t contracted, int mode, int64_t* P, int64_t* Q) {
+    int64_t p = 1, q = 1;
+    for (int k = 0; k < c->N; ++k) {
+        if (contracted & (1u << k)) continue;
+        if (k < mode) p *= c->dims[k];
+        if (k > mode) q *= c->dims[k];
+    }
+    *P = p;
+    *Q = q;
+}
+
+cp_status launch_ttm(cp_ctx* c, int mode, float* X) {
+    int64_t P, Q;
+    contract_dims(c, 0u, mode, &P, &Q);
+    const int K = (int)c->dims[mode];
+    const int prec = c->cfg.prec;
+    if (prec != CP_FP32_SIMT && cpk::ttm_tc_supported(P, K, Q, c->R)) {
+        cpk::TcOperand B{c->bhi[mode], c->blo[mode], c->bt32[mode], c->Rpad, c->Kpad[mode]};
+        LAUNCH(c, cpk::ttm_tc(c->T, B, X, P, K, Q, c->R, prec, c->num_sms, c->dev_err, c->st));
+    } else {
+        LAUNCH(c, cpk::ttm_simt(c->T, c->A32[mode], X, P, K, Q, c->R, c->st));
+    }
+    c->stats.ttm++;
+    c->stats.ttm_flops += 2.0 * (double)c->numel * c->R;
+    c->stats.ttm_bytes += 4.0 * ((double)c->numel + (double)(c->numel / K) * c->R);
+    return CP_OK;
+}
+
+cp_status launch_mttv(cp_ctx* c, const float* X, uint32_t contracted, int mode, float* Y) {
+    int64_t P, Q;
+    contract_dims(c, contracted, mode, &P, &Q);
+    const int K = (int)c->dims[mode];
+    if (P * Q == 0) return CP_OK;
+    LAUNCH(c, cpk::mttv(X, c->A32[mode], Y, P, K, Q, c->R, c->num_sms, c->st));
+    const double nin = (double)P * K * Q * c->R;
+    c->stats.mttv++;
+    c->stats.mttv_flops += 2.0 * nin;
+    c->stats.mttv_bytes += 4.0 * (nin + (double)P * Q * c->R);
+    return CP_OK;
+}
+
+// Ensure the node reached by contracting path[0..d-1] is in its slot; returns it.
+cp_status ensure_node(cp_ctx* c, const int* path, int d, float** out) {
+    uint32_t mask = 0;
+    for (int i = 0; i < d; ++i) mask |= 1u << path[i];
+    Slot& s = c->slot[c->N - d];
+    bool hit = s.valid && s.contracted == mask;
+    for (int i = 0; hit && i < d; ++i)
+        if (s.ver[path[i]] != c->ver[path[i]]) hit = false;
+    if (hit) {
+        *out = s.buf;
+        return CP_OK;
+    }
+    s.valid = false;
+    if (d == 1) {
+        CKST(launch_ttm(c, path[0], s.buf));
+    } else {
+        float* parent = nullptr;
+        CKST(ensure_node(c, path, d - 1, &parent));
+        CKST(launch_mttv(c, parent, mask & ~(1u << path[d - 1]), path[d - 1], s.buf));
+    }
+    s.valid = true;
+    s.contracted = mask;
+    for (int k = 0; k < c->N; ++k) s.ver[k] = c->ver[k];
+    *out = s.buf;
+    return CP_OK;
+}
+
+// Binary dimension tree over ordered leaves: append the contractions that lead
+// from the node holding `leaves` to leaf u.  First child: contract the later
+// half starting from its last leaf; second child: the earlier half in order.
+void tree_path(std::vector<int> leaves, int u, std::vector<int>& seq) {
+    while (leaves.size() > 1) {
+        const size_t h = (leaves.size() + 1) / 2;
+        std::vector<int> L1(leaves.begin(), leaves.begin() + h), L2(leaves.begin() + h, leaves.end());
+        if (std::find(L1.begin(), L1.end(), u) != L1.end()) {
+            for (size_t i = L2.size(); i-- > 0;) seq.push_back(L2[i]);
+            leaves = L1;
+        } else {
+            for (int m : L1) seq.push_back(m);
+            leaves = L2;
+        }
+    }
+}
+
+std::vector<int> dt_path(int N, int u) {
+    std::vector<int> leaves(N), seq;
+    for (int i = 0; i < N; ++i) leaves[i] = i;
+    tree_path(leaves, u, seq);
+    return seq;
+}
+
+// MSDT (Sec. III): update t belongs to subtree j = t / (N-1) with root mode
+// m = (N-1-j) mod N serving leaves m+1, ..., m+N-1 (mod N).
+std::vector<int> msdt_path(int N, int64_t t, int* u_out) {
+    const int64_t j = t / (N - 1);
+    const int m = (int)(((N - 1 - j) % N + N) % N);
+    std::vector<int> leaves(N - 1), seq;
+    for (int i = 0; i < N - 1; ++i) leaves[i] = (m + 1 + i) % N;
+    const int u = leaves[(size_t)(t % (N - 1))];
+    seq.push_back(m);
+    tree_path(leaves, u, seq);
+    *u_out = u;
+    return seq;
+}
+
+cp_status mttkrp_leaf(cp_ctx* c, const std::vector<int>& path, float** M) {
+    return ensure_node(c, path.data(), (int)path.size(), M);
+}
+
+double* scal_slot(cp_ctx* c, int k, int mode) {
+    return c->scal_hist + ((size_t)k * c->N + mode) * CP_NSCAL;
+}
+
+cp_status grow_hist(cp_ctx* c, int nsweeps) {
+    if (nsweeps <= c->scal_hist_cap) return CP_OK;
+    if (c->scal_hist) cudaFree(c->scal_hist);
+    c->scal_hist = nullptr;
+    c->scal_hist_cap = 0;
+    CKST(dalloc(c, &c->scal_hist, (size_t)nsweeps * c->N * CP_NSCAL));
+    c->scal_hist_cap = nsweeps;
+    return CP_OK;
+}
+
+// One factor update (Alg. 1 lines 6-9; in PP mode Alg. 2 lines 10-12 with V).
+cp_status update_mode(cp_ctx* c, int u, const float* M, bool pp, double* scal) {
+    const int R = c->R, s = (int)c->dims[u];
+    LAUNCH(c, cpk::gamma_chol(c->d_Slist, c->d_dSlist, c->N, u, R, pp ? 1 : 0, c->Gamma, c->L,
+                              c->invd, c->W, scal + SCAL_FLAGS, c->st));
+    cpk::SolveOut o;
+    o.A64 = c->A64[u];
+    o.A32 = c->A32[u];
+    o.bhi = c->bhi[u];
+    o.blo = c->blo[u];
+    o.bt32 = c->bt32[u];
+    o.Rpad = c->Rpad;
+    o.Kpad = c->Kpad[u];
+    o.Ap = pp ? c->Ap64[u] : nullptr;
+    o.dA32 = pp ? c->dA32[u] : nullptr;
+    o.dA64 = pp ? c->dA64[u] : nullptr;
+    int nblk = 0;
+    LAUNCH(c, cpk::solve_rows(M, pp ? c->W : nullptr, c->L, c->invd, o, s, R, c->scal_part, &nblk, c->st));
+    const int nchunk = std::max(1, std::min(c->nchunk, (s + 15) / 16));
+    LAUNCH(c, cpk::gram_partials(c->A64[u], pp ? c->dA64[u] : nullptr, s, R, c->gram_part, nchunk, c->st));
+    LAUNCH(c, cpk::finalize_update(c->gram_part, nchunk, c->scal_part, nblk, c->Gamma, R, pp ? 1 : 0,
+                                   c->S[u], c->dS[u], scal, c->st));
+    c->ver[u]++;
+    return CP_OK;
+}
+
+cp_status check_dev_err(cp_ctx* c) {
+    unsigned e = 0;
+    CKCUDA(c, cudaMemcpyAsync(&e, c->dev_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+    CKCUDA(c, cudaStreamSynchronize(c->st));
+    if (e & DEVERR_TIMEOUT) return fail(c, CP_ETIMEOUT, "a bounded device wait ran out");
+    if (e & DEVERR_BADARG) return fail(c, CP_ECUDA, "a kernel rejected its launch arguments");
+    return CP_OK;
+}
+
+// After `k` sweeps recorded in scal_hist: read them, append trace records.
+cp_status harvest(cp_ctx* c, int k, const int* kinds, const int* inits, int first_event) {
+    std::vector<double>& h = c->last_hist;
+    h.assign((size_t)k * c->N * CP_NSCAL, 0.0);
+    CKCUDA(c, cudaMemcpyAsync(h.data(), c->scal_hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CKST(check_dev_err(c));
+    for (int i = 0; i < k; ++i) {
+        const double* last = &h[((size_t)i * c->N + (c->N - 1)) * CP_NSCAL];
+        cp_trace_rec rec;
+        memset(&rec, 0, sizeof(rec));
+        rec.sweep = c->sweeps_done + i;
+        rec.kind = kinds[i];
+        rec.pp_init = inits ? inits[i] : 0;
+        const double r2 = c->normT2 + last[SCAL_GS] - 2.0 * last[SCAL_MA];
+        rec.resid = sqrt(r2 > 0 ? r2 : 0.0) / sqrt(c->normT2);
+        double mx = 0.0, mxp = 0.0;
+        bool bad = false;
+        for (int n = 0; n < c->N; ++n) {
+            const double* sc = &h[((size_t)i * c->N + n) * CP_NSCAL];
+            const double a = sqrt(sc[SCAL_A2]);
+            if (!isfinite(sc[SCAL_A2]) || !isfinite(sc[SCAL_MA])) bad = true;
+            if (sc[SCAL_FLAGS] >= 2.0) {
+                c->sweeps_done += i;
+                return fail(c, CP_ENOTSPD, "Gamma(" + std::to_string(n) + ") not positive definite");
+            }
+            if (a > 0) {
+                mx = std::max(mx, sqrt(sc[SCAL_STEP2]) / a);
+                mxp = std::max(mxp, sqrt(sc[SCAL_DAP2]) / a);
+            }
+        }
+        rec.max_rel_step = mx;
+        rec.max_rel_dAp = mxp;
+        if (kinds[i] == 2 && last[SCAL_M2] > 0) rec.v_share = sqrt(last[SCAL_V2] / last[SCAL_M2]);
+        float ms = 0.f;
+        if (first_event >= 0 && (size_t)(first_event + i + 1) < c->events.size())
+            cudaEventElapsedTime(&ms, c->events[first_event + i], c->events[first_event + i + 1]);
+        rec.ms = ms;
+        c->trace.push_back(rec);
+        c->last_resid = rec.resid;
+        c->have_last = true;
+        if (bad || !isfinite(rec.resid)) {
+            c->sweeps_done += i + 1;
+            return fail(c, CP_ENUMERIC, "non-finite factor or residual");
+        }
+    }
+    c->sweeps_done += k;
+    return CP_OK;
+}
+
+cp_status ensure_events(cp_ctx* c, size_t n) {
+    while (c->events.size() < n) {
+        cudaEvent_t e;
+        CKCUDA(c, cudaEventCreate(&e));
+        c->events.push_back(e);
+    }
+    return CP_OK;
+}
+
+cp_status entry_check(cp_ctx* c) {
+    if (!c) return CP_EINVAL;
+    if (c->poisoned) return CP_ESTATE;
+    return CP_OK;
+}
+
+// One exact sweep: DT (kind 0) or MSDT (kind 1/3).  Records into scal_hist[k].
+cp_status exact_sweep(cp_ctx* c, bool msdt, int k) {
+    for (int u0 = 0; u0 < c->N; ++u0) {
+        int u = u0;
+        std::vector<int> path;
+        if (msdt) {
+            path = msdt_path(c->N, c->t_msdt, &u);
+            c->t_msdt++;
+        } else {
+            path = dt_path(c->N, u0);
+        }
+        float* M = nullptr;
+        CKST(mttkrp_leaf(c, path, &M));
+        CKST(update_mode(c, u, M, false, scal_slot(c, k, u)));
+    }
+    c->stats.sweeps_exact++;
+    return CP_OK;
+}
+
+// ------------------------------------------------------------------ PP
+cp_status pp_alloc(cp_ctx* c) {
+    if (c->pp_alloc) return CP_OK;
+    const int N = c->N, R = c->R;
+    for (int i = 0; i < N; ++i) {
+        CKST(dalloc(c, &c->Ap64[i], (size_t)c->dims[i] * R));
+        CKST(dalloc(c, &c->dA32[i], (size_t)c->dims[i] * R));
+        CKST(dalloc(c, &c->dA64[i], (size_t)c->dims[i] * R));
+        CKST(dalloc(c, &c->Mp[i], (size_t)c->dims[i] * R));
+        for (int j = i + 1; j < N; ++j)
+            CKST(dalloc(c, &c->pair[i][j], (size_t)c->dims[i] * c->dims[j] * R));
+    }
+    CKST(dalloc(c, &c->Mt, (size_t)c->smax * R));
+    c->pp_alloc = true;
+    return CP_OK;
+}
+
+// PP dimension tree (Fig. 1b).  1-based level-l nodes are (i, j, j+1, ..., j+N-l-1),
+// i < j <= l+1 (Sec. II-D); level 2 nodes are first-level TTM results.  Parent
+// rule: j <= l -> (i, j, ..., j+N-l); j = l+1, i < l -> (i, l, ..., N);
+// j = l+1, i = l -> (1, l, ..., N).  Returns the contraction sequence from T to
+// the 0-based pair (a, b).
+std::vector<int> pp_pair_path(int N, int a, int b) {
+    // walk up from the pair (level N-1) to level 2, recording kept-mode sets (1-based)
+    std::vector<std::vector<int>> chain;
+    int i = a + 1, j = b + 1;
+    std::vector<int> node = {i, j};
+    chain.push_back(node);
+    for (int l = N - 1; l > 2; --l) {
+        // node at level l is (i, j, j+1, ..., j+N-l-1)
+        std::vector<int> parent;
+        if (j <= l) {
+            parent.push_back(i);
+            for (int m = j; m <= j + N - l; ++m) parent.push_back(m);
+        } else if (i < l) {
+            parent.push_back(i);
+            for (int m = l; m <= N; ++m) parent.push_back(m);
+            j = l;
+        } else {
+            parent.push_back(1);
+            for (int m = l; m <= N; ++m) parent.push_back(m);
+            i = 1;
+            j = l;
+        }
+        chain.push_back(parent);
+    }
+    // chain.back() is a level-2 node (N-1 modes); contractions from T downward
+    std::vector<int> seq;
+    std::vector<int> prev;
+    for (int m = 1; m <= N; ++m) prev.push_back(m);
+    for (size_t t = chain.size(); t-- > 0;) {
+        const std::vector<int>& cur = chain[t];
+        for (int m : prev)
+            if (std::find(cur.begin(), cur.end(), m) == cur.end()) seq.push_back(m - 1);
+        prev = cur;
+    }
+    return seq;
+}
+
+cp_status pp_init_impl(cp_ctx* c) {
+    CKST(pp_alloc(c));
+    const int N = c->N, R = c->R;
+    for (int i = 0; i < N; ++i) {
+        CKCUDA(c, cudaMemcpyAsync(c->Ap64[i], c->A64[i], sizeof(double) * c->dims[i] * R, cudaMemcpyDeviceToDevice, c->st));
+        CKCUDA(c, cudaMemsetAsync(c->dA32[i], 0, sizeof(float) * c->dims[i] * R, c->st));
+        CKCUDA(c, cudaMemsetAsync(c->dA64[i], 0, sizeof(double) * c->dims[i] * R, c->st));
+        CKCUDA(c, cudaMemsetAsync(c->dS[i], 0, sizeof(double) * R * R, c->st));
+    }
+    // pairs ordered by their contraction sequence so shared ancestors stay cached
+    struct PP { std::vector<int> seq; int a, b; };
+    std::vector<PP> items;
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b) items.push_back({pp_pair_path(N, a, b), a, b});
+    // the first-level node still cached from the last exact sweep is reused
+    // (the amortized root of Sec. II-D): its pairs go first
+    int cached = -1;
+    {
+        const Slot& r = c->slot[N - 1];
+        if (r.valid && __builtin_popcount(r.contracted) == 1) {
+            const int m = __builtin_ctz(r.contracted);
+            if (r.ver[m] == c->ver[m]) cached = m;
+        }
+    }
+    std::sort(items.begin(), items.end(), [cached](const PP& x, const PP& y) {
+        const bool cx = x.seq[0] == cached, cy = y.seq[0] == cached;
+        if (cx != cy) return cx;
+        return x.seq < y.seq;
+    });
+    for (const PP& it : items) {
+        const int d = (int)it.seq.size();  // N-2 contractions
+        uint32_t mask = 0;
+        for (int m : it.seq) mask |= 1u << m;
+        if (d == 1) {
+            if (it.seq[0] == cached)
+                CKCUDA(c, cudaMemcpyAsync(c->pair[it.a][it.b], c->slot[N - 1].buf,
+                                          sizeof(float) * c->dims[it.a] * c->dims[it.b] * R,
+                                          cudaMemcpyDeviceToDevice, c->st));
+            else
+                CKST(launch_ttm(c, it.seq[0], c->pair[it.a][it.b]));
+        } else {
+            float* parent = nullptr;
+            CKST(ensure_node(c, it.seq.data(), d - 1, &parent));
+            CKST(launch_mttv(c, parent, mask & ~(1u << it.seq[d - 1]), it.seq[d - 1], c->pair[it.a][it.b]));
+        }
+    }
+    // M_p(n) = M_p(n,i) x_i A_p(i)
+    for (int n = 0; n < N; ++n) {
+        const int i = (n == 0) ? 1 : 0;
+        const int a = std::min(n, i), b = std::max(n, i);
+        uint32_t mask = 0;
+        for (int k = 0; k < N; ++k)
+            if (k != a && k != b) mask |= 1u << k;
+        CKST(launch_mttv(c, c->pair[a][b], mask, i, c->Mp[n]));
+    }
+    c->pp_valid = true;
+    c->stats.pp_init++;
+    for (int i = 0; i < N; ++i) c->dA_rel[i] = 0.0;
+    return CP_OK;
+}
+
+cp_status pp_mttkrp_impl(cp_ctx* c, int n, float* Mt) {
+    std::vector<cpk::PPTerm> terms;
+    for (int i = 0; i < c->N; ++i) {
+        if (i == n) continue;
+        cpk::PPTerm t;
+        t.op = c->pair[std::min(n, i)][std::max(n, i)];
+        t.dA = c->dA32[i];
+        t.sy = (int)c->dims[i];
+        t.trans = (i < n) ? 1 : 0;
+        terms.push_back(t);
+    }
+    LAUNCH(c, cpk::pp_u(c->Mp[n], terms.data(), (int)terms.size(), Mt, (int)c->dims[n], c->R, c->st));
+    double s = (double)c->dims[n], R = c->R, N = c->N;
+    c->stats.pp_flops += 2.0 * (N * s * s * R + N * R * R + s * R * R);
+    return CP_OK;
+}
+
+cp_status pp_sweep(cp_ctx* c, int k) {
+    for (int n = 0; n < c->N; ++n) {
+        CKST(pp_mttkrp_impl(c, n, c->Mt));
+        CKST(update_mode(c, n, c->Mt, true, scal_slot(c, k, n)));
+    }
+    c->stats.sweeps_pp++;
+    return CP_OK;
+}
+
+cp_status init_grams(cp_ctx* c) {
+    for (int n = 0; n < c->N; ++n) {
+        const int s = (int)c->dims[n];
+        LAUNCH(c, cpk::factor_copies(c->A64[n], c->A32[n], c->bhi[n], c->blo[n], c->bt32[n], s, c->R,
+                                     c->Rpad, c->Kpad[n], c->st));
+        const int nchunk = std::max(1, std::min(c->nchunk, (s + 15) / 16));
+        LAUNCH(c, cpk::gram_partials(c->A64[n], nullptr, s, c->R, c->gram_part, nchunk, c->st));
+        LAUNCH(c, cpk::finalize_update(c->gram_part, nchunk, c->scal_part, 0, nullptr, c->R, 0, c->S[n],
+                                       nullptr, c->red_part, c->st));
+    }
+    return CP_OK;
+}
+
+void free_all(cp_ctx* c) {
+    auto F = [](void* p) { if (p) cudaFree(p); };
+    F(c->T_owned);
+    for (int i = 0; i < CP_MAXN; ++i) {
+        F(c->A64[i]); F(c->A32[i]); F(c->bhi[i]); F(c->blo[i]); F(c->bt32[i]);
+        F(c->S[i]); F(c->dS[i]); F(c->Ap64[i]); F(c->dA32[i]); F(c->dA64[i]); F(c->Mp[i]);
+        for (int j = 0; j < CP_MAXN; ++j) F(c->pair[i][j]);
+    }
+    for (int k = 0; k <= CP_MAXN; ++k) F(c->slot[k].buf);
+    F(c->Mt); F(c->d_Slist); F(c->d_dSlist); F(c->Gamma); F(c->L); F(c->invd); F(c->W);
+    F(c->gram_part); F(c->scal_part); F(c->scal_hist); F(c->red_part); F(c->d_red_out); F(c->dev_err);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    c->events.clear();
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void cp_config_default(cp_config* cfg) {
+    if (!cfg) return;
+    cfg->prec = CP_BF16X3;
+    cfg->pp_eps = 0.1;
+    cfg->delta = 0.0;
+    cfg->max_sweeps = 0;
+    cfg->judge_every = 5;
+    cfg->use_policy = 0;
+    cfg->seed = 20101205ull;
+}
+
+cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T_dev, int dtype,
+                  const double* A0_host, const cp_config* cfg, void* stream) {
+    if (!out) return CP_EINVAL;
+    *out = nullptr;
+    if (N < 3 || N > CP_MAXN || !dims || R < 1 || R > CP_MAXR || !T_dev || (dtype != 0 && dtype != 1))
+        return CP_EINVAL;
+    int64_t numel = 1;
+    for (int i = 0; i < N; ++i) {
+        if (dims[i] < 1 || dims[i] > (1 << 30)) return CP_EINVAL;
+        if (numel > ((int64_t)1 << 40) / dims[i]) return CP_EINVAL;
+        numel *= dims[i];
+    }
+    cp_ctx* c = new cp_ctx();
+    c->N = N;
+    c->R = R;
+    c->Rpad = (R + 15) / 16 * 16;
+    c->numel = numel;
+    c->st = (cudaStream_t)stream;
+    if (cfg) c->cfg = *cfg; else cp_config_default(&c->cfg);
+    if (c->cfg.prec < CP_FP32_SIMT || c->cfg.prec > CP_BF16) { delete c; return CP_EINVAL; }
+    memset(&c->stats, 0, sizeof(c->stats));
+    for (int i = 0; i < N; ++i) {
+        c->dims[i] = dims[i];
+        c->Kpad[i] = (int)((dims[i] + 63) / 64 * 64);
+        c->smax = std::max<int>(c->smax, (int)dims[i]);
+        c->dA_rel[i] = 1.0;  // Alg. 2 line 2: dA <- A
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+
+#define TRY(expr)                       \
+    do {                                \
+        cp_status s__ = (expr);         \
+        if (s__ != CP_OK) {             \
+            free_all(c);                \
+            delete c;                   \
+            return s__;                 \
+        }                               \
+    } while (0)
+#define TRYC(expr)                                  \
+    do {                                            \
+        if ((expr) != cudaSuccess) {                \
+            cudaGetLastError();                     \
+            free_all(c);                            \
+            delete c;                               \
+            return CP_ECUDA;                        \
+        }                                           \
+    } while (0)
+
+    if (dtype == 1) {
+        TRY(dalloc(c, &c->T_owned, (size_t)numel));
+        TRYC(cpk::f64_to_f32((const double*)T_dev, c->T_owned, numel, c->st));
+        c->T = c->T_owned;
+    } else {
+        c->T = (const float*)T_dev;
+    }
+    const int RR = R * R;
+    for (int i = 0; i < N; ++i) {
+        const size_t sR = (size_t)dims[i] * R;
+        TRY(dalloc(c, &c->A64[i], sR));
+        TRY(dalloc(c, &c->A32[i], sR));
+        TRY(dalloc(c, &c->S[i], RR));
+        TRY(dalloc(c, &c->dS[i], RR));
+        TRYC(cudaMemsetAsync(c->dS[i], 0, sizeof(double) * RR, c->st));
+        const size_t op = (size_t)c->Rpad * c->Kpad[i];
+        TRY(dalloc(c, &c->bhi[i], op));
+        TRY(dalloc(c, &c->blo[i], op));
+        TRY(dalloc(c, &c->bt32[i], op));
+        TRYC(cudaMemsetAsync(c->bhi[i], 0, op * sizeof(uint16_t), c->st));
+        TRYC(cudaMemsetAsync(c->blo[i], 0, op * sizeof(uint16_t), c->st));
+        TRYC(cudaMemsetAsync(c->bt32[i], 0, op * sizeof(float), c->st));
+    }
+    // one slot per number of kept modes k = 1..N-1: capacity = largest k-mode product x R
+    std::vector<int64_t> sd(dims, dims + N);
+    std::sort(sd.begin(), sd.end(), std::greater<int64_t>());
+    for (int k = 1; k < N; ++k) {
+        int64_t cap = R;
+        for (int i = 0; i < k; ++i) cap *= sd[i];
+        TRY(dalloc(c, &c->slot[k].buf, (size_t)cap));
+        c->slot[k].cap = (size_t)cap;
+    }
+    TRY(dalloc(c, &c->d_Slist, N));
+    TRY(dalloc(c, &c->d_dSlist, N));
+    TRYC(cudaMemcpyAsync(c->d_Slist, c->S, sizeof(double*) * N, cudaMemcpyHostToDevice, c->st));
+    TRYC(cudaMemcpyAsync(c->d_dSlist, c->dS, sizeof(double*) * N, cudaMemcpyHostToDevice, c->st));
+    TRY(dalloc(c, &c->Gamma, RR));
+    TRY(dalloc(c, &c->W, RR));
+    TRY(dalloc(c, &c->L, 2 * (size_t)RR));
+    TRY(dalloc(c, &c->invd, R));
+    c->nchunk = 16;
+    TRY(dalloc(c, &c->gram_part, (size_t)c->nchunk * 2 * RR));
+    TRY(dalloc(c, &c->scal_part, (size_t)((c->smax + 3) / 4) * CP_NSCAL));
+    TRY(dalloc(c, &c->red_part, 4096));
+    TRY(dalloc(c, &c->d_red_out, 16));
+    TRY(dalloc(c, &c->dev_err, 1));
+    TRYC(cudaMemsetAsync(c->dev_err, 0, sizeof(unsigned), c->st));
+    TRY(grow_hist(c, 8));
+
+    // initial factors (Alg. 1 line 2)
+    std::vector<double> h;
+    for (int i = 0; i < N; ++i) {
+        const size_t sR = (size_t)dims[i] * R;
+        h.resize(sR);
+        if (A0_host) {
+            size_t off = 0;
+            for (int k = 0; k < i; ++k) off += (size_t)dims[k] * R;
+            memcpy(h.data(), A0_host + off, sR * sizeof(double));
+        } else {
+            philox_uniform(c->cfg.seed, (uint32_t)i, sR, h.data());
+        }
+        TRYC(cudaMemcpyAsync(c->A64[i], h.data(), sR * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        TRYC(cudaStreamSynchronize(c->st));
+    }
+    TRY(init_grams(c));
+    // ||T||_F^2
+    int nb = cpk::norm2_partials(c->T, numel, c->red_part, 4096, c->st);
+    TRYC(cudaGetLastError());
+    TRYC(cpk::sum_partials(c->red_part, nb, c->d_red_out, c->st));
+    TRYC(cudaMemcpyAsync(&c->normT2, c->d_red_out, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    TRYC(cudaStreamSynchronize(c->st));
+#undef TRY
+#undef TRYC
+    *out = c;
+    return CP_OK;
+}
+
+void cp_free(cp_ctx* c) {
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    free_all(c);
+    delete c;
+}
+
+const char* cp_last_error(const cp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+cp_status cp_mttkrp(cp_ctx* c, int mode, float* M_dev) {
+    CKST(entry_check(c));
+    if (mode < 0 || mode >= c->N || !M_dev) return CP_EINVAL;
+    float* M = nullptr;
+    CKST(mttkrp_leaf(c, dt_path(c->N, mode), &M));
+    CKCUDA(c, cudaMemcpyAsync(M_dev, M, sizeof(float) * c->dims[mode] * c->R, cudaMemcpyDeviceToDevice, c->st));
+    return CP_OK;
+}
+
+cp_status cp_ttm(cp_ctx* c, int mode, float* X_dev) {
+    CKST(entry_check(c));
+    if (mode < 0 || mode >= c->N || !X_dev) return CP_EINVAL;
+    return launch_ttm(c, mode, X_dev);
+}
+
+static cp_status sweeps_exact(cp_ctx* c, int nsweeps, bool msdt) {
+    CKST(entry_check(c));
+    if (nsweeps < 0) return CP_EINVAL;
+    if (nsweeps == 0) return CP_OK;
+    CKST(grow_hist(c, nsweeps));
+    CKST(ensure_events(c, (size_t)nsweeps + 1));
+    c->pp_valid = false;
+    std::vector<int> kinds(nsweeps, msdt ? 1 : 0);
+    CKCUDA(c, cudaEventRecord(c->events[0], c->st));
+    for (int k = 0; k < nsweeps; ++k) {
+        CKST(exact_sweep(c, msdt, k));
+        CKCUDA(c, cudaEventRecord(c->events[k + 1], c->st));
+    }
+    CKST(harvest(c, nsweeps, kinds.data(), nullptr, 0));
+    // regular sweeps: dA(i) = this sweep's change (Alg. 2 line 14)
+    return CP_OK;
+}
+
+cp_status cp_sweep_dt(cp_ctx* c, int nsweeps) { return sweeps_exact(c, nsweeps, false); }
+cp_status cp_sweep_msdt(cp_ctx* c, int nsweeps) { return sweeps_exact(c, nsweeps, true); }
+
+cp_status cp_pp_init(cp_ctx* c) {
+    CKST(entry_check(c));
+    return pp_init_impl(c);
+}
+
+cp_status cp_pp_mttkrp(cp_ctx* c, int mode, float* M_dev) {
+    CKST(entry_check(c));
+    if (mode < 0 || mode >= c->N || !M_dev) return CP_EINVAL;
+    if (!c->pp_valid) return CP_ESTATE;
+    // first-order terms (Eq. U_ni) on top of M_p(n), then V = A(n) W (Eq. V_nij)
+    CKST(pp_mttkrp_impl(c, mode, c->Mt));
+    LAUNCH(c, cpk::gamma_chol(c->d_Slist, c->d_dSlist, c->N, mode, c->R, 1, c->Gamma, c->L, c->invd,
+                              c->W, c->red_part, c->st));
+    LAUNCH(c, cpk::add_aw(c->Mt, c->A64[mode], c->W, (int)c->dims[mode], c->R, M_dev, c->st));
+    return CP_OK;
+}
+
+cp_status cp_sweep_pp(cp_ctx* c, int nsweeps, double eps, cp_policy* policy) {
+    CKST(entry_check(c));
+    if (nsweeps < 0 || !(eps > 0.0 && eps < 1.0)) return CP_EINVAL;
+    (void)policy;
+    CKST(grow_hist(c, 1));
+    CKST(ensure_events(c, 2));
+    for (int k = 0; k < nsweeps; ++k) {
+        bool small = true;
+        for (int i = 0; i < c->N; ++i)
+            if (!(c->dA_rel[i] < eps)) small = false;
+        int init = 0;
+        if (!c->pp_valid && small) {
+            CKCUDA(c, cudaEventRecord(c->events[0], c->st));
+            CKST(pp_init_impl(c));
+            init = 1;
+        } else {
+            CKCUDA(c, cudaEventRecord(c->events[0], c->st));
+        }
+        int kind;
+        if (c->pp_valid && small) {
+            CKST(pp_sweep(c, 0));
+            kind = 2;
+        } else {
+            c->pp_valid = false;
+            CKST(exact_sweep(c, true, 0));
+            kind = 3;
+        }
+        CKCUDA(c, cudaEventRecord(c->events[1], c->st));
+        CKST(harvest(c, 1, &kind, &init, 0));
+        // regime test inputs for the next sweep
+        const std::vector<double>& h = c->last_hist;
+        for (int i = 0; i < c->N; ++i) {
+            const double* sc = &h[(size_t)i * CP_NSCAL];
+            const double a = sqrt(sc[SCAL_A2]);
+            const double d = (kind == 2) ? sqrt(sc[SCAL_DAP2]) : sqrt(sc[SCAL_STEP2]);
+            c->dA_rel[i] = a > 0 ? d / a : 1.0;
+        }
+    }
+    return CP_OK;
+}
+
+cp_status cp_fit(cp_ctx* c, int exact, double* fit, double* resid) {
+    CKST(entry_check(c));
+    double r;
+    if (!exact && c->have_last) {
+        r = c->last_resid;
+    } else {
+        cpk::ResidArgs a;
+        memset(&a, 0, sizeof(a));
+        a.T = c->T;
+        a.N = c->N;
+        a.R = c->R;
+        for (int i = 0; i < c->N; ++i) {
+            a.A32[i] = c->A32[i];
+            a.dims[i] = c->dims[i];
+        }
+        c->stats.launches += 2;
+        int nb = cpk::resid_direct_partials(a, c->red_part, 4096, c->st);
+        CKCUDA(c, cudaGetLastError());
+        CKCUDA(c, cpk::sum_partials(c->red_part, nb, c->d_red_out, c->st));
+        double s2 = 0.0;
+        CKCUDA(c, cudaMemcpyAsync(&s2, c->d_red_out, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CKCUDA(c, cudaStreamSynchronize(c->st));
+        r = sqrt(s2 > 0 ? s2 : 0.0) / sqrt(c->normT2);
+    }
+    if (!isfinite(r)) return fail(c, CP_ENUMERIC, "non-finite residual");
+    if (resid) *resid = r;
+    if (fit) *fit = 1.0 - r;
+    return CP_OK;
+}
+
+cp_status cp_get_factor(cp_ctx* c, int mode, double* A_host) {
+    CKST(entry_check(c));
+    if (mode < 0 || mode >= c->N || !A_host) return CP_EINVAL;
+    CKCUDA(c, cudaMemcpyAsync(A_host, c->A64[mode], sizeof(double) * c->dims[mode] * c->R, cudaMemcpyDeviceToHost, c->st));
+    CKCUDA(c, cudaStreamSynchronize(c->st));
+    return CP_OK;
+}
+
+cp_status cp_set_factor(cp_ctx* c, int mode, const double* A_host) {
+    CKST(entry_check(c));
+    if (mode < 0 || mode >= c->N || !A_host) return CP_EINVAL;
+    const int s = (int)c->dims[mode];
+    CKCUDA(c, cudaMemcpyAsync(c->A64[mode], A_host, sizeof(double) * s * c->R, cudaMemcpyHostToDevice, c->st));
+    LAUNCH(c, cpk::factor_copies(c->A64[mode], c->A32[mode], c->bhi[mode], c->blo[mode], c->bt32[mode], s, c->R,
+                                 c->Rpad, c->Kpad[mode], c->st));
+    const int nchunk = std::max(1, std::min(c->nchunk, (s + 15) / 16));
+    // with PP operators present, dA = A - A_p and dS = A^T dA follow the new factor
+    const bool pp = c->pp_valid;
+    if (pp)
+        LAUNCH(c, cpk::pp_delta(c->A64[mode], c->Ap64[mode], c->dA32[mode], c->dA64[mode], (int64_t)s * c->R, c->st));
+    LAUNCH(c, cpk::gram_partials(c->A64[mode], pp ? c->dA64[mode] : nullptr, s, c->R, c->gram_part, nchunk, c->st));
+    LAUNCH(c, cpk::finalize_update(c->gram_part, nchunk, c->scal_part, 0, nullptr, c->R, pp ? 1 : 0, c->S[mode],
+                                   c->dS[mode], c->red_part, c->st));
+    CKCUDA(c, cudaStreamSynchronize(c->st));
+    c->ver[mode]++;
+    c->have_last = false;
+    return CP_OK;
+}
+
+cp_status cp_get_trace(cp_ctx* c, cp_trace_rec* buf, size_t* len) {
+    if (!c || !len) return CP_EINVAL;
+    const size_t n = c->trace.size();
+    if (buf) memcpy(buf, c->trace.data(), std::min(*len, n) * sizeof(cp_trace_rec));
+    *len = n;
+    return CP_OK;
+}
+
+cp_status cp_get_stats(cp_ctx* c, cp_stats* st) {
+    if (!c || !st) return CP_EINVAL;
+    *st = c->stats;
+    return CP_OK;
+}
+
+// ---------------------------------------------------------------------- policy
+cp_status cp_policy_create(cp_policy** out, const float* theta_host, void* stream) {
+    if (!out || !theta_host) return CP_EINVAL;
+    *out = nullptr;
+    cp_policy* p = new cp_policy();
+    p->st = (cudaStream_t)stream;
+    const int n = cpk::mlp_nparams();
+    bool ok = cudaMalloc(&p->theta, n * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&p->m, n * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&p->v, n * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&p->grad, n * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&p->loss, sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&p->scratch, cpk::mlp_scratch_floats() * sizeof(float)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cp_policy_free(p);
+        return CP_ENOMEM;
+    }
+    if (cudaMemcpyAsync(p->theta, theta_host, n * sizeof(float), cudaMemcpyHostToDevice, p->st) != cudaSuccess ||
+        cudaMemsetAsync(p->m, 0, n * sizeof(float), p->st) != cudaSuccess ||
+        cudaMemsetAsync(p->v, 0, n * sizeof(float), p->st) != cudaSuccess ||
+        cudaStreamSynchronize(p->st) != cudaSuccess) {
+        cudaGetLastError();
+        cp_policy_free(p);
+        return CP_ECUDA;
+    }
+    *out = p;
+    return CP_OK;
+}
+
+cp_status cp_policy_get(cp_policy* p, float* theta_host) {
+    if (!p || !theta_host) return CP_EINVAL;
+    if (cudaMemcpyAsync(theta_host, p->theta, cpk::mlp_nparams() * sizeof(float), cudaMemcpyDeviceToHost, p->st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(p->st) != cudaSuccess)
+        return CP_ECUDA;
+    return CP_OK;
+}
+
+cp_status cp_policy_forward(cp_policy* p, const float* X_dev, int B, float* prob_dev) {
+    if (!p || B < 0 || (B > 0 && (!X_dev || !prob_dev))) return CP_EINVAL;
+    return cpk::mlp_forward(p->theta, X_dev, B, prob_dev, p->st) == cudaSuccess ? CP_OK : CP_ECUDA;
+}
+
+cp_status cp_policy_grad(cp_policy* p, const float* X_dev, const float* y_dev, int B, float* loss_dev,
+                         float* grad_dev) {
+    if (!p || B < 1 || !X_dev || !y_dev || !grad_dev) return CP_EINVAL;
+    return cpk::mlp_grad(p->theta, X_dev, y_dev, B, loss_dev, grad_dev, p->scratch, p->st) == cudaSuccess
+               ? CP_OK
+               : CP_ECUDA;
+}
+
+cp_status cp_policy_train(cp_policy* p, const float* X_dev, const float* y_dev, int B, int steps, float lr) {
+    if (!p || B < 1 || !X_dev || !y_dev || steps < 0) return CP_EINVAL;
+    for (int i = 0; i < steps; ++i) {
+        if (cpk::mlp_grad(p->theta, X_dev, y_dev, B, p->loss, p->grad, p->scratch, p->st) != cudaSuccess)
+            return CP_ECUDA;
+        p->t++;
+        if (cpk::mlp_adam(p->theta, p->grad, p->m, p->v, cpk::mlp_nparams(), p->t, lr, p->st) != cudaSuccess)
+            return CP_ECUDA;
+    }
+    return CP_OK;
+}
+
+void cp_policy_free(cp_policy* p) {
+    if (!p) return;
+    if (p->st) cudaStreamSynchronize(p->st);
+    for (float* q : {p->theta, p->m, p->v, p->grad, p->loss, p->scratch})
+        if (q) cudaFree(q);
+    delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cpals.h"
+
+#define CP_MAXN 8
+#define CP_MAXR 256
+#define CP_NSCAL 8  // per-update scalar slots, see SCAL_* below
+
+// Per-update scalar reductions written by the solve kernel (partials per block,
+// finalised by k_finalize into ctx->scal_mode[mode * CP_NSCAL + slot]).
+enum {
+    SCAL_A2 = 0,      // ||A_new||_F^2
+    SCAL_STEP2 = 1,   // ||A_new - A_old||_F^2   (change made by this update)
+    SCAL_DAP2 = 2,    // ||A_new - A_p||_F^2     (PP: accumulated change)
+    SCAL_MA = 3,      // <M, A_new>              (Eq. residual)
+    SCAL_GS = 4,      // <Gamma, S_new>          (Eq. residual)
+    SCAL_M2 = 5,      // ||M~||_F^2              (PP: size of the MTTKRP)
+    SCAL_V2 = 6,      // ||V||_F^2               (PP: size of the second-order term)
+    SCAL_FLAGS = 7    // Cholesky flags: 1 = shifted, 2 = failed
+};
+
+// ----------------------------------------------------------------------- device status
+// One device word per context; kernels OR error bits into it, host reads it at
+// synchronisation points.
+enum { DEVERR_TIMEOUT = 1, DEVERR_NOTSPD = 2, DEVERR_BADARG = 4 };
+
+// ----------------------------------------------------------------------- launchers
+// Each returns cudaGetLastError() after the launch.
+namespace cpk {
+
+// first-level TTM: X[p][q][r] = sum_k T[p][k][q] * A[k][r]   (A is K x R row-major)
+cudaError_t ttm_simt(const float* T, const float* A, float* X, int64_t P, int K, int64_t Q,
+                     int R, cudaStream_t st);
+
+// tensor-core first-level TTM; Bop = operand copy of A(mode), see k_ttm_tc.cu
+struct TcOperand {
+    const uint16_t* bhi;  // bf16 hi part, [Rpad][Kpad] (K contiguous)
+    const uint16_t* blo;  // bf16 lo part, same layout
+    const float* bt32;    // fp32 transposed copy [Rpad][Kpad] for kind::tf32
+    int Rpad, Kpad;
+};
+cudaError_t ttm_tc(const float* T, const TcOperand& B, float* X, int64_t P, int K, int64_t Q,
+                   int R, int prec, int num_sms, unsigned* dev_err, cudaStream_t st);
+bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R);
+
+// multi-TTV: Y[p][q][r] = sum_k X[p][k][q][r] * A[k][r]
+cudaError_t mttv(const float* X, const float* A, float* Y, int64_t P, int K, int64_t Q, int R,
+                 int num_sms, cudaStream_t st);
+
+// PP first-order corrections for one mode n (Eq. U_ni):
+//   Mt[x][r] = Mp[x][r] + sum_i sum_y Op_i(x, y, r) dA_i[y][r]
+// where operator i is stored [x][y][r] (trans=0) or [y][x][r] (trans=1).
+struct PPTerm {
+    const float* op;
+    const float* dA;
+    int sy;
+    int trans;
+};
+cudaError_t pp_u(const float* Mp, const PPTerm* terms, int nterms, float* Mt, int sx, int R,
+                 cudaStream_t st);
+
+// ||x||^2 over n floats -> partials (nblocks doubles), returns nblocks used
+int norm2_partials(const float* x, int64_t n, double* partials, int max_blocks, cudaStream_t st);
+cudaError_t sum_partials(const double* partials, int n, double* out, cudaStream_t st);
+
+// Gamma = *_{k != n} S(k) (+ PP's W); Cholesky Gamma = L L^T into L (R x R), invdiag.
+// S_list / dS_list: device arrays of N device pointers.  pp != 0 also builds
+// W = sum_{i<j; i,j != n} dS(i)*dS(j)*(*_{k != i,j,n} S(k)).
+cudaError_t gamma_chol(double* const* S_list, double* const* dS_list, int N, int n, int R,
+                       int pp, double* Gamma, double* L, double* invdiag, double* W,
+                       double* scal_flags, cudaStream_t st);
+
+// Row-wise solve A_new = (M + A_old W) Gamma^{-1}; writes every operand copy and
+// per-block partial scalars (CP_NSCAL per block).  Returns blocks used via *nblk.
+struct SolveOut {
+    double* A64;        // in: A_old, out: A_new (s x R)
+    float* A32;         // FP32 copy
+    uint16_t* bhi;      // bf16 hi, transposed [Rpad][Kpad]
+    uint16_t* blo;      // bf16 lo
+    float* bt32;        // fp32 transposed [Rpad][Kpad]
+    int Rpad, Kpad;
+    const double* Ap;   // PP base factor (NULL outside PP)
+    float* dA32;        // A_new - A_p (or - A_old outside PP), FP32
+    double* dA64;       // same in FP64
+};
+cudaError_t solve_rows(const float* M, const double* W, const double* L, const double* invdiag,
+                       const SolveOut& o, int s, int R, double* scal_part, int* nblk,
+                       cudaStream_t st);
+
+// Gram partials of A (and A^T dA) over row chunks; finalize reduces them.
+cudaError_t gram_partials(const double* A, const double* dA, int s, int R, double* part,
+                          int nchunk, cudaStream_t st);
+cudaError_t finalize_update(const double* gram_part, int nchunk, const double* scal_part,
+                            int nblk, const double* Gamma, int R, int want_dS, double* S,
+                            double* dS, double* scal_out, cudaStream_t st);
+
+// refresh all operand copies of a factor from its FP64 master (after set_factor / init)
+cudaError_t factor_copies(const double* A64, float* A32, uint16_t* bhi, uint16_t* blo,
+                          float* bt32, int s, int R, int Rpad, int Kpad, cudaStream_t st);
+
+// direct residual partials: sum (T - [[A]])^2 over the tensor, FP64 partials per block
+struct ResidArgs {
+    const float* T;
+    const float* A32[CP_MAXN];
+    int64_t dims[CP_MAXN];
+    int N, R;
+};
+int resid_direct_partials(const ResidArgs& a, double* partials, int max_blocks, cudaStream_t st);
+
+// PP: dA = A - A_p (FP64 and FP32); out = Mt + A W (the V term of Eq. ppupdate)
+cudaError_t pp_delta(const double* A, const double* Ap, float* d32, double* d64, int64_t n,
+                     cudaStream_t st);
+cudaError_t add_aw(const float* Mt, const double* A, const double* W, int s, int R, float* out,
+                   cudaStream_t st);
+// FP64 -> FP32 conversion
+cudaError_t f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t st);
+// MLP kernels
+int mlp_nparams();
+size_t mlp_scratch_floats();
+cudaError_t mlp_forward(const float* theta, const float* X, int B, float* prob, cudaStream_t st);
+cudaError_t mlp_grad(const float* theta, const float* X, const float* y, int B, float* loss,
+                     float* grad, float* scratch, cudaStream_t st);
+cudaError_t mlp_adam(float* theta, const float* grad, float* m, float* v, int n, int t, float lr,
+                     cudaStream_t st);
+
+}  // namespace cpk

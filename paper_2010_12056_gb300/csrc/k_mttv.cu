@@ -1,0 +1,97 @@
+// Multi-TTV (Sec. II-C): every dimension-tree contraction below the first level.
+// An intermediate keeps its modes in increasing order with the rank index r
+// fastest, so contracting one of its modes is
+//     Y[p][q][r] = sum_k X[p][k][q][r] * A[k][r]
+// (p: kept modes before the contracted one, q: those after it).  Reads of X are
+// contiguous along (q, r) for every k; the factor is tiny and stays in L1/L2.
+// The kernel is bandwidth-bound: one pass over X, 2 flops per element read.
+#include "cpals_internal.h"
+
+namespace {
+
+// Block = TX outputs (vectors of VEC along r) x KS partial sums over k.
+template <int VEC>
+__global__ void __launch_bounds__(256) k_mttv(const float* __restrict__ X,
+                                              const float* __restrict__ A,
+                                              float* __restrict__ Y, int64_t P, int K, int64_t Q,
+                                              int R, int TX, int KS) {
+    extern __shared__ float4 red[];  // TX * KS
+    const int RV = R / VEC;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int64_t nout = P * Q * RV;
+    const int64_t o = (int64_t)blockIdx.x * TX + tx;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (o < nout) {
+        const int64_t pq = o / RV;
+        const int rv = (int)(o - pq * RV);
+        const int64_t p = pq / Q, q = pq - p * Q;
+        const int64_t strideK = Q * R;
+        const float* xp = X + (p * K) * strideK + q * R + rv * VEC;
+        const float* ap = A + rv * VEC;
+        int k = ty;
+        if (VEC == 4) {
+            for (; k + 3 * KS < K; k += 4 * KS) {
+                float4 x0 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)k * strideK));
+                float4 x1 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)(k + KS) * strideK));
+                float4 x2 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)(k + 2 * KS) * strideK));
+                float4 x3 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)(k + 3 * KS) * strideK));
+                float4 a0 = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)k * R));
+                float4 a1 = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)(k + KS) * R));
+                float4 a2 = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)(k + 2 * KS) * R));
+                float4 a3 = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)(k + 3 * KS) * R));
+                acc.x = fmaf(x0.x, a0.x, acc.x); acc.y = fmaf(x0.y, a0.y, acc.y);
+                acc.z = fmaf(x0.z, a0.z, acc.z); acc.w = fmaf(x0.w, a0.w, acc.w);
+                acc.x = fmaf(x1.x, a1.x, acc.x); acc.y = fmaf(x1.y, a1.y, acc.y);
+                acc.z = fmaf(x1.z, a1.z, acc.z); acc.w = fmaf(x1.w, a1.w, acc.w);
+                acc.x = fmaf(x2.x, a2.x, acc.x); acc.y = fmaf(x2.y, a2.y, acc.y);
+                acc.z = fmaf(x2.z, a2.z, acc.z); acc.w = fmaf(x2.w, a2.w, acc.w);
+                acc.x = fmaf(x3.x, a3.x, acc.x); acc.y = fmaf(x3.y, a3.y, acc.y);
+                acc.z = fmaf(x3.z, a3.z, acc.z); acc.w = fmaf(x3.w, a3.w, acc.w);
+            }
+            for (; k < K; k += KS) {
+                float4 x0 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)k * strideK));
+                float4 a0 = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)k * R));
+                acc.x = fmaf(x0.x, a0.x, acc.x); acc.y = fmaf(x0.y, a0.y, acc.y);
+                acc.z = fmaf(x0.z, a0.z, acc.z); acc.w = fmaf(x0.w, a0.w, acc.w);
+            }
+        } else {
+            for (; k < K; k += KS) acc.x = fmaf(__ldg(xp + (int64_t)k * strideK), __ldg(ap + (int64_t)k * R), acc.x);
+        }
+    }
+    red[ty * TX + tx] = acc;
+    __syncthreads();
+    if (ty == 0 && o < nout) {
+        for (int j = 1; j < KS; ++j) {
+            float4 v = red[j * TX + tx];
+            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+        }
+        if (VEC == 4)
+            *reinterpret_cast<float4*>(Y + o * 4) = acc;
+        else
+            Y[o] = acc.x;
+    }
+}
+
+}  // namespace
+
+namespace cpk {
+
+cudaError_t mttv(const float* X, const float* A, float* Y, int64_t P, int K, int64_t Q, int R,
+                 int num_sms, cudaStream_t st) {
+    const bool v4 = (R % 4 == 0) && (((uintptr_t)X | (uintptr_t)A | (uintptr_t)Y) & 15) == 0;
+    const int VEC = v4 ? 4 : 1;
+    const int64_t nout = P * Q * (R / VEC);
+    // choose the k-split so that the grid covers the GPU at least twice
+    int KS = 1;
+    while (KS < 32 && KS < K && (nout * KS) < (int64_t)num_sms * 2 * 256) KS *= 2;
+    int TX = 256 / KS;
+    unsigned nblk = (unsigned)((nout + TX - 1) / TX);
+    size_t smem = sizeof(float4) * 256;
+    if (v4)
+        k_mttv<4><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
+    else
+        k_mttv<1><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
+    return cudaGetLastError();
+}
+
+}  // namespace cpk

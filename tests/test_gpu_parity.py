@@ -1,0 +1,188 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (from the arithmetic the kernels use): MTTKRP / TTM relative Frobenius
+error <= 1e-5 for FP32 SIMT and bf16x3 (FP32 accumulation; bf16x3 keeps about
+16 mantissa bits per operand); residuals within 1e-6 absolute after a fixed
+sweep count; PP approximated MTTKRPs <= 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import cp_oracle as co
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp32", "bf16x3"]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2010_12056_gb300 as p
+    return p
+
+
+def problem(dims, R, seed, eta=1e-2, law="uniform", C=None):
+    T64, F, A0 = synth.make_problem(seed, dims, R, law=law, eta=eta, C=C)
+    T32 = np.ascontiguousarray(T64.astype(np.float32))
+    return torch.from_numpy(T32).cuda(), T32.astype(np.float64), A0
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+SHAPES = [((33, 40, 29), 3), ((64, 64, 64), 16), ((17, 130, 9, 12), 17), ((6, 5, 7, 4, 5), 4),
+          ((150, 1, 70), 5), ((128, 96, 140), 100), ((40, 33, 260), 64), ((9, 8, 7), 1)]
+
+
+@pytest.mark.parametrize("dims,R", SHAPES)
+@pytest.mark.parametrize("prec", PRECS)
+def test_mttkrp_parity(pkg, dims, R, prec):
+    Td, Tref, A0 = problem(dims, R, 11)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    for n in range(len(dims)):
+        M = ctx.mttkrp(n).cpu().numpy()
+        assert relerr(M, co.mttkrp(Tref, A0, n)) <= 1e-5, (n, prec)
+    ctx.close()
+
+
+@pytest.mark.parametrize("dims,R", SHAPES[:6])
+@pytest.mark.parametrize("prec", PRECS)
+def test_ttm_parity(pkg, dims, R, prec):
+    Td, Tref, A0 = problem(dims, R, 12)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    for m in range(len(dims)):
+        X = ctx.ttm(m).cpu().numpy()
+        ref = np.tensordot(Tref, A0[m], axes=([m], [0]))
+        assert X.shape == ref.shape
+        assert relerr(X, ref) <= 1e-5, (m, prec)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_dt_sweeps_small_config(pkg, prec):
+    """Order-3 64^3, R = 16, U[0,1) factors, 1e-2 noise, 10 DT sweeps."""
+    Td, Tref, A0 = problem((64, 64, 64), 16, 20101205, eta=1e-2)
+    ctx = pkg.CPContext(Td, 16, A0=A0, prec=prec)
+    ctx.sweep_dt(10)
+    ref = co.cp_als(Tref, A0, 10, route="dt")
+    tr = ctx.trace()
+    assert [t["kind"] for t in tr] == ["dt"] * 10
+    got = np.array([t["resid"] for t in tr])
+    assert np.abs(got - np.array(ref.resid)).max() <= 1e-5
+    _, r_direct = ctx.fit(exact=True)
+    assert abs(r_direct - co.residual_direct(Tref, ref.A)) <= 1e-6
+    st = ctx.stats()
+    assert st["ttm"] == 20 and st["sweeps_exact"] == 10
+    ctx.close()
+
+
+@pytest.mark.parametrize("dims,R", [((24, 20, 22, 18), 8), ((30, 26, 28), 6), ((7, 6, 8, 5, 6), 3)])
+def test_msdt_sweeps_match_oracle(pkg, dims, R):
+    N = len(dims)
+    Td, Tref, A0 = problem(dims, R, 31, eta=0.05)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec="fp32")
+    nsw = 2 * (N - 1)
+    ctx.sweep_msdt(nsw)
+    ref = co.cp_als(Tref, A0, nsw, route="msdt")
+    got = np.array([t["resid"] for t in ctx.trace()])
+    assert np.abs(got - np.array(ref.resid)).max() <= 1e-5
+    for n in range(N):
+        assert relerr(ctx.get_factor(n), ref.A[n]) <= 1e-4
+    # MSDT: N first-level TTMs per N-1 sweeps (Sec. III)
+    assert ctx.stats()["ttm"] == 2 * N
+    ctx.close()
+
+
+def test_msdt_resumes_across_calls(pkg):
+    """The MSDT root cache persists across calls: 1+2 sweeps equal 3 sweeps."""
+    dims, R = (20, 18, 22, 16), 5
+    Td, Tref, A0 = problem(dims, R, 32, eta=0.05)
+    a = pkg.CPContext(Td, R, A0=A0, prec="fp32")
+    a.sweep_msdt(3)
+    b = pkg.CPContext(Td, R, A0=A0, prec="fp32")
+    b.sweep_msdt(1)
+    b.sweep_msdt(2)
+    for n in range(4):
+        assert relerr(b.get_factor(n), a.get_factor(n)) <= 1e-12
+    assert a.stats()["ttm"] == b.stats()["ttm"] == 4
+    a.close()
+    b.close()
+
+
+def test_direct_residual(pkg):
+    dims, R = (37, 41, 35), 7
+    Td, Tref, A0 = problem(dims, R, 40, eta=0.1)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec="fp32")
+    _, r = ctx.fit(exact=True)
+    assert abs(r - co.residual_direct(Tref, A0)) <= 1e-6
+    ctx.close()
+
+
+def _pp_case(pkg, dims, R, seed, t, cp_tensor=False, only=None):
+    Ap = synth.uniform_factors(seed, dims, R)
+    D = synth.gaussian_factors(seed + 1, dims, R)
+    A = [Ap[i] + (t * D[i] if (only is None or i == only) else 0.0) for i in range(len(dims))]
+    T64 = synth.cp_full(A) if cp_tensor else synth.normal(seed + 2, 0, int(np.prod(dims))).reshape(dims)
+    T32 = np.ascontiguousarray(T64.astype(np.float32))
+    Tref = T32.astype(np.float64)
+    ctx = pkg.CPContext(torch.from_numpy(T32).cuda(), R, A0=Ap, prec="fp32")
+    ctx.pp_init()
+    for i in range(len(dims)):
+        ctx.set_factor(i, A[i])
+    pairs, Mp = co.pp_operators(Tref, Ap)
+    dA = [A[i] - Ap[i] for i in range(len(dims))]
+    S = [co.gram(a) for a in A]
+    return ctx, Tref, A, pairs, Mp, dA, S
+
+
+@pytest.mark.parametrize("dims,R", [((20, 24, 18), 4), ((12, 10, 14, 11), 5), ((6, 7, 5, 6, 5), 3)])
+@pytest.mark.parametrize("t", [0.0, 0.05])
+def test_pp_mttkrp_parity(pkg, dims, R, t):
+    ctx, Tref, A, pairs, Mp, dA, S = _pp_case(pkg, dims, R, 50, t)
+    for n in range(len(dims)):
+        got = ctx.pp_mttkrp(n).cpu().numpy()
+        ref = co.pp_mttkrp(pairs, Mp, A, dA, S, n)
+        assert relerr(got, ref) <= 1e-5, n
+        if t == 0.0:
+            assert relerr(got, co.mttkrp(Tref, A, n)) <= 1e-5
+    ctx.close()
+
+
+def test_pp_mttkrp_exact_on_order3_cp_tensor(pkg):
+    ctx, Tref, A, pairs, Mp, dA, S = _pp_case(pkg, (20, 22, 18), 4, 60, 0.2, cp_tensor=True)
+    for n in range(3):
+        assert relerr(ctx.pp_mttkrp(n).cpu().numpy(), co.mttkrp(Tref, A, n)) <= 1e-5
+    ctx.close()
+
+
+def test_pp_sweeps_follow_oracle(pkg):
+    dims, R = (30, 32, 28), 4
+    Td, Tref, A0 = problem(dims, R, 70, eta=1e-3)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec="fp32")
+    ctx.sweep_pp(25, eps=0.1)
+    ref = co.pp_cp_als(Tref, A0, 25, eps=0.1)
+    tr = ctx.trace()
+    kinds = ["pp" if t["kind"] == "pp" else "als" for t in tr]
+    assert kinds == ref.kinds
+    assert sum(t["pp_init"] for t in tr) == ref.n_pp_init
+    got = np.array([t["resid"] for t in tr])
+    assert np.abs(got - np.array(ref.resid)).max() <= 1e-5
+    ctx.close()
+
+
+def test_float64_input_and_default_init(pkg):
+    """FP64 tensors are converted once; NULL initial factors follow the documented Philox stream."""
+    dims, R = (16, 18, 20), 3
+    T64, _, _ = synth.make_problem(80, dims, R, eta=0.01)
+    ctx = pkg.CPContext(torch.from_numpy(T64).cuda(), R, A0=None, seed=12345, prec="fp32")
+    A0 = synth.uniform_factors(12345, dims, R)
+    for n in range(3):
+        assert np.array_equal(ctx.get_factor(n), A0[n])
+    Tref = T64.astype(np.float32).astype(np.float64)
+    assert relerr(ctx.mttkrp(2).cpu().numpy(), co.mttkrp(Tref, A0, 2)) <= 1e-5
+    ctx.close()
