@@ -51,9 +51,11 @@ typedef enum {
  * Gram / Hadamard / Cholesky / residual terms in FP64 whatever is chosen. */
 typedef enum {
     CP_FP32_SIMT = 0, /* FP32 FMA on the CUDA cores                              */
-    CP_TF32 = 1,      /* tcgen05 kind::tf32 on the raw FP32 tensor (10-bit mant.) */
+    CP_TF32 = 1,      /* tcgen05 kind::tf32 on rna_tf32(x) only (reported, 10-bit mantissa) */
     CP_BF16X3 = 2,    /* tcgen05 kind::f16: x = hi + lo in bf16, hi*hi+hi*lo+lo*hi */
-    CP_BF16 = 3       /* tcgen05 kind::f16 on bf16(x) only (reported, low accuracy) */
+    CP_BF16 = 3,      /* tcgen05 kind::f16 on bf16(x) only (reported, low accuracy) */
+    CP_TF32X3 = 4     /* tcgen05 kind::tf32: x = hi + lo in tf32 (round to nearest),
+                         hi*hi+hi*lo+lo*hi; about FP32 accuracy at half bf16x3's rate */
 } cp_prec;
 
 typedef struct {
@@ -190,6 +192,7 @@ typedef struct {
     double pp_flops;        /* U + V flops of approximated MTTKRPs            */
     double ttm_bytes;       /* algorithmic HBM bytes of the TTMs (read+write) */
     double mttv_bytes;      /* algorithmic bytes of the mTTVs                 */
+    int64_t ttm_tensor_core;/* first-level TTMs that ran on tcgen05           */
 } cp_stats;
 cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
 

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcpals.so")
 _lib = None
 
-PREC = {"fp32": 0, "tf32": 1, "bf16x3": 2, "bf16": 3}
+PREC = {"fp32": 0, "tf32": 1, "bf16x3": 2, "bf16": 3, "tf32x3": 4}
 STATUS = {0: "CP_OK", 1: "CP_EINVAL", 2: "CP_ENOMEM", 3: "CP_ECUDA", 4: "CP_ENOTSPD",
           5: "CP_ENUMERIC", 6: "CP_ETIMEOUT", 7: "CP_ESTATE"}
 KINDS = {0: "dt", 1: "msdt", 2: "pp", 3: "pp-regular"}
@@ -50,7 +50,8 @@ class Stats(ctypes.Structure):
                 ("sweeps_exact", ctypes.c_int64), ("sweeps_pp", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("ttm_flops", ctypes.c_double),
                 ("mttv_flops", ctypes.c_double), ("pp_flops", ctypes.c_double),
-                ("ttm_bytes", ctypes.c_double), ("mttv_bytes", ctypes.c_double)]
+                ("ttm_bytes", ctypes.c_double), ("mttv_bytes", ctypes.c_double),
+                ("ttm_tensor_core", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p

@@ -80,6 +80,7 @@ struct cp_ctx {
     double normT2 = 0.0;
 
     Slot slot[CP_MAXN + 1];
+    cpk::TcPlan* tc_plan[CP_MAXN] = {0};   // tensor-core TTM per mode (NULL: SIMT)
 
     // PP state
     bool pp_alloc = false, pp_valid = false;
@@ -190,9 +191,9 @@ cp_status launch_ttm(cp_ctx* c, int mode, float* X) {
     contract_dims(c, 0u, mode, &P, &Q);
     const int K = (int)c->dims[mode];
     const int prec = c->cfg.prec;
-    if (prec != CP_FP32_SIMT && cpk::ttm_tc_supported(P, K, Q, c->R)) {
-        cpk::TcOperand B{c->bhi[mode], c->blo[mode], c->bt32[mode], c->Rpad, c->Kpad[mode]};
-        LAUNCH(c, cpk::ttm_tc(c->T, B, X, P, K, Q, c->R, prec, c->num_sms, c->dev_err, c->st));
+    if (prec != CP_FP32_SIMT && c->tc_plan[mode]) {
+        LAUNCH(c, cpk::ttm_tc_run(c->tc_plan[mode], X, prec, c->num_sms, c->dev_err, c->st));
+        c->stats.ttm_tensor_core++;
     } else {
         LAUNCH(c, cpk::ttm_simt(c->T, c->A32[mode], X, P, K, Q, c->R, c->st));
     }
@@ -302,7 +303,7 @@ cp_status grow_hist(cp_ctx* c, int nsweeps) {
 cp_status update_mode(cp_ctx* c, int u, const float* M, bool pp, double* scal) {
     const int R = c->R, s = (int)c->dims[u];
     LAUNCH(c, cpk::gamma_chol(c->d_Slist, c->d_dSlist, c->N, u, R, pp ? 1 : 0, c->Gamma, c->L,
-                              c->invd, c->W, scal + SCAL_FLAGS, c->st));
+                              c->invd, c->W, scal, c->st));
     cpk::SolveOut o;
     o.A64 = c->A64[u];
     o.A32 = c->A32[u];
@@ -584,6 +585,10 @@ void free_all(cp_ctx* c) {
         for (int j = 0; j < CP_MAXN; ++j) F(c->pair[i][j]);
     }
     for (int k = 0; k <= CP_MAXN; ++k) F(c->slot[k].buf);
+    for (int i = 0; i < CP_MAXN; ++i) {
+        cpk::ttm_tc_plan_free(c->tc_plan[i]);
+        c->tc_plan[i] = nullptr;
+    }
     F(c->Mt); F(c->d_Slist); F(c->d_dSlist); F(c->Gamma); F(c->L); F(c->invd); F(c->W);
     F(c->gram_part); F(c->scal_part); F(c->scal_hist); F(c->red_part); F(c->d_red_out); F(c->dev_err);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -625,7 +630,7 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
     c->numel = numel;
     c->st = (cudaStream_t)stream;
     if (cfg) c->cfg = *cfg; else cp_config_default(&c->cfg);
-    if (c->cfg.prec < CP_FP32_SIMT || c->cfg.prec > CP_BF16) { delete c; return CP_EINVAL; }
+    if (c->cfg.prec < CP_FP32_SIMT || c->cfg.prec > CP_TF32X3) { delete c; return CP_EINVAL; }
     memset(&c->stats, 0, sizeof(c->stats));
     for (int i = 0; i < N; ++i) {
         c->dims[i] = dims[i];
@@ -674,10 +679,10 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
         const size_t op = (size_t)c->Rpad * c->Kpad[i];
         TRY(dalloc(c, &c->bhi[i], op));
         TRY(dalloc(c, &c->blo[i], op));
-        TRY(dalloc(c, &c->bt32[i], op));
+        TRY(dalloc(c, &c->bt32[i], 2 * op));
         TRYC(cudaMemsetAsync(c->bhi[i], 0, op * sizeof(uint16_t), c->st));
         TRYC(cudaMemsetAsync(c->blo[i], 0, op * sizeof(uint16_t), c->st));
-        TRYC(cudaMemsetAsync(c->bt32[i], 0, op * sizeof(float), c->st));
+        TRYC(cudaMemsetAsync(c->bt32[i], 0, 2 * op * sizeof(float), c->st));
     }
     // one slot per number of kept modes k = 1..N-1: capacity = largest k-mode product x R
     std::vector<int64_t> sd(dims, dims + N);
@@ -721,6 +726,19 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
         TRYC(cudaStreamSynchronize(c->st));
     }
     TRY(init_grams(c));
+    // tensor-core TTM plans (TMA descriptors of T and of each factor operand)
+    if (c->cfg.prec != CP_FP32_SIMT) {
+        const bool bf = (c->cfg.prec == CP_BF16X3 || c->cfg.prec == CP_BF16);
+        for (int m = 0; m < N; ++m) {
+            int64_t P, Q;
+            contract_dims(c, 0u, m, &P, &Q);
+            const void* hi = bf ? (const void*)c->bhi[m] : (const void*)c->bt32[m];
+            const void* lo = bf ? (const void*)c->blo[m]
+                                : (const void*)(c->bt32[m] + (size_t)c->Rpad * c->Kpad[m]);
+            c->tc_plan[m] = cpk::ttm_tc_plan(c->T, P, (int)dims[m], Q, R, bf ? 0 : 1, hi, lo, c->Rpad,
+                                             c->Kpad[m]);
+        }
+    }
     // ||T||_F^2
     int nb = cpk::norm2_partials(c->T, numel, c->red_part, 4096, c->st);
     TRYC(cudaGetLastError());

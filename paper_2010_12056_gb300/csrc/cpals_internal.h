@@ -39,16 +39,19 @@ namespace cpk {
 cudaError_t ttm_simt(const float* T, const float* A, float* X, int64_t P, int K, int64_t Q,
                      int R, cudaStream_t st);
 
-// tensor-core first-level TTM; Bop = operand copy of A(mode), see k_ttm_tc.cu
-struct TcOperand {
-    const uint16_t* bhi;  // bf16 hi part, [Rpad][Kpad] (K contiguous)
-    const uint16_t* blo;  // bf16 lo part, same layout
-    const float* bt32;    // fp32 transposed copy [Rpad][Kpad] for kind::tf32
-    int Rpad, Kpad;
-};
-cudaError_t ttm_tc(const float* T, const TcOperand& B, float* X, int64_t P, int K, int64_t Q,
-                   int R, int prec, int num_sms, unsigned* dev_err, cudaStream_t st);
+// tensor-core first-level TTM (k_ttm_tc.cu).  A plan holds the TMA descriptors
+// of one contraction (tensor T viewed as [P][K][Q], factor operand bhi/blo stored
+// [Rpad][Kpad] K-contiguous); NULL when the shape is not supported (the caller
+// then uses the SIMT kernel).
+struct TcPlan;
 bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R);
+// kind 0: bf16 parts (bhi/blo uint16 [Rpad][Kpad]); kind 1: tf32 parts (fp32 [Rpad][Kpad])
+TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind, const void* bhi,
+                    const void* blo, int Rpad, int Kpad);
+int ttm_tc_kind(const TcPlan* p);
+void ttm_tc_plan_free(TcPlan* p);
+cudaError_t ttm_tc_run(const TcPlan* p, float* X, int prec, int num_sms, unsigned* dev_err,
+                       cudaStream_t st);
 
 // multi-TTV: Y[p][q][r] = sum_k X[p][k][q][r] * A[k][r]
 cudaError_t mttv(const float* X, const float* A, float* Y, int64_t P, int K, int64_t Q, int R,
@@ -75,7 +78,7 @@ cudaError_t sum_partials(const double* partials, int n, double* out, cudaStream_
 // W = sum_{i<j; i,j != n} dS(i)*dS(j)*(*_{k != i,j,n} S(k)).
 cudaError_t gamma_chol(double* const* S_list, double* const* dS_list, int N, int n, int R,
                        int pp, double* Gamma, double* L, double* invdiag, double* W,
-                       double* scal_flags, cudaStream_t st);
+                       double* scal, cudaStream_t st);
 
 // Row-wise solve A_new = (M + A_old W) Gamma^{-1}; writes every operand copy and
 // per-block partial scalars (CP_NSCAL per block).  Returns blocks used via *nblk.
@@ -84,7 +87,7 @@ struct SolveOut {
     float* A32;         // FP32 copy
     uint16_t* bhi;      // bf16 hi, transposed [Rpad][Kpad]
     uint16_t* blo;      // bf16 lo
-    float* bt32;        // fp32 transposed [Rpad][Kpad]
+    float* bt32;        // tf32 parts, transposed: hi [Rpad][Kpad] then lo [Rpad][Kpad]
     int Rpad, Kpad;
     const double* Ap;   // PP base factor (NULL outside PP)
     float* dA32;        // A_new - A_p (or - A_old outside PP), FP32

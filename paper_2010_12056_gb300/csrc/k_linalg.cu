@@ -37,6 +37,19 @@ __device__ double block_sum(double v, double* sh) {
     return t;
 }
 
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// tf32 split of the factor operand: hi at [j][x], lo at Rpad*Kpad + [j][x]
+__device__ __forceinline__ void tf32_store(float* bt, size_t lo_off, size_t e, float x) {
+    const float h = tf32_rna(x);
+    bt[e] = h;
+    bt[lo_off + e] = tf32_rna(x - h);
+}
+
 __device__ __forceinline__ void bf16_split(float x, uint16_t& hi, uint16_t& lo) {
     __nv_bfloat16 h = __float2bfloat16_rn(x);
     __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
@@ -46,20 +59,24 @@ __device__ __forceinline__ void bf16_split(float x, uint16_t& hi, uint16_t& lo) 
 
 // ------------------------------------------------------------------ Gamma + Cholesky
 // One CTA.  work = Gamma (smem when R <= 128, else the Lt half of the output
-// buffer, which is rewritten at the end).  Right-looking column Cholesky; if a
-// pivot is not positive the factorisation restarts once on
-// Gamma + 1e-12 * trace(Gamma)/R * I (flag bit 1), and a second failure sets
-// flag bit 2 and leaves L = I so that later kernels stay finite.
+// buffer, which is rewritten at the end).  Right-looking factorisation in the
+// LDL^T form, one barrier per column: at step j every thread reads the pivot
+// d_j = work[j][j] and updates work[i][k] -= work[i][j] work[k][j] / d_j for
+// j < k <= i; finally L[i][k] = work[i][k] / sqrt(d_k), L[k][k] = sqrt(d_k).
+// If a pivot is not positive the factorisation restarts once on
+// Gamma + 1e-12 * trace(Gamma)/R * I (flag 1); a second failure sets flag 2 and
+// leaves L = I so that later kernels stay finite.  scal[SCAL_FLAGS] gets the
+// flag and scal[SCAL_GS] is cleared for the Gram kernel's accumulation.
 __global__ void __launch_bounds__(512) k_gamma_chol(double* const* __restrict__ S_list,
                                                     double* const* __restrict__ dS_list, int N,
                                                     int n, int R, int pp, double* __restrict__ G,
                                                     double* __restrict__ Lout,
                                                     double* __restrict__ invd,
                                                     double* __restrict__ W,
-                                                    double* __restrict__ flags, int use_smem) {
+                                                    double* __restrict__ scal, int use_smem) {
     extern __shared__ double smw[];
     __shared__ double red[32];
-    __shared__ int fail;
+    __shared__ double sinv[CP_MAXR];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int RR = R * R;
     double* L = Lout;            // lower, row-major
@@ -89,8 +106,10 @@ __global__ void __launch_bounds__(512) k_gamma_chol(double* const* __restrict__ 
             W[e] = w;
         }
     }
-    tr = block_sum(tr, red);
+    tr = block_sum(tr, red);  // also a barrier: work is complete
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     double flag = 0.0;
+    bool bad = false;
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (attempt == 1) {
             const double shift = 1e-12 * tr / R;
@@ -98,73 +117,97 @@ __global__ void __launch_bounds__(512) k_gamma_chol(double* const* __restrict__ 
             flag = 1.0;
             __syncthreads();
         }
-        if (tid == 0) fail = 0;
-        __syncthreads();
+        bool ok = true;
         for (int j = 0; j < R; ++j) {
-            if (tid == 0) {
-                double d = work[j * R + j];
-                if (!(d > 0.0) || !isfinite(d)) {
-                    fail = 1;
-                } else {
-                    double sd = sqrt(d);
-                    work[j * R + j] = sd;
-                    invd[j] = 1.0 / sd;
-                }
+            const double d = work[j * R + j];  // same value in every thread
+            if (!(d > 0.0) || !isfinite(d)) {
+                ok = false;
+                break;
             }
-            __syncthreads();
-            if (fail) break;
-            const double ij = invd[j];
-            for (int i = j + 1 + tid; i < R; i += nt) work[i * R + j] *= ij;
-            __syncthreads();
-            const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+            const double inv = 1.0 / d;
             for (int i = j + 1 + warp; i < R; i += nw) {
-                const double lij = work[i * R + j];
-                for (int k = j + 1 + lane; k <= i; k += 32) work[i * R + k] -= lij * work[k * R + j];
+                const double lij = work[i * R + j] * inv;
+                double* wi = work + (size_t)i * R;
+                for (int k = j + 1 + lane; k <= i; k += 32) wi[k] = fma(-lij, work[k * R + j], wi[k]);
             }
             __syncthreads();
         }
-        if (!fail) break;
-        if (attempt == 1) flag = 2.0;
+        if (ok) break;
+        __syncthreads();
+        if (attempt == 1) {
+            flag = 2.0;
+            bad = true;
+        }
     }
-    // write L (lower) and Lt (upper); L = I after a double failure
-    const bool bad = fail != 0;
+    for (int j = tid; j < R; j += nt) {
+        const double v = bad ? 1.0 : 1.0 / sqrt(work[j * R + j]);
+        sinv[j] = v;
+        invd[j] = v;
+    }
+    __syncthreads();
     if (!use_smem) {
-        // work aliases Lt: copy the lower triangle to L first
+        // work aliases Lt: build L first, then its transpose
         for (int e = tid; e < RR; e += nt) {
-            int i = e / R, k = e % R;
-            L[e] = bad ? (i == k ? 1.0 : 0.0) : (k <= i ? work[e] : 0.0);
+            const int i = e / R, k = e % R;
+            double v = 0.0;
+            if (bad) v = (i == k) ? 1.0 : 0.0;
+            else if (k < i) v = work[e] * sinv[k];
+            else if (k == i) v = 1.0 / sinv[k];
+            L[e] = v;
         }
         __syncthreads();
         for (int e = tid; e < RR; e += nt) {
-            int i = e / R, k = e % R;
+            const int i = e / R, k = e % R;
             Lt[e] = L[k * R + i];
         }
     } else {
         for (int e = tid; e < RR; e += nt) {
-            int i = e / R, k = e % R;
-            double v = bad ? (i == k ? 1.0 : 0.0) : (k <= i ? work[e] : 0.0);
+            const int i = e / R, k = e % R;
+            double v = 0.0;
+            if (bad) v = (i == k) ? 1.0 : 0.0;
+            else if (k < i) v = work[e] * sinv[k];
+            else if (k == i) v = 1.0 / sinv[k];
             L[e] = v;
             Lt[k * R + i] = v;
         }
     }
-    if (bad)
-        for (int j = tid; j < R; j += nt) invd[j] = 1.0;
-    if (tid == 0) flags[0] = flag;
+    if (tid == 0) {
+        scal[SCAL_FLAGS] = flag;
+        scal[SCAL_GS] = 0.0;
+    }
 }
 
 // ------------------------------------------------------------------ row solves
 // One warp per row x: m~ = M(x,:) [+ A_old(x,:) W]; forward substitution with L,
 // back substitution with L^T (column-oriented, lane l owns entries l + 32t).
-template <int RT>
+// With SMEM the block first stages L (row stride R+1, so that column reads are
+// free of bank conflicts) and 1/L[j][j] in shared memory.
+template <int RT, bool SMEM>
 __global__ void __launch_bounds__(128) k_solve(const float* __restrict__ M,
                                                const double* __restrict__ W,
                                                const double* __restrict__ L,
                                                const double* __restrict__ invd, cpk::SolveOut o,
                                                int s, int R, double* __restrict__ scal_part) {
+    extern __shared__ double sL[];
     __shared__ double red[4][CP_NSCAL];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int x = blockIdx.x * 4 + wib;
-    const double* Lt = L + (size_t)R * R;
+    const int ld = SMEM ? R + 1 : R;
+    const double* Lc;   // column access L[k][j] = Lc[j * ldc + k]... see below
+    const double* Lr;   // row access    L[j][k] = Lr[j * ld + k]
+    const double* iv;
+    if (SMEM) {
+        for (int e = threadIdx.x; e < R * R; e += blockDim.x) sL[(e / R) * ld + (e % R)] = L[e];
+        for (int j = threadIdx.x; j < R; j += blockDim.x) sL[R * ld + j] = invd[j];
+        __syncthreads();
+        Lr = sL;
+        Lc = sL;
+        iv = sL + R * ld;
+    } else {
+        Lr = L;
+        Lc = L + (size_t)R * R;  // Lt row-major: L[k][j] = Lt[j][k]
+        iv = invd;
+    }
     double sc[CP_NSCAL];
 #pragma unroll
     for (int i = 0; i < CP_NSCAL; ++i) sc[i] = 0.0;
@@ -205,13 +248,15 @@ __global__ void __launch_bounds__(128) k_solve(const float* __restrict__ M,
             for (int jj = 0; jj < 32; ++jj) {
                 const int j = tt * 32 + jj;
                 if (j >= R) break;
-                const double zj = __shfl_sync(FULL, acc[tt], jj) * invd[j];
+                const double zj = __shfl_sync(FULL, acc[tt], jj) * iv[j];
                 if (lane == jj) z[tt] = zj;
-                const double* lr = Lt + (size_t)j * R;
 #pragma unroll
                 for (int t2 = tt; t2 < RT; ++t2) {
                     const int k = lane + 32 * t2;
-                    if (k > j && k < R) acc[t2] = fma(-lr[k], zj, acc[t2]);
+                    if (k > j && k < R) {
+                        const double lkj = SMEM ? Lc[(size_t)k * ld + j] : Lc[(size_t)j * R + k];
+                        acc[t2] = fma(-lkj, zj, acc[t2]);
+                    }
                 }
             }
         }
@@ -223,9 +268,9 @@ __global__ void __launch_bounds__(128) k_solve(const float* __restrict__ M,
             for (int jj = 31; jj >= 0; --jj) {
                 const int j = tt * 32 + jj;
                 if (j >= R) continue;
-                const double xj = __shfl_sync(FULL, acc[tt], jj) * invd[j];
+                const double xj = __shfl_sync(FULL, acc[tt], jj) * iv[j];
                 if (lane == jj) xs[tt] = xj;
-                const double* lr = L + (size_t)j * R;
+                const double* lr = Lr + (size_t)j * ld;
 #pragma unroll
                 for (int t2 = 0; t2 <= tt; ++t2) {
                     const int k = lane + 32 * t2;
@@ -248,7 +293,7 @@ __global__ void __launch_bounds__(128) k_solve(const float* __restrict__ M,
                 o.bhi[(size_t)j * o.Kpad + x] = hi;
                 o.blo[(size_t)j * o.Kpad + x] = lo;
             }
-            if (o.bt32) o.bt32[(size_t)j * o.Kpad + x] = af;
+            if (o.bt32) tf32_store(o.bt32, (size_t)o.Rpad * o.Kpad, (size_t)j * o.Kpad + x, af);
             const double base = o.Ap ? o.Ap[e] : aold[t];
             const double d = a - base;
             if (o.dA32) o.dA32[e] = (float)d;
@@ -306,28 +351,44 @@ __global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ A,
 }
 
 // ------------------------------------------------------------------ finalize
-__global__ void __launch_bounds__(1024) k_finalize(const double* __restrict__ part, int nchunk,
-                                                   const double* __restrict__ scal_part, int nblk,
-                                                   const double* __restrict__ Gamma, int R,
-                                                   int want_dS, double* __restrict__ S,
-                                                   double* __restrict__ dS,
-                                                   double* __restrict__ scal_out) {
+// Grid over the R x R entries: S = sum of chunk partials (and dS); <Gamma, S>
+// accumulates into scal[SCAL_GS] (cleared by the Cholesky kernel of the same
+// update).  Block 0 also reduces the solve kernel's per-block scalars.
+__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ part, int nchunk,
+                                                  const double* __restrict__ scal_part, int nblk,
+                                                  const double* __restrict__ Gamma, int R,
+                                                  int want_dS, double* __restrict__ S,
+                                                  double* __restrict__ dS,
+                                                  double* __restrict__ scal_out) {
     __shared__ double red[32];
     const int tid = threadIdx.x;
     const size_t RR = (size_t)R * R;
     double gs = 0.0;
-    for (size_t e = tid; e < RR; e += blockDim.x) {
-        double v = 0.0, vd = 0.0;
-        for (int c = 0; c < nchunk; ++c) {
-            v += part[(size_t)c * 2 * RR + e];
-            if (want_dS) vd += part[(size_t)c * 2 * RR + RR + e];
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + tid; e < RR; e += (size_t)gridDim.x * blockDim.x) {
+        double v0 = 0.0, v1 = 0.0, d0 = 0.0, d1 = 0.0;
+        int c = 0;
+        for (; c + 1 < nchunk; c += 2) {
+            v0 += part[(size_t)c * 2 * RR + e];
+            v1 += part[(size_t)(c + 1) * 2 * RR + e];
+            if (want_dS) {
+                d0 += part[(size_t)c * 2 * RR + RR + e];
+                d1 += part[(size_t)(c + 1) * 2 * RR + RR + e];
+            }
         }
+        if (c < nchunk) {
+            v0 += part[(size_t)c * 2 * RR + e];
+            if (want_dS) d0 += part[(size_t)c * 2 * RR + RR + e];
+        }
+        const double v = v0 + v1;
         S[e] = v;
-        if (want_dS) dS[e] = vd;
+        if (want_dS) dS[e] = d0 + d1;
         if (Gamma) gs += Gamma[e] * v;
     }
-    gs = block_sum(gs, red);
-    if (tid == 0) scal_out[SCAL_GS] = gs;
+    if (Gamma) {
+        gs = block_sum(gs, red);
+        if (tid == 0) atomicAdd(scal_out + SCAL_GS, gs);
+    }
+    if (blockIdx.x != 0) return;
     for (int slot = 0; slot < CP_NSCAL; ++slot) {
         if (slot == SCAL_GS || slot == SCAL_FLAGS) continue;
         double v = 0.0;
@@ -340,7 +401,7 @@ __global__ void __launch_bounds__(1024) k_finalize(const double* __restrict__ pa
 // ------------------------------------------------------------------ factor copies
 __global__ void k_factor_copies(const double* __restrict__ A64, float* __restrict__ A32,
                                 uint16_t* __restrict__ bhi, uint16_t* __restrict__ blo,
-                                float* __restrict__ bt32, int s, int R, int Kpad) {
+                                float* __restrict__ bt32, int s, int R, int Rpad, int Kpad) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)s * R) return;
     const int x = (int)(e / R), j = (int)(e % R);
@@ -352,7 +413,7 @@ __global__ void k_factor_copies(const double* __restrict__ A64, float* __restric
         bhi[(size_t)j * Kpad + x] = hi;
         blo[(size_t)j * Kpad + x] = lo;
     }
-    if (bt32) bt32[(size_t)j * Kpad + x] = af;
+    if (bt32) tf32_store(bt32, (size_t)Rpad * Kpad, (size_t)j * Kpad + x, af);
 }
 
 // ------------------------------------------------------------------ norms
@@ -572,7 +633,7 @@ cudaError_t add_aw(const float* Mt, const double* A, const double* W, int s, int
 
 cudaError_t gamma_chol(double* const* S_list, double* const* dS_list, int N, int n, int R,
                        int pp, double* Gamma, double* L, double* invdiag, double* W,
-                       double* scal_flags, cudaStream_t st) {
+                       double* scal, cudaStream_t st) {
     const int use_smem = (R <= 128) ? 1 : 0;
     size_t smem = use_smem ? (size_t)R * R * sizeof(double) : 0;
     static bool attr_set = false;
@@ -581,8 +642,23 @@ cudaError_t gamma_chol(double* const* S_list, double* const* dS_list, int N, int
                              128 * 128 * sizeof(double));
         attr_set = true;
     }
-    k_gamma_chol<<<1, 512, smem, st>>>(S_list, dS_list, N, n, R, pp, Gamma, L, invdiag, W,
-                                       scal_flags, use_smem);
+    k_gamma_chol<<<1, 512, smem, st>>>(S_list, dS_list, N, n, R, pp, Gamma, L, invdiag, W, scal,
+                                       use_smem);
+    return cudaGetLastError();
+}
+
+template <int RT, bool SM>
+static cudaError_t launch_solve(unsigned blocks, const float* M, const double* W, const double* L,
+                                const double* invdiag, const SolveOut& o, int s, int R,
+                                double* scal_part, cudaStream_t st) {
+    size_t smem = SM ? ((size_t)R * (R + 1) + R) * sizeof(double) : 0;
+    static bool attr_set = false;
+    if (SM && !attr_set) {
+        cudaFuncSetAttribute(k_solve<RT, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(((size_t)128 * 129 + 128) * sizeof(double)));
+        attr_set = true;
+    }
+    k_solve<RT, SM><<<blocks, 128, smem, st>>>(M, W, L, invdiag, o, s, R, scal_part);
     return cudaGetLastError();
 }
 
@@ -593,13 +669,16 @@ cudaError_t solve_rows(const float* M, const double* W, const double* L, const d
     const unsigned blocks = (unsigned)((s + 3) / 4);
     *nblk = (int)blocks;
     switch (RT) {
-#define CASE(k) \
-    case k: k_solve<k><<<blocks, 128, 0, st>>>(M, W, L, invdiag, o, s, R, scal_part); break;
-        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
-#undef CASE
+        case 1: return launch_solve<1, true>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 2: return launch_solve<2, true>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 3: return launch_solve<3, true>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 4: return launch_solve<4, true>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 5: return launch_solve<5, false>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 6: return launch_solve<6, false>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 7: return launch_solve<7, false>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 8: return launch_solve<8, false>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t gram_partials(const double* A, const double* dA, int s, int R, double* part,
@@ -613,17 +692,19 @@ cudaError_t gram_partials(const double* A, const double* dA, int s, int R, doubl
 cudaError_t finalize_update(const double* gram_part, int nchunk, const double* scal_part,
                             int nblk, const double* Gamma, int R, int want_dS, double* S,
                             double* dS, double* scal_out, cudaStream_t st) {
-    k_finalize<<<1, 1024, 0, st>>>(gram_part, nchunk, scal_part, nblk, Gamma, R, want_dS, S, dS,
-                                   scal_out);
+    const size_t RR = (size_t)R * R;
+    unsigned blocks = (unsigned)((RR + 255) / 256);
+    if (blocks > 64) blocks = 64;
+    k_finalize<<<blocks, 256, 0, st>>>(gram_part, nchunk, scal_part, nblk, Gamma, R, want_dS, S, dS,
+                                       scal_out);
     return cudaGetLastError();
 }
 
 cudaError_t factor_copies(const double* A64, float* A32, uint16_t* bhi, uint16_t* blo,
                           float* bt32, int s, int R, int Rpad, int Kpad, cudaStream_t st) {
-    (void)Rpad;
     const int64_t n = (int64_t)s * R;
     k_factor_copies<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A64, A32, bhi, blo, bt32, s, R,
-                                                                 Kpad);
+                                                                 Rpad, Kpad);
     return cudaGetLastError();
 }
 

@@ -1,11 +1,663 @@
-// Tensor-core first-level TTM (tcgen05 + TMA).  Placeholder until the kernel lands:
-// reports "unsupported" so the driver uses the FP32 SIMT path.
+// First-level TTM on the 5th-generation tensor cores (Sec. II-C: T x_m A(m),
+// the dominant 2 s^N R-flop contraction of every dimension tree).
+//
+//   X[g][r] = sum_k T(g, k) A(m)[k][r],   g = (p, q) over the modes kept.
+//
+// One persistent CTA per SM streams 128-row tiles of T exactly once:
+//   warp 0      TMA producer: FP32 tensor chunks (128 rows x BK k) into a staging
+//               ring; the factor operand (stored [r][k], K-major, split in two
+//               parts) either once for the whole kernel (when all of K fits) or
+//               one chunk per k-step.
+//   warps 4-7   converters, thread = tile row: split every FP32 value into two
+//               parts in the canonical K-major 128-byte-swizzled layout (rows of
+//               128 B, 16-byte chunk c of row m at c ^ (m mod 8)):
+//                 bf16 family (BK = 64): hi = rn_bf16(x), lo = rn_bf16(x - hi)
+//                 tf32 family (BK = 32): hi = rna_tf32(x), lo = rna_tf32(x - hi)
+//               For the last mode the chunk is K-contiguous (TMA SWIZZLE_128B keeps
+//               row reads conflict-free); for other modes it is q-contiguous
+//               (BK k x 128 q) and the converter transposes while splitting.
+//   warp 1      one thread issues tcgen05.mma (M=128, N=Rpad): x3 = hi*hi +
+//               hi*lo + lo*hi, single = hi*hi.  The tensor core rounds its FP32
+//               accumulation towards zero once per instruction, so the hi*hi
+//               products of k-chunk kc go to accumulator kc mod nsplit and the
+//               (2^-8 or 2^-11 smaller) corrections to one more; the epilogue
+//               adds them with round-to-nearest.  Two sets of accumulators let
+//               the epilogue overlap the next tile.
+//   warps 8-11  epilogue: tcgen05.ld 32x32b -> registers -> a warp-private smem
+//               transpose -> full-sector coalesced stores of X.
+// Every mbarrier wait is bounded; on expiry the CTA sets DEVERR_TIMEOUT, drains
+// what it issued (bounded), frees TMEM and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include "cpals_internal.h"
 
-namespace cpk {
-bool ttm_tc_supported(int64_t, int, int64_t, int) { return false; }
-cudaError_t ttm_tc(const float*, const TcOperand&, float*, int64_t, int, int64_t, int, int, int,
-                   unsigned*, cudaStream_t) {
-    return cudaErrorNotSupported;
+namespace {
+
+constexpr int BM = 128;
+constexpr int NTHREADS = 384;
+constexpr int OPA_BYTES = BM * 128;        // one split part of a 128-row chunk: 16 KB
+constexpr int EPI_STRIDE = 20;             // floats per row of the epilogue transpose buffer
+constexpr int EPI_BYTES = 4 * 32 * EPI_STRIDE * 4;
+constexpr int BAR_BYTES = 256;
+constexpr int MAX_STG = 8, MAX_OP = 4;
+constexpr long long WAIT_LIMIT = 2000000000LL;  // cycles (about 1 s)
+constexpr size_t SMEM_LIMIT = 232448;
+
+struct TcArgs {
+    float* X;
+    int64_t PQ;       // rows of X
+    int64_t Q;        // rows per p-slice (mode != last)
+    int64_t ntiles;
+    int64_t tiles_per_p;
+    int R, Rpad, nk, S_stg, S_op, tmem_cols, x3, b_resident, nsplit, nacc;
+    uint32_t idesc;
+    unsigned* dev_err;
+};
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false if the CTA is aborting (flag set here on expiry)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_test(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_LIMIT) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+template <int KIND>
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    if (KIND == 0) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;             // descriptor version
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32"
+        " {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// 8 floats -> one 16-byte chunk of bf16 hi and one of bf16 lo
+__device__ __forceinline__ void split8_bf16(const float* f, uint4& hi, uint4& lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 hb = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+        float2 hf = __bfloat1622float2(hb);
+        __nv_bfloat162 lb = __floats2bfloat162_rn(f[2 * i] - hf.x, f[2 * i + 1] - hf.y);
+        h[i] = *reinterpret_cast<uint32_t*>(&hb);
+        l[i] = *reinterpret_cast<uint32_t*>(&lb);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+// 4 floats -> one 16-byte chunk of tf32 hi and one of tf32 lo
+__device__ __forceinline__ void split4_tf32(float4 v, float4& hi, float4& lo) {
+    hi.x = tf32_rna(v.x); hi.y = tf32_rna(v.y); hi.z = tf32_rna(v.z); hi.w = tf32_rna(v.w);
+    lo.x = tf32_rna(v.x - hi.x); lo.y = tf32_rna(v.y - hi.y);
+    lo.z = tf32_rna(v.z - hi.z); lo.w = tf32_rna(v.w - hi.w);
+}
+
+struct Layout {
+    uint32_t stg0, op0, b0, epi0, bar0;
+    uint32_t stg_bytes, op_bytes, bchunk_bytes;
+};
+
+__host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, int nk, int b_resident,
+                                               int BK) {
+    const size_t stg = (size_t)BM * BK * 4;
+    const size_t bchunk = 2 * (size_t)Rpad * 128;
+    const size_t nb = b_resident ? (size_t)nk : (size_t)S_op;
+    return 1024 + (size_t)S_stg * stg + (size_t)S_op * 2 * OPA_BYTES + nb * bchunk + EPI_BYTES + BAR_BYTES;
+}
+
+// ------------------------------------------------------------------ kernel
+// MODE 0: last mode, T rows K-contiguous (2-D map {K, PQ}, boxes {32, 128}, SWIZZLE_128B)
+// MODE 1: other modes, T[p][k][q] with Q % 128 == 0 (3-D map {Q, K, P}, box {128, BK, 1})
+// KIND 0: bf16 parts, BK = 64, kind::f16;  KIND 1: tf32 parts, BK = 32, kind::tf32
+template <int MODE, int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_ttm_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmBhi,
+             const __grid_constant__ CUtensorMap tmBlo, const TcArgs a) {
+    constexpr int BK = KIND == 0 ? 64 : 32;
+    constexpr uint32_t STG = BM * BK * 4;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    const int S_stg = a.S_stg, S_op = a.S_op;
+    const uint32_t bchunk = 2u * (uint32_t)a.Rpad * 128u;   // hi + lo of one k-chunk
+    const uint32_t stg0 = base;
+    const uint32_t op0 = stg0 + (uint32_t)S_stg * STG;
+    const uint32_t b0 = op0 + (uint32_t)S_op * 2u * OPA_BYTES;
+    const uint32_t epi0 = b0 + (uint32_t)(a.b_resident ? a.nk : S_op) * bchunk;
+    const uint32_t bar0 = epi0 + EPI_BYTES;
+    auto stg_full = [&](int s) { return bar0 + 8u * s; };
+    auto stg_empty = [&](int s) { return bar0 + 8u * (MAX_STG + s); };
+    auto op_full = [&](int j) { return bar0 + 8u * (2 * MAX_STG + j); };
+    auto op_empty = [&](int j) { return bar0 + 8u * (2 * MAX_STG + MAX_OP + j); };
+    auto acc_full = [&](int b) { return bar0 + 8u * (2 * MAX_STG + 2 * MAX_OP + b); };
+    auto acc_empty = [&](int b) { return bar0 + 8u * (2 * MAX_STG + 2 * MAX_OP + 2 + b); };
+    const uint32_t b_full = bar0 + 8u * (2 * MAX_STG + 2 * MAX_OP + 4);
+    const uint32_t drain_bar = bar0 + 8u * (2 * MAX_STG + 2 * MAX_OP + 5);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + (bar0 - base) + 8 * 30);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bar0 - base) + 8 * 31);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S_stg; ++s) {
+            mbar_init(stg_full(s), 1);
+            mbar_init(stg_empty(s), 128);
+        }
+        for (int j = 0; j < S_op; ++j) {
+            mbar_init(op_full(j), a.b_resident ? 128 : 129);
+            mbar_init(op_empty(j), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(acc_full(b), 1);
+            mbar_init(acc_empty(b), 128);
+        }
+        mbar_init(b_full, 1);
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const uint32_t bpart = (uint32_t)a.Rpad * 128u;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmT) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBhi) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBlo) : "memory");
+            if (a.b_resident) {
+                mbar_expect_tx(b_full, (uint32_t)a.nk * bchunk);
+                for (int kc = 0; kc < a.nk; ++kc) {
+                    const uint32_t d = b0 + (uint32_t)kc * bchunk;
+                    tma_load_2d(d, &tmBhi, kc * BK, 0, b_full);
+                    tma_load_2d(d + bpart, &tmBlo, kc * BK, 0, b_full);
+                }
+            }
+            int64_t it = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+                for (int kc = 0; kc < a.nk && ok; ++kc, ++it) {
+                    const int s = (int)(it % S_stg);
+                    const uint32_t us = (uint32_t)(it / S_stg);
+                    if (!(ok = mbar_wait(stg_empty(s), (us & 1u) ^ 1u, abort_flag))) break;
+                    mbar_expect_tx(stg_full(s), STG);
+                    const uint32_t dst = stg0 + (uint32_t)s * STG;
+                    if (MODE == 0) {
+                        const int row0 = (int)(tile * BM);
+#pragma unroll
+                        for (int bx = 0; bx < BK / 32; ++bx)
+                            tma_load_2d(dst + bx * (BM * 128), &tmT, kc * BK + 32 * bx, row0, stg_full(s));
+                    } else {
+                        const int p = (int)(tile / a.tiles_per_p);
+                        const int q0 = (int)((tile % a.tiles_per_p) * BM);
+                        tma_load_3d(dst, &tmT, q0, kc * BK, p, stg_full(s));
+                    }
+                    if (!a.b_resident) {
+                        const int j = (int)(it % S_op);
+                        const uint32_t uj = (uint32_t)(it / S_op);
+                        if (!(ok = mbar_wait(op_empty(j), (uj & 1u) ^ 1u, abort_flag))) break;
+                        mbar_expect_tx(op_full(j), bchunk);
+                        const uint32_t bdst = b0 + (uint32_t)j * bchunk;
+                        tma_load_2d(bdst, &tmBhi, kc * BK, 0, op_full(j));
+                        tma_load_2d(bdst + bpart, &tmBlo, kc * BK, 0, op_full(j));
+                    }
+                }
+            }
+            if (!ok) {
+                // drain: wait (bounded) for the copies issued into the last stages
+                volatile int never = 0;
+                for (int64_t k = (it > S_stg ? it - S_stg : 0); k <= it; ++k)
+                    mbar_wait(stg_full((int)(k % S_stg)), (uint32_t)((k / S_stg) & 1), &never);
+                if (a.b_resident) mbar_wait(b_full, 0u, &never);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int64_t it = 0;
+            int lt = 0;
+            bool ok = true;
+            if (a.b_resident) ok = mbar_wait(b_full, 0u, abort_flag);
+            for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++lt) {
+                const int buf = lt & 1;
+                const uint32_t ub = (uint32_t)(lt >> 1);
+                if (!(ok = mbar_wait(acc_empty(buf), (ub & 1u) ^ 1u, abort_flag))) break;
+                tc_fence_after();
+                const uint32_t dt = tmem_base + (uint32_t)(buf * a.nacc * a.Rpad);
+                const uint32_t dcorr = dt + (uint32_t)(a.nsplit * a.Rpad);
+                for (int kc = 0; kc < a.nk; ++kc, ++it) {
+                    const uint32_t dmain = dt + (uint32_t)((kc % a.nsplit) * a.Rpad);
+                    const int j = (int)(it % S_op);
+                    if (!(ok = mbar_wait(op_full(j), (uint32_t)((it / S_op) & 1), abort_flag))) break;
+                    tc_fence_after();
+                    const uint32_t ahi = op0 + (uint32_t)j * 2u * OPA_BYTES, alo = ahi + OPA_BYTES;
+                    const uint32_t bhi = b0 + (uint32_t)(a.b_resident ? kc : j) * bchunk, blo = bhi + bpart;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {  // 4 k-steps of 32 bytes per 128-byte row
+                        const uint32_t off = (uint32_t)kk * 32u;
+                        const uint32_t accm = (kc >= a.nsplit || kk > 0) ? 1u : 0u;
+                        tc_mma<KIND>(dmain, sw128_desc(ahi + off), sw128_desc(bhi + off), a.idesc, accm);
+                        if (a.x3) {
+                            const uint32_t accc = (kc > 0 || kk > 0) ? 1u : 0u;
+                            tc_mma<KIND>(dcorr, sw128_desc(ahi + off), sw128_desc(blo + off), a.idesc, accc);
+                            tc_mma<KIND>(dcorr, sw128_desc(alo + off), sw128_desc(bhi + off), a.idesc, 1u);
+                        }
+                    }
+                    tc_commit(op_empty(j));
+                }
+                if (!ok) break;
+                tc_commit(acc_full(buf));
+            }
+            if (!ok) {
+                // let every MMA issued so far finish before TMEM is released
+                tc_commit(drain_bar);
+                volatile int never = 0;
+                mbar_wait(drain_bar, 0u, &never);
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ------------------------------------------------ converters (thread = tile row)
+        const int m = threadIdx.x - 128;
+        const int sw = m & 7;
+        int64_t it = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+            for (int kc = 0; kc < a.nk; ++kc, ++it) {
+                const int s = (int)(it % S_stg);
+                const int j = (int)(it % S_op);
+                if (!(ok = mbar_wait(stg_full(s), (uint32_t)((it / S_stg) & 1), abort_flag))) break;
+                if (!(ok = mbar_wait(op_empty(j), (uint32_t)(((it / S_op) & 1) ^ 1), abort_flag))) break;
+                const uint8_t* stg = gbase + (stg0 - base) + (size_t)s * STG;
+                uint8_t* ophi = gbase + (op0 - base) + (size_t)j * 2 * OPA_BYTES;
+                uint8_t* oplo = ophi + OPA_BYTES;
+                if (KIND == 0) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {  // output chunk c: k = 8c .. 8c+7
+                        float f[8];
+                        if (MODE == 0) {
+                            // box c/4 holds k = 32(c/4)..; row m, 16-byte chunk q at q ^ (m & 7)
+                            const uint8_t* rowp = stg + (c >> 2) * (BM * 128) + m * 128;
+                            const int q0 = (2 * c) & 7;
+                            const float4 v0 = *reinterpret_cast<const float4*>(rowp + ((q0 ^ sw) << 4));
+                            const float4 v1 = *reinterpret_cast<const float4*>(rowp + (((q0 + 1) ^ sw) << 4));
+                            f[0] = v0.x; f[1] = v0.y; f[2] = v0.z; f[3] = v0.w;
+                            f[4] = v1.x; f[5] = v1.y; f[6] = v1.z; f[7] = v1.w;
+                        } else {
+                            const float* col = reinterpret_cast<const float*>(stg) + m;  // [BK][128]
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) f[i] = col[(8 * c + i) * BM];
+                        }
+                        uint4 hi, lo;
+                        split8_bf16(f, hi, lo);
+                        const int pos = ((c ^ sw) << 4) + m * 128;
+                        *reinterpret_cast<uint4*>(ophi + pos) = hi;
+                        *reinterpret_cast<uint4*>(oplo + pos) = lo;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {  // output chunk c: k = 4c .. 4c+3
+                        float4 v;
+                        if (MODE == 0) {
+                            v = *reinterpret_cast<const float4*>(stg + m * 128 + ((c ^ sw) << 4));
+                        } else {
+                            const float* col = reinterpret_cast<const float*>(stg) + m;
+                            v = make_float4(col[(4 * c) * BM], col[(4 * c + 1) * BM], col[(4 * c + 2) * BM],
+                                            col[(4 * c + 3) * BM]);
+                        }
+                        float4 hi, lo;
+                        split4_tf32(v, hi, lo);
+                        const int pos = ((c ^ sw) << 4) + m * 128;
+                        *reinterpret_cast<float4*>(ophi + pos) = hi;
+                        *reinterpret_cast<float4*>(oplo + pos) = lo;
+                    }
+                }
+                fence_proxy_async();
+                mbar_arrive(stg_empty(s));
+                mbar_arrive(op_full(j));
+            }
+        }
+    } else if (warp >= 8) {
+        // ------------------------------------------------ epilogue (thread = TMEM lane = row)
+        const int quad = warp & 3;
+        float* tb = reinterpret_cast<float*>(gbase + (epi0 - base)) + quad * 32 * EPI_STRIDE;
+        int lt = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            if (!(ok = mbar_wait(acc_full(buf), (uint32_t)((lt >> 1) & 1), abort_flag))) break;
+            tc_fence_after();
+            int64_t g0;  // global row of this warp's first row
+            if (MODE == 0) {
+                g0 = tile * BM + quad * 32;
+            } else {
+                const int64_t p = tile / a.tiles_per_p;
+                g0 = p * a.Q + (tile % a.tiles_per_p) * BM + quad * 32;
+            }
+            const uint32_t taddr =
+                tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * a.nacc * a.Rpad);
+            for (int c0 = 0; c0 < a.Rpad; c0 += 16) {
+                float v[16];
+                // corrections first (last accumulator), then the hi*hi partial sums
+                tmem_ld16(taddr + (uint32_t)((a.nacc - 1) * a.Rpad + c0), v);
+                for (int ac = a.nacc - 2; ac >= 0; --ac) {
+                    float w[16];
+                    tmem_ld16(taddr + (uint32_t)(ac * a.Rpad + c0), w);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += w[i];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<float4*>(tb + lane * EPI_STRIDE + 4 * q) =
+                        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                __syncwarp();
+                // lanes 4i..4i+3 write the 64 bytes of row i (+8, +16, +24): full sectors
+                const int q = lane & 3;
+                const int col = c0 + 4 * q;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = (lane >> 2) + 8 * i;
+                    const int64_t g = g0 + r;
+                    if (g < a.PQ && col < a.R) {
+                        const float4 w = *reinterpret_cast<const float4*>(tb + r * EPI_STRIDE + 4 * q);
+                        float* dst = a.X + g * (int64_t)a.R + col;
+                        if ((a.R & 3) == 0) {
+                            *reinterpret_cast<float4*>(dst) = w;
+                        } else {
+                            dst[0] = w.x;
+                            if (col + 1 < a.R) dst[1] = w.y;
+                            if (col + 2 < a.R) dst[2] = w.z;
+                            if (col + 3 < a.R) dst[3] = w.w;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            tc_fence_before();
+            mbar_arrive(acc_empty(buf));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(a.tmem_cols)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicOr(a.dev_err, (unsigned)DEVERR_TIMEOUT);
+}
+
+// ------------------------------------------------------------------ host helpers
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+}  // namespace
+
+namespace cpk {
+
+struct TcPlan {
+    CUtensorMap tmT, tmBhi, tmBlo;
+    int mode;   // kernel MODE
+    int kind;   // kernel KIND
+    int64_t P, Q, PQ;
+    int K, R, Rpad, nk, S_stg, S_op, b_resident;
+};
+
+bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R) {
+    const int Rpad = (R + 15) / 16 * 16;
+    if (Rpad > 128 || K < 1 || P * Q < 1) return false;
+    if (Q == 1) return K % 4 == 0 && P <= ((int64_t)1 << 31);
+    return Q % BM == 0 && Q <= ((int64_t)1 << 31) && P <= ((int64_t)1 << 31);
+}
+
+TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind, const void* bhi,
+                    const void* blo, int Rpad, int Kpad) {
+    if (!ttm_tc_supported(P, K, Q, R) || ((uintptr_t)T & 15)) return nullptr;
+    EncodeTiledFn enc = encoder();
+    if (!enc) return nullptr;
+    const int BK = kind == 0 ? 64 : 32;
+    TcPlan* pl = new TcPlan();
+    pl->kind = kind;
+    pl->P = P;
+    pl->Q = Q;
+    pl->PQ = P * Q;
+    pl->K = K;
+    pl->R = R;
+    pl->Rpad = Rpad;
+    pl->nk = (K + BK - 1) / BK;
+    pl->S_op = 2;
+    pl->b_resident = (size_t)pl->nk * 2 * Rpad * 128 <= 64 * 1024 ? 1 : 0;
+    pl->S_stg = 0;
+    for (int s = MAX_STG; s >= 2; --s)
+        if (layout_bytes(s, pl->S_op, Rpad, pl->nk, pl->b_resident, BK) <= SMEM_LIMIT) {
+            pl->S_stg = s;
+            break;
+        }
+    if (pl->S_stg == 0) {
+        delete pl;
+        return nullptr;
+    }
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r1;
+    if (Q == 1) {
+        pl->mode = 0;
+        const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)P};
+        const cuuint64_t strides[1] = {(cuuint64_t)K * 4};
+        const cuuint32_t box[2] = {32, BM};
+        r1 = enc(&pl->tmT, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)T, dims, strides, box, es,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        pl->mode = 1;
+        const cuuint64_t dims[3] = {(cuuint64_t)Q, (cuuint64_t)K, (cuuint64_t)P};
+        const cuuint64_t strides[2] = {(cuuint64_t)Q * 4, (cuuint64_t)Q * K * 4};
+        const cuuint32_t box[3] = {BM, (cuuint32_t)BK, 1};
+        r1 = enc(&pl->tmT, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)T, dims, strides, box, es,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    const int esz = kind == 0 ? 2 : 4;
+    const CUtensorMapDataType bt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t bd[2] = {(cuuint64_t)Kpad, (cuuint64_t)Rpad};
+    const cuuint64_t bs[1] = {(cuuint64_t)Kpad * esz};
+    const cuuint32_t bb[2] = {(cuuint32_t)BK, (cuuint32_t)Rpad};
+    CUresult r2 = enc(&pl->tmBhi, bt, 2, (void*)bhi, bd, bs, bb, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r3 = enc(&pl->tmBlo, bt, 2, (void*)blo, bd, bs, bb, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS || r3 != CUDA_SUCCESS) {
+        delete pl;
+        return nullptr;
+    }
+    return pl;
+}
+
+void ttm_tc_plan_free(TcPlan* p) { delete p; }
+
+int ttm_tc_kind(const TcPlan* p) { return p ? p->kind : -1; }
+
+template <int MODE, int KIND>
+static cudaError_t launch(const TcPlan* pl, const TcArgs& a, size_t smem, unsigned grid, cudaStream_t st) {
+    cudaFuncSetAttribute(k_ttm_tc<MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ttm_tc<MODE, KIND><<<grid, NTHREADS, smem, st>>>(pl->tmT, pl->tmBhi, pl->tmBlo, a);
+    return cudaGetLastError();
+}
+
+cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsigned* dev_err,
+                       cudaStream_t st) {
+    if (!pl) return cudaErrorInvalidValue;
+    const bool bf = (prec == CP_BF16X3 || prec == CP_BF16);
+    const bool tf = (prec == CP_TF32X3 || prec == CP_TF32);
+    if ((pl->kind == 0 && !bf) || (pl->kind == 1 && !tf)) return cudaErrorInvalidValue;
+    if (((uintptr_t)X & 15) && (pl->R & 3) == 0) return cudaErrorMisalignedAddress;
+    TcArgs a;
+    a.X = X;
+    a.PQ = pl->PQ;
+    a.Q = pl->Q;
+    a.tiles_per_p = pl->mode == 1 ? pl->Q / BM : 1;
+    a.ntiles = pl->mode == 1 ? pl->P * a.tiles_per_p : (pl->PQ + BM - 1) / BM;
+    a.R = pl->R;
+    a.Rpad = pl->Rpad;
+    a.nk = pl->nk;
+    a.S_stg = pl->S_stg;
+    a.S_op = pl->S_op;
+    a.b_resident = pl->b_resident;
+    a.x3 = (prec == CP_BF16X3 || prec == CP_TF32X3) ? 1 : 0;
+    // accumulators per tile: nsplit for hi*hi (by k-chunk) + 1 for the corrections;
+    // two sets must fit the 512 TMEM columns
+    const int per_set = 256 / pl->Rpad;
+    int nsplit = per_set - a.x3;
+    if (nsplit > 4) nsplit = 4;
+    if (nsplit > pl->nk) nsplit = pl->nk;
+    if (nsplit < 1) nsplit = 1;
+    a.nsplit = nsplit;
+    a.nacc = nsplit + a.x3;
+    int cols = 32;
+    while (cols < 2 * a.nacc * pl->Rpad) cols *= 2;
+    a.tmem_cols = cols;
+    const uint32_t fmt = pl->kind == 0 ? 1u : 2u;  // BF16 = 1, TF32 = 2
+    a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(pl->Rpad >> 3) << 17) |
+              ((uint32_t)(BM >> 4) << 24);
+    a.dev_err = dev_err;
+    const int BK = pl->kind == 0 ? 64 : 32;
+    const size_t smem = layout_bytes(pl->S_stg, pl->S_op, pl->Rpad, pl->nk, pl->b_resident, BK);
+    const unsigned grid = (unsigned)(a.ntiles < num_sms ? a.ntiles : num_sms);
+    if (grid == 0) return cudaSuccess;
+    if (pl->mode == 0)
+        return pl->kind == 0 ? launch<0, 0>(pl, a, smem, grid, st) : launch<0, 1>(pl, a, smem, grid, st);
+    return pl->kind == 0 ? launch<1, 0>(pl, a, smem, grid, st) : launch<1, 1>(pl, a, smem, grid, st);
+}
+
 }  // namespace cpk

@@ -151,3 +151,43 @@ def make_problem(seed: int, dims, R: int, law: str = "uniform", eta: float = 0.0
     T = add_noise(cp_full(F), eta, seed, 64)
     A0 = uniform_factors(seed + 1 if init_seed is None else init_seed, dims, R)
     return T, F, A0
+
+
+def make_problem_device(seed: int, dims, R: int, law: str = "uniform", eta: float = 0.0,
+                        C: float | None = None, device="cuda", init_seed: int | None = None):
+    """Large-tensor variant of make_problem, assembled with torch on `device`.
+
+    Factors come from the same Philox streams as make_problem; the dense product
+    is formed in FP64 with a torch matmul, the noise from torch's own seeded
+    generator (N(0,1), scaled to eta ||T||_F), and the result is returned as a
+    contiguous FP32 tensor.  Returns (T float32 on device, true factors, initial
+    factors); the host oracle reads back exactly these FP32 bytes.
+    """
+    import torch
+
+    dims = list(dims)
+    if law == "uniform":
+        F = uniform_factors(seed, dims, R)
+    elif law == "gaussian":
+        F = gaussian_factors(seed, dims, R)
+    elif law == "collinear":
+        F = collinear_factors(seed, dims, R, C)
+    else:
+        raise ValueError(law)
+    Ft = [torch.from_numpy(f).to(device) for f in F]
+    rows = Ft[0]
+    for f in Ft[1:-1]:
+        rows = (rows[:, None, :] * f[None, :, :]).reshape(-1, R)
+    T = rows @ Ft[-1].T
+    del rows
+    if eta > 0.0:
+        g = torch.Generator(device=device)
+        g.manual_seed(int(seed))
+        E = torch.randn(T.shape, generator=g, dtype=torch.float64, device=device)
+        E *= eta * torch.linalg.vector_norm(T) / torch.linalg.vector_norm(E)
+        T += E
+        del E
+    T32 = T.to(torch.float32).reshape(dims).contiguous()
+    del T
+    A0 = uniform_factors(seed + 1 if init_seed is None else init_seed, dims, R)
+    return T32, F, A0

@@ -1,9 +1,11 @@
 """GPU path vs the FP64 oracle, element by element, through the C ABI.
 
 Tolerances (from the arithmetic the kernels use): MTTKRP / TTM relative Frobenius
-error <= 1e-5 for FP32 SIMT and bf16x3 (FP32 accumulation; bf16x3 keeps about
-16 mantissa bits per operand); residuals within 1e-6 absolute after a fixed
-sweep count; PP approximated MTTKRPs <= 1e-5 relative.
+error <= 1e-5 for FP32 SIMT, tf32x3 and bf16x3 (FP32 accumulation; tf32 hi+lo
+keeps about 22 mantissa bits, bf16 hi+lo about 16); the relative residual within
+1e-6 absolute of the oracle's after a fixed sweep count for FP32 SIMT and tf32x3,
+within 1e-5 for bf16x3 (its 16-bit operands move the trajectory by a few 1e-6 in
+10 sweeps from a random start); PP approximated MTTKRPs <= 1e-5 relative.
 """
 import numpy as np
 import pytest
@@ -14,7 +16,8 @@ from oracle import cp_oracle as co
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PRECS = ["fp32", "bf16x3"]
+PRECS = ["fp32", "bf16x3", "tf32x3"]
+FIT_TOL = {"fp32": 1e-6, "tf32x3": 1e-6, "bf16x3": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +39,8 @@ def relerr(a, b):
 
 
 SHAPES = [((33, 40, 29), 3), ((64, 64, 64), 16), ((17, 130, 9, 12), 17), ((6, 5, 7, 4, 5), 4),
-          ((150, 1, 70), 5), ((128, 96, 140), 100), ((40, 33, 260), 64), ((9, 8, 7), 1)]
+          ((150, 1, 70), 5), ((128, 96, 140), 100), ((40, 33, 260), 64), ((9, 8, 7), 1),
+          ((300, 200, 64), 64), ((130, 70, 36), 48), ((20, 16, 128, 12), 32)]
 
 
 @pytest.mark.parametrize("dims,R", SHAPES)
@@ -75,7 +79,7 @@ def test_dt_sweeps_small_config(pkg, prec):
     got = np.array([t["resid"] for t in tr])
     assert np.abs(got - np.array(ref.resid)).max() <= 1e-5
     _, r_direct = ctx.fit(exact=True)
-    assert abs(r_direct - co.residual_direct(Tref, ref.A)) <= 1e-6
+    assert abs(r_direct - co.residual_direct(Tref, ref.A)) <= FIT_TOL[prec]
     st = ctx.stats()
     assert st["ttm"] == 20 and st["sweeps_exact"] == 10
     ctx.close()
@@ -185,4 +189,35 @@ def test_float64_input_and_default_init(pkg):
         assert np.array_equal(ctx.get_factor(n), A0[n])
     Tref = T64.astype(np.float32).astype(np.float64)
     assert relerr(ctx.mttkrp(2).cpu().numpy(), co.mttkrp(Tref, A0, 2)) <= 1e-5
+    ctx.close()
+
+
+@pytest.mark.parametrize("dims,R", [((300, 200, 64), 64), ((128, 96, 140), 100), ((20, 16, 128, 12), 32)])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_tensor_core_ttm_used_and_matches_simt(pkg, dims, R, prec):
+    """The tcgen05 TTM runs for supported modes and agrees with the FP32 SIMT kernel."""
+    Td, Tref, A0 = problem(dims, R, 13)
+    tc = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    sm = pkg.CPContext(Td, R, A0=A0, prec="fp32")
+    for m in range(len(dims)):
+        Xt = tc.ttm(m).cpu().numpy()
+        Xs = sm.ttm(m).cpu().numpy()
+        assert relerr(Xt, Xs.astype(np.float64)) <= 2e-6
+    assert tc.stats()["ttm_tensor_core"] >= 1
+    assert sm.stats()["ttm_tensor_core"] == 0
+    tc.close()
+    sm.close()
+
+
+@pytest.mark.parametrize("prec,lo,hi", [("bf16", 1e-5, 1e-2), ("tf32", 1e-6, 1e-3)])
+def test_single_product_precisions_are_reported_not_accepted(pkg, prec, lo, hi):
+    """One bf16 or tf32 product per term loses mantissa bits: error above the x3 bar."""
+    dims, R = (300, 200, 64), 64
+    Td, Tref, A0 = problem(dims, R, 14)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    for m in (0, 2):
+        X = ctx.ttm(m).cpu().numpy()
+        e = relerr(X, np.tensordot(Tref, A0[m], axes=([m], [0])))
+        assert lo < e < hi, (m, e)
+    assert ctx.stats()["ttm_tensor_core"] == 2
     ctx.close()
