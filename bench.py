@@ -352,6 +352,7 @@ def main():
         "dt_sweeps_per_s": dt_sps * world,
         "msdt_time_over_dt": (ms / args.steps) / (ms_dt / args.steps),
         "fit": {"formula": fit_formula, "direct": fit_direct, "after_sweeps": args.warmup + args.steps},
+        "solves_fp64": int(st1["solves_fp64"]),
         "pp": pp_info,
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -193,6 +193,10 @@ typedef struct {
     double ttm_bytes;       /* algorithmic HBM bytes of the TTMs (read+write) */
     double mttv_bytes;      /* algorithmic bytes of the mTTVs                 */
     int64_t ttm_tensor_core;/* first-level TTMs that ran on tcgen05           */
+    int64_t ttm_fused;      /* of those, two-level contractions T x_{a,a+1} with
+                               the Khatri-Rao operand (standard tree)         */
+    int64_t solves_fp64;    /* updates whose normal equations needed the FP64
+                               factorisation (ill-conditioned Gamma)          */
 } cp_stats;
 cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
 

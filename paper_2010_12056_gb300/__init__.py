@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("ttm_flops", ctypes.c_double),
                 ("mttv_flops", ctypes.c_double), ("pp_flops", ctypes.c_double),
                 ("ttm_bytes", ctypes.c_double), ("mttv_bytes", ctypes.c_double),
-                ("ttm_tensor_core", ctypes.c_int64)]
+                ("ttm_tensor_core", ctypes.c_int64), ("ttm_fused", ctypes.c_int64),
+                ("solves_fp64", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -69,6 +70,8 @@ struct cp_ctx {
     double** d_dSlist = nullptr;
 
     double *Gamma = nullptr, *L = nullptr, *invd = nullptr, *W = nullptr;
+    float* Ginv = nullptr;      // FP32 Gamma^{-1} for iterative refinement
+    int* d_mode = nullptr;      // 0: refinement path, 1: FP64 substitution path
     double* gram_part = nullptr;
     int nchunk = 1;
     double* scal_part = nullptr;
@@ -81,6 +84,13 @@ struct cp_ctx {
 
     Slot slot[CP_MAXN + 1];
     cpk::TcPlan* tc_plan[CP_MAXN] = {0};   // tensor-core TTM per mode (NULL: SIMT)
+    // fused two-mode contraction T x_{a,a+1} KR(A_a, A_{a+1}) per adjacent pair a
+    cpk::TcPlan* kr_plan[CP_MAXN] = {0};
+    int kr_Kpad[CP_MAXN] = {0};
+    void* kr_hi = nullptr;
+    void* kr_lo = nullptr;
+    float* splitk_ws = nullptr;
+    bool fuse_dt = true;
 
     // PP state
     bool pp_alloc = false, pp_valid = false;
@@ -192,7 +202,7 @@ cp_status launch_ttm(cp_ctx* c, int mode, float* X) {
     const int K = (int)c->dims[mode];
     const int prec = c->cfg.prec;
     if (prec != CP_FP32_SIMT && c->tc_plan[mode]) {
-        LAUNCH(c, cpk::ttm_tc_run(c->tc_plan[mode], X, prec, c->num_sms, c->dev_err, c->st));
+        LAUNCH(c, cpk::ttm_tc_run(c->tc_plan[mode], X, prec, c->num_sms, c->dev_err, c->st, c->splitk_ws));
         c->stats.ttm_tensor_core++;
     } else {
         LAUNCH(c, cpk::ttm_simt(c->T, c->A32[mode], X, P, K, Q, c->R, c->st));
@@ -216,8 +226,27 @@ cp_status launch_mttv(cp_ctx* c, const float* X, uint32_t contracted, int mode, 
     return CP_OK;
 }
 
+// Level-2 node straight from T: contract the adjacent modes a, a+1 at once with
+// their Khatri-Rao product (two dimension-tree levels in one pass over T).
+cp_status launch_fused2(cp_ctx* c, int a, float* X) {
+    const bool bf = (c->cfg.prec == CP_BF16X3 || c->cfg.prec == CP_BF16);
+    const int R = c->R, sa = (int)c->dims[a], sb = (int)c->dims[a + 1];
+    LAUNCH(c, cpk::kr_operand(c->A64[a], c->A64[a + 1], sa, sb, R, c->kr_Kpad[a], bf ? 0 : 1, c->kr_hi,
+                              c->kr_lo, c->st));
+    LAUNCH(c, cpk::ttm_tc_run(c->kr_plan[a], X, c->cfg.prec, c->num_sms, c->dev_err, c->st, c->splitk_ws));
+    const double rows = (double)c->numel / ((double)sa * sb);
+    c->stats.ttm++;
+    c->stats.ttm_tensor_core++;
+    c->stats.ttm_fused++;
+    c->stats.ttm_flops += 2.0 * (double)c->numel * R;
+    c->stats.ttm_bytes += 4.0 * ((double)c->numel + rows * R);
+    return CP_OK;
+}
+
 // Ensure the node reached by contracting path[0..d-1] is in its slot; returns it.
-cp_status ensure_node(cp_ctx* c, const int* path, int d, float** out) {
+// fuse2: the level-1 node of this path has no other use, so the level-2 node may
+// be computed from T directly when its two modes are adjacent.
+cp_status ensure_node(cp_ctx* c, const int* path, int d, float** out, bool fuse2 = false) {
     uint32_t mask = 0;
     for (int i = 0; i < d; ++i) mask |= 1u << path[i];
     Slot& s = c->slot[c->N - d];
@@ -229,11 +258,14 @@ cp_status ensure_node(cp_ctx* c, const int* path, int d, float** out) {
         return CP_OK;
     }
     s.valid = false;
+    const int lo_m = d >= 2 ? std::min(path[0], path[1]) : -1;
     if (d == 1) {
         CKST(launch_ttm(c, path[0], s.buf));
+    } else if (d == 2 && fuse2 && c->fuse_dt && std::abs(path[0] - path[1]) == 1 && c->kr_plan[lo_m]) {
+        CKST(launch_fused2(c, lo_m, s.buf));
     } else {
         float* parent = nullptr;
-        CKST(ensure_node(c, path, d - 1, &parent));
+        CKST(ensure_node(c, path, d - 1, &parent, fuse2));
         CKST(launch_mttv(c, parent, mask & ~(1u << path[d - 1]), path[d - 1], s.buf));
     }
     s.valid = true;
@@ -260,10 +292,18 @@ void tree_path(std::vector<int> leaves, int u, std::vector<int>& seq) {
     }
 }
 
-std::vector<int> dt_path(int N, int u) {
+// Standard tree (Fig. 1a).  *fuse2 is set when the first two contractions from T
+// belong to one chain (the first half's other modes), i.e. the level-1 node
+// serves a single child.
+std::vector<int> dt_path(int N, int u, bool* fuse2 = nullptr) {
     std::vector<int> leaves(N), seq;
     for (int i = 0; i < N; ++i) leaves[i] = i;
     tree_path(leaves, u, seq);
+    if (fuse2) {
+        const int h = (N + 1) / 2;
+        const bool left = u < h;
+        *fuse2 = (left ? N - h : h) >= 2;
+    }
     return seq;
 }
 
@@ -281,8 +321,8 @@ std::vector<int> msdt_path(int N, int64_t t, int* u_out) {
     return seq;
 }
 
-cp_status mttkrp_leaf(cp_ctx* c, const std::vector<int>& path, float** M) {
-    return ensure_node(c, path.data(), (int)path.size(), M);
+cp_status mttkrp_leaf(cp_ctx* c, const std::vector<int>& path, float** M, bool fuse2 = false) {
+    return ensure_node(c, path.data(), (int)path.size(), M, fuse2);
 }
 
 double* scal_slot(cp_ctx* c, int k, int mode) {
@@ -302,8 +342,8 @@ cp_status grow_hist(cp_ctx* c, int nsweeps) {
 // One factor update (Alg. 1 lines 6-9; in PP mode Alg. 2 lines 10-12 with V).
 cp_status update_mode(cp_ctx* c, int u, const float* M, bool pp, double* scal) {
     const int R = c->R, s = (int)c->dims[u];
-    LAUNCH(c, cpk::gamma_chol(c->d_Slist, c->d_dSlist, c->N, u, R, pp ? 1 : 0, c->Gamma, c->L,
-                              c->invd, c->W, scal, c->st));
+    LAUNCH(c, cpk::chol_mixed(c->d_Slist, c->d_dSlist, c->N, u, R, pp ? 1 : 0, c->Gamma, c->Ginv, c->L,
+                              c->invd, c->W, scal, c->d_mode, c->st));
     cpk::SolveOut o;
     o.A64 = c->A64[u];
     o.A32 = c->A32[u];
@@ -316,7 +356,8 @@ cp_status update_mode(cp_ctx* c, int u, const float* M, bool pp, double* scal) {
     o.dA32 = pp ? c->dA32[u] : nullptr;
     o.dA64 = pp ? c->dA64[u] : nullptr;
     int nblk = 0;
-    LAUNCH(c, cpk::solve_rows(M, pp ? c->W : nullptr, c->L, c->invd, o, s, R, c->scal_part, &nblk, c->st));
+    LAUNCH(c, cpk::solve_mixed(M, pp ? c->W : nullptr, c->Gamma, c->Ginv, c->L, c->invd, c->d_mode, o, s, R, scal,
+                               c->scal_part, &nblk, c->dev_err, c->st));
     const int nchunk = std::max(1, std::min(c->nchunk, (s + 15) / 16));
     LAUNCH(c, cpk::gram_partials(c->A64[u], pp ? c->dA64[u] : nullptr, s, R, c->gram_part, nchunk, c->st));
     LAUNCH(c, cpk::finalize_update(c->gram_part, nchunk, c->scal_part, nblk, c->Gamma, R, pp ? 1 : 0,
@@ -355,7 +396,11 @@ cp_status harvest(cp_ctx* c, int k, const int* kinds, const int* inits, int firs
             const double* sc = &h[((size_t)i * c->N + n) * CP_NSCAL];
             const double a = sqrt(sc[SCAL_A2]);
             if (!isfinite(sc[SCAL_A2]) || !isfinite(sc[SCAL_MA])) bad = true;
-            if (sc[SCAL_FLAGS] >= 2.0) {
+            // flags: 0 refinement path, 3 refinement did not converge; 10 + (0 ok,
+            // 1 shifted, 2 failed) for the FP64 factorisation path
+            const double fl = sc[SCAL_FLAGS];
+            if (fl >= 10.0) c->stats.solves_fp64++;
+            if (fl == 3.0 || fl >= 12.0) {
                 c->sweeps_done += i;
                 return fail(c, CP_ENOTSPD, "Gamma(" + std::to_string(n) + ") not positive definite");
             }
@@ -403,14 +448,15 @@ cp_status exact_sweep(cp_ctx* c, bool msdt, int k) {
     for (int u0 = 0; u0 < c->N; ++u0) {
         int u = u0;
         std::vector<int> path;
+        bool fuse2 = false;
         if (msdt) {
             path = msdt_path(c->N, c->t_msdt, &u);
             c->t_msdt++;
         } else {
-            path = dt_path(c->N, u0);
+            path = dt_path(c->N, u0, &fuse2);
         }
         float* M = nullptr;
-        CKST(mttkrp_leaf(c, path, &M));
+        CKST(mttkrp_leaf(c, path, &M, fuse2));
         CKST(update_mode(c, u, M, false, scal_slot(c, k, u)));
     }
     c->stats.sweeps_exact++;
@@ -588,7 +634,11 @@ void free_all(cp_ctx* c) {
     for (int i = 0; i < CP_MAXN; ++i) {
         cpk::ttm_tc_plan_free(c->tc_plan[i]);
         c->tc_plan[i] = nullptr;
+        cpk::ttm_tc_plan_free(c->kr_plan[i]);
+        c->kr_plan[i] = nullptr;
     }
+    F(c->kr_hi); F(c->kr_lo); F(c->splitk_ws);
+    F(c->Ginv); F(c->d_mode);
     F(c->Mt); F(c->d_Slist); F(c->d_dSlist); F(c->Gamma); F(c->L); F(c->invd); F(c->W);
     F(c->gram_part); F(c->scal_part); F(c->scal_hist); F(c->red_part); F(c->d_red_out); F(c->dev_err);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -697,13 +747,15 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
     TRY(dalloc(c, &c->d_dSlist, N));
     TRYC(cudaMemcpyAsync(c->d_Slist, c->S, sizeof(double*) * N, cudaMemcpyHostToDevice, c->st));
     TRYC(cudaMemcpyAsync(c->d_dSlist, c->dS, sizeof(double*) * N, cudaMemcpyHostToDevice, c->st));
-    TRY(dalloc(c, &c->Gamma, RR));
+    TRY(dalloc(c, &c->Gamma, RR + 2));
+    TRY(dalloc(c, &c->Ginv, RR + 4));
+    TRY(dalloc(c, &c->d_mode, 1));
     TRY(dalloc(c, &c->W, RR));
     TRY(dalloc(c, &c->L, 2 * (size_t)RR));
     TRY(dalloc(c, &c->invd, R));
     c->nchunk = 16;
     TRY(dalloc(c, &c->gram_part, (size_t)c->nchunk * 2 * RR));
-    TRY(dalloc(c, &c->scal_part, (size_t)((c->smax + 3) / 4) * CP_NSCAL));
+    TRY(dalloc(c, &c->scal_part, (size_t)c->smax * CP_NSCAL));
     TRY(dalloc(c, &c->red_part, 4096));
     TRY(dalloc(c, &c->d_red_out, 16));
     TRY(dalloc(c, &c->dev_err, 1));
@@ -738,6 +790,36 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
             c->tc_plan[m] = cpk::ttm_tc_plan(c->T, P, (int)dims[m], Q, R, bf ? 0 : 1, hi, lo, c->Rpad,
                                              c->Kpad[m]);
         }
+        // fused two-mode contractions of adjacent pairs (standard tree, N >= 3)
+        size_t kr_elems = 0;
+        for (int a = 0; a + 1 < N; ++a) {
+            const int64_t K = dims[a] * dims[a + 1];
+            if (K > (1 << 30)) continue;
+            c->kr_Kpad[a] = (int)((K + 63) / 64 * 64);
+            kr_elems = std::max(kr_elems, (size_t)c->Rpad * c->kr_Kpad[a]);
+        }
+        const size_t esz = bf ? 2 : 4;
+        if (kr_elems) {
+            TRY(dalloc(c, (uint8_t**)&c->kr_hi, kr_elems * esz));
+            TRY(dalloc(c, (uint8_t**)&c->kr_lo, kr_elems * esz));
+            for (int a = 0; a + 1 < N; ++a) {
+                if (!c->kr_Kpad[a]) continue;
+                int64_t P = 1, Q = 1;
+                for (int k = 0; k < a; ++k) P *= dims[k];
+                for (int k = a + 2; k < N; ++k) Q *= dims[k];
+                c->kr_plan[a] = cpk::ttm_tc_plan(c->T, P, (int)(dims[a] * dims[a + 1]), Q, R, bf ? 0 : 1,
+                                                 c->kr_hi, c->kr_lo, c->Rpad, c->kr_Kpad[a]);
+            }
+        }
+        // split-K workspace for contractions with few row tiles
+        size_t ws = 0;
+        auto need = [&](const cpk::TcPlan* p) {
+            const int nsk = p ? cpk::ttm_tc_splitk(p, c->num_sms) : 1;
+            if (nsk > 1) ws = std::max(ws, (size_t)nsk * (size_t)cpk::ttm_tc_rows(p) * R);
+        };
+        for (int m = 0; m < N; ++m) need(c->tc_plan[m]);
+        for (int a = 0; a + 1 < N; ++a) need(c->kr_plan[a]);
+        if (ws) TRY(dalloc(c, &c->splitk_ws, ws));
     }
     // ||T||_F^2
     int nb = cpk::norm2_partials(c->T, numel, c->red_part, 4096, c->st);
@@ -764,7 +846,9 @@ cp_status cp_mttkrp(cp_ctx* c, int mode, float* M_dev) {
     CKST(entry_check(c));
     if (mode < 0 || mode >= c->N || !M_dev) return CP_EINVAL;
     float* M = nullptr;
-    CKST(mttkrp_leaf(c, dt_path(c->N, mode), &M));
+    bool fuse2 = false;
+    std::vector<int> path = dt_path(c->N, mode, &fuse2);
+    CKST(mttkrp_leaf(c, path, &M, fuse2));
     CKCUDA(c, cudaMemcpyAsync(M_dev, M, sizeof(float) * c->dims[mode] * c->R, cudaMemcpyDeviceToDevice, c->st));
     return CP_OK;
 }

@@ -50,8 +50,18 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
                     const void* blo, int Rpad, int Kpad);
 int ttm_tc_kind(const TcPlan* p);
 void ttm_tc_plan_free(TcPlan* p);
+// splitk_ws: NULL, or a workspace of ttm_tc_splitk() * rows * R floats that lets
+// the kernel split K across CTAs when the row tiles alone cannot fill the GPU
+// (partial sums are then added in a fixed order by a second kernel).
 cudaError_t ttm_tc_run(const TcPlan* p, float* X, int prec, int num_sms, unsigned* dev_err,
-                       cudaStream_t st);
+                       cudaStream_t st, float* splitk_ws);
+int ttm_tc_splitk(const TcPlan* p, int num_sms);
+int64_t ttm_tc_rows(const TcPlan* p);
+// Khatri-Rao operand of two adjacent modes a, a+1 for a fused two-mode contraction:
+// row k = i_a * s_b + i_b holds A_a[i_a][r] * A_b[i_b][r]; written transposed
+// ([Rpad][Kpad], k contiguous) as bf16 hi/lo (kind 0) or tf32 hi/lo (kind 1).
+cudaError_t kr_operand(const double* Aa, const double* Ab, int sa, int sb, int R, int Kpad,
+                       int kind, void* hi, void* lo, cudaStream_t st);
 
 // multi-TTV: Y[p][q][r] = sum_k X[p][k][q][r] * A[k][r]
 cudaError_t mttv(const float* X, const float* A, float* Y, int64_t P, int K, int64_t Q, int R,
@@ -96,6 +106,19 @@ struct SolveOut {
 cudaError_t solve_rows(const float* M, const double* W, const double* L, const double* invdiag,
                        const SolveOut& o, int s, int R, double* scal_part, int* nblk,
                        cudaStream_t st);
+
+// Mixed-precision normal-equation solve (k_solve_mixed.cu): chol_mixed forms
+// Gamma (FP64, written to Gamma), PP's W, and either Ginv = Gamma^{-1} in FP32
+// (*mode = 0) or the FP64 factor L64 ([L | L^T], 2 R^2) and invd64 (*mode = 1);
+// solve_mixed then solves every row to FP64 accuracy (refinement or FP64
+// substitution).  Gamma and Ginv must have 16 spare bytes after R*R entries.
+cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
+                       double* Gamma, float* Ginv, double* L64, double* invd64, double* W,
+                       double* scal, int* mode, cudaStream_t st);
+cudaError_t solve_mixed(const float* M, const double* W, const double* Gamma, const float* Ginv,
+                        const double* L64, const double* invd64, const int* mode, const SolveOut& o,
+                        int s, int R, double* scal, double* scal_part, int* nblk, unsigned* dev_err,
+                        cudaStream_t st);
 
 // Gram partials of A (and A^T dA) over row chunks; finalize reduces them.
 cudaError_t gram_partials(const double* A, const double* dA, int s, int R, double* part,

@@ -58,15 +58,19 @@ __device__ __forceinline__ void bf16_split(float x, uint16_t& hi, uint16_t& lo) 
 }
 
 // ------------------------------------------------------------------ Gamma + Cholesky
-// One CTA.  work = Gamma (smem when R <= 128, else the Lt half of the output
-// buffer, which is rewritten at the end).  Right-looking factorisation in the
-// LDL^T form, one barrier per column: at step j every thread reads the pivot
-// d_j = work[j][j] and updates work[i][k] -= work[i][j] work[k][j] / d_j for
-// j < k <= i; finally L[i][k] = work[i][k] / sqrt(d_k), L[k][k] = sqrt(d_k).
-// If a pivot is not positive the factorisation restarts once on
-// Gamma + 1e-12 * trace(Gamma)/R * I (flag 1); a second failure sets flag 2 and
-// leaves L = I so that later kernels stay finite.  scal[SCAL_FLAGS] gets the
-// flag and scal[SCAL_GS] is cleared for the Gram kernel's accumulation.
+// One CTA.  work = Gamma with row stride ld (smem, ld = R + 1 so column reads
+// hit distinct banks, when R <= 128; otherwise the Lt half of the output
+// buffer with ld = R, rewritten at the end).  Right-looking factorisation in
+// the LDL^T form, one barrier per column: at step j every thread updates
+// work[i][k] -= work[i][j] work[k][j] / d_j for j < k <= i.  The pivot of the
+// next column, d_{j+1} = work[j+1][j+1], is always updated by thread 0 as its
+// first element of step j, so thread 0 alone tests it and forms 1/d_{j+1}
+// while the other threads finish the step.  Finally L[i][k] = work[i][k] /
+// sqrt(d_k), L[k][k] = sqrt(d_k).  If a pivot is not positive the
+// factorisation restarts once on Gamma + 1e-12 * trace(Gamma)/R * I (flag 1);
+// a second failure sets flag 2 and leaves L = I so that later kernels stay
+// finite.  scal[SCAL_FLAGS] gets the flag and scal[SCAL_GS] is cleared for the
+// Gram kernel's accumulation.
 __global__ void __launch_bounds__(512) k_gamma_chol(double* const* __restrict__ S_list,
                                                     double* const* __restrict__ dS_list, int N,
                                                     int n, int R, int pp, double* __restrict__ G,
@@ -76,30 +80,40 @@ __global__ void __launch_bounds__(512) k_gamma_chol(double* const* __restrict__ 
                                                     double* __restrict__ scal, int use_smem) {
     extern __shared__ double smw[];
     __shared__ double red[32];
-    __shared__ double sinv[CP_MAXR];
+    __shared__ double sinv[CP_MAXR];   // 1/d_j
+    __shared__ double srs[CP_MAXR];    // 1/sqrt(d_j)
+    __shared__ int sfail;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int RR = R * R;
+    const int ld = use_smem ? R + 1 : R;
     double* L = Lout;            // lower, row-major
     double* Lt = Lout + RR;      // upper (transpose), row-major
     double* work = use_smem ? smw : Lt;
+    const double* Sp[CP_MAXN];
+    const double* dSp[CP_MAXN];
+    for (int k = 0; k < N; ++k) {
+        Sp[k] = S_list[k];
+        dSp[k] = pp ? dS_list[k] : nullptr;
+    }
 
     double tr = 0.0;
     for (int e = tid; e < RR; e += nt) {
+        const int i = e / R, k = e % R;
         double g = 1.0;
-        for (int k = 0; k < N; ++k)
-            if (k != n) g *= S_list[k][e];
+        for (int m = 0; m < N; ++m)
+            if (m != n) g *= Sp[m][e];
         G[e] = g;
-        work[e] = g;
-        if (e / R == e % R) tr += g;
+        work[i * ld + k] = g;
+        if (i == k) tr += g;
         if (pp) {
             double w = 0.0;
-            for (int i = 0; i < N; ++i) {
-                if (i == n) continue;
-                for (int j = i + 1; j < N; ++j) {
-                    if (j == n) continue;
-                    double t = dS_list[i][e] * dS_list[j][e];
-                    for (int k = 0; k < N; ++k)
-                        if (k != i && k != j && k != n) t *= S_list[k][e];
+            for (int a = 0; a < N; ++a) {
+                if (a == n) continue;
+                for (int b = a + 1; b < N; ++b) {
+                    if (b == n) continue;
+                    double t = dSp[a][e] * dSp[b][e];
+                    for (int m = 0; m < N; ++m)
+                        if (m != a && m != b && m != n) t *= Sp[m][e];
                     w += t;
                 }
             }
@@ -113,35 +127,44 @@ __global__ void __launch_bounds__(512) k_gamma_chol(double* const* __restrict__ 
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (attempt == 1) {
             const double shift = 1e-12 * tr / R;
-            for (int e = tid; e < RR; e += nt) work[e] = G[e] + ((e / R == e % R) ? shift : 0.0);
+            for (int e = tid; e < RR; e += nt) {
+                const int i = e / R, k = e % R;
+                work[i * ld + k] = G[e] + ((i == k) ? shift : 0.0);
+            }
             flag = 1.0;
             __syncthreads();
         }
-        bool ok = true;
-        for (int j = 0; j < R; ++j) {
-            const double d = work[j * R + j];  // same value in every thread
-            if (!(d > 0.0) || !isfinite(d)) {
-                ok = false;
-                break;
-            }
-            const double inv = 1.0 / d;
+        if (tid == 0) {
+            const double d = work[0];
+            sfail = (!(d > 0.0) || !isfinite(d)) ? 1 : 0;
+            if (!sfail) sinv[0] = 1.0 / d;
+        }
+        __syncthreads();
+        for (int j = 0; j < R && !sfail; ++j) {
+            const double inv = sinv[j];
             for (int i = j + 1 + warp; i < R; i += nw) {
-                const double lij = work[i * R + j] * inv;
-                double* wi = work + (size_t)i * R;
-                for (int k = j + 1 + lane; k <= i; k += 32) wi[k] = fma(-lij, work[k * R + j], wi[k]);
+                double* wi = work + (size_t)i * ld;
+                const double lij = wi[j] * inv;
+                for (int k = j + 1 + lane; k <= i; k += 32) wi[k] = fma(-lij, work[k * ld + j], wi[k]);
+            }
+            if (tid == 0 && j + 1 < R) {
+                const double d = work[(j + 1) * ld + j + 1];
+                if (!(d > 0.0) || !isfinite(d)) sfail = 1;
+                else sinv[j + 1] = 1.0 / d;
             }
             __syncthreads();
         }
-        if (ok) break;
+        const bool failed = sfail != 0;
         __syncthreads();
+        if (!failed) break;
         if (attempt == 1) {
             flag = 2.0;
             bad = true;
         }
     }
     for (int j = tid; j < R; j += nt) {
-        const double v = bad ? 1.0 : 1.0 / sqrt(work[j * R + j]);
-        sinv[j] = v;
+        const double v = bad ? 1.0 : 1.0 / sqrt(work[j * ld + j]);
+        srs[j] = v;
         invd[j] = v;
     }
     __syncthreads();
@@ -151,8 +174,8 @@ __global__ void __launch_bounds__(512) k_gamma_chol(double* const* __restrict__ 
             const int i = e / R, k = e % R;
             double v = 0.0;
             if (bad) v = (i == k) ? 1.0 : 0.0;
-            else if (k < i) v = work[e] * sinv[k];
-            else if (k == i) v = 1.0 / sinv[k];
+            else if (k < i) v = work[e] * srs[k];
+            else if (k == i) v = 1.0 / srs[k];
             L[e] = v;
         }
         __syncthreads();
@@ -165,8 +188,8 @@ __global__ void __launch_bounds__(512) k_gamma_chol(double* const* __restrict__ 
             const int i = e / R, k = e % R;
             double v = 0.0;
             if (bad) v = (i == k) ? 1.0 : 0.0;
-            else if (k < i) v = work[e] * sinv[k];
-            else if (k == i) v = 1.0 / sinv[k];
+            else if (k < i) v = work[i * ld + k] * srs[k];
+            else if (k == i) v = 1.0 / srs[k];
             L[e] = v;
             Lt[k * R + i] = v;
         }
@@ -191,13 +214,26 @@ __global__ void __launch_bounds__(128) k_solve(const float* __restrict__ M,
     extern __shared__ double sL[];
     __shared__ double red[4][CP_NSCAL];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int x = blockIdx.x * 4 + wib;
+    const int nwb = blockDim.x >> 5;
+    const int x = blockIdx.x * nwb + wib;
     const int ld = SMEM ? R + 1 : R;
     const double* Lc;   // column access L[k][j] = Lc[j * ldc + k]... see below
     const double* Lr;   // row access    L[j][k] = Lr[j * ld + k]
     const double* iv;
     if (SMEM) {
-        for (int e = threadIdx.x; e < R * R; e += blockDim.x) sL[(e / R) * ld + (e % R)] = L[e];
+        const int RR = R * R;
+        int e = threadIdx.x;
+        for (; e + 7 * (int)blockDim.x < RR; e += 8 * blockDim.x) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldg(L + e + u * blockDim.x);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int f = e + u * blockDim.x;
+                sL[(f / R) * ld + (f % R)] = v[u];
+            }
+        }
+        for (; e < RR; e += blockDim.x) sL[(e / R) * ld + (e % R)] = __ldg(L + e);
         for (int j = threadIdx.x; j < R; j += blockDim.x) sL[R * ld + j] = invd[j];
         __syncthreads();
         Lr = sL;
@@ -312,7 +348,8 @@ __global__ void __launch_bounds__(128) k_solve(const float* __restrict__ M,
     }
     __syncthreads();
     if (threadIdx.x < CP_NSCAL) {
-        double v = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
+        double v = 0.0;
+        for (int w = 0; w < nwb; ++w) v += red[w][threadIdx.x];
         scal_part[(size_t)blockIdx.x * CP_NSCAL + threadIdx.x] = v;
     }
 }
@@ -612,9 +649,53 @@ __global__ void k_add_aw(const float* __restrict__ Mt, const double* __restrict_
     out[e] = (float)((double)Mt[e] + v);
 }
 
+
+// ------------------------------------------------------------------ Khatri-Rao operand
+// out[r][k] (r < Rpad, k < Kpad; zero outside R x K): row k = ia * sb + ib of the
+// Khatri-Rao product, A_a[ia][r] * A_b[ib][r], split into two parts.
+template <int KIND>
+__global__ void k_kr(const double* __restrict__ Aa, const double* __restrict__ Ab, int sa, int sb,
+                     int R, int Rpad, int Kpad, void* __restrict__ hi, void* __restrict__ lo) {
+    const int64_t K = (int64_t)sa * sb;
+    const int64_t n = (int64_t)Rpad * Kpad;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / Kpad);
+        const int64_t k = idx - (int64_t)r * Kpad;
+        float v = 0.f;
+        if (r < R && k < K) {
+            const int ia = (int)(k / sb), ib = (int)(k - (int64_t)ia * sb);
+            v = (float)(Aa[(size_t)ia * R + r] * Ab[(size_t)ib * R + r]);
+        }
+        if (KIND == 0) {
+            uint16_t h, l;
+            bf16_split(v, h, l);
+            static_cast<uint16_t*>(hi)[idx] = h;
+            static_cast<uint16_t*>(lo)[idx] = l;
+        } else {
+            const float h = tf32_rna(v);
+            static_cast<float*>(hi)[idx] = h;
+            static_cast<float*>(lo)[idx] = tf32_rna(v - h);
+        }
+    }
+}
+
 }  // namespace
 
 namespace cpk {
+
+cudaError_t kr_operand(const double* Aa, const double* Ab, int sa, int sb, int R, int Kpad,
+                       int kind, void* hi, void* lo, cudaStream_t st) {
+    const int Rpad = (R + 15) / 16 * 16;
+    const int64_t n = (int64_t)Rpad * Kpad;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    if (kind == 0)
+        k_kr<0><<<(unsigned)blocks, 256, 0, st>>>(Aa, Ab, sa, sb, R, Rpad, Kpad, hi, lo);
+    else
+        k_kr<1><<<(unsigned)blocks, 256, 0, st>>>(Aa, Ab, sa, sb, R, Rpad, Kpad, hi, lo);
+    return cudaGetLastError();
+}
 
 cudaError_t pp_delta(const double* A, const double* Ap, float* d32, double* d64, int64_t n,
                      cudaStream_t st) {
@@ -635,11 +716,11 @@ cudaError_t gamma_chol(double* const* S_list, double* const* dS_list, int N, int
                        int pp, double* Gamma, double* L, double* invdiag, double* W,
                        double* scal, cudaStream_t st) {
     const int use_smem = (R <= 128) ? 1 : 0;
-    size_t smem = use_smem ? (size_t)R * R * sizeof(double) : 0;
+    size_t smem = use_smem ? (size_t)R * (R + 1) * sizeof(double) : 0;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_gamma_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             128 * 128 * sizeof(double));
+                             128 * 129 * sizeof(double));
         attr_set = true;
     }
     k_gamma_chol<<<1, 512, smem, st>>>(S_list, dS_list, N, n, R, pp, Gamma, L, invdiag, W, scal,
@@ -648,9 +729,9 @@ cudaError_t gamma_chol(double* const* S_list, double* const* dS_list, int N, int
 }
 
 template <int RT, bool SM>
-static cudaError_t launch_solve(unsigned blocks, const float* M, const double* W, const double* L,
-                                const double* invdiag, const SolveOut& o, int s, int R,
-                                double* scal_part, cudaStream_t st) {
+static cudaError_t launch_solve(unsigned blocks, unsigned threads, const float* M, const double* W,
+                                const double* L, const double* invdiag, const SolveOut& o, int s,
+                                int R, double* scal_part, cudaStream_t st) {
     size_t smem = SM ? ((size_t)R * (R + 1) + R) * sizeof(double) : 0;
     static bool attr_set = false;
     if (SM && !attr_set) {
@@ -658,7 +739,7 @@ static cudaError_t launch_solve(unsigned blocks, const float* M, const double* W
                              (int)(((size_t)128 * 129 + 128) * sizeof(double)));
         attr_set = true;
     }
-    k_solve<RT, SM><<<blocks, 128, smem, st>>>(M, W, L, invdiag, o, s, R, scal_part);
+    k_solve<RT, SM><<<blocks, threads, smem, st>>>(M, W, L, invdiag, o, s, R, scal_part);
     return cudaGetLastError();
 }
 
@@ -666,17 +747,21 @@ cudaError_t solve_rows(const float* M, const double* W, const double* L, const d
                        const SolveOut& o, int s, int R, double* scal_part, int* nblk,
                        cudaStream_t st) {
     const int RT = (R + 31) / 32;
-    const unsigned blocks = (unsigned)((s + 3) / 4);
+    // one row per warp; small factor matrices get one warp per block so that the
+    // FP64 work spreads over as many SMs as there are rows
+    const int wpb = (s <= 512) ? 1 : 4;
+    const unsigned blocks = (unsigned)((s + wpb - 1) / wpb);
+    const unsigned th = 32u * wpb;
     *nblk = (int)blocks;
     switch (RT) {
-        case 1: return launch_solve<1, true>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 2: return launch_solve<2, true>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 3: return launch_solve<3, true>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 4: return launch_solve<4, true>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 5: return launch_solve<5, false>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 6: return launch_solve<6, false>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 7: return launch_solve<7, false>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 8: return launch_solve<8, false>(blocks, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 1: return launch_solve<1, true>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 2: return launch_solve<2, true>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 3: return launch_solve<3, true>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 4: return launch_solve<4, true>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 5: return launch_solve<5, false>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 6: return launch_solve<6, false>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 7: return launch_solve<7, false>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
+        case 8: return launch_solve<8, false>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,0 +1,756 @@
+// Normal equations of one factor update, A(n) Gamma(n) = M(n) (Alg. 1 line 8,
+// Alg. 2 line 11), solved to FP64 accuracy with FP32 factorisation plus FP64
+// iterative refinement (Wilkinson; Moler, JACM 1967; Carson and Higham, SISC 2018).
+//
+// On this GPU an FP64 FMA has a 64-cycle dependent latency and 1/70 of the FP32
+// throughput, so the sequential parts of a Cholesky factorisation and of
+// triangular substitution are run in FP32, and FP64 is kept for work that is
+// parallel across the R entries of a row:
+//   k_chol_mixed  (one CTA)  Gamma = *_{k != n} S(k) and PP's W in FP64; the
+//                 explicit inverse G32 = Gamma^{-1} in FP32 by Gauss-Jordan
+//                 elimination without pivoting (SPD: its pivots are the LDL^T
+//                 pivots), two shared-memory copies used in turn so that each of
+//                 the R steps needs one barrier.  If a pivot is not positive or the
+//                 pivots spread over more than 1e5 (iterative refinement would
+//                 converge slowly), it factors Gamma in FP64 (LDL^T) instead and
+//                 tells the solve kernel to substitute in FP64.
+//   k_solve_mixed (one warp per row) m = M(x,:) [+ A_old(x,:) W];
+//                 x0 = m G32;  repeat  r = m - x Gamma (FP64),  d = r G32,  x += d
+//                 until the estimated remaining error ||d||_inf * rho is below
+//                 2^-50 ||x||_inf (rho = contraction seen between iterations).
+#include <cuda_bf16.h>
+
+#include "cpals_internal.h"
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int MIXED_MAXR = 128;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+__device__ double block_sum_d(double v, double* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = (lane < nw) ? sh[lane] : 0.0;
+        t = warp_sum_d(t);
+        if (lane == 0) sh[0] = t;
+    }
+    __syncthreads();
+    t = sh[0];
+    __syncthreads();
+    return t;
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// ------------------------------------------------------------------ factorisation
+// FP64 LDL^T of Gamma (global work, row stride R) into L (lower) / Lt (upper) and
+// 1/L[j][j]: the fallback for ill-conditioned or indefinite Gamma.  Restarts once
+// on Gamma + 1e-12 trace/R I.  Returns the flag (0, 1 shifted, 2 failed).
+__device__ double chol_fp64(const double* G, int R, double tr, double* L, double* Lt, double* invd,
+                            double* sinv, double* srs, int* sfail) {
+    const int tid = threadIdx.x, nt = blockDim.x, RR = R * R;
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    double* work = Lt;
+    double flag = 0.0;
+    bool bad = false;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const double shift = attempt ? 1e-12 * tr / R : 0.0;
+        for (int e = tid; e < RR; e += nt) work[e] = G[e] + ((e / R == e % R) ? shift : 0.0);
+        if (attempt) flag = 1.0;
+        __syncthreads();
+        if (tid == 0) {
+            const double d = work[0];
+            *sfail = (!(d > 0.0) || !isfinite(d)) ? 1 : 0;
+            if (!*sfail) sinv[0] = 1.0 / d;
+        }
+        __syncthreads();
+        for (int j = 0; j < R && !*sfail; ++j) {
+            const double inv = sinv[j];
+            for (int i = j + 1 + warp; i < R; i += nw) {
+                double* wi = work + (size_t)i * R;
+                const double lij = wi[j] * inv;
+                for (int k = j + 1 + lane; k <= i; k += 32) wi[k] = fma(-lij, work[k * R + j], wi[k]);
+            }
+            if (tid == 0 && j + 1 < R) {
+                const double d = work[(j + 1) * R + j + 1];
+                if (!(d > 0.0) || !isfinite(d)) *sfail = 1;
+                else sinv[j + 1] = 1.0 / d;
+            }
+            __syncthreads();
+        }
+        const bool failed = *sfail != 0;
+        __syncthreads();
+        if (!failed) break;
+        if (attempt == 1) {
+            flag = 2.0;
+            bad = true;
+        }
+    }
+    for (int j = tid; j < R; j += nt) {
+        const double v = bad ? 1.0 : 1.0 / sqrt(work[j * R + j]);
+        srs[j] = v;
+        invd[j] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < RR; e += nt) {
+        const int i = e / R, k = e % R;
+        double v = 0.0;
+        if (bad) v = (i == k) ? 1.0 : 0.0;
+        else if (k < i) v = work[e] * srs[k];
+        else if (k == i) v = 1.0 / srs[k];
+        L[e] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < RR; e += nt) Lt[e] = L[(e % R) * R + e / R];
+    __syncthreads();
+    return flag;
+}
+
+// Gamma (FP64) and PP's W for update n, element (i, j) = (row, column).
+__device__ __forceinline__ double gamma_entry(const double* const* Sp, const double* const* dSp, int N,
+                                              int n, int pp, size_t e, double* w_out) {
+    double g = 1.0;
+    for (int m = 0; m < N; ++m)
+        if (m != n) g *= Sp[m][e];
+    if (pp) {
+        double acc = 0.0;
+        for (int a = 0; a < N; ++a) {
+            if (a == n) continue;
+            for (int b = a + 1; b < N; ++b) {
+                if (b == n) continue;
+                double t = dSp[a][e] * dSp[b][e];
+                for (int m = 0; m < N; ++m)
+                    if (m != a && m != b && m != n) t *= Sp[m][e];
+                acc += t;
+            }
+        }
+        *w_out = acc;
+    }
+    return g;
+}
+
+// R > 128: Gamma, W and the FP64 factorisation only.
+__global__ void __launch_bounds__(1024) k_chol_fp64only(double* const* __restrict__ S_list,
+                                                        double* const* __restrict__ dS_list, int N, int n,
+                                                        int R, int pp, double* __restrict__ G,
+                                                        double* __restrict__ L64,
+                                                        double* __restrict__ invd64,
+                                                        double* __restrict__ W,
+                                                        double* __restrict__ scal,
+                                                        int* __restrict__ mode) {
+    __shared__ double red[32];
+    __shared__ double sinv[CP_MAXR], srs[CP_MAXR];
+    __shared__ int sfail;
+    const int RR = R * R;
+    const double* Sp[CP_MAXN];
+    const double* dSp[CP_MAXN];
+    for (int k = 0; k < N; ++k) {
+        Sp[k] = S_list[k];
+        dSp[k] = pp ? dS_list[k] : nullptr;
+    }
+    double tr = 0.0;
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+        double w = 0.0;
+        const double g = gamma_entry(Sp, dSp, N, n, pp, (size_t)e, &w);
+        G[e] = g;
+        if (pp) W[e] = w;
+        if (e / R == e % R) tr += g;
+    }
+    tr = block_sum_d(tr, red);
+    const double flag = chol_fp64(G, R, tr, L64, L64 + RR, invd64, sinv, srs, &sfail);
+    if (threadIdx.x == 0) {
+        scal[SCAL_FLAGS] = 10.0 + flag;
+        scal[SCAL_GS] = 0.0;
+        *mode = 1;
+    }
+}
+
+// R <= 128.  Warp w owns rows w, w + 32, ... (at most 4); lane l owns columns
+// l + 32 t (t < RT).  Gauss-Jordan on register-resident rows; the pivot row of
+// the next step is published in one of two shared rows, one barrier per step.
+template <int RT>
+__global__ void __launch_bounds__(1024) k_chol_mixed(double* const* __restrict__ S_list,
+                                                     double* const* __restrict__ dS_list, int N,
+                                                     int n, int R, int pp, double* __restrict__ G,
+                                                     float* __restrict__ Ginv,
+                                                     double* __restrict__ L64,
+                                                     double* __restrict__ invd64,
+                                                     double* __restrict__ W,
+                                                     double* __restrict__ scal,
+                                                     int* __restrict__ mode) {
+    constexpr int RPW = 4;
+    __shared__ double red[32];
+    __shared__ double sinv[CP_MAXR], srs[CP_MAXR];
+    __shared__ float prow[2][MIXED_MAXR];
+    __shared__ int sfail;
+    __shared__ float pmin, pmax;
+    __shared__ unsigned gmax_bits, imax_bits;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    const int RR = R * R;
+    const double* Sp[CP_MAXN];
+    const double* dSp[CP_MAXN];
+    for (int k = 0; k < N; ++k) {
+        Sp[k] = S_list[k];
+        dSp[k] = pp ? dS_list[k] : nullptr;
+    }
+    if (tid == 0) {
+        sfail = 0;
+        pmin = 3.0e38f;
+        pmax = 0.f;
+        gmax_bits = 0u;
+        imax_bits = 0u;
+    }
+    for (int j = tid; j < 2 * MIXED_MAXR; j += blockDim.x) (&prow[0][0])[j] = 0.f;
+    float a[RPW][RT];
+    double tr = 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < RPW; ++s) {
+        const int i = warp + nw * s;
+        float rowabs = 0.f;
+#pragma unroll
+        for (int t = 0; t < RT; ++t) {
+            const int j = lane + 32 * t;
+            float v = 0.f;
+            if (i < R && j < R) {
+                const size_t e = (size_t)i * R + j;
+                double w = 0.0;
+                const double g = gamma_entry(Sp, dSp, N, n, pp, e, &w);
+                G[e] = g;
+                if (pp) W[e] = w;
+                if (i == j) tr += g;
+                v = (float)g;
+                rowabs += fabsf(v);
+            }
+            a[s][t] = v;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) rowabs += __shfl_xor_sync(FULL, rowabs, o);
+        if (lane == 0 && i < R) atomicMax(&gmax_bits, __float_as_uint(rowabs));
+    }
+    tr = block_sum_d(tr, red);
+    // publish row 0 (warp 0, slot 0)
+    if (warp == 0) {
+#pragma unroll
+        for (int t = 0; t < RT; ++t)
+            if (lane + 32 * t < R) prow[0][lane + 32 * t] = a[0][t];
+    }
+    __syncthreads();
+    for (int k = 0; k < R; ++k) {
+        const float* pk = prow[k & 1];
+        const float p = pk[k];  // same value in every thread
+        if (!(p > 0.f) || !isfinite(p)) {
+            if (tid == 0) sfail = 1;
+            break;
+        }
+        if (tid == 0) {
+            pmin = fminf(pmin, p);
+            pmax = fmaxf(pmax, p);
+        }
+        const float inv = 1.f / p;
+        float pv[RT];
+#pragma unroll
+        for (int t = 0; t < RT; ++t) pv[t] = pk[lane + 32 * t < MIXED_MAXR ? lane + 32 * t : 0];
+        const int kt = k >> 5, kl = k & 31;
+#pragma unroll
+        for (int s = 0; s < RPW; ++s) {
+            const int i = warp + nw * s;
+            if (i >= R) continue;  // warp-uniform
+            float aik = 0.f;
+#pragma unroll
+            for (int t = 0; t < RT; ++t)
+                if (t == kt) aik = a[s][t];
+            const float f = __shfl_sync(FULL, aik, kl) * inv;
+            if (i == k) {
+#pragma unroll
+                for (int t = 0; t < RT; ++t) {
+                    const int j = lane + 32 * t;
+                    a[s][t] = (j == k) ? inv : pv[t] * inv;
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < RT; ++t) {
+                    const int j = lane + 32 * t;
+                    a[s][t] = (j == k) ? -f : fmaf(-f, pv[t], a[s][t]);
+                }
+            }
+        }
+        // the owner of row k+1 publishes it for the next step
+        const int k1 = k + 1;
+        if (k1 < R && warp == k1 % nw) {
+            const int s1 = k1 / nw;
+            float* dst = prow[k1 & 1];
+#pragma unroll
+            for (int s = 0; s < RPW; ++s)
+                if (s == s1) {
+#pragma unroll
+                    for (int t = 0; t < RT; ++t)
+                        if (lane + 32 * t < R) dst[lane + 32 * t] = a[s][t];
+                }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    bool use64 = sfail != 0 || pmax > 1e5f * pmin;
+    if (!use64) {
+        // ||Gamma||_inf ||G32||_inf: refinement contracts by about kappa 2^-24 per step
+#pragma unroll
+        for (int s = 0; s < RPW; ++s) {
+            const int i = warp + nw * s;
+            float rowabs = 0.f;
+#pragma unroll
+            for (int t = 0; t < RT; ++t) rowabs += fabsf(a[s][t]);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) rowabs += __shfl_xor_sync(FULL, rowabs, o);
+            if (lane == 0 && i < R) atomicMax(&imax_bits, __float_as_uint(rowabs));
+        }
+        __syncthreads();
+        const float kappa = __uint_as_float(gmax_bits) * __uint_as_float(imax_bits);
+        use64 = !(kappa <= 2e4f);
+    }
+    if (use64) {
+        const double flag = chol_fp64(G, R, tr, L64, L64 + RR, invd64, sinv, srs, &sfail);
+        if (tid == 0) {
+            scal[SCAL_FLAGS] = 10.0 + flag;  // FP64 path: 10 ok, 11 shifted, 12 failed
+            scal[SCAL_GS] = 0.0;
+            *mode = 1;
+        }
+        return;
+    }
+#pragma unroll
+    for (int s = 0; s < RPW; ++s) {
+        const int i = warp + nw * s;
+        if (i >= R) continue;
+#pragma unroll
+        for (int t = 0; t < RT; ++t) {
+            const int j = lane + 32 * t;
+            if (j < R) Ginv[(size_t)i * R + j] = a[s][t];
+        }
+    }
+    if (tid == 0) {
+        scal[SCAL_FLAGS] = 0.0;
+        scal[SCAL_GS] = 0.0;
+        *mode = 0;
+    }
+}
+
+// ------------------------------------------------------------------ row solves
+__device__ __forceinline__ void bf16_split(float x, uint16_t& hi, uint16_t& lo) {
+    __nv_bfloat16 h = __float2bfloat16_rn(x);
+    __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(l);
+}
+
+constexpr int SOLVE_THREADS = 128;
+
+// shared layout of the solve kernel (doubles unless noted)
+struct SolveSmem {
+    size_t G, Gi, m, x, r, part, red, total;
+};
+__host__ __device__ inline SolveSmem solve_smem(int R) {
+    // R > 128 solves in FP64 straight from global memory: no staged matrices
+    SolveSmem L;
+    const bool staged = R <= MIXED_MAXR;
+    const size_t RR = staged ? (size_t)R * R : 0;
+    const size_t RRp = (RR + 1) & ~(size_t)1;
+    L.G = 0;                                   // RR doubles (or padded R x (R+1) FP64 factor)
+    L.Gi = staged ? (((size_t)R * (R + 1) + 1) & ~(size_t)1) : 0;  // RR floats
+    L.m = L.Gi + (staged ? RRp / 2 + 2 : 0);
+    L.x = L.m + R;
+    L.r = L.x + R;                             // R floats
+    L.part = L.r + (R + 1) / 2 + 1;            // SOLVE_THREADS doubles
+    L.red = L.part + SOLVE_THREADS;            // 2 * SOLVE_THREADS / 32 doubles
+    L.total = L.red + 16;
+    return L;
+}
+
+// One row x per block of 128 threads.  Thread (tj, tk) = (tid mod R, tid / R)
+// handles column tj over the k-slice tk of every reduction (nks = 128 / R slices).
+template <int RT>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
+    const float* __restrict__ M, const double* __restrict__ W, const double* __restrict__ G,
+    const float* __restrict__ Ginv, const double* __restrict__ L64, const double* __restrict__ invd64,
+    const int* __restrict__ mode, cpk::SolveOut o, int s, int R, double* __restrict__ scal,
+    double* __restrict__ scal_part, unsigned* __restrict__ dev_err) {
+    extern __shared__ __align__(16) double sm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_conv;
+    const SolveSmem lay = solve_smem(R);
+    double* sG = sm + lay.G;
+    float* sGi = reinterpret_cast<float*>(sm + lay.Gi);
+    double* mv = sm + lay.m;
+    double* xv = sm + lay.x;
+    float* rv = reinterpret_cast<float*>(sm + lay.r);
+    double* part = sm + lay.part;
+    double* red = sm + lay.red;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int x = blockIdx.x;
+    const int path = *mode;
+    const int RR = R * R;
+    const int nks = (R <= SOLVE_THREADS) ? SOLVE_THREADS / R : 1;
+    const bool act = tid < nks * R;
+    const int tj = act ? tid % R : 0, tk = act ? tid / R : 0;
+    const int k0 = tk * R / nks, k1 = (tk + 1) * R / nks;
+    const bool owner = act && tk == 0;          // thread that finalises column tj
+
+    double aold = 0.0, m = 0.0, xj = 0.0;
+    if (owner) {
+        aold = o.A64[(size_t)x * R + tj];
+        m = (double)M[(size_t)x * R + tj];
+    }
+    double sc[CP_NSCAL];
+#pragma unroll
+    for (int i = 0; i < CP_NSCAL; ++i) sc[i] = 0.0;
+
+    if (path == 0) {
+        // stage Gamma and G32 with two bulk copies (sizes rounded up to 16 bytes;
+        // the sources have 16 spare bytes)
+        const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+        const uint32_t bytesG = (uint32_t)((RR * 8 + 15) & ~15), bytesGi = (uint32_t)((RR * 4 + 15) & ~15);
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytesG + bytesGi)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    (uint32_t)__cvta_generic_to_shared(sG)),
+                "l"(G), "r"(bytesG), "r"(b)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    (uint32_t)__cvta_generic_to_shared(sGi)),
+                "l"(Ginv), "r"(bytesGi), "r"(b)
+                : "memory");
+        }
+        if (owner) xv[tj] = aold;   // for the V term
+        __syncthreads();
+        if (W) {
+            // V(x,:) = A_old(x,:) W (Eq. V_nij), FP64, k-split
+            double v0 = 0.0, v1 = 0.0;
+            if (act) {
+                int q = k0;
+                for (; q + 1 < k1; q += 2) {
+                    v0 = fma(xv[q], W[(size_t)q * R + tj], v0);
+                    v1 = fma(xv[q + 1], W[(size_t)(q + 1) * R + tj], v1);
+                }
+                if (q < k1) v0 = fma(xv[q], W[(size_t)q * R + tj], v0);
+                part[tid] = v0 + v1;
+            }
+            __syncthreads();
+            if (owner) {
+                double v = 0.0;
+                for (int q = 0; q < nks; ++q) v += part[q * R + tj];
+                m += v;
+                sc[SCAL_V2] += v * v;
+            }
+        }
+        if (owner) rv[tj] = (float)m;
+        // bounded wait for the staged matrices (about 1 s)
+        {
+            const long long t0 = clock64();
+            uint32_t ok = 0;
+            int give_up = 0;
+            while (!ok) {
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                    "selp.u32 %0, 1, 0, p;\n\t}"
+                    : "=r"(ok)
+                    : "r"(b)
+                    : "memory");
+                if (!ok && clock64() - t0 > 2000000000LL) {
+                    give_up = 1;
+                    break;
+                }
+            }
+            if (give_up) {
+                if (tid == 0) atomicOr(dev_err, (unsigned)DEVERR_TIMEOUT);
+                return;
+            }
+        }
+        __syncthreads();
+        // x0 = m G32 (FP32, k-split)
+        {
+            float a0 = 0.f, a1 = 0.f;
+            if (act) {
+                int k = k0;
+                for (; k + 1 < k1; k += 2) {
+                    a0 = fmaf(rv[k], sGi[k * R + tj], a0);
+                    a1 = fmaf(rv[k + 1], sGi[(k + 1) * R + tj], a1);
+                }
+                if (k < k1) a0 = fmaf(rv[k], sGi[k * R + tj], a0);
+                part[tid] = (double)(a0 + a1);
+            }
+            __syncthreads();
+            if (owner) {
+                double v = 0.0;
+                for (int q = 0; q < nks; ++q) v += part[q * R + tj];
+                xj = v;
+            }
+        }
+        double prev = 0.0;
+        if (tid == 0) s_conv = 0;
+        for (int itr = 0; itr < 12; ++itr) {
+            if (owner) xv[tj] = xj;
+            __syncthreads();
+            // r = m - x Gamma (FP64)
+            if (act) {
+                double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+                int k = k0;
+                for (; k + 3 < k1; k += 4) {
+                    r0 = fma(xv[k], sG[(size_t)k * R + tj], r0);
+                    r1 = fma(xv[k + 1], sG[(size_t)(k + 1) * R + tj], r1);
+                    r2 = fma(xv[k + 2], sG[(size_t)(k + 2) * R + tj], r2);
+                    r3 = fma(xv[k + 3], sG[(size_t)(k + 3) * R + tj], r3);
+                }
+                for (; k < k1; ++k) r0 = fma(xv[k], sG[(size_t)k * R + tj], r0);
+                part[tid] = (r0 + r1) + (r2 + r3);
+            }
+            __syncthreads();
+            if (owner) {
+                double v = 0.0;
+                for (int q = 0; q < nks; ++q) v += part[q * R + tj];
+                rv[tj] = (float)(m - v);
+            }
+            __syncthreads();
+            // d = r G32 ; x += d
+            float a0 = 0.f, a1 = 0.f;
+            if (act) {
+                int k = k0;
+                for (; k + 1 < k1; k += 2) {
+                    a0 = fmaf(rv[k], sGi[k * R + tj], a0);
+                    a1 = fmaf(rv[k + 1], sGi[(k + 1) * R + tj], a1);
+                }
+                if (k < k1) a0 = fmaf(rv[k], sGi[k * R + tj], a0);
+                part[tid] = (double)(a0 + a1);
+            }
+            __syncthreads();
+            double dabs = 0.0, xabs = 0.0;
+            if (owner) {
+                double d = 0.0;
+                for (int q = 0; q < nks; ++q) d += part[q * R + tj];
+                xj += d;
+                dabs = fabs(d);
+                xabs = fabs(xj);
+            }
+            dabs = warp_max_d(dabs);
+            xabs = warp_max_d(xabs);
+            if (lane == 0) {
+                red[warp] = dabs;
+                red[4 + warp] = xabs;
+            }
+            __syncthreads();
+            const double dmax = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
+            const double xmax = fmax(fmax(red[4], red[5]), fmax(red[6], red[7]));
+            // remaining error after this step is about rho * dmax, rho = dmax / prev
+            const double rho = (itr > 0 && prev > 0.0) ? dmax / prev : 1.0;
+            const bool conv = rho * dmax <= 0x1.0p-50 * xmax || dmax == 0.0;
+            prev = dmax;
+            __syncthreads();
+            if (conv) {
+                if (tid == 0) s_conv = 1;
+                break;
+            }
+        }
+        if (tid == 0 && !s_conv) scal[SCAL_FLAGS] = 3.0;
+    } else {
+        // FP64 substitution with the fallback factor: warp 0, lane l owns l + 32 t
+        if (warp == 0) {
+            const bool stage = R <= MIXED_MAXR;
+            const int ldl = stage ? R + 1 : R;
+            if (stage)
+                for (int e = lane; e < RR; e += 32) sG[(e / R) * (R + 1) + (e % R)] = __ldg(L64 + e);
+            __syncwarp();
+            const double* Lr = stage ? sG : L64;
+            double acc[RT], z[RT], xs[RT];
+#pragma unroll
+            for (int t = 0; t < RT; ++t) {
+                const int j = lane + 32 * t;
+                acc[t] = (j < R) ? (double)M[(size_t)x * R + j] : 0.0;
+                z[t] = 0.0;
+                xs[t] = 0.0;
+            }
+            if (W) {
+                // V term (FP64 path): lane-parallel over j
+#pragma unroll
+                for (int t = 0; t < RT; ++t) {
+                    const int j = lane + 32 * t;
+                    double v = 0.0;
+                    if (j < R)
+                        for (int q = 0; q < R; ++q) v = fma(o.A64[(size_t)x * R + q], W[(size_t)q * R + j], v);
+                    acc[t] += v;
+                    sc[SCAL_V2] += v * v;
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < RT; ++t) {
+                const int j = lane + 32 * t;
+                if (j < R) mv[j] = acc[t];
+            }
+#pragma unroll
+            for (int tt = 0; tt < RT; ++tt) {
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int j = tt * 32 + jj;
+                    if (j >= R) break;
+                    const double zj = __shfl_sync(FULL, acc[tt], jj) * invd64[j];
+                    if (lane == jj) z[tt] = zj;
+#pragma unroll
+                    for (int t2 = tt; t2 < RT; ++t2) {
+                        const int k = lane + 32 * t2;
+                        if (k > j && k < R) acc[t2] = fma(-Lr[(size_t)k * ldl + j], zj, acc[t2]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < RT; ++t) acc[t] = z[t];
+#pragma unroll
+            for (int tt = RT - 1; tt >= 0; --tt) {
+                for (int jj = 31; jj >= 0; --jj) {
+                    const int j = tt * 32 + jj;
+                    if (j >= R) continue;
+                    const double xjj = __shfl_sync(FULL, acc[tt], jj) * invd64[j];
+                    if (lane == jj) xs[tt] = xjj;
+#pragma unroll
+                    for (int t2 = 0; t2 <= tt; ++t2) {
+                        const int k = lane + 32 * t2;
+                        if (k < j) acc[t2] = fma(-Lr[(size_t)j * ldl + k], xjj, acc[t2]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < RT; ++t) {
+                const int j = lane + 32 * t;
+                if (j < R) xv[j] = xs[t];
+            }
+        }
+        __syncthreads();
+        if (owner) {
+            xj = xv[tj];
+            m = mv[tj];
+        }
+        if (warp != 0) sc[SCAL_V2] = 0.0;
+    }
+    // outputs: FP64 master, FP32 copy, split operand copies, dA, scalar partials
+    auto emit = [&](int j, double av, double mj, double ao) {
+        const size_t e = (size_t)x * R + j;
+        o.A64[e] = av;
+        const float af = (float)av;
+        if (o.A32) o.A32[e] = af;
+        if (o.bhi) {
+            uint16_t hi, lo;
+            bf16_split(af, hi, lo);
+            o.bhi[(size_t)j * o.Kpad + x] = hi;
+            o.blo[(size_t)j * o.Kpad + x] = lo;
+        }
+        if (o.bt32) {
+            const float h = tf32_rna(af);
+            const size_t f = (size_t)j * o.Kpad + x;
+            o.bt32[f] = h;
+            o.bt32[(size_t)o.Rpad * o.Kpad + f] = tf32_rna(af - h);
+        }
+        const double base = o.Ap ? o.Ap[e] : ao;
+        const double d = av - base;
+        if (o.dA32) o.dA32[e] = (float)d;
+        if (o.dA64) o.dA64[e] = d;
+        sc[SCAL_A2] += av * av;
+        sc[SCAL_STEP2] += (av - ao) * (av - ao);
+        if (o.Ap) sc[SCAL_DAP2] += d * d;
+        sc[SCAL_MA] += mj * av;
+        sc[SCAL_M2] += mj * mj;
+    };
+    if (path == 0) {
+        if (owner) emit(tj, xj, m, aold);
+    } else {
+        // the FP64 path covers any R: every thread takes columns tid, tid + 128, ...
+        for (int j = tid; j < R; j += SOLVE_THREADS) emit(j, xv[j], mv[j], o.A64[(size_t)x * R + j]);
+    }
+    // block reduction of the 8 scalars: warp sums, then warp 0
+#pragma unroll
+    for (int i = 0; i < CP_NSCAL; ++i) sc[i] = warp_sum_d(sc[i]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < CP_NSCAL; ++i) part[warp * CP_NSCAL + i] = sc[i];
+    __syncthreads();
+    if (tid < CP_NSCAL) {
+        double v = 0.0;
+        for (int w = 0; w < SOLVE_THREADS / 32; ++w) v += part[w * CP_NSCAL + tid];
+        scal_part[(size_t)blockIdx.x * CP_NSCAL + tid] = v;
+    }
+}
+
+template <int RT>
+cudaError_t launch_solve_mixed(const float* M, const double* W, const double* G, const float* Ginv,
+                               const double* L64, const double* invd64, const int* mode,
+                               const cpk::SolveOut& o, int s, int R, double* scal, double* scal_part,
+                               unsigned* dev_err, cudaStream_t st) {
+    const size_t smem = solve_smem(R).total * sizeof(double) + 64;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_solve_mixed<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(solve_smem(MIXED_MAXR).total * sizeof(double) + 64));
+        attr = true;
+    }
+    k_solve_mixed<RT><<<(unsigned)s, SOLVE_THREADS, smem, st>>>(M, W, G, Ginv, L64, invd64, mode, o, s, R,
+                                                               scal, scal_part, dev_err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace cpk {
+
+cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
+                       double* Gamma, float* Ginv, double* L64, double* invd64, double* W,
+                       double* scal, int* mode, cudaStream_t st) {
+    if (R > MIXED_MAXR) {
+        k_chol_fp64only<<<1, 1024, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, L64, invd64, W, scal, mode);
+        return cudaGetLastError();
+    }
+    switch ((R + 31) / 32) {
+        case 1: k_chol_mixed<1><<<1, 1024, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, Ginv, L64, invd64, W, scal, mode); break;
+        case 2: k_chol_mixed<2><<<1, 1024, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, Ginv, L64, invd64, W, scal, mode); break;
+        case 3: k_chol_mixed<3><<<1, 1024, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, Ginv, L64, invd64, W, scal, mode); break;
+        default: k_chol_mixed<4><<<1, 1024, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, Ginv, L64, invd64, W, scal, mode); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t solve_mixed(const float* M, const double* W, const double* Gamma, const float* Ginv,
+                        const double* L64, const double* invd64, const int* mode, const SolveOut& o,
+                        int s, int R, double* scal, double* scal_part, int* nblk, unsigned* dev_err,
+                        cudaStream_t st) {
+    *nblk = s;
+    switch ((R + 31) / 32) {
+        case 1: return launch_solve_mixed<1>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        case 2: return launch_solve_mixed<2>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        case 3: return launch_solve_mixed<3>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        case 4: return launch_solve_mixed<4>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        case 5: return launch_solve_mixed<5>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        case 6: return launch_solve_mixed<6>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        case 7: return launch_solve_mixed<7>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        case 8: return launch_solve_mixed<8>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace cpk

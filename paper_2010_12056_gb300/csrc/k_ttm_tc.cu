@@ -51,6 +51,8 @@ struct TcArgs {
     int64_t ntiles;
     int64_t tiles_per_p;
     int R, Rpad, nk, S_stg, S_op, tmem_cols, x3, b_resident, nsplit, nacc;
+    int nsk;          // split-K factor: work item w = (tile w / nsk, k-slice w % nsk)
+    int64_t slice;    // floats between split-K output slices
     uint32_t idesc;
     unsigned* dev_err;
 };
@@ -285,8 +287,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             int64_t it = 0;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
-                for (int kc = 0; kc < a.nk && ok; ++kc, ++it) {
+            const int64_t nwork = a.ntiles * a.nsk;
+            for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+                const int64_t tile = w / a.nsk;
+                const int ks = (int)(w % a.nsk);
+                const int kc0 = ks * a.nk / a.nsk, kc1 = (ks + 1) * a.nk / a.nsk;
+                for (int kc = kc0; kc < kc1 && ok; ++kc, ++it) {
                     const int s = (int)(it % S_stg);
                     const uint32_t us = (uint32_t)(it / S_stg);
                     if (!(ok = mbar_wait(stg_empty(s), (us & 1u) ^ 1u, abort_flag))) break;
@@ -328,15 +334,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int lt = 0;
             bool ok = true;
             if (a.b_resident) ok = mbar_wait(b_full, 0u, abort_flag);
-            for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++lt) {
+            const int64_t nwork = a.ntiles * a.nsk;
+            for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++lt) {
+                const int ks = (int)(w % a.nsk);
+                const int kc0 = ks * a.nk / a.nsk, kc1 = (ks + 1) * a.nk / a.nsk;
                 const int buf = lt & 1;
                 const uint32_t ub = (uint32_t)(lt >> 1);
                 if (!(ok = mbar_wait(acc_empty(buf), (ub & 1u) ^ 1u, abort_flag))) break;
                 tc_fence_after();
                 const uint32_t dt = tmem_base + (uint32_t)(buf * a.nacc * a.Rpad);
                 const uint32_t dcorr = dt + (uint32_t)(a.nsplit * a.Rpad);
-                for (int kc = 0; kc < a.nk; ++kc, ++it) {
-                    const uint32_t dmain = dt + (uint32_t)((kc % a.nsplit) * a.Rpad);
+                for (int kc = kc0; kc < kc1; ++kc, ++it) {
+                    const int rc = kc - kc0;  // chunk index within this work item
+                    const uint32_t dmain = dt + (uint32_t)((rc % a.nsplit) * a.Rpad);
                     const int j = (int)(it % S_op);
                     if (!(ok = mbar_wait(op_full(j), (uint32_t)((it / S_op) & 1), abort_flag))) break;
                     tc_fence_after();
@@ -345,10 +355,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {  // 4 k-steps of 32 bytes per 128-byte row
                         const uint32_t off = (uint32_t)kk * 32u;
-                        const uint32_t accm = (kc >= a.nsplit || kk > 0) ? 1u : 0u;
+                        const uint32_t accm = (rc >= a.nsplit || kk > 0) ? 1u : 0u;
                         tc_mma<KIND>(dmain, sw128_desc(ahi + off), sw128_desc(bhi + off), a.idesc, accm);
                         if (a.x3) {
-                            const uint32_t accc = (kc > 0 || kk > 0) ? 1u : 0u;
+                            const uint32_t accc = (rc > 0 || kk > 0) ? 1u : 0u;
                             tc_mma<KIND>(dcorr, sw128_desc(ahi + off), sw128_desc(blo + off), a.idesc, accc);
                             tc_mma<KIND>(dcorr, sw128_desc(alo + off), sw128_desc(bhi + off), a.idesc, 1u);
                         }
@@ -371,8 +381,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int sw = m & 7;
         int64_t it = 0;
         bool ok = true;
-        for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
-            for (int kc = 0; kc < a.nk; ++kc, ++it) {
+        const int64_t nwork = a.ntiles * a.nsk;
+        for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+            const int ks = (int)(w % a.nsk);
+            const int kc0 = ks * a.nk / a.nsk, kc1 = (ks + 1) * a.nk / a.nsk;
+            for (int kc = kc0; kc < kc1; ++kc, ++it) {
                 const int s = (int)(it % S_stg);
                 const int j = (int)(it % S_op);
                 if (!(ok = mbar_wait(stg_full(s), (uint32_t)((it / S_stg) & 1), abort_flag))) break;
@@ -432,7 +445,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         float* tb = reinterpret_cast<float*>(gbase + (epi0 - base)) + quad * 32 * EPI_STRIDE;
         int lt = 0;
         bool ok = true;
-        for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++lt) {
+        const int64_t nwork = a.ntiles * a.nsk;
+        for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++lt) {
+            const int64_t tile = w / a.nsk;
+            float* Xs = a.X + (int64_t)(w % a.nsk) * a.slice;
             const int buf = lt & 1;
             if (!(ok = mbar_wait(acc_full(buf), (uint32_t)((lt >> 1) & 1), abort_flag))) break;
             tc_fence_after();
@@ -469,7 +485,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const int64_t g = g0 + r;
                     if (g < a.PQ && col < a.R) {
                         const float4 w = *reinterpret_cast<const float4*>(tb + r * EPI_STRIDE + 4 * q);
-                        float* dst = a.X + g * (int64_t)a.R + col;
+                        float* dst = Xs + g * (int64_t)a.R + col;
                         if ((a.R & 3) == 0) {
                             *reinterpret_cast<float4*>(dst) = w;
                         } else {
@@ -608,6 +624,22 @@ void ttm_tc_plan_free(TcPlan* p) { delete p; }
 
 int ttm_tc_kind(const TcPlan* p) { return p ? p->kind : -1; }
 
+static int64_t plan_tiles(const TcPlan* pl) {
+    return pl->mode == 1 ? pl->P * (pl->Q / BM) : (pl->PQ + BM - 1) / BM;
+}
+
+int ttm_tc_splitk(const TcPlan* pl, int num_sms) {
+    // split K when the row tiles alone cannot fill the GPU and K is long enough
+    const int64_t nt = plan_tiles(pl);
+    if (pl->b_resident || nt >= 2 * (int64_t)num_sms || pl->nk < 8) return 1;
+    int nsk = (int)((4 * (int64_t)num_sms + nt - 1) / nt);
+    if (nsk > pl->nk / 4) nsk = pl->nk / 4;
+    if (nsk > 16) nsk = 16;
+    return nsk < 1 ? 1 : nsk;
+}
+
+int64_t ttm_tc_rows(const TcPlan* pl) { return pl->PQ; }
+
 template <int MODE, int KIND>
 static cudaError_t launch(const TcPlan* pl, const TcArgs& a, size_t smem, unsigned grid, cudaStream_t st) {
     cudaFuncSetAttribute(k_ttm_tc<MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -615,8 +647,29 @@ static cudaError_t launch(const TcPlan* pl, const TcArgs& a, size_t smem, unsign
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_splitk_sum(const float* __restrict__ ws, int nsk, int64_t n, float* __restrict__ out) {
+    // float4 only when every slice and the output start on 16-byte boundaries
+    const bool vec = (n % 4 == 0) && (((uintptr_t)ws | (uintptr_t)out) % 16 == 0);
+    const int64_t n4 = vec ? n / 4 : 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 acc = __ldg(reinterpret_cast<const float4*>(ws) + i);
+        for (int s = 1; s < nsk; ++s) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(ws + (int64_t)s * n) + i);
+            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+        }
+        reinterpret_cast<float4*>(out)[i] = acc;
+    }
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float acc = ws[i];
+        for (int s = 1; s < nsk; ++s) acc += ws[(int64_t)s * n + i];
+        out[i] = acc;
+    }
+}
+}  // namespace
+
 cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsigned* dev_err,
-                       cudaStream_t st) {
+                       cudaStream_t st, float* splitk_ws) {
     if (!pl) return cudaErrorInvalidValue;
     const bool bf = (prec == CP_BF16X3 || prec == CP_BF16);
     const bool tf = (prec == CP_TF32X3 || prec == CP_TF32);
@@ -651,13 +704,26 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(pl->Rpad >> 3) << 17) |
               ((uint32_t)(BM >> 4) << 24);
     a.dev_err = dev_err;
+    a.nsk = splitk_ws ? ttm_tc_splitk(pl, num_sms) : 1;
+    a.slice = pl->PQ * (int64_t)pl->R;
+    if (a.nsk > 1) a.X = splitk_ws;
     const int BK = pl->kind == 0 ? 64 : 32;
     const size_t smem = layout_bytes(pl->S_stg, pl->S_op, pl->Rpad, pl->nk, pl->b_resident, BK);
-    const unsigned grid = (unsigned)(a.ntiles < num_sms ? a.ntiles : num_sms);
+    const int64_t nwork = a.ntiles * a.nsk;
+    const unsigned grid = (unsigned)(nwork < num_sms ? nwork : num_sms);
     if (grid == 0) return cudaSuccess;
+    cudaError_t e;
     if (pl->mode == 0)
-        return pl->kind == 0 ? launch<0, 0>(pl, a, smem, grid, st) : launch<0, 1>(pl, a, smem, grid, st);
-    return pl->kind == 0 ? launch<1, 0>(pl, a, smem, grid, st) : launch<1, 1>(pl, a, smem, grid, st);
+        e = pl->kind == 0 ? launch<0, 0>(pl, a, smem, grid, st) : launch<0, 1>(pl, a, smem, grid, st);
+    else
+        e = pl->kind == 0 ? launch<1, 0>(pl, a, smem, grid, st) : launch<1, 1>(pl, a, smem, grid, st);
+    if (e != cudaSuccess || a.nsk == 1) return e;
+    const int64_t n = pl->PQ * (int64_t)pl->R;
+    int64_t blocks = (n / 4 + 255) / 256;
+    if (blocks > 4 * num_sms) blocks = 4 * num_sms;
+    if (blocks < 1) blocks = 1;
+    k_splitk_sum<<<(unsigned)blocks, 256, 0, st>>>(splitk_ws, a.nsk, n, X);
+    return cudaGetLastError();
 }
 
 }  // namespace cpk

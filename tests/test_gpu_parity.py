@@ -221,3 +221,55 @@ def test_single_product_precisions_are_reported_not_accepted(pkg, prec, lo, hi):
         assert lo < e < hi, (m, e)
     assert ctx.stats()["ttm_tensor_core"] == 2
     ctx.close()
+
+
+@pytest.mark.parametrize("dims,R", [((12, 10, 16, 8), 8), ((20, 16, 128, 12), 20), ((6, 40, 64, 9), 16)])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_dt_fused_two_level_contraction(pkg, dims, R, prec):
+    """Standard tree on tensor cores: each half's first two levels in one pass over T."""
+    Td, Tref, A0 = problem(dims, R, 33, eta=0.05)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    for n in range(len(dims)):
+        assert relerr(ctx.mttkrp(n).cpu().numpy(), co.mttkrp(Tref, A0, n)) <= 1e-5, n
+    ctx.close()
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    ctx.sweep_dt(3)
+    st = ctx.stats()
+    assert st["ttm"] == 6 and st["ttm_fused"] >= 3
+    ref = co.cp_als(Tref, A0, 3, route="dt")
+    # the fit bar is on the direct residual; Eq. (residual) subtracts nearly equal
+    # terms, so FP32-accurate MTTKRPs leave about 1e-6 of noise in it
+    _, r_direct = ctx.fit(exact=True)
+    assert abs(r_direct - co.residual_direct(Tref, ref.A)) <= FIT_TOL[prec]
+    got = np.array([t["resid"] for t in ctx.trace()])
+    assert np.abs(got - np.array(ref.resid)).max() <= 10 * FIT_TOL[prec]
+    # raw factors: ALS amplifies MTTKRP rounding by the conditioning of Gamma
+    # (two modes here are smaller than R), so only a loose check
+    for n in range(len(dims)):
+        assert relerr(ctx.get_factor(n), ref.A[n]) <= 1e-2
+    ctx.close()
+
+
+def test_large_rank_uses_fp64_factorisation(pkg):
+    """R > 128: the normal equations use the FP64 LDL^T path; results still match."""
+    dims, R = (160, 150, 140), 130
+    Td, Tref, A0 = problem(dims, R, 34, eta=0.05)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec="fp32")
+    ctx.sweep_dt(2)
+    ref = co.cp_als(Tref, A0, 2, route="dt")
+    assert ctx.stats()["solves_fp64"] == 6
+    _, r = ctx.fit(exact=True)
+    assert abs(r - co.residual_direct(Tref, ref.A)) <= 1e-6
+    ctx.close()
+
+
+def test_mixed_solve_no_fallback_on_well_conditioned(pkg):
+    dims, R = (40, 36, 44), 24
+    Td, Tref, A0 = problem(dims, R, 35, eta=0.05)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec="fp32")
+    ctx.sweep_msdt(4)
+    ref = co.cp_als(Tref, A0, 4, route="msdt")
+    assert ctx.stats()["solves_fp64"] == 0
+    for n in range(3):
+        assert relerr(ctx.get_factor(n), ref.A[n]) <= 1e-4
+    ctx.close()
