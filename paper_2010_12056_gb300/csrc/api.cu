@@ -71,6 +71,10 @@ struct cp_ctx {
 
     double *Gamma = nullptr, *L = nullptr, *invd = nullptr, *W = nullptr;
     float* Ginv = nullptr;      // FP32 Gamma^{-1} for iterative refinement
+    float* G32 = nullptr;       // FP32 copy of Gamma (input of the inverse)
+    cudaStream_t side = nullptr;            // normal-equation factorisation runs here,
+    cudaEvent_t ev_ready = nullptr, ev_chol = nullptr;  // overlapped with the MTTKRP
+    bool chol_pending = false;
     int* d_mode = nullptr;      // 0: refinement path, 1: FP64 substitution path
     double* gram_part = nullptr;
     int nchunk = 1;
@@ -339,11 +343,26 @@ cp_status grow_hist(cp_ctx* c, int nsweeps) {
     return CP_OK;
 }
 
+// Hadamard chain and factorisation of Gamma(u) (Alg. 1 line 6) on the side
+// stream: Gamma(u) needs only the Grams of the other modes, so it is enqueued
+// before the MTTKRP of update u and runs concurrently with it.
+cp_status launch_chol(cp_ctx* c, int u, bool pp, double* scal) {
+    CKCUDA(c, cudaEventRecord(c->ev_ready, c->st));
+    CKCUDA(c, cudaStreamWaitEvent(c->side, c->ev_ready, 0));
+    LAUNCH(c, cpk::chol_mixed(c->d_Slist, c->d_dSlist, c->N, u, c->R, pp ? 1 : 0, c->Gamma, c->G32, c->Ginv,
+                              c->L, c->invd, c->W, scal, c->d_mode, c->side));
+    CKCUDA(c, cudaEventRecord(c->ev_chol, c->side));
+    c->chol_pending = true;
+    return CP_OK;
+}
+
 // One factor update (Alg. 1 lines 6-9; in PP mode Alg. 2 lines 10-12 with V).
+// launch_chol(u) must have been called for this update.
 cp_status update_mode(cp_ctx* c, int u, const float* M, bool pp, double* scal) {
     const int R = c->R, s = (int)c->dims[u];
-    LAUNCH(c, cpk::chol_mixed(c->d_Slist, c->d_dSlist, c->N, u, R, pp ? 1 : 0, c->Gamma, c->Ginv, c->L,
-                              c->invd, c->W, scal, c->d_mode, c->st));
+    if (!c->chol_pending) CKST(launch_chol(c, u, pp, scal));
+    CKCUDA(c, cudaStreamWaitEvent(c->st, c->ev_chol, 0));
+    c->chol_pending = false;
     cpk::SolveOut o;
     o.A64 = c->A64[u];
     o.A32 = c->A32[u];
@@ -455,6 +474,7 @@ cp_status exact_sweep(cp_ctx* c, bool msdt, int k) {
         } else {
             path = dt_path(c->N, u0, &fuse2);
         }
+        CKST(launch_chol(c, u, false, scal_slot(c, k, u)));
         float* M = nullptr;
         CKST(mttkrp_leaf(c, path, &M, fuse2));
         CKST(update_mode(c, u, M, false, scal_slot(c, k, u)));
@@ -602,6 +622,7 @@ cp_status pp_mttkrp_impl(cp_ctx* c, int n, float* Mt) {
 
 cp_status pp_sweep(cp_ctx* c, int k) {
     for (int n = 0; n < c->N; ++n) {
+        CKST(launch_chol(c, n, true, scal_slot(c, k, n)));
         CKST(pp_mttkrp_impl(c, n, c->Mt));
         CKST(update_mode(c, n, c->Mt, true, scal_slot(c, k, n)));
     }
@@ -638,7 +659,10 @@ void free_all(cp_ctx* c) {
         c->kr_plan[i] = nullptr;
     }
     F(c->kr_hi); F(c->kr_lo); F(c->splitk_ws);
-    F(c->Ginv); F(c->d_mode);
+    F(c->Ginv); F(c->G32); F(c->d_mode);
+    if (c->side) { cudaStreamSynchronize(c->side); cudaStreamDestroy(c->side); c->side = nullptr; }
+    if (c->ev_ready) { cudaEventDestroy(c->ev_ready); c->ev_ready = nullptr; }
+    if (c->ev_chol) { cudaEventDestroy(c->ev_chol); c->ev_chol = nullptr; }
     F(c->Mt); F(c->d_Slist); F(c->d_dSlist); F(c->Gamma); F(c->L); F(c->invd); F(c->W);
     F(c->gram_part); F(c->scal_part); F(c->scal_hist); F(c->red_part); F(c->d_red_out); F(c->dev_err);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -749,6 +773,10 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
     TRYC(cudaMemcpyAsync(c->d_dSlist, c->dS, sizeof(double*) * N, cudaMemcpyHostToDevice, c->st));
     TRY(dalloc(c, &c->Gamma, RR + 2));
     TRY(dalloc(c, &c->Ginv, RR + 4));
+    TRY(dalloc(c, &c->G32, RR + 4));
+    TRYC(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    TRYC(cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming));
+    TRYC(cudaEventCreateWithFlags(&c->ev_chol, cudaEventDisableTiming));
     TRY(dalloc(c, &c->d_mode, 1));
     TRY(dalloc(c, &c->W, RR));
     TRY(dalloc(c, &c->L, 2 * (size_t)RR));
@@ -891,8 +919,9 @@ cp_status cp_pp_mttkrp(cp_ctx* c, int mode, float* M_dev) {
     if (!c->pp_valid) return CP_ESTATE;
     // first-order terms (Eq. U_ni) on top of M_p(n), then V = A(n) W (Eq. V_nij)
     CKST(pp_mttkrp_impl(c, mode, c->Mt));
-    LAUNCH(c, cpk::gamma_chol(c->d_Slist, c->d_dSlist, c->N, mode, c->R, 1, c->Gamma, c->L, c->invd,
-                              c->W, c->red_part, c->st));
+    CKST(launch_chol(c, mode, true, c->red_part));
+    CKCUDA(c, cudaStreamWaitEvent(c->st, c->ev_chol, 0));
+    c->chol_pending = false;
     LAUNCH(c, cpk::add_aw(c->Mt, c->A64[mode], c->W, (int)c->dims[mode], c->R, M_dev, c->st));
     return CP_OK;
 }

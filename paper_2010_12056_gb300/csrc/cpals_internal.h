@@ -113,7 +113,7 @@ cudaError_t solve_rows(const float* M, const double* W, const double* L, const d
 // solve_mixed then solves every row to FP64 accuracy (refinement or FP64
 // substitution).  Gamma and Ginv must have 16 spare bytes after R*R entries.
 cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
-                       double* Gamma, float* Ginv, double* L64, double* invd64, double* W,
+                       double* Gamma, float* G32, float* Ginv, double* L64, double* invd64, double* W,
                        double* scal, int* mode, cudaStream_t st);
 cudaError_t solve_mixed(const float* M, const double* W, const double* Gamma, const float* Ginv,
                         const double* L64, const double* invd64, const int* mode, const SolveOut& o,

@@ -183,34 +183,52 @@ __global__ void __launch_bounds__(1024) k_chol_fp64only(double* const* __restric
     }
 }
 
-// R <= 128.  Warp w owns rows w, w + 32, ... (at most 4); lane l owns columns
-// l + 32 t (t < RT).  Gauss-Jordan on register-resident rows; the pivot row of
-// the next step is published in one of two shared rows, one barrier per step.
-template <int RT>
-__global__ void __launch_bounds__(1024) k_chol_mixed(double* const* __restrict__ S_list,
-                                                     double* const* __restrict__ dS_list, int N,
-                                                     int n, int R, int pp, double* __restrict__ G,
-                                                     float* __restrict__ Ginv,
-                                                     double* __restrict__ L64,
-                                                     double* __restrict__ invd64,
-                                                     double* __restrict__ W,
-                                                     double* __restrict__ scal,
-                                                     int* __restrict__ mode) {
-    constexpr int RPW = 4;
-    __shared__ double red[32];
-    __shared__ double sinv[CP_MAXR], srs[CP_MAXR];
-    __shared__ float prow[2][MIXED_MAXR];
-    __shared__ int sfail;
-    __shared__ float pmin, pmax;
-    __shared__ unsigned gmax_bits, imax_bits;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-    const int RR = R * R;
+// Gamma (FP64), its FP32 copy and PP's W, one entry per thread over many
+// blocks: FP64 throughput per SM is low, so this work is spread over the GPU.
+__global__ void __launch_bounds__(256) k_gamma_form(double* const* __restrict__ S_list,
+                                                    double* const* __restrict__ dS_list, int N,
+                                                    int n, int R, int pp, double* __restrict__ G,
+                                                    float* __restrict__ G32,
+                                                    double* __restrict__ W) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= R * R) return;
     const double* Sp[CP_MAXN];
     const double* dSp[CP_MAXN];
     for (int k = 0; k < N; ++k) {
         Sp[k] = S_list[k];
         dSp[k] = pp ? dS_list[k] : nullptr;
     }
+    double w = 0.0;
+    const double g = gamma_entry(Sp, dSp, N, n, pp, (size_t)e, &w);
+    G[e] = g;
+    G32[e] = (float)g;
+    if (pp) W[e] = w;
+}
+
+// R <= 128, 256 threads.  Warp w owns rows w, w + 8, ... (RPW = 16 at most);
+// lane l owns columns l + 32 t (t < RT).  Gauss-Jordan on register-resident
+// rows; the pivot row of the next step is published in one of two shared rows,
+// one barrier per step.  Few warps with many rows each keep the per-step
+// overhead (pivot, reciprocal, broadcast) small against the R^2 updates.
+constexpr int CHOL_THREADS = 256;
+constexpr int CHOL_RPW = MIXED_MAXR / (CHOL_THREADS / 32);
+
+template <int RT>
+__global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_mixed(const float* __restrict__ G32, int R,
+                                                             const double* __restrict__ G,
+                                                             float* __restrict__ Ginv,
+                                                             double* __restrict__ L64,
+                                                             double* __restrict__ invd64,
+                                                             double* __restrict__ scal,
+                                                             int* __restrict__ mode) {
+    __shared__ double red[32];
+    __shared__ double sinv[CP_MAXR], srs[CP_MAXR];
+    __shared__ float prow[2][MIXED_MAXR];
+    __shared__ int sfail;
+    __shared__ float pmin, pmax;
+    __shared__ unsigned gmax_bits, imax_bits;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = CHOL_THREADS / 32;
+    const int RR = R * R;
     if (tid == 0) {
         sfail = 0;
         pmin = 3.0e38f;
@@ -218,29 +236,28 @@ __global__ void __launch_bounds__(1024) k_chol_mixed(double* const* __restrict__
         gmax_bits = 0u;
         imax_bits = 0u;
     }
-    for (int j = tid; j < 2 * MIXED_MAXR; j += blockDim.x) (&prow[0][0])[j] = 0.f;
-    float a[RPW][RT];
-    double tr = 0.0;
+    for (int j = tid; j < 2 * MIXED_MAXR; j += CHOL_THREADS) (&prow[0][0])[j] = 0.f;
     __syncthreads();
+    float a[CHOL_RPW][RT];
+    double tr = 0.0;
+    // rows of Gamma (FP32 copy from k_gamma_form), all loads first
 #pragma unroll
-    for (int s = 0; s < RPW; ++s) {
-        const int i = warp + nw * s;
-        float rowabs = 0.f;
+    for (int sl = 0; sl < CHOL_RPW; ++sl) {
+        const int i = warp + nw * sl;
 #pragma unroll
         for (int t = 0; t < RT; ++t) {
             const int j = lane + 32 * t;
-            float v = 0.f;
-            if (i < R && j < R) {
-                const size_t e = (size_t)i * R + j;
-                double w = 0.0;
-                const double g = gamma_entry(Sp, dSp, N, n, pp, e, &w);
-                G[e] = g;
-                if (pp) W[e] = w;
-                if (i == j) tr += g;
-                v = (float)g;
-                rowabs += fabsf(v);
-            }
-            a[s][t] = v;
+            a[sl][t] = (i < R && j < R) ? __ldg(G32 + (size_t)i * R + j) : 0.f;
+        }
+    }
+#pragma unroll
+    for (int sl = 0; sl < CHOL_RPW; ++sl) {
+        const int i = warp + nw * sl;
+        float rowabs = 0.f;
+#pragma unroll
+        for (int t = 0; t < RT; ++t) {
+            rowabs += fabsf(a[sl][t]);
+            if (i == lane + 32 * t && i < R) tr += (double)G[(size_t)i * R + i];
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) rowabs += __shfl_xor_sync(FULL, rowabs, o);
@@ -265,32 +282,25 @@ __global__ void __launch_bounds__(1024) k_chol_mixed(double* const* __restrict__
             pmin = fminf(pmin, p);
             pmax = fmaxf(pmax, p);
         }
-        const float inv = 1.f / p;
+        const float inv = __frcp_rn(p);
         float pv[RT];
 #pragma unroll
-        for (int t = 0; t < RT; ++t) pv[t] = pk[lane + 32 * t < MIXED_MAXR ? lane + 32 * t : 0];
+        for (int t = 0; t < RT; ++t) pv[t] = pk[lane + 32 * t];
         const int kt = k >> 5, kl = k & 31;
 #pragma unroll
-        for (int s = 0; s < RPW; ++s) {
-            const int i = warp + nw * s;
-            if (i >= R) continue;  // warp-uniform
-            float aik = 0.f;
+        for (int sl = 0; sl < CHOL_RPW; ++sl) {
+            const int i = warp + nw * sl;  // rows past R hold zeros and stay zero
+            float aik = a[sl][0];
 #pragma unroll
-            for (int t = 0; t < RT; ++t)
-                if (t == kt) aik = a[s][t];
+            for (int t = 1; t < RT; ++t)
+                if (t == kt) aik = a[sl][t];
             const float f = __shfl_sync(FULL, aik, kl) * inv;
             if (i == k) {
 #pragma unroll
-                for (int t = 0; t < RT; ++t) {
-                    const int j = lane + 32 * t;
-                    a[s][t] = (j == k) ? inv : pv[t] * inv;
-                }
+                for (int t = 0; t < RT; ++t) a[sl][t] = (lane + 32 * t == k) ? inv : pv[t] * inv;
             } else {
 #pragma unroll
-                for (int t = 0; t < RT; ++t) {
-                    const int j = lane + 32 * t;
-                    a[s][t] = (j == k) ? -f : fmaf(-f, pv[t], a[s][t]);
-                }
+                for (int t = 0; t < RT; ++t) a[sl][t] = (lane + 32 * t == k) ? -f : fmaf(-f, pv[t], a[sl][t]);
             }
         }
         // the owner of row k+1 publishes it for the next step
@@ -299,11 +309,11 @@ __global__ void __launch_bounds__(1024) k_chol_mixed(double* const* __restrict__
             const int s1 = k1 / nw;
             float* dst = prow[k1 & 1];
 #pragma unroll
-            for (int s = 0; s < RPW; ++s)
-                if (s == s1) {
+            for (int sl = 0; sl < CHOL_RPW; ++sl)
+                if (sl == s1) {
 #pragma unroll
                     for (int t = 0; t < RT; ++t)
-                        if (lane + 32 * t < R) dst[lane + 32 * t] = a[s][t];
+                        if (lane + 32 * t < R) dst[lane + 32 * t] = a[sl][t];
                 }
         }
         __syncthreads();
@@ -313,11 +323,11 @@ __global__ void __launch_bounds__(1024) k_chol_mixed(double* const* __restrict__
     if (!use64) {
         // ||Gamma||_inf ||G32||_inf: refinement contracts by about kappa 2^-24 per step
 #pragma unroll
-        for (int s = 0; s < RPW; ++s) {
-            const int i = warp + nw * s;
+        for (int sl = 0; sl < CHOL_RPW; ++sl) {
+            const int i = warp + nw * sl;
             float rowabs = 0.f;
 #pragma unroll
-            for (int t = 0; t < RT; ++t) rowabs += fabsf(a[s][t]);
+            for (int t = 0; t < RT; ++t) rowabs += fabsf(a[sl][t]);
 #pragma unroll
             for (int o = 16; o; o >>= 1) rowabs += __shfl_xor_sync(FULL, rowabs, o);
             if (lane == 0 && i < R) atomicMax(&imax_bits, __float_as_uint(rowabs));
@@ -336,13 +346,13 @@ __global__ void __launch_bounds__(1024) k_chol_mixed(double* const* __restrict__
         return;
     }
 #pragma unroll
-    for (int s = 0; s < RPW; ++s) {
-        const int i = warp + nw * s;
-        if (i >= R) continue;
+    for (int sl = 0; sl < CHOL_RPW; ++sl) {
+        const int i = warp + nw * sl;
+        if (i >= R) break;
 #pragma unroll
         for (int t = 0; t < RT; ++t) {
             const int j = lane + 32 * t;
-            if (j < R) Ginv[(size_t)i * R + j] = a[s][t];
+            if (j < R) Ginv[(size_t)i * R + j] = a[sl][t];
         }
     }
     if (tid == 0) {
@@ -720,17 +730,18 @@ cudaError_t launch_solve_mixed(const float* M, const double* W, const double* G,
 namespace cpk {
 
 cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
-                       double* Gamma, float* Ginv, double* L64, double* invd64, double* W,
+                       double* Gamma, float* G32, float* Ginv, double* L64, double* invd64, double* W,
                        double* scal, int* mode, cudaStream_t st) {
     if (R > MIXED_MAXR) {
         k_chol_fp64only<<<1, 1024, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, L64, invd64, W, scal, mode);
         return cudaGetLastError();
     }
+    k_gamma_form<<<(R * R + 255) / 256, 256, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, G32, W);
     switch ((R + 31) / 32) {
-        case 1: k_chol_mixed<1><<<1, 1024, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, Ginv, L64, invd64, W, scal, mode); break;
-        case 2: k_chol_mixed<2><<<1, 1024, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, Ginv, L64, invd64, W, scal, mode); break;
-        case 3: k_chol_mixed<3><<<1, 1024, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, Ginv, L64, invd64, W, scal, mode); break;
-        default: k_chol_mixed<4><<<1, 1024, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, Ginv, L64, invd64, W, scal, mode); break;
+        case 1: k_chol_mixed<1><<<1, CHOL_THREADS, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode); break;
+        case 2: k_chol_mixed<2><<<1, CHOL_THREADS, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode); break;
+        case 3: k_chol_mixed<3><<<1, CHOL_THREADS, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode); break;
+        default: k_chol_mixed<4><<<1, CHOL_THREADS, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode); break;
     }
     return cudaGetLastError();
 }
