@@ -200,6 +200,36 @@ typedef struct {
 } cp_stats;
 cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
 
+/*
+ * cp_resid_noalloc - the direct residual of cp_fit(exact = 1) for callers that
+ * cannot allocate device memory when they need it: programs whose own memory
+ * pool has reserved the GPU (a raw cudaMalloc would fail or fragment it) and
+ * latency-critical loops where cudaMalloc/cudaFree would synchronise the device.
+ * The paper has no counterpart; this is a library convenience.
+ *   N, dims, R  as in cp_init (3 <= N <= 8, 1 <= R <= 256).
+ *   T_dev       FP32 tensor, C order, device.
+ *   A_dev       host array of N device pointers to FP32 factors (s_n x R,
+ *               row-major).
+ *   out_dev     device buffer of 2 doubles: out[0] = ||T - [[A]]||_F^2,
+ *               out[1] = ||T||_F^2; the relative residual is sqrt(out[0]/out[1]).
+ *   stream      cudaStream_t (as void*) the two kernels are enqueued on; the
+ *               call does not synchronise.
+ * It allocates nothing: its scratch (one partial sum per 64 x 64 tile of T seen
+ * as (modes 0..N-2) x mode N-1) is a fixed array of 2 x 65536 doubles (1 MiB) in
+ * the library's device memory, held by every GPU that loads the library until
+ * the process exits.  Tensors needing more than 65536 tiles are rejected with
+ * CP_EINVAL (for example 128^4 fits exactly, 1024^3 does not).  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current, so make that first call before any stream capture.  All
+ * calls share the array, and it keeps the last call's contents (each call writes
+ * every slot it reads, so nothing needs clearing): calls that overlap on the GPU,
+ * on different streams or devices' threads sharing a context, race and must be
+ * serialised by the caller.  Returns CP_EINVAL on bad arguments, CP_ECUDA if a
+ * CUDA call fails.
+ */
+cp_status cp_resid_noalloc(int N, const int64_t *dims, int R, const float *T_dev,
+                           const float *const *A_dev, double *out_dev, void *stream);
+
 /* Description of the first failure of this context ("" if none); never NULL. */
 const char *cp_last_error(const cp_ctx *ctx);
 

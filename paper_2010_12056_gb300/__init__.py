@@ -82,6 +82,7 @@ _SIGS = {
     "cp_policy_grad": (_I, [_P, _P, _P, _I, _P, _P]),
     "cp_policy_train": (_I, [_P, _P, _P, _I, _I, ctypes.c_float]),
     "cp_policy_free": (None, [_P]),
+    "cp_resid_noalloc": (_I, [_I, ctypes.POINTER(ctypes.c_int64), _I, _P, ctypes.POINTER(_P), _P, _P]),
 }
 
 
@@ -242,6 +243,23 @@ class CPContext:
         s = Stats()
         self._ck(self._L.cp_get_stats(self._h, ctypes.byref(s)))
         return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+
+def resid_noalloc(T, factors, out, stream=None):
+    """cp_resid_noalloc: out[0] = ||T - [[A]]||^2, out[1] = ||T||^2 (no device allocation).
+
+    T: contiguous float32 CUDA tensor; factors: float32 CUDA tensors (s_n x R);
+    out: float64 CUDA tensor with 2 elements.  Enqueued on `stream` (default: the
+    current torch stream); does not synchronise.
+    """
+    L = lib()
+    N = T.dim()
+    R = int(factors[0].shape[1])
+    dims = (ctypes.c_int64 * N)(*[int(d) for d in T.shape])
+    ptrs = (ctypes.c_void_p * N)(*[f.data_ptr() for f in factors])
+    st = L.cp_resid_noalloc(N, dims, R, _dptr(T), ptrs, _dptr(out), _stream_ptr(stream))
+    if st != 0:
+        raise CPError(st, "cp_resid_noalloc failed")
 
 
 class Policy:
