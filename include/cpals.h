@@ -64,7 +64,7 @@ typedef struct {
     double delta;     /* stopping tolerance on |r - r_old| (Alg. 1); <= 0: never  */
     int max_sweeps;   /* cap used by cp_run (<= 0: no cap)                        */
     int judge_every;  /* policy mode: direct residual every k sweeps (0 = off)    */
-    int use_policy;   /* reserved: the policy is passed to cp_sweep_pp            */
+    int use_policy;   /* unused: a policy is passed to cp_sweep_pp directly       */
     uint64_t seed;    /* Philox4x32-10 seed of the default U[0,1) initial factors */
 } cp_config;
 
@@ -130,14 +130,65 @@ cp_status cp_sweep_msdt(cp_ctx *ctx, int nsweeps);
  * operators M_p(i,j), M_p(n) built at the PP initialization (not counted as a
  * sweep); otherwise a regular MSDT sweep runs and dA(i) is that sweep's change.
  *   eps     PP tolerance, 0 < eps < 1.
- *   policy  NULL: the rule above.  Otherwise a cp_policy from cp_policy_create:
- *           its network decides, before each sweep, between an approximated
- *           sweep, a rebuild of the operators, and a regular sweep; a direct
- *           residual every cfg.judge_every sweeps rolls back any sweep that
- *           raised it.
+ *   policy  NULL: the rule above.  Otherwise a cp_policy from cp_policy_create
+ *           (no counterpart in the paper): before each sweep its network scores
+ *           two choices from the features of cp_policy_features - an
+ *           approximated sweep with the current operators (p_cur) and one with
+ *           operators rebuilt now (p_new).  The sweep is approximated with the
+ *           current operators if they exist and p_cur >= 0.5, else rebuilt and
+ *           approximated if p_new >= 0.5, else regular (MSDT).  Every
+ *           cfg.judge_every sweeps (the judge; 0 = never) the direct residual
+ *           is computed; if it exceeds (1 + 1e-8) times the previous judged
+ *           value, the factors return to their state at that judgement, the
+ *           operators are dropped, the undone sweeps stay in the trace with
+ *           rolled_back = 1, and the rule above decides the next judge_every
+ *           sweeps.  The judge's time is added to the sweep it follows.
  */
 typedef struct cp_policy cp_policy;
 cp_status cp_sweep_pp(cp_ctx *ctx, int nsweeps, double eps, cp_policy *policy);
+
+/*
+ * cp_policy_features - the 8 inputs of the PP policy network for the current
+ * state (no counterpart in the paper), twice: f16[0..7] for an approximated
+ * sweep with the current operators, f16[8..15] as if the operators were
+ * rebuilt now.  L(x) = log10(clamp(x, 1e-12, 1)) / 6 + 1 maps [1e-12, 1] to
+ * [-1, 1]; "last" is the newest trace record, r its residual, r' the one before.
+ *   f0  min(3, sweeps done / 100)
+ *   f1  L(last max_rel_step)                  (1 before any sweep)
+ *   f2  L(max_i ||A(i) - A_p(i)|| / ||A(i)||) with operators; -1 without
+ *       operators and in the rebuilt query
+ *   f3  L(|r - r'| / r)
+ *   f4  L(r)
+ *   f5  min(3, approximated sweeps since the operators were built / 10);
+ *       3 without operators, 0 in the rebuilt query
+ *   f6  1 if the last sweep was approximated, else 0
+ *   f7  L(last v_share) if the last sweep was approximated and not in the
+ *       rebuilt query, else -1
+ */
+cp_status cp_policy_features(cp_ctx *ctx, float *f16);
+
+/*
+ * cp_pp_probe - one sweep step that also labels the PP choices (no counterpart
+ * in the paper; it produces the policy's training data).  From the current
+ * state it runs, each from the same starting factors: an approximated sweep
+ * with the current operators (if any), a regular MSDT sweep, and an operator
+ * rebuild followed by an approximated sweep, and evaluates the direct residual
+ * (Eq. residual-def) before and after each.  An approximated choice is labelled
+ * safe when r_pp - r_exact <= 0.1 max(0, r0 - r_exact) + 1e-9 r0, i.e. it
+ * keeps at least 90% of the regular sweep's decrease.  The context then
+ * continues along `follow`: 0 regular, 1 current operators (CP_EINVAL without
+ * operators), 2 rebuilt, -1 the cheapest safe choice (current, else rebuilt,
+ * else regular).  The trace gets one record (decided_by 3).  A second operator
+ * set is allocated on first use.
+ */
+typedef struct {
+    float feat_cur[8], feat_new[8];  /* cp_policy_features before the step     */
+    double r0;                       /* direct residual before                  */
+    double r_exact, r_cur, r_new;    /* after each branch (r_cur NaN w/o ops)   */
+    double ms_exact, ms_cur, ms_new; /* device time of each branch              */
+    int32_t has_ops, label_cur, label_new, followed;
+} cp_probe_rec;
+cp_status cp_pp_probe(cp_ctx *ctx, int follow, cp_probe_rec *out);
 
 /*
  * cp_pp_init / cp_pp_mttkrp - the two PP steps exposed separately.  cp_pp_init
@@ -173,7 +224,13 @@ typedef struct {
     double max_rel_step;  /* max_i ||A(i)_after - A(i)_before||_F / ||A(i)||_F    */
     double max_rel_dAp;   /* max_i ||A(i) - A_p(i)||_F / ||A(i)||_F (0 if no ops)  */
     double v_share;       /* ||V(N-1)||_F / ||M~(N-1)||_F in PP sweeps, else 0    */
-    double ms;            /* device time of the sweep (CUDA events)               */
+    double ms;            /* device time of the sweep (CUDA events), including
+                             its operator build and, with a policy, the network
+                             query and the judge                               */
+    float p_cur, p_new;   /* policy scores before the sweep (-1: not queried)     */
+    int32_t decided_by;   /* 0 eps rule, 1 policy network, 2 eps rule after a
+                             rollback, 3 cp_pp_probe                            */
+    int32_t reserved;
 } cp_trace_rec;
 
 /* Copy up to *len records into buf (may be NULL); *len returns the total count. */
@@ -197,6 +254,7 @@ typedef struct {
                                the Khatri-Rao operand (standard tree)         */
     int64_t solves_fp64;    /* updates whose normal equations needed the FP64
                                factorisation (ill-conditioned Gamma)          */
+    int64_t rollbacks;      /* policy judge rollbacks                         */
 } cp_stats;
 cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
 

@@ -42,7 +42,17 @@ class TraceRec(ctypes.Structure):
     _fields_ = [("sweep", ctypes.c_int32), ("kind", ctypes.c_int32), ("pp_init", ctypes.c_int32),
                 ("rolled_back", ctypes.c_int32), ("resid", ctypes.c_double),
                 ("max_rel_step", ctypes.c_double), ("max_rel_dAp", ctypes.c_double),
-                ("v_share", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("v_share", ctypes.c_double), ("ms", ctypes.c_double),
+                ("p_cur", ctypes.c_float), ("p_new", ctypes.c_float),
+                ("decided_by", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ProbeRec(ctypes.Structure):
+    _fields_ = [("feat_cur", ctypes.c_float * 8), ("feat_new", ctypes.c_float * 8),
+                ("r0", ctypes.c_double), ("r_exact", ctypes.c_double), ("r_cur", ctypes.c_double),
+                ("r_new", ctypes.c_double), ("ms_exact", ctypes.c_double), ("ms_cur", ctypes.c_double),
+                ("ms_new", ctypes.c_double), ("has_ops", ctypes.c_int32), ("label_cur", ctypes.c_int32),
+                ("label_new", ctypes.c_int32), ("followed", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -52,7 +62,7 @@ class Stats(ctypes.Structure):
                 ("mttv_flops", ctypes.c_double), ("pp_flops", ctypes.c_double),
                 ("ttm_bytes", ctypes.c_double), ("mttv_bytes", ctypes.c_double),
                 ("ttm_tensor_core", ctypes.c_int64), ("ttm_fused", ctypes.c_int64),
-                ("solves_fp64", ctypes.c_int64)]
+                ("solves_fp64", ctypes.c_int64), ("rollbacks", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -68,6 +78,8 @@ _SIGS = {
     "cp_sweep_msdt": (_I, [_P, _I]),
     "cp_sweep_pp": (_I, [_P, _I, _D, _P]),
     "cp_pp_init": (_I, [_P]),
+    "cp_pp_probe": (_I, [_P, _I, ctypes.POINTER(ProbeRec)]),
+    "cp_policy_features": (_I, [_P, ctypes.POINTER(ctypes.c_float)]),
     "cp_pp_mttkrp": (_I, [_P, _I, _P]),
     "cp_fit": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "cp_get_factor": (_I, [_P, _I, ctypes.POINTER(_D)]),
@@ -236,8 +248,25 @@ class CPContext:
             out.append({"sweep": r.sweep, "kind": KINDS.get(r.kind, r.kind), "pp_init": r.pp_init,
                         "rolled_back": r.rolled_back, "resid": r.resid,
                         "max_rel_step": r.max_rel_step, "max_rel_dAp": r.max_rel_dAp,
-                        "v_share": r.v_share, "ms": r.ms})
+                        "v_share": r.v_share, "ms": r.ms, "p_cur": r.p_cur, "p_new": r.p_new,
+                        "decided_by": r.decided_by})
         return out
+
+    def policy_features(self):
+        """cp_policy_features: (current-operator features, rebuilt-operator features), 8 each."""
+        f = (ctypes.c_float * 16)()
+        self._ck(self._L.cp_policy_features(self._h, f))
+        a = np.array(f[:], dtype=np.float32)
+        return a[:8], a[8:]
+
+    def probe(self, follow=-1):
+        """cp_pp_probe: run the three PP choices from this state, keep `follow` (-1 cheapest safe)."""
+        r = ProbeRec()
+        self._ck(self._L.cp_pp_probe(self._h, int(follow), ctypes.byref(r)))
+        return {"feat_cur": np.array(r.feat_cur[:], np.float32), "feat_new": np.array(r.feat_new[:], np.float32),
+                "r0": r.r0, "r_exact": r.r_exact, "r_cur": r.r_cur, "r_new": r.r_new,
+                "ms_exact": r.ms_exact, "ms_cur": r.ms_cur, "ms_new": r.ms_new, "has_ops": r.has_ops,
+                "label_cur": r.label_cur, "label_new": r.label_new, "followed": r.followed}
 
     def stats(self):
         s = Stats()

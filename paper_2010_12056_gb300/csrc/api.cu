@@ -77,6 +77,8 @@ struct cp_ctx {
     bool chol_pending = false;
     int* d_mode = nullptr;      // 0: refinement path, 1: FP64 substitution path
     double* gram_part = nullptr;
+    double* tile_gs = nullptr;     // per-tile <Gamma, S> of the fused Gram kernel
+    unsigned* gram_cnt = nullptr;  // its completion counters (zero between launches)
     int nchunk = 1;
     double* scal_part = nullptr;
     double* scal_hist = nullptr;   // [cap][N][CP_NSCAL]
@@ -96,17 +98,45 @@ struct cp_ctx {
     float* splitk_ws = nullptr;
     bool fuse_dt = true;
 
-    // PP state
-    bool pp_alloc = false, pp_valid = false;
+    // PP state.  An operator set is A_p with the M_p(i,j) and M_p(n) built from
+    // it; pair/Mp/Ap64 point into the current set.  A second set is allocated
+    // only for branch probing, where a rebuild writes the idle set so that the
+    // operators of the starting state survive.
+    bool pp_alloc = false, pp_valid = false, ops2 = false;
+    int ops = 0;
+    float* pairset[2][CP_MAXN][CP_MAXN] = {{{0}}};
+    float* Mpset[2][CP_MAXN] = {{0}};
+    double* Apset[2][CP_MAXN] = {{0}};
     float* pair[CP_MAXN][CP_MAXN] = {{0}};
     float* Mp[CP_MAXN] = {0};
     float* Mt = nullptr;
     double dA_rel[CP_MAXN];  // ||dA(i)|| / ||A(i)|| as Alg. 2 tests it
+    int since_init = 0;      // approximated sweeps since the operators were built
 
     int64_t t_msdt = 0;
     int sweeps_done = 0;
     bool have_last = false;
     double last_resid = 1.0;
+    // factor versions come from one clock, so a version number names one factor
+    // value for the life of the context (restored snapshots keep cache keys sound)
+    int vclock = 0;
+
+    // state snapshots: [0] branch probing, [1] the policy judge's rollback point
+    struct Snap {
+        bool have = false;
+        double* A64[CP_MAXN] = {0};
+        int ver[CP_MAXN] = {0};
+        bool pp_valid = false;
+        int ops = 0, since_init = 0, sweeps_done = 0;
+        double dA_rel[CP_MAXN] = {0};
+        int64_t t_msdt = 0;
+        bool have_last = false;
+        double last_resid = 1.0;
+        size_t trace_len = 0;
+    } snap[2];
+    float* pol_io = nullptr;   // device: 16 policy features + 2 scores
+    double judge_r = -1.0;     // direct residual at the judge's rollback point
+    int since_judge = 0, fallback_left = 0;
 
     std::vector<cp_trace_rec> trace;
     std::vector<double> last_hist;   // host copy of the last harvested scalars
@@ -378,10 +408,9 @@ cp_status update_mode(cp_ctx* c, int u, const float* M, bool pp, double* scal) {
     LAUNCH(c, cpk::solve_mixed(M, pp ? c->W : nullptr, c->Gamma, c->Ginv, c->L, c->invd, c->d_mode, o, s, R, scal,
                                c->scal_part, &nblk, c->dev_err, c->st));
     const int nchunk = std::max(1, std::min(c->nchunk, (s + 15) / 16));
-    LAUNCH(c, cpk::gram_partials(c->A64[u], pp ? c->dA64[u] : nullptr, s, R, c->gram_part, nchunk, c->st));
-    LAUNCH(c, cpk::finalize_update(c->gram_part, nchunk, c->scal_part, nblk, c->Gamma, R, pp ? 1 : 0,
-                                   c->S[u], c->dS[u], scal, c->st));
-    c->ver[u]++;
+    LAUNCH(c, cpk::gram_update(c->A64[u], pp ? c->dA64[u] : nullptr, s, R, c->gram_part, nchunk, c->scal_part,
+                               nblk, c->Gamma, c->S[u], c->dS[u], scal, c->tile_gs, c->gram_cnt, c->st));
+    c->ver[u] = ++c->vclock;
     return CP_OK;
 }
 
@@ -407,6 +436,7 @@ cp_status harvest(cp_ctx* c, int k, const int* kinds, const int* inits, int firs
         rec.sweep = c->sweeps_done + i;
         rec.kind = kinds[i];
         rec.pp_init = inits ? inits[i] : 0;
+        rec.p_cur = rec.p_new = -1.f;
         const double r2 = c->normT2 + last[SCAL_GS] - 2.0 * last[SCAL_MA];
         rec.resid = sqrt(r2 > 0 ? r2 : 0.0) / sqrt(c->normT2);
         double mx = 0.0, mxp = 0.0;
@@ -484,19 +514,46 @@ cp_status exact_sweep(cp_ctx* c, bool msdt, int k) {
 }
 
 // ------------------------------------------------------------------ PP
+void use_ops(cp_ctx* c, int k) {
+    c->ops = k;
+    for (int i = 0; i < CP_MAXN; ++i) {
+        c->Ap64[i] = c->Apset[k][i];
+        c->Mp[i] = c->Mpset[k][i];
+        for (int j = 0; j < CP_MAXN; ++j) c->pair[i][j] = c->pairset[k][i][j];
+    }
+}
+
+cp_status alloc_ops(cp_ctx* c, int k) {
+    const int N = c->N, R = c->R;
+    for (int i = 0; i < N; ++i) {
+        CKST(dalloc(c, &c->Apset[k][i], (size_t)c->dims[i] * R));
+        CKST(dalloc(c, &c->Mpset[k][i], (size_t)c->dims[i] * R));
+        for (int j = i + 1; j < N; ++j)
+            CKST(dalloc(c, &c->pairset[k][i][j], (size_t)c->dims[i] * c->dims[j] * R));
+    }
+    return CP_OK;
+}
+
 cp_status pp_alloc(cp_ctx* c) {
     if (c->pp_alloc) return CP_OK;
     const int N = c->N, R = c->R;
+    CKST(alloc_ops(c, 0));
+    use_ops(c, 0);
     for (int i = 0; i < N; ++i) {
-        CKST(dalloc(c, &c->Ap64[i], (size_t)c->dims[i] * R));
         CKST(dalloc(c, &c->dA32[i], (size_t)c->dims[i] * R));
         CKST(dalloc(c, &c->dA64[i], (size_t)c->dims[i] * R));
-        CKST(dalloc(c, &c->Mp[i], (size_t)c->dims[i] * R));
-        for (int j = i + 1; j < N; ++j)
-            CKST(dalloc(c, &c->pair[i][j], (size_t)c->dims[i] * c->dims[j] * R));
     }
     CKST(dalloc(c, &c->Mt, (size_t)c->smax * R));
     c->pp_alloc = true;
+    return CP_OK;
+}
+
+// second operator set, for probing (a rebuild then writes the idle set)
+cp_status pp_alloc2(cp_ctx* c) {
+    CKST(pp_alloc(c));
+    if (c->ops2) return CP_OK;
+    CKST(alloc_ops(c, 1));
+    c->ops2 = true;
     return CP_OK;
 }
 
@@ -544,6 +601,7 @@ std::vector<int> pp_pair_path(int N, int a, int b) {
 
 cp_status pp_init_impl(cp_ctx* c) {
     CKST(pp_alloc(c));
+    if (c->ops2) use_ops(c, c->ops ^ 1);
     const int N = c->N, R = c->R;
     for (int i = 0; i < N; ++i) {
         CKCUDA(c, cudaMemcpyAsync(c->Ap64[i], c->A64[i], sizeof(double) * c->dims[i] * R, cudaMemcpyDeviceToDevice, c->st));
@@ -598,6 +656,7 @@ cp_status pp_init_impl(cp_ctx* c) {
         CKST(launch_mttv(c, c->pair[a][b], mask, i, c->Mp[n]));
     }
     c->pp_valid = true;
+    c->since_init = 0;
     c->stats.pp_init++;
     for (int i = 0; i < N; ++i) c->dA_rel[i] = 0.0;
     return CP_OK;
@@ -636,10 +695,179 @@ cp_status init_grams(cp_ctx* c) {
         LAUNCH(c, cpk::factor_copies(c->A64[n], c->A32[n], c->bhi[n], c->blo[n], c->bt32[n], s, c->R,
                                      c->Rpad, c->Kpad[n], c->st));
         const int nchunk = std::max(1, std::min(c->nchunk, (s + 15) / 16));
-        LAUNCH(c, cpk::gram_partials(c->A64[n], nullptr, s, c->R, c->gram_part, nchunk, c->st));
-        LAUNCH(c, cpk::finalize_update(c->gram_part, nchunk, c->scal_part, 0, nullptr, c->R, 0, c->S[n],
-                                       nullptr, c->red_part, c->st));
+        LAUNCH(c, cpk::gram_update(c->A64[n], nullptr, s, c->R, c->gram_part, nchunk, c->scal_part, 0, nullptr,
+                                   c->S[n], nullptr, c->red_part, c->tile_gs, c->gram_cnt, c->st));
     }
+    return CP_OK;
+}
+
+// ||T - [[A]]||_F / ||T||_F (Eq. residual-def), one streaming pass over T
+cp_status direct_resid(cp_ctx* c, double* r) {
+    cpk::ResidArgs a;
+    memset(&a, 0, sizeof(a));
+    a.T = c->T;
+    a.N = c->N;
+    a.R = c->R;
+    for (int i = 0; i < c->N; ++i) {
+        a.A32[i] = c->A32[i];
+        a.dims[i] = c->dims[i];
+    }
+    c->stats.launches += 2;
+    int nb = cpk::resid_direct_partials(a, c->red_part, 4096, c->st);
+    CKCUDA(c, cudaGetLastError());
+    CKCUDA(c, cpk::sum_partials(c->red_part, nb, c->d_red_out, c->st));
+    double s2 = 0.0;
+    CKCUDA(c, cudaMemcpyAsync(&s2, c->d_red_out, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CKCUDA(c, cudaStreamSynchronize(c->st));
+    *r = sqrt(s2 > 0 ? s2 : 0.0) / sqrt(c->normT2);
+    if (!isfinite(*r)) return fail(c, CP_ENUMERIC, "non-finite residual");
+    return CP_OK;
+}
+
+// S(i) (and dS(i) when `pp`) from the factors now in A64 (and dA64)
+cp_status regram(cp_ctx* c, int i, bool pp) {
+    const int s = (int)c->dims[i];
+    const int nchunk = std::max(1, std::min(c->nchunk, (s + 15) / 16));
+    LAUNCH(c, cpk::gram_update(c->A64[i], pp ? c->dA64[i] : nullptr, s, c->R, c->gram_part, nchunk, c->scal_part,
+                               0, nullptr, c->S[i], c->dS[i], c->red_part, c->tile_gs, c->gram_cnt, c->st));
+    return CP_OK;
+}
+
+// Snapshot of the iteration state at a sweep boundary: factors (device copies)
+// and the host-side schedule state.  Intermediates are not copied: their cache
+// keys are factor versions, restored with the factors.
+cp_status snap_take(cp_ctx* c, cp_ctx::Snap& sn) {
+    for (int i = 0; i < c->N; ++i) {
+        if (!sn.A64[i]) CKST(dalloc(c, &sn.A64[i], (size_t)c->dims[i] * c->R));
+        CKCUDA(c, cudaMemcpyAsync(sn.A64[i], c->A64[i], sizeof(double) * c->dims[i] * c->R,
+                                  cudaMemcpyDeviceToDevice, c->st));
+        sn.ver[i] = c->ver[i];
+        sn.dA_rel[i] = c->dA_rel[i];
+    }
+    sn.pp_valid = c->pp_valid;
+    sn.ops = c->ops;
+    sn.since_init = c->since_init;
+    sn.sweeps_done = c->sweeps_done;
+    sn.t_msdt = c->t_msdt;
+    sn.have_last = c->have_last;
+    sn.last_resid = c->last_resid;
+    sn.trace_len = c->trace.size();
+    sn.have = true;
+    return CP_OK;
+}
+
+// Back to a snapshot.  keep_ops: the snapshot's operator set is still intact
+// (probing); otherwise the operators are dropped and the next sweep is regular.
+// truncate: forget the trace records written since the snapshot.
+cp_status snap_restore(cp_ctx* c, const cp_ctx::Snap& sn, bool keep_ops, bool truncate) {
+    if (!sn.have) return fail(c, CP_ESTATE, "no snapshot to restore");
+    const bool pp = keep_ops && sn.pp_valid;
+    if (pp) use_ops(c, sn.ops);
+    c->pp_valid = pp;
+    for (int i = 0; i < c->N; ++i) {
+        const int s = (int)c->dims[i];
+        CKCUDA(c, cudaMemcpyAsync(c->A64[i], sn.A64[i], sizeof(double) * s * c->R, cudaMemcpyDeviceToDevice,
+                                  c->st));
+        LAUNCH(c, cpk::factor_copies(c->A64[i], c->A32[i], c->bhi[i], c->blo[i], c->bt32[i], s, c->R, c->Rpad,
+                                     c->Kpad[i], c->st));
+        if (pp)
+            LAUNCH(c, cpk::pp_delta(c->A64[i], c->Ap64[i], c->dA32[i], c->dA64[i], (int64_t)s * c->R, c->st));
+        CKST(regram(c, i, pp));
+        c->ver[i] = sn.ver[i];
+        c->dA_rel[i] = (sn.pp_valid && !pp) ? 1.0 : sn.dA_rel[i];
+    }
+    c->since_init = sn.since_init;
+    c->sweeps_done = sn.sweeps_done;
+    c->t_msdt = sn.t_msdt;
+    c->have_last = sn.have_last;
+    c->last_resid = sn.last_resid;
+    if (truncate && c->trace.size() > sn.trace_len) c->trace.resize(sn.trace_len);
+    c->chol_pending = false;
+    return CP_OK;
+}
+
+// Alg. 2's inputs to the regime test after a sweep: dA = A - A_p inside PP,
+// the sweep's own change after a regular sweep.
+void note_sweep(cp_ctx* c, int kind) {
+    const std::vector<double>& h = c->last_hist;
+    for (int i = 0; i < c->N; ++i) {
+        const double* sc = &h[(size_t)i * CP_NSCAL];
+        const double a = sqrt(sc[SCAL_A2]);
+        const double d = (kind == 2) ? sqrt(sc[SCAL_DAP2]) : sqrt(sc[SCAL_STEP2]);
+        c->dA_rel[i] = a > 0 ? d / a : 1.0;
+    }
+    if (kind == 2) c->since_init++;
+}
+
+// log10 of x clamped to [1e-12, 1], mapped to [-1, 1]
+float logfeat(double x) {
+    const double l = log10(std::min(1.0, std::max(x, 1e-12)));
+    return (float)(l / 6.0 + 1.0);
+}
+
+// The policy's 8 inputs (see cp_policy_features in cpals.h).  rebuilt: as if
+// the operators were built now (A_p = A).
+void features(const cp_ctx* c, bool rebuilt, float f[8]) {
+    const size_t n = c->trace.size();
+    const cp_trace_rec* last = n ? &c->trace[n - 1] : nullptr;
+    const double r1 = last ? last->resid : 1.0;
+    const double r0 = n > 1 ? c->trace[n - 2].resid : 1.0;
+    const bool in_pp = last && last->kind == 2;
+    double dap = 0.0;
+    for (int i = 0; i < c->N; ++i) dap = std::max(dap, c->dA_rel[i]);
+    f[0] = (float)std::min(3.0, c->sweeps_done / 100.0);
+    f[1] = logfeat(last ? last->max_rel_step : 1.0);
+    f[2] = (rebuilt || !c->pp_valid) ? -1.f : logfeat(dap);
+    f[3] = logfeat(n ? fabs(r1 - r0) / std::max(r1, 1e-300) : 1.0);
+    f[4] = logfeat(r1);
+    f[5] = rebuilt ? 0.f : (c->pp_valid ? (float)std::min(3.0, c->since_init / 10.0) : 3.f);
+    f[6] = in_pp ? 1.f : 0.f;
+    f[7] = (!rebuilt && in_pp) ? logfeat(last->v_share) : -1.f;
+}
+
+// network scores of the two choices: [0] current operators, [1] rebuilt ones
+cp_status policy_scores(cp_ctx* c, cp_policy* p, float sc[2]) {
+    if (!c->pol_io) CKST(dalloc(c, &c->pol_io, 32));
+    float f[16];
+    features(c, false, f);
+    features(c, true, f + 8);
+    CKCUDA(c, cudaMemcpyAsync(c->pol_io, f, sizeof(f), cudaMemcpyHostToDevice, c->st));
+    LAUNCH(c, cpk::mlp_forward(p->theta, c->pol_io, 2, c->pol_io + 16, c->st));
+    CKCUDA(c, cudaMemcpyAsync(sc, c->pol_io + 16, 2 * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+    CKCUDA(c, cudaStreamSynchronize(c->st));
+    for (int k = 0; k < 2; ++k)
+        if (!(sc[k] >= 0.f && sc[k] <= 1.f)) sc[k] = 0.f;  // NaN or garbage: not safe
+    return CP_OK;
+}
+
+enum { CH_EXACT = 0, CH_CUR = 1, CH_NEW = 2 };
+
+// the policy judge's rollback point no longer describes a predecessor state
+void drop_judge(cp_ctx* c) {
+    c->snap[1].have = false;
+    c->since_judge = 0;
+    c->fallback_left = 0;
+}
+
+// One PP-mode sweep of the given choice, timed from events[0] (recorded by the
+// caller) to events[1]; appends its trace record.
+cp_status run_choice(cp_ctx* c, int choice) {
+    int init = 0, kind;
+    if (choice == CH_NEW) {
+        CKST(pp_init_impl(c));
+        init = 1;
+    }
+    if (choice != CH_EXACT && c->pp_valid) {
+        CKST(pp_sweep(c, 0));
+        kind = 2;
+    } else {
+        c->pp_valid = false;
+        CKST(exact_sweep(c, true, 0));
+        kind = 3;
+    }
+    CKCUDA(c, cudaEventRecord(c->events[1], c->st));
+    CKST(harvest(c, 1, &kind, &init, 0));
+    note_sweep(c, kind);
     return CP_OK;
 }
 
@@ -648,9 +876,14 @@ void free_all(cp_ctx* c) {
     F(c->T_owned);
     for (int i = 0; i < CP_MAXN; ++i) {
         F(c->A64[i]); F(c->A32[i]); F(c->bhi[i]); F(c->blo[i]); F(c->bt32[i]);
-        F(c->S[i]); F(c->dS[i]); F(c->Ap64[i]); F(c->dA32[i]); F(c->dA64[i]); F(c->Mp[i]);
-        for (int j = 0; j < CP_MAXN; ++j) F(c->pair[i][j]);
+        F(c->S[i]); F(c->dS[i]); F(c->dA32[i]); F(c->dA64[i]);
+        for (int k = 0; k < 2; ++k) {
+            F(c->Apset[k][i]); F(c->Mpset[k][i]);
+            for (int j = 0; j < CP_MAXN; ++j) F(c->pairset[k][i][j]);
+            F(c->snap[k].A64[i]);
+        }
     }
+    F(c->pol_io);
     for (int k = 0; k <= CP_MAXN; ++k) F(c->slot[k].buf);
     for (int i = 0; i < CP_MAXN; ++i) {
         cpk::ttm_tc_plan_free(c->tc_plan[i]);
@@ -664,7 +897,7 @@ void free_all(cp_ctx* c) {
     if (c->ev_ready) { cudaEventDestroy(c->ev_ready); c->ev_ready = nullptr; }
     if (c->ev_chol) { cudaEventDestroy(c->ev_chol); c->ev_chol = nullptr; }
     F(c->Mt); F(c->d_Slist); F(c->d_dSlist); F(c->Gamma); F(c->L); F(c->invd); F(c->W);
-    F(c->gram_part); F(c->scal_part); F(c->scal_hist); F(c->red_part); F(c->d_red_out); F(c->dev_err);
+    F(c->gram_part); F(c->tile_gs); F(c->gram_cnt); F(c->scal_part); F(c->scal_hist); F(c->red_part); F(c->d_red_out); F(c->dev_err);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
 }
@@ -783,6 +1016,12 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
     TRY(dalloc(c, &c->invd, R));
     c->nchunk = 16;
     TRY(dalloc(c, &c->gram_part, (size_t)c->nchunk * 2 * RR));
+    {
+        const size_t nt = (size_t)((R + 15) / 16) * ((R + 15) / 16);
+        TRY(dalloc(c, &c->tile_gs, nt));
+        TRY(dalloc(c, &c->gram_cnt, nt + 1));
+        TRYC(cudaMemsetAsync(c->gram_cnt, 0, sizeof(unsigned) * (nt + 1), c->st));
+    }
     TRY(dalloc(c, &c->scal_part, (size_t)c->smax * CP_NSCAL));
     TRY(dalloc(c, &c->red_part, 4096));
     TRY(dalloc(c, &c->d_red_out, 16));
@@ -894,6 +1133,7 @@ static cp_status sweeps_exact(cp_ctx* c, int nsweeps, bool msdt) {
     CKST(grow_hist(c, nsweeps));
     CKST(ensure_events(c, (size_t)nsweeps + 1));
     c->pp_valid = false;
+    drop_judge(c);
     std::vector<int> kinds(nsweeps, msdt ? 1 : 0);
     CKCUDA(c, cudaEventRecord(c->events[0], c->st));
     for (int k = 0; k < nsweeps; ++k) {
@@ -910,6 +1150,7 @@ cp_status cp_sweep_msdt(cp_ctx* c, int nsweeps) { return sweeps_exact(c, nsweeps
 
 cp_status cp_pp_init(cp_ctx* c) {
     CKST(entry_check(c));
+    drop_judge(c);
     return pp_init_impl(c);
 }
 
@@ -929,41 +1170,126 @@ cp_status cp_pp_mttkrp(cp_ctx* c, int mode, float* M_dev) {
 cp_status cp_sweep_pp(cp_ctx* c, int nsweeps, double eps, cp_policy* policy) {
     CKST(entry_check(c));
     if (nsweeps < 0 || !(eps > 0.0 && eps < 1.0)) return CP_EINVAL;
-    (void)policy;
     CKST(grow_hist(c, 1));
-    CKST(ensure_events(c, 2));
+    CKST(ensure_events(c, 4));
+    const int judge = policy ? std::max(0, c->cfg.judge_every) : 0;
+    if (!judge) drop_judge(c);
+    if (judge && !c->snap[1].have) {
+        // rollback point at the start of policy-driven sweeps
+        CKST(direct_resid(c, &c->judge_r));
+        CKST(snap_take(c, c->snap[1]));
+        c->since_judge = 0;
+    }
     for (int k = 0; k < nsweeps; ++k) {
-        bool small = true;
-        for (int i = 0; i < c->N; ++i)
-            if (!(c->dA_rel[i] < eps)) small = false;
-        int init = 0;
-        if (!c->pp_valid && small) {
-            CKCUDA(c, cudaEventRecord(c->events[0], c->st));
-            CKST(pp_init_impl(c));
-            init = 1;
+        CKCUDA(c, cudaEventRecord(c->events[0], c->st));
+        float sc[2] = {-1.f, -1.f};
+        int by = 0, choice;
+        if (policy && c->fallback_left == 0) {
+            // the network's two queries: approximate with the current operators,
+            // or with operators rebuilt now; neither safe -> regular sweep
+            CKST(policy_scores(c, policy, sc));
+            by = 1;
+            if (c->pp_valid && sc[0] >= 0.5f) choice = CH_CUR;
+            else if (sc[1] >= 0.5f) choice = CH_NEW;
+            else choice = CH_EXACT;
         } else {
-            CKCUDA(c, cudaEventRecord(c->events[0], c->st));
+            // Alg. 2: enter / stay while every ||dA(i)|| < eps ||A(i)||
+            bool small = true;
+            for (int i = 0; i < c->N; ++i)
+                if (!(c->dA_rel[i] < eps)) small = false;
+            by = policy ? 2 : 0;
+            if (!small) choice = CH_EXACT;
+            else choice = c->pp_valid ? CH_CUR : CH_NEW;
+            if (c->fallback_left > 0) c->fallback_left--;
         }
-        int kind;
-        if (c->pp_valid && small) {
-            CKST(pp_sweep(c, 0));
-            kind = 2;
-        } else {
-            c->pp_valid = false;
-            CKST(exact_sweep(c, true, 0));
-            kind = 3;
-        }
-        CKCUDA(c, cudaEventRecord(c->events[1], c->st));
-        CKST(harvest(c, 1, &kind, &init, 0));
-        // regime test inputs for the next sweep
-        const std::vector<double>& h = c->last_hist;
-        for (int i = 0; i < c->N; ++i) {
-            const double* sc = &h[(size_t)i * CP_NSCAL];
-            const double a = sqrt(sc[SCAL_A2]);
-            const double d = (kind == 2) ? sqrt(sc[SCAL_DAP2]) : sqrt(sc[SCAL_STEP2]);
-            c->dA_rel[i] = a > 0 ? d / a : 1.0;
+        CKST(run_choice(c, choice));
+        cp_trace_rec& rec = c->trace.back();
+        rec.p_cur = sc[0];
+        rec.p_new = sc[1];
+        rec.decided_by = by;
+        if (judge && ++c->since_judge >= judge) {
+            // the judge: a direct residual; if it rose since the last judgement,
+            // undo every sweep since then and let Alg. 2's rule decide until the
+            // next judgement
+            CKCUDA(c, cudaEventRecord(c->events[2], c->st));
+            double r;
+            CKST(direct_resid(c, &r));
+            if (r > c->judge_r * (1.0 + 1e-8)) {
+                const size_t from = c->snap[1].trace_len;
+                for (size_t t = from; t < c->trace.size(); ++t) c->trace[t].rolled_back = 1;
+                const int done = c->sweeps_done;
+                CKST(snap_restore(c, c->snap[1], false, false));
+                c->sweeps_done = done;  // the undone sweeps stay in the count and the trace
+                c->fallback_left = judge;
+                c->stats.rollbacks++;
+            } else {
+                c->judge_r = r;
+            }
+            CKST(snap_take(c, c->snap[1]));
+            c->since_judge = 0;
+            CKCUDA(c, cudaEventRecord(c->events[3], c->st));
+            CKCUDA(c, cudaEventSynchronize(c->events[3]));
+            float jms = 0.f;
+            CKCUDA(c, cudaEventElapsedTime(&jms, c->events[2], c->events[3]));
+            c->trace.back().ms += jms;
         }
     }
+    return CP_OK;
+}
+
+// Branch probe: the three choices from one state, each judged by the direct
+// residual; the context then continues along `follow`.
+cp_status cp_pp_probe(cp_ctx* c, int follow, cp_probe_rec* out) {
+    CKST(entry_check(c));
+    if (!out || follow < -1 || follow > 2 || (follow == CH_CUR && !c->pp_valid)) return CP_EINVAL;
+    CKST(pp_alloc2(c));
+    CKST(grow_hist(c, 1));
+    CKST(ensure_events(c, 2));
+    drop_judge(c);
+    memset(out, 0, sizeof(*out));
+    features(c, false, out->feat_cur);
+    features(c, true, out->feat_new);
+    out->has_ops = c->pp_valid ? 1 : 0;
+    CKST(direct_resid(c, &out->r0));
+    CKST(snap_take(c, c->snap[0]));
+    auto branch = [&](int ch, double* r, double* ms) -> cp_status {
+        CKCUDA(c, cudaEventRecord(c->events[0], c->st));
+        CKST(run_choice(c, ch));
+        *ms = c->trace.back().ms;
+        CKST(direct_resid(c, r));
+        return CP_OK;
+    };
+    out->r_cur = NAN;
+    if (out->has_ops) {
+        CKST(branch(CH_CUR, &out->r_cur, &out->ms_cur));
+        CKST(snap_restore(c, c->snap[0], true, true));
+    }
+    CKST(branch(CH_EXACT, &out->r_exact, &out->ms_exact));
+    CKST(snap_restore(c, c->snap[0], true, true));
+    CKST(branch(CH_NEW, &out->r_new, &out->ms_new));
+    // safe: the approximated sweep achieves at least 90% of the regular sweep's
+    // decrease of the direct residual (plus a rounding allowance)
+    const double gain = std::max(0.0, out->r0 - out->r_exact);
+    const double slack = 0.1 * gain + 1e-9 * out->r0;
+    out->label_cur = (out->has_ops && out->r_cur - out->r_exact <= slack) ? 1 : 0;
+    out->label_new = (out->r_new - out->r_exact <= slack) ? 1 : 0;
+    int ch = follow;
+    if (ch < 0) ch = out->label_cur ? CH_CUR : (out->label_new ? CH_NEW : CH_EXACT);
+    if (ch != CH_NEW) {
+        CKST(snap_restore(c, c->snap[0], true, true));
+        double r, ms;
+        CKST(branch(ch, &r, &ms));
+    }
+    out->followed = ch;
+    c->trace.back().decided_by = 3;
+    return CP_OK;
+}
+
+cp_status cp_policy_features(cp_ctx* c, float* f16) {
+    CKST(entry_check(c));
+    if (!f16) return CP_EINVAL;
+    features(c, false, f16);
+    features(c, true, f16 + 8);
     return CP_OK;
 }
 
@@ -973,23 +1299,7 @@ cp_status cp_fit(cp_ctx* c, int exact, double* fit, double* resid) {
     if (!exact && c->have_last) {
         r = c->last_resid;
     } else {
-        cpk::ResidArgs a;
-        memset(&a, 0, sizeof(a));
-        a.T = c->T;
-        a.N = c->N;
-        a.R = c->R;
-        for (int i = 0; i < c->N; ++i) {
-            a.A32[i] = c->A32[i];
-            a.dims[i] = c->dims[i];
-        }
-        c->stats.launches += 2;
-        int nb = cpk::resid_direct_partials(a, c->red_part, 4096, c->st);
-        CKCUDA(c, cudaGetLastError());
-        CKCUDA(c, cpk::sum_partials(c->red_part, nb, c->d_red_out, c->st));
-        double s2 = 0.0;
-        CKCUDA(c, cudaMemcpyAsync(&s2, c->d_red_out, sizeof(double), cudaMemcpyDeviceToHost, c->st));
-        CKCUDA(c, cudaStreamSynchronize(c->st));
-        r = sqrt(s2 > 0 ? s2 : 0.0) / sqrt(c->normT2);
+        CKST(direct_resid(c, &r));
     }
     if (!isfinite(r)) return fail(c, CP_ENUMERIC, "non-finite residual");
     if (resid) *resid = r;
@@ -1017,12 +1327,13 @@ cp_status cp_set_factor(cp_ctx* c, int mode, const double* A_host) {
     const bool pp = c->pp_valid;
     if (pp)
         LAUNCH(c, cpk::pp_delta(c->A64[mode], c->Ap64[mode], c->dA32[mode], c->dA64[mode], (int64_t)s * c->R, c->st));
-    LAUNCH(c, cpk::gram_partials(c->A64[mode], pp ? c->dA64[mode] : nullptr, s, c->R, c->gram_part, nchunk, c->st));
-    LAUNCH(c, cpk::finalize_update(c->gram_part, nchunk, c->scal_part, 0, nullptr, c->R, pp ? 1 : 0, c->S[mode],
-                                   c->dS[mode], c->red_part, c->st));
+    LAUNCH(c, cpk::gram_update(c->A64[mode], pp ? c->dA64[mode] : nullptr, s, c->R, c->gram_part, nchunk,
+                               c->scal_part, 0, nullptr, c->S[mode], c->dS[mode], c->red_part, c->tile_gs,
+                               c->gram_cnt, c->st));
     CKCUDA(c, cudaStreamSynchronize(c->st));
-    c->ver[mode]++;
+    c->ver[mode] = ++c->vclock;
     c->have_last = false;
+    drop_judge(c);
     return CP_OK;
 }
 

@@ -83,15 +83,8 @@ cudaError_t pp_u(const float* Mp, const PPTerm* terms, int nterms, float* Mt, in
 int norm2_partials(const float* x, int64_t n, double* partials, int max_blocks, cudaStream_t st);
 cudaError_t sum_partials(const double* partials, int n, double* out, cudaStream_t st);
 
-// Gamma = *_{k != n} S(k) (+ PP's W); Cholesky Gamma = L L^T into L (R x R), invdiag.
-// S_list / dS_list: device arrays of N device pointers.  pp != 0 also builds
-// W = sum_{i<j; i,j != n} dS(i)*dS(j)*(*_{k != i,j,n} S(k)).
-cudaError_t gamma_chol(double* const* S_list, double* const* dS_list, int N, int n, int R,
-                       int pp, double* Gamma, double* L, double* invdiag, double* W,
-                       double* scal, cudaStream_t st);
-
-// Row-wise solve A_new = (M + A_old W) Gamma^{-1}; writes every operand copy and
-// per-block partial scalars (CP_NSCAL per block).  Returns blocks used via *nblk.
+// Outputs of the row solve A_new = (M + A_old W) Gamma^{-1}: every operand copy
+// of the new factor and, in PP, its difference from the base factor.
 struct SolveOut {
     double* A64;        // in: A_old, out: A_new (s x R)
     float* A32;         // FP32 copy
@@ -103,13 +96,10 @@ struct SolveOut {
     float* dA32;        // A_new - A_p (or - A_old outside PP), FP32
     double* dA64;       // same in FP64
 };
-cudaError_t solve_rows(const float* M, const double* W, const double* L, const double* invdiag,
-                       const SolveOut& o, int s, int R, double* scal_part, int* nblk,
-                       cudaStream_t st);
-
 // Mixed-precision normal-equation solve (k_solve_mixed.cu): chol_mixed forms
-// Gamma (FP64, written to Gamma), PP's W, and either Ginv = Gamma^{-1} in FP32
-// (*mode = 0) or the FP64 factor L64 ([L | L^T], 2 R^2) and invd64 (*mode = 1);
+// Gamma (FP64, written to Gamma), PP's W, and either Ginv ~ Gamma^{-1} in FP32
+// from the diagonally scaled matrix (*mode = 0) or the FP64 factor L64
+// ([L | L^T], 2 R^2) and invd64 (*mode = 1);
 // solve_mixed then solves every row to FP64 accuracy (refinement or FP64
 // substitution).  Gamma and Ginv must have 16 spare bytes after R*R entries.
 cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
@@ -120,12 +110,13 @@ cudaError_t solve_mixed(const float* M, const double* W, const double* Gamma, co
                         int s, int R, double* scal, double* scal_part, int* nblk, unsigned* dev_err,
                         cudaStream_t st);
 
-// Gram partials of A (and A^T dA) over row chunks; finalize reduces them.
-cudaError_t gram_partials(const double* A, const double* dA, int s, int R, double* part,
-                          int nchunk, cudaStream_t st);
-cudaError_t finalize_update(const double* gram_part, int nchunk, const double* scal_part,
-                            int nblk, const double* Gamma, int R, int want_dS, double* S,
-                            double* dS, double* scal_out, cudaStream_t st);
+// S = A^T A (and dS = A^T dA when dA != NULL) in one launch over row chunks;
+// with Gamma, scal_out[SCAL_GS] = <Gamma, S>; the solve's per-block scalars
+// (nblk blocks) are reduced into scal_out.  part: nchunk x 2 R^2 doubles;
+// tile_gs: ceil(R/16)^2 doubles; cnt: ceil(R/16)^2 + 1 counters, zero at first use.
+cudaError_t gram_update(const double* A, const double* dA, int s, int R, double* part, int nchunk,
+                        const double* scal_part, int nblk, const double* Gamma, double* S, double* dS,
+                        double* scal_out, double* tile_gs, unsigned* cnt, cudaStream_t st);
 
 // refresh all operand copies of a factor from its FP64 master (after set_factor / init)
 cudaError_t factor_copies(const double* A64, float* A32, uint16_t* bhi, uint16_t* blo,

@@ -57,315 +57,34 @@ __device__ __forceinline__ void bf16_split(float x, uint16_t& hi, uint16_t& lo) 
     lo = __bfloat16_as_ushort(l);
 }
 
-// ------------------------------------------------------------------ Gamma + Cholesky
-// One CTA.  work = Gamma with row stride ld (smem, ld = R + 1 so column reads
-// hit distinct banks, when R <= 128; otherwise the Lt half of the output
-// buffer with ld = R, rewritten at the end).  Right-looking factorisation in
-// the LDL^T form, one barrier per column: at step j every thread updates
-// work[i][k] -= work[i][j] work[k][j] / d_j for j < k <= i.  The pivot of the
-// next column, d_{j+1} = work[j+1][j+1], is always updated by thread 0 as its
-// first element of step j, so thread 0 alone tests it and forms 1/d_{j+1}
-// while the other threads finish the step.  Finally L[i][k] = work[i][k] /
-// sqrt(d_k), L[k][k] = sqrt(d_k).  If a pivot is not positive the
-// factorisation restarts once on Gamma + 1e-12 * trace(Gamma)/R * I (flag 1);
-// a second failure sets flag 2 and leaves L = I so that later kernels stay
-// finite.  scal[SCAL_FLAGS] gets the flag and scal[SCAL_GS] is cleared for the
-// Gram kernel's accumulation.
-__global__ void __launch_bounds__(512) k_gamma_chol(double* const* __restrict__ S_list,
-                                                    double* const* __restrict__ dS_list, int N,
-                                                    int n, int R, int pp, double* __restrict__ G,
-                                                    double* __restrict__ Lout,
-                                                    double* __restrict__ invd,
-                                                    double* __restrict__ W,
-                                                    double* __restrict__ scal, int use_smem) {
-    extern __shared__ double smw[];
-    __shared__ double red[32];
-    __shared__ double sinv[CP_MAXR];   // 1/d_j
-    __shared__ double srs[CP_MAXR];    // 1/sqrt(d_j)
-    __shared__ int sfail;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int RR = R * R;
-    const int ld = use_smem ? R + 1 : R;
-    double* L = Lout;            // lower, row-major
-    double* Lt = Lout + RR;      // upper (transpose), row-major
-    double* work = use_smem ? smw : Lt;
-    const double* Sp[CP_MAXN];
-    const double* dSp[CP_MAXN];
-    for (int k = 0; k < N; ++k) {
-        Sp[k] = S_list[k];
-        dSp[k] = pp ? dS_list[k] : nullptr;
-    }
 
-    double tr = 0.0;
-    for (int e = tid; e < RR; e += nt) {
-        const int i = e / R, k = e % R;
-        double g = 1.0;
-        for (int m = 0; m < N; ++m)
-            if (m != n) g *= Sp[m][e];
-        G[e] = g;
-        work[i * ld + k] = g;
-        if (i == k) tr += g;
-        if (pp) {
-            double w = 0.0;
-            for (int a = 0; a < N; ++a) {
-                if (a == n) continue;
-                for (int b = a + 1; b < N; ++b) {
-                    if (b == n) continue;
-                    double t = dSp[a][e] * dSp[b][e];
-                    for (int m = 0; m < N; ++m)
-                        if (m != a && m != b && m != n) t *= Sp[m][e];
-                    w += t;
-                }
-            }
-            W[e] = w;
-        }
-    }
-    tr = block_sum(tr, red);  // also a barrier: work is complete
-    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    double flag = 0.0;
-    bool bad = false;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        if (attempt == 1) {
-            const double shift = 1e-12 * tr / R;
-            for (int e = tid; e < RR; e += nt) {
-                const int i = e / R, k = e % R;
-                work[i * ld + k] = G[e] + ((i == k) ? shift : 0.0);
-            }
-            flag = 1.0;
-            __syncthreads();
-        }
-        if (tid == 0) {
-            const double d = work[0];
-            sfail = (!(d > 0.0) || !isfinite(d)) ? 1 : 0;
-            if (!sfail) sinv[0] = 1.0 / d;
-        }
-        __syncthreads();
-        for (int j = 0; j < R && !sfail; ++j) {
-            const double inv = sinv[j];
-            for (int i = j + 1 + warp; i < R; i += nw) {
-                double* wi = work + (size_t)i * ld;
-                const double lij = wi[j] * inv;
-                for (int k = j + 1 + lane; k <= i; k += 32) wi[k] = fma(-lij, work[k * ld + j], wi[k]);
-            }
-            if (tid == 0 && j + 1 < R) {
-                const double d = work[(j + 1) * ld + j + 1];
-                if (!(d > 0.0) || !isfinite(d)) sfail = 1;
-                else sinv[j + 1] = 1.0 / d;
-            }
-            __syncthreads();
-        }
-        const bool failed = sfail != 0;
-        __syncthreads();
-        if (!failed) break;
-        if (attempt == 1) {
-            flag = 2.0;
-            bad = true;
-        }
-    }
-    for (int j = tid; j < R; j += nt) {
-        const double v = bad ? 1.0 : 1.0 / sqrt(work[j * ld + j]);
-        srs[j] = v;
-        invd[j] = v;
-    }
-    __syncthreads();
-    if (!use_smem) {
-        // work aliases Lt: build L first, then its transpose
-        for (int e = tid; e < RR; e += nt) {
-            const int i = e / R, k = e % R;
-            double v = 0.0;
-            if (bad) v = (i == k) ? 1.0 : 0.0;
-            else if (k < i) v = work[e] * srs[k];
-            else if (k == i) v = 1.0 / srs[k];
-            L[e] = v;
-        }
-        __syncthreads();
-        for (int e = tid; e < RR; e += nt) {
-            const int i = e / R, k = e % R;
-            Lt[e] = L[k * R + i];
-        }
-    } else {
-        for (int e = tid; e < RR; e += nt) {
-            const int i = e / R, k = e % R;
-            double v = 0.0;
-            if (bad) v = (i == k) ? 1.0 : 0.0;
-            else if (k < i) v = work[i * ld + k] * srs[k];
-            else if (k == i) v = 1.0 / srs[k];
-            L[e] = v;
-            Lt[k * R + i] = v;
-        }
-    }
-    if (tid == 0) {
-        scal[SCAL_FLAGS] = flag;
-        scal[SCAL_GS] = 0.0;
-    }
-}
+// Gram of an updated factor, one launch: S = A^T A (and dS = A^T dA) over
+// row chunks, grid (R/16, R/16, chunks).  Each block writes its tile's partial
+// sum; the last block to finish a tile adds the chunk partials in chunk order
+// and contributes <Gamma, S> over the tile; the last tile to finish adds those
+// in tile order and reduces the solve kernel's per-block scalars.  Counters
+// return to zero, so the next launch may reuse them.  Partials written by
+// other blocks are read with ld.global.cg (L2), after a fence.
+constexpr int GRAM_MAX_CHUNKS = 16;
 
-// ------------------------------------------------------------------ row solves
-// One warp per row x: m~ = M(x,:) [+ A_old(x,:) W]; forward substitution with L,
-// back substitution with L^T (column-oriented, lane l owns entries l + 32t).
-// With SMEM the block first stages L (row stride R+1, so that column reads are
-// free of bank conflicts) and 1/L[j][j] in shared memory.
-template <int RT, bool SMEM>
-__global__ void __launch_bounds__(128) k_solve(const float* __restrict__ M,
-                                               const double* __restrict__ W,
-                                               const double* __restrict__ L,
-                                               const double* __restrict__ invd, cpk::SolveOut o,
-                                               int s, int R, double* __restrict__ scal_part) {
-    extern __shared__ double sL[];
-    __shared__ double red[4][CP_NSCAL];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nwb = blockDim.x >> 5;
-    const int x = blockIdx.x * nwb + wib;
-    const int ld = SMEM ? R + 1 : R;
-    const double* Lc;   // column access L[k][j] = Lc[j * ldc + k]... see below
-    const double* Lr;   // row access    L[j][k] = Lr[j * ld + k]
-    const double* iv;
-    if (SMEM) {
-        const int RR = R * R;
-        int e = threadIdx.x;
-        for (; e + 7 * (int)blockDim.x < RR; e += 8 * blockDim.x) {
-            double v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldg(L + e + u * blockDim.x);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int f = e + u * blockDim.x;
-                sL[(f / R) * ld + (f % R)] = v[u];
-            }
-        }
-        for (; e < RR; e += blockDim.x) sL[(e / R) * ld + (e % R)] = __ldg(L + e);
-        for (int j = threadIdx.x; j < R; j += blockDim.x) sL[R * ld + j] = invd[j];
-        __syncthreads();
-        Lr = sL;
-        Lc = sL;
-        iv = sL + R * ld;
-    } else {
-        Lr = L;
-        Lc = L + (size_t)R * R;  // Lt row-major: L[k][j] = Lt[j][k]
-        iv = invd;
-    }
-    double sc[CP_NSCAL];
-#pragma unroll
-    for (int i = 0; i < CP_NSCAL; ++i) sc[i] = 0.0;
-    if (x < s) {
-        double aold[RT], acc[RT], mt[RT], z[RT], xs[RT];
-#pragma unroll
-        for (int t = 0; t < RT; ++t) {
-            const int j = lane + 32 * t;
-            aold[t] = (j < R) ? o.A64[(size_t)x * R + j] : 0.0;
-            acc[t] = (j < R) ? (double)M[(size_t)x * R + j] : 0.0;
-            z[t] = 0.0;
-            xs[t] = 0.0;
-        }
-        if (W) {
-            double vt[RT];
-#pragma unroll
-            for (int t = 0; t < RT; ++t) vt[t] = 0.0;
-            for (int q = 0; q < R; ++q) {
-                const double aq = o.A64[(size_t)x * R + q];
-                const double* wr = W + (size_t)q * R;
-#pragma unroll
-                for (int t = 0; t < RT; ++t) {
-                    const int j = lane + 32 * t;
-                    if (j < R) vt[t] = fma(aq, wr[j], vt[t]);
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < RT; ++t) {
-                acc[t] += vt[t];
-                sc[SCAL_V2] += vt[t] * vt[t];
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < RT; ++t) mt[t] = acc[t];
-        // forward: z_j = (m_j - sum_{k<j} L[j][k] z_k) / L[j][j]
-#pragma unroll
-        for (int tt = 0; tt < RT; ++tt) {
-            for (int jj = 0; jj < 32; ++jj) {
-                const int j = tt * 32 + jj;
-                if (j >= R) break;
-                const double zj = __shfl_sync(FULL, acc[tt], jj) * iv[j];
-                if (lane == jj) z[tt] = zj;
-#pragma unroll
-                for (int t2 = tt; t2 < RT; ++t2) {
-                    const int k = lane + 32 * t2;
-                    if (k > j && k < R) {
-                        const double lkj = SMEM ? Lc[(size_t)k * ld + j] : Lc[(size_t)j * R + k];
-                        acc[t2] = fma(-lkj, zj, acc[t2]);
-                    }
-                }
-            }
-        }
-        // back: x_j = (z_j - sum_{k>j} L[k][j] x_k) / L[j][j]
-#pragma unroll
-        for (int t = 0; t < RT; ++t) acc[t] = z[t];
-#pragma unroll
-        for (int tt = RT - 1; tt >= 0; --tt) {
-            for (int jj = 31; jj >= 0; --jj) {
-                const int j = tt * 32 + jj;
-                if (j >= R) continue;
-                const double xj = __shfl_sync(FULL, acc[tt], jj) * iv[j];
-                if (lane == jj) xs[tt] = xj;
-                const double* lr = Lr + (size_t)j * ld;
-#pragma unroll
-                for (int t2 = 0; t2 <= tt; ++t2) {
-                    const int k = lane + 32 * t2;
-                    if (k < j) acc[t2] = fma(-lr[k], xj, acc[t2]);
-                }
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < RT; ++t) {
-            const int j = lane + 32 * t;
-            if (j >= R) continue;
-            const double a = xs[t];
-            const size_t e = (size_t)x * R + j;
-            o.A64[e] = a;
-            const float af = (float)a;
-            if (o.A32) o.A32[e] = af;
-            if (o.bhi) {
-                uint16_t hi, lo;
-                bf16_split(af, hi, lo);
-                o.bhi[(size_t)j * o.Kpad + x] = hi;
-                o.blo[(size_t)j * o.Kpad + x] = lo;
-            }
-            if (o.bt32) tf32_store(o.bt32, (size_t)o.Rpad * o.Kpad, (size_t)j * o.Kpad + x, af);
-            const double base = o.Ap ? o.Ap[e] : aold[t];
-            const double d = a - base;
-            if (o.dA32) o.dA32[e] = (float)d;
-            if (o.dA64) o.dA64[e] = d;
-            sc[SCAL_A2] += a * a;
-            sc[SCAL_STEP2] += (a - aold[t]) * (a - aold[t]);
-            if (o.Ap) sc[SCAL_DAP2] += d * d;
-            sc[SCAL_MA] += mt[t] * a;
-            sc[SCAL_M2] += mt[t] * mt[t];
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < CP_NSCAL; ++i) {
-        double v = warp_sum(sc[i]);
-        if (lane == 0) red[wib][i] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < CP_NSCAL) {
-        double v = 0.0;
-        for (int w = 0; w < nwb; ++w) v += red[w][threadIdx.x];
-        scal_part[(size_t)blockIdx.x * CP_NSCAL + threadIdx.x] = v;
-    }
-}
-
-// ------------------------------------------------------------------ Gram partials
-// grid (ceil(R/16), ceil(R/16), nchunk), block 16x16: part[c][0] = A_c^T A_c,
-// part[c][1] = A_c^T dA_c over the rows of chunk c.
-__global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ A,
+__global__ void __launch_bounds__(256) k_gram_fin(const double* __restrict__ A,
                                                   const double* __restrict__ dA, int s, int R,
-                                                  double* __restrict__ part, int rows_per) {
+                                                  double* __restrict__ part, int rows_per,
+                                                  const double* __restrict__ scal_part, int nblk,
+                                                  const double* __restrict__ Gamma, int want_dS,
+                                                  double* __restrict__ S, double* __restrict__ dS,
+                                                  double* __restrict__ scal_out,
+                                                  double* __restrict__ tile_gs,
+                                                  unsigned* __restrict__ cnt) {
     __shared__ double a1[16][17], a2[16][17], d2[16][17];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    __shared__ double red[32];
+    __shared__ unsigned s_last;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int r1 = blockIdx.x * 16 + ty, r2 = blockIdx.y * 16 + tx;
     const int c = blockIdx.z;
     const int x0 = c * rows_per, x1 = min(s, x0 + rows_per);
-    double acc = 0.0, accd = 0.0;
+    const size_t RR = (size_t)R * R;
+    double acc = 0.0, accd = 0.0, acc2 = 0.0, accd2 = 0.0;
     for (int xb = x0; xb < x1; xb += 16) {
         const int x = xb + ty;
         const int ca = blockIdx.x * 16 + tx, cb = blockIdx.y * 16 + tx;
@@ -374,64 +93,83 @@ __global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ A,
         if (dA) d2[ty][tx] = (x < x1 && cb < R) ? dA[(size_t)x * R + cb] : 0.0;
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 16; k += 2) {
             acc = fma(a1[k][ty], a2[k][tx], acc);
-            if (dA) accd = fma(a1[k][ty], d2[k][tx], accd);
+            acc2 = fma(a1[k + 1][ty], a2[k + 1][tx], acc2);
+            if (dA) {
+                accd = fma(a1[k][ty], d2[k][tx], accd);
+                accd2 = fma(a1[k + 1][ty], d2[k + 1][tx], accd2);
+            }
         }
         __syncthreads();
     }
-    if (r1 < R && r2 < R) {
-        const size_t RR = (size_t)R * R;
-        part[(size_t)c * 2 * RR + (size_t)r1 * R + r2] = acc;
-        if (dA) part[(size_t)c * 2 * RR + RR + (size_t)r1 * R + r2] = accd;
+    acc += acc2;
+    accd += accd2;
+    const bool in = r1 < R && r2 < R;
+    const size_t e = (size_t)r1 * R + r2;
+    if (in) {
+        part[(size_t)c * 2 * RR + e] = acc;
+        if (dA) part[(size_t)c * 2 * RR + RR + e] = accd;
     }
-}
-
-// ------------------------------------------------------------------ finalize
-// Grid over the R x R entries: S = sum of chunk partials (and dS); <Gamma, S>
-// accumulates into scal[SCAL_GS] (cleared by the Cholesky kernel of the same
-// update).  Block 0 also reduces the solve kernel's per-block scalars.
-__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ part, int nchunk,
-                                                  const double* __restrict__ scal_part, int nblk,
-                                                  const double* __restrict__ Gamma, int R,
-                                                  int want_dS, double* __restrict__ S,
-                                                  double* __restrict__ dS,
-                                                  double* __restrict__ scal_out) {
-    __shared__ double red[32];
-    const int tid = threadIdx.x;
-    const size_t RR = (size_t)R * R;
+    const unsigned tile = blockIdx.y * gridDim.x + blockIdx.x, ntiles = gridDim.x * gridDim.y;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&cnt[tile], 1u) == gridDim.z - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // chunk partials of this tile: all loads issued before the sums (chunk order kept)
     double gs = 0.0;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + tid; e < RR; e += (size_t)gridDim.x * blockDim.x) {
-        double v0 = 0.0, v1 = 0.0, d0 = 0.0, d1 = 0.0;
-        int c = 0;
-        for (; c + 1 < nchunk; c += 2) {
-            v0 += part[(size_t)c * 2 * RR + e];
-            v1 += part[(size_t)(c + 1) * 2 * RR + e];
-            if (want_dS) {
-                d0 += part[(size_t)c * 2 * RR + RR + e];
-                d1 += part[(size_t)(c + 1) * 2 * RR + RR + e];
-            }
+    if (in) {
+        const int nc = (int)gridDim.z;
+        double pv[GRAM_MAX_CHUNKS], pd[GRAM_MAX_CHUNKS];
+#pragma unroll
+        for (int q = 0; q < GRAM_MAX_CHUNKS; ++q) {
+            pv[q] = q < nc ? __ldcg(part + (size_t)q * 2 * RR + e) : 0.0;
+            pd[q] = (q < nc && want_dS) ? __ldcg(part + (size_t)q * 2 * RR + RR + e) : 0.0;
         }
-        if (c < nchunk) {
-            v0 += part[(size_t)c * 2 * RR + e];
-            if (want_dS) d0 += part[(size_t)c * 2 * RR + RR + e];
+        double v = 0.0, d = 0.0;
+#pragma unroll
+        for (int q = 0; q < GRAM_MAX_CHUNKS; ++q) {
+            v += pv[q];
+            d += pd[q];
         }
-        const double v = v0 + v1;
         S[e] = v;
-        if (want_dS) dS[e] = d0 + d1;
-        if (Gamma) gs += Gamma[e] * v;
+        if (want_dS) dS[e] = d;
+        if (Gamma) gs = Gamma[e] * v;
     }
-    if (Gamma) {
-        gs = block_sum(gs, red);
-        if (tid == 0) atomicAdd(scal_out + SCAL_GS, gs);
+    gs = block_sum(gs, red);
+    if (tid == 0) {
+        tile_gs[tile] = gs;
+        cnt[tile] = 0u;
     }
-    if (blockIdx.x != 0) return;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&cnt[ntiles], 1u) == ntiles - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid == 0) cnt[ntiles] = 0u;
+    // <Gamma, S> over tiles and the solve's scalars: loads first, then fixed-order sums
+    double t = 0.0;
+    for (unsigned q = tid; q < ntiles; q += blockDim.x) t += __ldcg(tile_gs + q);
+    double v[CP_NSCAL];
+#pragma unroll
+    for (int slot = 0; slot < CP_NSCAL; ++slot) v[slot] = 0.0;
+    for (int b = tid; b < nblk; b += blockDim.x) {
+        double w[CP_NSCAL];
+#pragma unroll
+        for (int slot = 0; slot < CP_NSCAL; ++slot) w[slot] = __ldcg(scal_part + (size_t)b * CP_NSCAL + slot);
+#pragma unroll
+        for (int slot = 0; slot < CP_NSCAL; ++slot) v[slot] += w[slot];
+    }
+    t = block_sum(t, red);
+    if (tid == 0 && Gamma) scal_out[SCAL_GS] = t;
+#pragma unroll
     for (int slot = 0; slot < CP_NSCAL; ++slot) {
         if (slot == SCAL_GS || slot == SCAL_FLAGS) continue;
-        double v = 0.0;
-        for (int b = tid; b < nblk; b += blockDim.x) v += scal_part[(size_t)b * CP_NSCAL + slot];
-        v = block_sum(v, red);
-        if (tid == 0) scal_out[slot] = v;
+        const double r = block_sum(v[slot], red);
+        if (tid == 0) scal_out[slot] = r;
     }
 }
 
@@ -712,76 +450,15 @@ cudaError_t add_aw(const float* Mt, const double* A, const double* W, int s, int
     return cudaGetLastError();
 }
 
-cudaError_t gamma_chol(double* const* S_list, double* const* dS_list, int N, int n, int R,
-                       int pp, double* Gamma, double* L, double* invdiag, double* W,
-                       double* scal, cudaStream_t st) {
-    const int use_smem = (R <= 128) ? 1 : 0;
-    size_t smem = use_smem ? (size_t)R * (R + 1) * sizeof(double) : 0;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_gamma_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             128 * 129 * sizeof(double));
-        attr_set = true;
-    }
-    k_gamma_chol<<<1, 512, smem, st>>>(S_list, dS_list, N, n, R, pp, Gamma, L, invdiag, W, scal,
-                                       use_smem);
-    return cudaGetLastError();
-}
-
-template <int RT, bool SM>
-static cudaError_t launch_solve(unsigned blocks, unsigned threads, const float* M, const double* W,
-                                const double* L, const double* invdiag, const SolveOut& o, int s,
-                                int R, double* scal_part, cudaStream_t st) {
-    size_t smem = SM ? ((size_t)R * (R + 1) + R) * sizeof(double) : 0;
-    static bool attr_set = false;
-    if (SM && !attr_set) {
-        cudaFuncSetAttribute(k_solve<RT, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(((size_t)128 * 129 + 128) * sizeof(double)));
-        attr_set = true;
-    }
-    k_solve<RT, SM><<<blocks, threads, smem, st>>>(M, W, L, invdiag, o, s, R, scal_part);
-    return cudaGetLastError();
-}
-
-cudaError_t solve_rows(const float* M, const double* W, const double* L, const double* invdiag,
-                       const SolveOut& o, int s, int R, double* scal_part, int* nblk,
-                       cudaStream_t st) {
-    const int RT = (R + 31) / 32;
-    // one row per warp; small factor matrices get one warp per block so that the
-    // FP64 work spreads over as many SMs as there are rows
-    const int wpb = (s <= 512) ? 1 : 4;
-    const unsigned blocks = (unsigned)((s + wpb - 1) / wpb);
-    const unsigned th = 32u * wpb;
-    *nblk = (int)blocks;
-    switch (RT) {
-        case 1: return launch_solve<1, true>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 2: return launch_solve<2, true>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 3: return launch_solve<3, true>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 4: return launch_solve<4, true>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 5: return launch_solve<5, false>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 6: return launch_solve<6, false>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 7: return launch_solve<7, false>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
-        case 8: return launch_solve<8, false>(blocks, th, M, W, L, invdiag, o, s, R, scal_part, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-cudaError_t gram_partials(const double* A, const double* dA, int s, int R, double* part,
-                          int nchunk, cudaStream_t st) {
+cudaError_t gram_update(const double* A, const double* dA, int s, int R, double* part, int nchunk,
+                        const double* scal_part, int nblk, const double* Gamma, double* S, double* dS,
+                        double* scal_out, double* tile_gs, unsigned* cnt, cudaStream_t st) {
+    if (nchunk > GRAM_MAX_CHUNKS) nchunk = GRAM_MAX_CHUNKS;
     const int rows_per = (s + nchunk - 1) / nchunk;
+    nchunk = (s + rows_per - 1) / rows_per;  // every chunk non-empty
     dim3 grid((R + 15) / 16, (R + 15) / 16, nchunk);
-    k_gram_part<<<grid, 256, 0, st>>>(A, dA, s, R, part, rows_per);
-    return cudaGetLastError();
-}
-
-cudaError_t finalize_update(const double* gram_part, int nchunk, const double* scal_part,
-                            int nblk, const double* Gamma, int R, int want_dS, double* S,
-                            double* dS, double* scal_out, cudaStream_t st) {
-    const size_t RR = (size_t)R * R;
-    unsigned blocks = (unsigned)((RR + 255) / 256);
-    if (blocks > 64) blocks = 64;
-    k_finalize<<<blocks, 256, 0, st>>>(gram_part, nchunk, scal_part, nblk, Gamma, R, want_dS, S, dS,
-                                       scal_out);
+    k_gram_fin<<<grid, 256, 0, st>>>(A, dA, s, R, part, rows_per, scal_part, nblk, Gamma, dA ? 1 : 0, S, dS,
+                                     scal_out, tile_gs, cnt);
     return cudaGetLastError();
 }
 

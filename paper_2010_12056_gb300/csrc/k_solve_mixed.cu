@@ -6,14 +6,11 @@
 // throughput, so the sequential parts of a Cholesky factorisation and of
 // triangular substitution are run in FP32, and FP64 is kept for work that is
 // parallel across the R entries of a row:
-//   k_chol_mixed  (one CTA)  Gamma = *_{k != n} S(k) and PP's W in FP64; the
-//                 explicit inverse G32 = Gamma^{-1} in FP32 by Gauss-Jordan
-//                 elimination without pivoting (SPD: its pivots are the LDL^T
-//                 pivots), two shared-memory copies used in turn so that each of
-//                 the R steps needs one barrier.  If a pivot is not positive or the
-//                 pivots spread over more than 1e5 (iterative refinement would
-//                 converge slowly), it factors Gamma in FP64 (LDL^T) instead and
-//                 tells the solve kernel to substitute in FP64.
+//   k_gamma_form  Gamma = *_{k != n} S(k) and PP's W in FP64 (many blocks)
+//   k_gj_inv      (one CTA) the FP32 inverse of the diagonally scaled Gamma by
+//                 Gauss-Jordan elimination; if the scaled condition number is
+//                 above 2e5 or a pivot is not positive, an FP64 LDL^T of Gamma
+//                 instead, and the solve kernel substitutes in FP64.
 //   k_solve_mixed (one warp per row) m = M(x,:) [+ A_old(x,:) W];
 //                 x0 = m G32;  repeat  r = m - x Gamma (FP64),  d = r G32,  x += d
 //                 until the estimated remaining error ||d||_inf * rho is below
@@ -205,139 +202,165 @@ __global__ void __launch_bounds__(256) k_gamma_form(double* const* __restrict__ 
     if (pp) W[e] = w;
 }
 
-// R <= 128, 256 threads.  Warp w owns rows w, w + 8, ... (RPW = 16 at most);
-// lane l owns columns l + 32 t (t < RT).  Gauss-Jordan on register-resident
-// rows; the pivot row of the next step is published in one of two shared rows,
-// one barrier per step.  Few warps with many rows each keep the per-step
-// overhead (pivot, reciprocal, broadcast) small against the R^2 updates.
-constexpr int CHOL_THREADS = 256;
-constexpr int CHOL_RPW = MIXED_MAXR / (CHOL_THREADS / 32);
-
-template <int RT>
-__global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_mixed(const float* __restrict__ G32, int R,
-                                                             const double* __restrict__ G,
-                                                             float* __restrict__ Ginv,
-                                                             double* __restrict__ L64,
-                                                             double* __restrict__ invd64,
-                                                             double* __restrict__ scal,
-                                                             int* __restrict__ mode) {
+// R <= 128: explicit inverse of the diagonally scaled matrix
+//   Gt = D Gamma D,  D = diag(Gamma)^(-1/2),   Ginv = D Gt^{-1} D,
+// by Gauss-Jordan elimination without pivoting (Gt is SPD with unit diagonal, so
+// its pivots are its LDL^T pivots) in FP32.  32 TY threads as a TY x 32 grid:
+// thread (ty, tx) keeps rows ty IR + a (a < IR) of columns tx JC + b (b < JC) in
+// registers.  Step k reads the pivot row and column of the matrix after step
+// k - 1 from one of two shared buffers (their owners publish them after their
+// own update, so each step has one barrier).  The step loop is unrolled by IR:
+// the register slot of row k and of column k is then a compile-time constant.
+// Row i != k: a_ij <- a_ij - (a_ik / p) a_kj for j != k, a_ik <- -a_ik / p;
+// row k: a_kj <- a_kj / p, a_kk <- 1 / p.  Scaling removes the part of Gamma's
+// condition number that comes from unequal column norms; if the scaled
+// condition number ||Gt||_inf ||Gt^{-1}||_inf exceeds 2e5 (refinement would
+// contract too slowly) or a pivot is not positive, Gamma is factored in FP64
+// (LDL^T) instead.
+template <int TY, int IR, int JC>
+__global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(const float* __restrict__ G32, int R,
+                                                       const double* __restrict__ G,
+                                                       float* __restrict__ Ginv,
+                                                       double* __restrict__ L64,
+                                                       double* __restrict__ invd64,
+                                                       double* __restrict__ scal,
+                                                       int* __restrict__ mode) {
+    constexpr int NT = 32 * TY, RMAX = TY * IR;
+    static_assert(RMAX <= MIXED_MAXR && 32 * JC <= MIXED_MAXR && IR % JC == 0 && IR % 4 == 0,
+                  "tile shape");
     __shared__ double red[32];
     __shared__ double sinv[CP_MAXR], srs[CP_MAXR];
-    __shared__ float prow[2][MIXED_MAXR];
+    __shared__ __align__(16) float prow[2][MIXED_MAXR];
+    __shared__ __align__(16) float pcol[2][MIXED_MAXR];
+    __shared__ float dsc[MIXED_MAXR];
     __shared__ int sfail;
-    __shared__ float pmin, pmax;
     __shared__ unsigned gmax_bits, imax_bits;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = CHOL_THREADS / 32;
-    const int RR = R * R;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int r0 = ty * IR, c0 = tx * JC;
     if (tid == 0) {
-        sfail = 0;
-        pmin = 3.0e38f;
-        pmax = 0.f;
+        sfail = (R > RMAX || R > 32 * JC) ? 1 : 0;
         gmax_bits = 0u;
         imax_bits = 0u;
     }
-    for (int j = tid; j < 2 * MIXED_MAXR; j += CHOL_THREADS) (&prow[0][0])[j] = 0.f;
     __syncthreads();
-    float a[CHOL_RPW][RT];
-    double tr = 0.0;
-    // rows of Gamma (FP32 copy from k_gamma_form), all loads first
-#pragma unroll
-    for (int sl = 0; sl < CHOL_RPW; ++sl) {
-        const int i = warp + nw * sl;
-#pragma unroll
-        for (int t = 0; t < RT; ++t) {
-            const int j = lane + 32 * t;
-            a[sl][t] = (i < R && j < R) ? __ldg(G32 + (size_t)i * R + j) : 0.f;
+    for (int r = tid; r < MIXED_MAXR; r += NT) {
+        float d = 0.f;
+        if (r < R) {
+            const float g = __ldg(G32 + (size_t)r * R + r);
+            d = (g > 0.f && isfinite(g)) ? rsqrtf(g) : 0.f;
+            if (!(d > 0.f)) sfail = 1;
         }
-    }
-#pragma unroll
-    for (int sl = 0; sl < CHOL_RPW; ++sl) {
-        const int i = warp + nw * sl;
-        float rowabs = 0.f;
-#pragma unroll
-        for (int t = 0; t < RT; ++t) {
-            rowabs += fabsf(a[sl][t]);
-            if (i == lane + 32 * t && i < R) tr += (double)G[(size_t)i * R + i];
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) rowabs += __shfl_xor_sync(FULL, rowabs, o);
-        if (lane == 0 && i < R) atomicMax(&gmax_bits, __float_as_uint(rowabs));
-    }
-    tr = block_sum_d(tr, red);
-    // publish row 0 (warp 0, slot 0)
-    if (warp == 0) {
-#pragma unroll
-        for (int t = 0; t < RT; ++t)
-            if (lane + 32 * t < R) prow[0][lane + 32 * t] = a[0][t];
+        dsc[r] = d;
     }
     __syncthreads();
-    for (int k = 0; k < R; ++k) {
-        const float* pk = prow[k & 1];
-        const float p = pk[k];  // same value in every thread
-        if (!(p > 0.f) || !isfinite(p)) {
-            if (tid == 0) sfail = 1;
-            break;
+    float a[IR][JC];
+#pragma unroll
+    for (int i = 0; i < IR; ++i) {
+        const int r = r0 + i;
+#pragma unroll
+        for (int j = 0; j < JC; ++j) {
+            const int c = c0 + j;
+            a[i][j] = (r < R && c < R) ? __ldg(G32 + (size_t)r * R + c) * (dsc[r] * dsc[c]) : 0.f;
         }
-        if (tid == 0) {
-            pmin = fminf(pmin, p);
-            pmax = fmaxf(pmax, p);
-        }
-        const float inv = __frcp_rn(p);
-        float pv[RT];
+    }
+    // ||Gt||_inf: a warp holds whole rows
 #pragma unroll
-        for (int t = 0; t < RT; ++t) pv[t] = pk[lane + 32 * t];
-        const int kt = k >> 5, kl = k & 31;
+    for (int i = 0; i < IR; ++i) {
+        float rs = 0.f;
 #pragma unroll
-        for (int sl = 0; sl < CHOL_RPW; ++sl) {
-            const int i = warp + nw * sl;  // rows past R hold zeros and stay zero
-            float aik = a[sl][0];
+        for (int j = 0; j < JC; ++j) rs += fabsf(a[i][j]);
 #pragma unroll
-            for (int t = 1; t < RT; ++t)
-                if (t == kt) aik = a[sl][t];
-            const float f = __shfl_sync(FULL, aik, kl) * inv;
-            if (i == k) {
+        for (int o = 16; o; o >>= 1) rs += __shfl_xor_sync(FULL, rs, o);
+        if (tx == 0 && r0 + i < R) atomicMax(&gmax_bits, __float_as_uint(rs));
+    }
+    // publish row 0 and column 0
+    if (ty == 0)
 #pragma unroll
-                for (int t = 0; t < RT; ++t) a[sl][t] = (lane + 32 * t == k) ? inv : pv[t] * inv;
-            } else {
+        for (int j = 0; j < JC; ++j) prow[0][c0 + j] = a[0][j];
+    if (tx == 0)
 #pragma unroll
-                for (int t = 0; t < RT; ++t) a[sl][t] = (lane + 32 * t == k) ? -f : fmaf(-f, pv[t], a[sl][t]);
+        for (int i = 0; i < IR; ++i) pcol[0][r0 + i] = a[i][0];
+    __syncthreads();
+    bool bad = sfail != 0;
+    for (int kb = 0; kb < R && !bad; kb += IR) {
+        const bool own_rows = ty == kb / IR;  // this warp holds rows kb .. kb + IR - 1
+#pragma unroll
+        for (int kk = 0; kk < IR; ++kk) {
+            const int k = kb + kk;
+            if (k >= R) break;
+            const int cur = k & 1;
+            const float p = prow[cur][k];
+            if (!(p > 0.f) || !isfinite(p)) {
+                bad = true;
+                break;
             }
-        }
-        // the owner of row k+1 publishes it for the next step
-        const int k1 = k + 1;
-        if (k1 < R && warp == k1 % nw) {
-            const int s1 = k1 / nw;
-            float* dst = prow[k1 & 1];
+            const float inv = __frcp_rn(p);
+            const int jk = kk % JC;  // register slot of column k (constant once unrolled)
+            const bool kcol = tx == k / JC;
+            float rp[JC];
 #pragma unroll
-            for (int sl = 0; sl < CHOL_RPW; ++sl)
-                if (sl == s1) {
+            for (int j = 0; j < JC; ++j) rp[j] = prow[cur][c0 + j];
+            if (kcol) rp[jk] = 1.f;
+            float f[IR];
 #pragma unroll
-                    for (int t = 0; t < RT; ++t)
-                        if (lane + 32 * t < R) dst[lane + 32 * t] = a[sl][t];
+            for (int i = 0; i < IR; i += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(&pcol[cur][r0 + i]);
+                f[i] = v.x * inv;
+                f[i + 1] = v.y * inv;
+                f[i + 2] = v.z * inv;
+                f[i + 3] = v.w * inv;
+            }
+#pragma unroll
+            for (int i = 0; i < IR; ++i) {
+                if (own_rows && i == kk) {
+#pragma unroll
+                    for (int j = 0; j < JC; ++j) a[i][j] = rp[j] * inv;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < JC; ++j) {
+                        const float g = fmaf(-f[i], rp[j], a[i][j]);
+                        a[i][j] = (j == jk && kcol) ? -f[i] : g;
+                    }
                 }
+            }
+            // owners of row / column k + 1 publish them for the next step
+            const int k1 = k + 1;
+            if (k1 < R) {
+                const int nxt = cur ^ 1;
+                const int i1 = (kk + 1) % IR, j1 = (kk + 1) % JC;
+                if (ty == k1 / IR)
+#pragma unroll
+                    for (int j = 0; j < JC; ++j) prow[nxt][c0 + j] = a[i1][j];
+                if (tx == k1 / JC)
+#pragma unroll
+                    for (int i = 0; i < IR; i += 4)
+                        *reinterpret_cast<float4*>(&pcol[nxt][r0 + i]) =
+                            make_float4(a[i][j1], a[i + 1][j1], a[i + 2][j1], a[i + 3][j1]);
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
     __syncthreads();
-    bool use64 = sfail != 0 || pmax > 1e5f * pmin;
+    bool use64 = bad;
     if (!use64) {
-        // ||Gamma||_inf ||G32||_inf: refinement contracts by about kappa 2^-24 per step
 #pragma unroll
-        for (int sl = 0; sl < CHOL_RPW; ++sl) {
-            const int i = warp + nw * sl;
-            float rowabs = 0.f;
+        for (int i = 0; i < IR; ++i) {
+            float rs = 0.f;
 #pragma unroll
-            for (int t = 0; t < RT; ++t) rowabs += fabsf(a[sl][t]);
+            for (int j = 0; j < JC; ++j) rs += fabsf(a[i][j]);
 #pragma unroll
-            for (int o = 16; o; o >>= 1) rowabs += __shfl_xor_sync(FULL, rowabs, o);
-            if (lane == 0 && i < R) atomicMax(&imax_bits, __float_as_uint(rowabs));
+            for (int o = 16; o; o >>= 1) rs += __shfl_xor_sync(FULL, rs, o);
+            if (tx == 0 && r0 + i < R) atomicMax(&imax_bits, __float_as_uint(rs));
         }
         __syncthreads();
         const float kappa = __uint_as_float(gmax_bits) * __uint_as_float(imax_bits);
-        use64 = !(kappa <= 2e4f);
+        use64 = !(kappa <= 2e5f);
     }
     if (use64) {
-        const double flag = chol_fp64(G, R, tr, L64, L64 + RR, invd64, sinv, srs, &sfail);
+        double tr = 0.0;
+        for (int j = tid; j < R; j += NT) tr += G[(size_t)j * R + j];
+        tr = block_sum_d(tr, red);
+        const double flag = chol_fp64(G, R, tr, L64, L64 + (size_t)R * R, invd64, sinv, srs, &sfail);
         if (tid == 0) {
             scal[SCAL_FLAGS] = 10.0 + flag;  // FP64 path: 10 ok, 11 shifted, 12 failed
             scal[SCAL_GS] = 0.0;
@@ -346,13 +369,13 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_mixed(const float* __r
         return;
     }
 #pragma unroll
-    for (int sl = 0; sl < CHOL_RPW; ++sl) {
-        const int i = warp + nw * sl;
-        if (i >= R) break;
+    for (int i = 0; i < IR; ++i) {
+        const int r = r0 + i;
+        if (r >= R) break;
 #pragma unroll
-        for (int t = 0; t < RT; ++t) {
-            const int j = lane + 32 * t;
-            if (j < R) Ginv[(size_t)i * R + j] = a[sl][t];
+        for (int j = 0; j < JC; ++j) {
+            const int c = c0 + j;
+            if (c < R) Ginv[(size_t)r * R + c] = a[i][j] * (dsc[r] * dsc[c]);
         }
     }
     if (tid == 0) {
@@ -370,7 +393,7 @@ __device__ __forceinline__ void bf16_split(float x, uint16_t& hi, uint16_t& lo) 
     lo = __bfloat16_as_ushort(l);
 }
 
-constexpr int SOLVE_THREADS = 128;
+constexpr int SOLVE_THREADS = 64;
 
 // shared layout of the solve kernel (doubles unless noted)
 struct SolveSmem {
@@ -393,17 +416,24 @@ __host__ __device__ inline SolveSmem solve_smem(int R) {
     return L;
 }
 
-// One row x per block of 128 threads.  Thread (tj, tk) = (tid mod R, tid / R)
-// handles column tj over the k-slice tk of every reduction (nks = 128 / R slices).
+// One row x per block of 64 threads; in the refinement path thread t owns the
+// columns t + 64 c (c < CT) and computes every dot product of those columns by
+// itself (four partial sums, no reductions across threads).  Per iteration:
+//   r = m - x Gamma   (FP64, Gamma staged in shared memory)
+//   d = r G32         (FP32; r is small, so FP32 carries it to full accuracy)
+//   x += d
+// and two barriers.  It stops once the error left after the step, estimated as
+// rho ||d||_inf with rho the contraction seen between steps, is below
+// 2^-44 ||x||_inf: far below the FP32 error of the MTTKRP that forms m.
 template <int RT>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
     const float* __restrict__ M, const double* __restrict__ W, const double* __restrict__ G,
     const float* __restrict__ Ginv, const double* __restrict__ L64, const double* __restrict__ invd64,
     const int* __restrict__ mode, cpk::SolveOut o, int s, int R, double* __restrict__ scal,
     double* __restrict__ scal_part, unsigned* __restrict__ dev_err) {
+    constexpr int CT = (RT + 1) / 2;  // columns per thread in the refinement path
     extern __shared__ __align__(16) double sm[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ int s_conv;
     const SolveSmem lay = solve_smem(R);
     double* sG = sm + lay.G;
     float* sGi = reinterpret_cast<float*>(sm + lay.Gi);
@@ -416,20 +446,17 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
     const int x = blockIdx.x;
     const int path = *mode;
     const int RR = R * R;
-    const int nks = (R <= SOLVE_THREADS) ? SOLVE_THREADS / R : 1;
-    const bool act = tid < nks * R;
-    const int tj = act ? tid % R : 0, tk = act ? tid / R : 0;
-    const int k0 = tk * R / nks, k1 = (tk + 1) * R / nks;
-    const bool owner = act && tk == 0;          // thread that finalises column tj
-
-    double aold = 0.0, m = 0.0, xj = 0.0;
-    if (owner) {
-        aold = o.A64[(size_t)x * R + tj];
-        m = (double)M[(size_t)x * R + tj];
-    }
     double sc[CP_NSCAL];
 #pragma unroll
     for (int i = 0; i < CP_NSCAL; ++i) sc[i] = 0.0;
+    double xj[CT], mj[CT], aold[CT];
+#pragma unroll
+    for (int c = 0; c < CT; ++c) {
+        const int j = tid + SOLVE_THREADS * c;
+        xj[c] = 0.0;
+        aold[c] = (j < R) ? o.A64[(size_t)x * R + j] : 0.0;
+        mj[c] = (j < R) ? (double)M[(size_t)x * R + j] : 0.0;
+    }
 
     if (path == 0) {
         // stage Gamma and G32 with two bulk copies (sizes rounded up to 16 bytes;
@@ -452,29 +479,35 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
                 "l"(Ginv), "r"(bytesGi), "r"(b)
                 : "memory");
         }
-        if (owner) xv[tj] = aold;   // for the V term
+#pragma unroll
+        for (int c = 0; c < CT; ++c) {
+            const int j = tid + SOLVE_THREADS * c;
+            if (j < R) xv[j] = aold[c];  // for the V term
+        }
         __syncthreads();
         if (W) {
-            // V(x,:) = A_old(x,:) W (Eq. V_nij), FP64, k-split
-            double v0 = 0.0, v1 = 0.0;
-            if (act) {
-                int q = k0;
-                for (; q + 1 < k1; q += 2) {
-                    v0 = fma(xv[q], W[(size_t)q * R + tj], v0);
-                    v1 = fma(xv[q + 1], W[(size_t)(q + 1) * R + tj], v1);
+            // V(x,:) = A_old(x,:) W (Eq. V_nij), FP64
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                const int j = tid + SOLVE_THREADS * c;
+                if (j >= R) continue;
+                double v0 = 0.0, v1 = 0.0;
+                int q = 0;
+                for (; q + 1 < R; q += 2) {
+                    v0 = fma(xv[q], W[(size_t)q * R + j], v0);
+                    v1 = fma(xv[q + 1], W[(size_t)(q + 1) * R + j], v1);
                 }
-                if (q < k1) v0 = fma(xv[q], W[(size_t)q * R + tj], v0);
-                part[tid] = v0 + v1;
-            }
-            __syncthreads();
-            if (owner) {
-                double v = 0.0;
-                for (int q = 0; q < nks; ++q) v += part[q * R + tj];
-                m += v;
+                if (q < R) v0 = fma(xv[q], W[(size_t)q * R + j], v0);
+                const double v = v0 + v1;
+                mj[c] += v;
                 sc[SCAL_V2] += v * v;
             }
         }
-        if (owner) rv[tj] = (float)m;
+#pragma unroll
+        for (int c = 0; c < CT; ++c) {
+            const int j = tid + SOLVE_THREADS * c;
+            if (j < R) rv[j] = (float)mj[c];
+        }
         // bounded wait for the staged matrices (about 1 s)
         {
             const long long t0 = clock64();
@@ -498,90 +531,86 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
             }
         }
         __syncthreads();
-        // x0 = m G32 (FP32, k-split)
-        {
-            float a0 = 0.f, a1 = 0.f;
-            if (act) {
-                int k = k0;
-                for (; k + 1 < k1; k += 2) {
-                    a0 = fmaf(rv[k], sGi[k * R + tj], a0);
-                    a1 = fmaf(rv[k + 1], sGi[(k + 1) * R + tj], a1);
+        // d = rv G32 for the owned columns (FP32, four partial sums)
+        auto apply_ginv = [&](float* d) {
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                const int j = tid + SOLVE_THREADS * c;
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                if (j < R) {
+                    int k = 0;
+                    for (; k + 3 < R; k += 4) {
+                        a0 = fmaf(rv[k], sGi[k * R + j], a0);
+                        a1 = fmaf(rv[k + 1], sGi[(k + 1) * R + j], a1);
+                        a2 = fmaf(rv[k + 2], sGi[(k + 2) * R + j], a2);
+                        a3 = fmaf(rv[k + 3], sGi[(k + 3) * R + j], a3);
+                    }
+                    for (; k < R; ++k) a0 = fmaf(rv[k], sGi[k * R + j], a0);
                 }
-                if (k < k1) a0 = fmaf(rv[k], sGi[k * R + tj], a0);
-                part[tid] = (double)(a0 + a1);
+                d[c] = (a0 + a1) + (a2 + a3);
             }
-            __syncthreads();
-            if (owner) {
-                double v = 0.0;
-                for (int q = 0; q < nks; ++q) v += part[q * R + tj];
-                xj = v;
-            }
+        };
+        float d0[CT];
+        apply_ginv(d0);
+        float dmx = 0.f, xmx = 0.f;
+#pragma unroll
+        for (int c = 0; c < CT; ++c) {
+            const int j = tid + SOLVE_THREADS * c;
+            xj[c] = (double)d0[c];
+            if (j < R) xv[j] = xj[c];
         }
+        __syncthreads();
         double prev = 0.0;
-        if (tid == 0) s_conv = 0;
-        for (int itr = 0; itr < 12; ++itr) {
-            if (owner) xv[tj] = xj;
-            __syncthreads();
-            // r = m - x Gamma (FP64)
-            if (act) {
+        bool conv = false;
+        for (int itr = 0; itr < 30; ++itr) {
+            // r = m - x Gamma (FP64, four partial sums)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                const int j = tid + SOLVE_THREADS * c;
+                if (j >= R) continue;
                 double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
-                int k = k0;
-                for (; k + 3 < k1; k += 4) {
-                    r0 = fma(xv[k], sG[(size_t)k * R + tj], r0);
-                    r1 = fma(xv[k + 1], sG[(size_t)(k + 1) * R + tj], r1);
-                    r2 = fma(xv[k + 2], sG[(size_t)(k + 2) * R + tj], r2);
-                    r3 = fma(xv[k + 3], sG[(size_t)(k + 3) * R + tj], r3);
+                int k = 0;
+                for (; k + 3 < R; k += 4) {
+                    r0 = fma(xv[k], sG[(size_t)k * R + j], r0);
+                    r1 = fma(xv[k + 1], sG[(size_t)(k + 1) * R + j], r1);
+                    r2 = fma(xv[k + 2], sG[(size_t)(k + 2) * R + j], r2);
+                    r3 = fma(xv[k + 3], sG[(size_t)(k + 3) * R + j], r3);
                 }
-                for (; k < k1; ++k) r0 = fma(xv[k], sG[(size_t)k * R + tj], r0);
-                part[tid] = (r0 + r1) + (r2 + r3);
+                for (; k < R; ++k) r0 = fma(xv[k], sG[(size_t)k * R + j], r0);
+                rv[j] = (float)(mj[c] - ((r0 + r1) + (r2 + r3)));
             }
             __syncthreads();
-            if (owner) {
-                double v = 0.0;
-                for (int q = 0; q < nks; ++q) v += part[q * R + tj];
-                rv[tj] = (float)(m - v);
+            float dd[CT];
+            apply_ginv(dd);
+            dmx = 0.f;
+            xmx = 0.f;
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                const int j = tid + SOLVE_THREADS * c;
+                xj[c] += (double)dd[c];
+                dmx = fmaxf(dmx, fabsf(dd[c]));
+                xmx = fmaxf(xmx, fabsf((float)xj[c]));
+                if (j < R) xv[j] = xj[c];
             }
-            __syncthreads();
-            // d = r G32 ; x += d
-            float a0 = 0.f, a1 = 0.f;
-            if (act) {
-                int k = k0;
-                for (; k + 1 < k1; k += 2) {
-                    a0 = fmaf(rv[k], sGi[k * R + tj], a0);
-                    a1 = fmaf(rv[k + 1], sGi[(k + 1) * R + tj], a1);
-                }
-                if (k < k1) a0 = fmaf(rv[k], sGi[k * R + tj], a0);
-                part[tid] = (double)(a0 + a1);
+#pragma unroll
+            for (int o2 = 16; o2; o2 >>= 1) {
+                dmx = fmaxf(dmx, __shfl_xor_sync(FULL, dmx, o2));
+                xmx = fmaxf(xmx, __shfl_xor_sync(FULL, xmx, o2));
             }
-            __syncthreads();
-            double dabs = 0.0, xabs = 0.0;
-            if (owner) {
-                double d = 0.0;
-                for (int q = 0; q < nks; ++q) d += part[q * R + tj];
-                xj += d;
-                dabs = fabs(d);
-                xabs = fabs(xj);
-            }
-            dabs = warp_max_d(dabs);
-            xabs = warp_max_d(xabs);
             if (lane == 0) {
-                red[warp] = dabs;
-                red[4 + warp] = xabs;
+                red[warp] = dmx;
+                red[2 + warp] = xmx;
             }
-            __syncthreads();
-            const double dmax = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
-            const double xmax = fmax(fmax(red[4], red[5]), fmax(red[6], red[7]));
+            __syncthreads();  // also publishes xv for the next residual
+            const double dmax = fmax(red[0], red[1]), xmax = fmax(red[2], red[3]);
             // remaining error after this step is about rho * dmax, rho = dmax / prev
             const double rho = (itr > 0 && prev > 0.0) ? dmax / prev : 1.0;
-            const bool conv = rho * dmax <= 0x1.0p-50 * xmax || dmax == 0.0;
+            conv = rho * dmax <= 0x1.0p-44 * xmax || dmax == 0.0;
             prev = dmax;
-            __syncthreads();
-            if (conv) {
-                if (tid == 0) s_conv = 1;
-                break;
-            }
+            if (conv) break;
+            __syncthreads();  // red[] is rewritten by the next step
         }
-        if (tid == 0 && !s_conv) scal[SCAL_FLAGS] = 3.0;
+        if (tid == 0 && !conv) scal[SCAL_FLAGS] = 3.0;
     } else {
         // FP64 substitution with the fallback factor: warp 0, lane l owns l + 32 t
         if (warp == 0) {
@@ -653,10 +682,6 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
             }
         }
         __syncthreads();
-        if (owner) {
-            xj = xv[tj];
-            m = mv[tj];
-        }
         if (warp != 0) sc[SCAL_V2] = 0.0;
     }
     // outputs: FP64 master, FP32 copy, split operand copies, dA, scalar partials
@@ -688,9 +713,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
         sc[SCAL_M2] += mj * mj;
     };
     if (path == 0) {
-        if (owner) emit(tj, xj, m, aold);
+#pragma unroll
+        for (int c = 0; c < CT; ++c) {
+            const int j = tid + SOLVE_THREADS * c;
+            if (j < R) emit(j, xj[c], mj[c], aold[c]);
+        }
     } else {
-        // the FP64 path covers any R: every thread takes columns tid, tid + 128, ...
+        // the FP64 path covers any R: every thread takes columns tid, tid + 64, ...
         for (int j = tid; j < R; j += SOLVE_THREADS) emit(j, xv[j], mv[j], o.A64[(size_t)x * R + j]);
     }
     // block reduction of the 8 scalars: warp sums, then warp 0
@@ -737,12 +766,15 @@ cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int
         return cudaGetLastError();
     }
     k_gamma_form<<<(R * R + 255) / 256, 256, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, G32, W);
-    switch ((R + 31) / 32) {
-        case 1: k_chol_mixed<1><<<1, CHOL_THREADS, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode); break;
-        case 2: k_chol_mixed<2><<<1, CHOL_THREADS, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode); break;
-        case 3: k_chol_mixed<3><<<1, CHOL_THREADS, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode); break;
-        default: k_chol_mixed<4><<<1, CHOL_THREADS, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode); break;
-    }
+    // (threads / 32, rows per thread, columns per thread): TY x IR >= R, 32 JC >= R
+    if (R <= 32)
+        k_gj_inv<4, 8, 1><<<1, 128, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
+    else if (R <= 64)
+        k_gj_inv<4, 16, 2><<<1, 128, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
+    else if (R <= 96)
+        k_gj_inv<8, 12, 3><<<1, 256, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
+    else
+        k_gj_inv<8, 16, 4><<<1, 256, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
     return cudaGetLastError();
 }
 
