@@ -76,11 +76,12 @@ struct cp_ctx {
     cudaEvent_t ev_ready = nullptr, ev_chol = nullptr;  // overlapped with the MTTKRP
     bool chol_pending = false;
     int* d_mode = nullptr;      // 0: refinement path, 1: FP64 substitution path
-    double* gram_part = nullptr;
-    double* tile_gs = nullptr;     // per-tile <Gamma, S> of the fused Gram kernel
-    unsigned* gram_cnt = nullptr;  // its completion counters (zero between launches)
-    int nchunk = 1;
-    double* scal_part = nullptr;
+    double* tile_gs = nullptr;     // per mode: tile shares of <Gamma, S>
+    int ntiles = 1;
+    double* scal_part = nullptr;   // per mode: the solve's per-block scalars
+    // the update's scalars are reduced on their own stream, off the critical path
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_g = nullptr, ev_a = nullptr, ev_scal[CP_MAXN] = {0};
     double* scal_hist = nullptr;   // [cap][N][CP_NSCAL]
     int scal_hist_cap = 0;
     double* red_part = nullptr;
@@ -405,11 +406,17 @@ cp_status update_mode(cp_ctx* c, int u, const float* M, bool pp, double* scal) {
     o.dA32 = pp ? c->dA32[u] : nullptr;
     o.dA64 = pp ? c->dA64[u] : nullptr;
     int nblk = 0;
+    double* sp = c->scal_part + (size_t)u * c->smax * CP_NSCAL;
+    double* tg = c->tile_gs + (size_t)u * c->ntiles;
+    CKCUDA(c, cudaStreamWaitEvent(c->st, c->ev_scal[u], 0));  // sp / tg of mode u are free
     LAUNCH(c, cpk::solve_mixed(M, pp ? c->W : nullptr, c->Gamma, c->Ginv, c->L, c->invd, c->d_mode, o, s, R, scal,
-                               c->scal_part, &nblk, c->dev_err, c->st));
-    const int nchunk = std::max(1, std::min(c->nchunk, (s + 15) / 16));
-    LAUNCH(c, cpk::gram_update(c->A64[u], pp ? c->dA64[u] : nullptr, s, R, c->gram_part, nchunk, c->scal_part,
-                               nblk, c->Gamma, c->S[u], c->dS[u], scal, c->tile_gs, c->gram_cnt, c->st));
+                               sp, &nblk, c->dev_err, c->st));
+    LAUNCH(c, cpk::gram(c->A64[u], pp ? c->dA64[u] : nullptr, s, R, c->Gamma, c->S[u], c->dS[u], tg, c->st));
+    CKCUDA(c, cudaEventRecord(c->ev_g, c->st));
+    CKCUDA(c, cudaStreamWaitEvent(c->aux, c->ev_g, 0));
+    LAUNCH(c, cpk::scal_fin(sp, nblk, tg, c->ntiles, scal, c->aux));
+    CKCUDA(c, cudaEventRecord(c->ev_scal[u], c->aux));
+    CKCUDA(c, cudaEventRecord(c->ev_a, c->aux));
     c->ver[u] = ++c->vclock;
     return CP_OK;
 }
@@ -427,6 +434,7 @@ cp_status check_dev_err(cp_ctx* c) {
 cp_status harvest(cp_ctx* c, int k, const int* kinds, const int* inits, int first_event) {
     std::vector<double>& h = c->last_hist;
     h.assign((size_t)k * c->N * CP_NSCAL, 0.0);
+    CKCUDA(c, cudaStreamWaitEvent(c->st, c->ev_a, 0));
     CKCUDA(c, cudaMemcpyAsync(h.data(), c->scal_hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CKST(check_dev_err(c));
     for (int i = 0; i < k; ++i) {
@@ -694,9 +702,7 @@ cp_status init_grams(cp_ctx* c) {
         const int s = (int)c->dims[n];
         LAUNCH(c, cpk::factor_copies(c->A64[n], c->A32[n], c->bhi[n], c->blo[n], c->bt32[n], s, c->R,
                                      c->Rpad, c->Kpad[n], c->st));
-        const int nchunk = std::max(1, std::min(c->nchunk, (s + 15) / 16));
-        LAUNCH(c, cpk::gram_update(c->A64[n], nullptr, s, c->R, c->gram_part, nchunk, c->scal_part, 0, nullptr,
-                                   c->S[n], nullptr, c->red_part, c->tile_gs, c->gram_cnt, c->st));
+        LAUNCH(c, cpk::gram(c->A64[n], nullptr, s, c->R, nullptr, c->S[n], nullptr, nullptr, c->st));
     }
     return CP_OK;
 }
@@ -727,9 +733,7 @@ cp_status direct_resid(cp_ctx* c, double* r) {
 // S(i) (and dS(i) when `pp`) from the factors now in A64 (and dA64)
 cp_status regram(cp_ctx* c, int i, bool pp) {
     const int s = (int)c->dims[i];
-    const int nchunk = std::max(1, std::min(c->nchunk, (s + 15) / 16));
-    LAUNCH(c, cpk::gram_update(c->A64[i], pp ? c->dA64[i] : nullptr, s, c->R, c->gram_part, nchunk, c->scal_part,
-                               0, nullptr, c->S[i], c->dS[i], c->red_part, c->tile_gs, c->gram_cnt, c->st));
+    LAUNCH(c, cpk::gram(c->A64[i], pp ? c->dA64[i] : nullptr, s, c->R, nullptr, c->S[i], c->dS[i], nullptr, c->st));
     return CP_OK;
 }
 
@@ -897,7 +901,12 @@ void free_all(cp_ctx* c) {
     if (c->ev_ready) { cudaEventDestroy(c->ev_ready); c->ev_ready = nullptr; }
     if (c->ev_chol) { cudaEventDestroy(c->ev_chol); c->ev_chol = nullptr; }
     F(c->Mt); F(c->d_Slist); F(c->d_dSlist); F(c->Gamma); F(c->L); F(c->invd); F(c->W);
-    F(c->gram_part); F(c->tile_gs); F(c->gram_cnt); F(c->scal_part); F(c->scal_hist); F(c->red_part); F(c->d_red_out); F(c->dev_err);
+    if (c->aux) { cudaStreamSynchronize(c->aux); cudaStreamDestroy(c->aux); c->aux = nullptr; }
+    F(c->tile_gs); F(c->scal_part);
+    for (cudaEvent_t* e : {&c->ev_g, &c->ev_a})
+        if (*e) { cudaEventDestroy(*e); *e = nullptr; }
+    for (int i = 0; i < CP_MAXN; ++i)
+        if (c->ev_scal[i]) { cudaEventDestroy(c->ev_scal[i]); c->ev_scal[i] = nullptr; } F(c->scal_hist); F(c->red_part); F(c->d_red_out); F(c->dev_err);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
 }
@@ -1014,15 +1023,13 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
     TRY(dalloc(c, &c->W, RR));
     TRY(dalloc(c, &c->L, 2 * (size_t)RR));
     TRY(dalloc(c, &c->invd, R));
-    c->nchunk = 16;
-    TRY(dalloc(c, &c->gram_part, (size_t)c->nchunk * 2 * RR));
-    {
-        const size_t nt = (size_t)((R + 15) / 16) * ((R + 15) / 16);
-        TRY(dalloc(c, &c->tile_gs, nt));
-        TRY(dalloc(c, &c->gram_cnt, nt + 1));
-        TRYC(cudaMemsetAsync(c->gram_cnt, 0, sizeof(unsigned) * (nt + 1), c->st));
-    }
-    TRY(dalloc(c, &c->scal_part, (size_t)c->smax * CP_NSCAL));
+    c->ntiles = cpk::gram_tiles(R);
+    TRY(dalloc(c, &c->tile_gs, (size_t)N * c->ntiles));
+    TRY(dalloc(c, &c->scal_part, (size_t)N * c->smax * CP_NSCAL));
+    TRYC(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+    TRYC(cudaEventCreateWithFlags(&c->ev_g, cudaEventDisableTiming));
+    TRYC(cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming));
+    for (int i = 0; i < N; ++i) TRYC(cudaEventCreateWithFlags(&c->ev_scal[i], cudaEventDisableTiming));
     TRY(dalloc(c, &c->red_part, 4096));
     TRY(dalloc(c, &c->d_red_out, 16));
     TRY(dalloc(c, &c->dev_err, 1));
@@ -1322,14 +1329,12 @@ cp_status cp_set_factor(cp_ctx* c, int mode, const double* A_host) {
     CKCUDA(c, cudaMemcpyAsync(c->A64[mode], A_host, sizeof(double) * s * c->R, cudaMemcpyHostToDevice, c->st));
     LAUNCH(c, cpk::factor_copies(c->A64[mode], c->A32[mode], c->bhi[mode], c->blo[mode], c->bt32[mode], s, c->R,
                                  c->Rpad, c->Kpad[mode], c->st));
-    const int nchunk = std::max(1, std::min(c->nchunk, (s + 15) / 16));
     // with PP operators present, dA = A - A_p and dS = A^T dA follow the new factor
     const bool pp = c->pp_valid;
     if (pp)
         LAUNCH(c, cpk::pp_delta(c->A64[mode], c->Ap64[mode], c->dA32[mode], c->dA64[mode], (int64_t)s * c->R, c->st));
-    LAUNCH(c, cpk::gram_update(c->A64[mode], pp ? c->dA64[mode] : nullptr, s, c->R, c->gram_part, nchunk,
-                               c->scal_part, 0, nullptr, c->S[mode], c->dS[mode], c->red_part, c->tile_gs,
-                               c->gram_cnt, c->st));
+    LAUNCH(c, cpk::gram(c->A64[mode], pp ? c->dA64[mode] : nullptr, s, c->R, nullptr, c->S[mode], c->dS[mode],
+                        nullptr, c->st));
     CKCUDA(c, cudaStreamSynchronize(c->st));
     c->ver[mode] = ++c->vclock;
     c->have_last = false;

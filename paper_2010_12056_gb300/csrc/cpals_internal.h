@@ -110,13 +110,15 @@ cudaError_t solve_mixed(const float* M, const double* W, const double* Gamma, co
                         int s, int R, double* scal, double* scal_part, int* nblk, unsigned* dev_err,
                         cudaStream_t st);
 
-// S = A^T A (and dS = A^T dA when dA != NULL) in one launch over row chunks;
-// with Gamma, scal_out[SCAL_GS] = <Gamma, S>; the solve's per-block scalars
-// (nblk blocks) are reduced into scal_out.  part: nchunk x 2 R^2 doubles;
-// tile_gs: ceil(R/16)^2 doubles; cnt: ceil(R/16)^2 + 1 counters, zero at first use.
-cudaError_t gram_update(const double* A, const double* dA, int s, int R, double* part, int nchunk,
-                        const double* scal_part, int nblk, const double* Gamma, double* S, double* dS,
-                        double* scal_out, double* tile_gs, unsigned* cnt, cudaStream_t st);
+// S = A^T A (and dS = A^T dA when dA != NULL), one cluster launch over row
+// chunks; with Gamma and tile_gs (gram_tiles(R) doubles) also the tile shares of
+// <Gamma, S>.  scal_fin adds the solve's nblk per-block scalars and those shares
+// into scal_out (every slot but SCAL_FLAGS).
+int gram_tiles(int R);
+cudaError_t gram(const double* A, const double* dA, int s, int R, const double* Gamma, double* S,
+                 double* dS, double* tile_gs, cudaStream_t st);
+cudaError_t scal_fin(const double* scal_part, int nblk, const double* tile_gs, int ntiles, double* scal_out,
+                     cudaStream_t st);
 
 // refresh all operand copies of a factor from its FP64 master (after set_factor / init)
 cudaError_t factor_copies(const double* A64, float* A32, uint16_t* bhi, uint16_t* blo,

@@ -58,33 +58,38 @@ __device__ __forceinline__ void bf16_split(float x, uint16_t& hi, uint16_t& lo) 
 }
 
 
-// Gram of an updated factor, one launch: S = A^T A (and dS = A^T dA) over
-// row chunks, grid (R/16, R/16, chunks).  Each block writes its tile's partial
-// sum; the last block to finish a tile adds the chunk partials in chunk order
-// and contributes <Gamma, S> over the tile; the last tile to finish adds those
-// in tile order and reduces the solve kernel's per-block scalars.  Counters
-// return to zero, so the next launch may reuse them.  Partials written by
-// other blocks are read with ld.global.cg (L2), after a fence.
-constexpr int GRAM_MAX_CHUNKS = 16;
+// Gram of an updated factor: S = A^T A (and dS = A^T dA), grid (R/16, R/16, nc)
+// with clusters of (1, 1, nc): the nc CTAs of a cluster each sum one row chunk
+// of the same 16 x 16 tile; the partials meet in distributed shared memory and
+// CTA 0 of the cluster adds them in chunk order, writes the tile and its share
+// of <Gamma, S> (tile_gs).  No global fences or counters.
+constexpr int GRAM_MAX_CHUNKS = 8;
 
-__global__ void __launch_bounds__(256) k_gram_fin(const double* __restrict__ A,
-                                                  const double* __restrict__ dA, int s, int R,
-                                                  double* __restrict__ part, int rows_per,
-                                                  const double* __restrict__ scal_part, int nblk,
-                                                  const double* __restrict__ Gamma, int want_dS,
-                                                  double* __restrict__ S, double* __restrict__ dS,
-                                                  double* __restrict__ scal_out,
-                                                  double* __restrict__ tile_gs,
-                                                  unsigned* __restrict__ cnt) {
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ double ld_cluster_f64(const double* local, unsigned rank) {
+    uint32_t la = (uint32_t)__cvta_generic_to_shared(local), ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(rank));
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_gram_cl(const double* __restrict__ A,
+                                                 const double* __restrict__ dA, int s, int R,
+                                                 int rows_per, const double* __restrict__ Gamma,
+                                                 double* __restrict__ S, double* __restrict__ dS,
+                                                 double* __restrict__ tile_gs) {
     __shared__ double a1[16][17], a2[16][17], d2[16][17];
+    __shared__ double ps[256], pd[256];
     __shared__ double red[32];
-    __shared__ unsigned s_last;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int r1 = blockIdx.x * 16 + ty, r2 = blockIdx.y * 16 + tx;
-    const int c = blockIdx.z;
+    const int c = blockIdx.z, nc = gridDim.z;
     const int x0 = c * rows_per, x1 = min(s, x0 + rows_per);
-    const size_t RR = (size_t)R * R;
-    double acc = 0.0, accd = 0.0, acc2 = 0.0, accd2 = 0.0;
+    double acc0 = 0.0, acc1 = 0.0, accd0 = 0.0, accd1 = 0.0;
     for (int xb = x0; xb < x1; xb += 16) {
         const int x = xb + ty;
         const int ca = blockIdx.x * 16 + tx, cb = blockIdx.y * 16 + tx;
@@ -94,77 +99,68 @@ __global__ void __launch_bounds__(256) k_gram_fin(const double* __restrict__ A,
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < 16; k += 2) {
-            acc = fma(a1[k][ty], a2[k][tx], acc);
-            acc2 = fma(a1[k + 1][ty], a2[k + 1][tx], acc2);
+            acc0 = fma(a1[k][ty], a2[k][tx], acc0);
+            acc1 = fma(a1[k + 1][ty], a2[k + 1][tx], acc1);
             if (dA) {
-                accd = fma(a1[k][ty], d2[k][tx], accd);
-                accd2 = fma(a1[k + 1][ty], d2[k + 1][tx], accd2);
+                accd0 = fma(a1[k][ty], d2[k][tx], accd0);
+                accd1 = fma(a1[k + 1][ty], d2[k + 1][tx], accd1);
             }
         }
         __syncthreads();
     }
-    acc += acc2;
-    accd += accd2;
-    const bool in = r1 < R && r2 < R;
-    const size_t e = (size_t)r1 * R + r2;
-    if (in) {
-        part[(size_t)c * 2 * RR + e] = acc;
-        if (dA) part[(size_t)c * 2 * RR + RR + e] = accd;
-    }
-    const unsigned tile = blockIdx.y * gridDim.x + blockIdx.x, ntiles = gridDim.x * gridDim.y;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&cnt[tile], 1u) == gridDim.z - 1) ? 1u : 0u;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // chunk partials of this tile: all loads issued before the sums (chunk order kept)
-    double gs = 0.0;
-    if (in) {
-        const int nc = (int)gridDim.z;
-        double pv[GRAM_MAX_CHUNKS], pd[GRAM_MAX_CHUNKS];
+    ps[tid] = acc0 + acc1;
+    pd[tid] = accd0 + accd1;
+    cluster_sync_all();
+    if (c == 0) {
+        // cluster dims (1, 1, nc): the rank of a CTA in its cluster is blockIdx.z
+        double pv[GRAM_MAX_CHUNKS], pq[GRAM_MAX_CHUNKS];
 #pragma unroll
         for (int q = 0; q < GRAM_MAX_CHUNKS; ++q) {
-            pv[q] = q < nc ? __ldcg(part + (size_t)q * 2 * RR + e) : 0.0;
-            pd[q] = (q < nc && want_dS) ? __ldcg(part + (size_t)q * 2 * RR + RR + e) : 0.0;
+            pv[q] = q < nc ? ld_cluster_f64(&ps[tid], (unsigned)q) : 0.0;
+            pq[q] = (q < nc && dA) ? ld_cluster_f64(&pd[tid], (unsigned)q) : 0.0;
         }
         double v = 0.0, d = 0.0;
 #pragma unroll
         for (int q = 0; q < GRAM_MAX_CHUNKS; ++q) {
             v += pv[q];
-            d += pd[q];
+            d += pq[q];
         }
-        S[e] = v;
-        if (want_dS) dS[e] = d;
-        if (Gamma) gs = Gamma[e] * v;
+        double gs = 0.0;
+        if (r1 < R && r2 < R) {
+            const size_t e = (size_t)r1 * R + r2;
+            S[e] = v;
+            if (dA) dS[e] = d;
+            if (Gamma) gs = Gamma[e] * v;
+        }
+        if (tile_gs) {
+            gs = block_sum(gs, red);
+            if (tid == 0) tile_gs[blockIdx.y * gridDim.x + blockIdx.x] = gs;
+        }
     }
-    gs = block_sum(gs, red);
-    if (tid == 0) {
-        tile_gs[tile] = gs;
-        cnt[tile] = 0u;
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&cnt[ntiles], 1u) == ntiles - 1) ? 1u : 0u;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (tid == 0) cnt[ntiles] = 0u;
-    // <Gamma, S> over tiles and the solve's scalars: loads first, then fixed-order sums
-    double t = 0.0;
-    for (unsigned q = tid; q < ntiles; q += blockDim.x) t += __ldcg(tile_gs + q);
+    cluster_sync_all();  // every CTA's partials stay readable until CTA 0 is done
+}
+
+// The update's scalars: the solve's per-block partials and the tile shares of
+// <Gamma, S>, added in a fixed order.  Off the critical path (own stream).
+__global__ void __launch_bounds__(256) k_scal_fin(const double* __restrict__ scal_part, int nblk,
+                                                  const double* __restrict__ tile_gs, int ntiles,
+                                                  double* __restrict__ scal_out) {
+    __shared__ double red[32];
+    const int tid = threadIdx.x;
     double v[CP_NSCAL];
 #pragma unroll
     for (int slot = 0; slot < CP_NSCAL; ++slot) v[slot] = 0.0;
     for (int b = tid; b < nblk; b += blockDim.x) {
         double w[CP_NSCAL];
 #pragma unroll
-        for (int slot = 0; slot < CP_NSCAL; ++slot) w[slot] = __ldcg(scal_part + (size_t)b * CP_NSCAL + slot);
+        for (int slot = 0; slot < CP_NSCAL; ++slot) w[slot] = scal_part[(size_t)b * CP_NSCAL + slot];
 #pragma unroll
         for (int slot = 0; slot < CP_NSCAL; ++slot) v[slot] += w[slot];
     }
+    double t = 0.0;
+    for (int q = tid; q < ntiles; q += blockDim.x) t += tile_gs[q];
     t = block_sum(t, red);
-    if (tid == 0 && Gamma) scal_out[SCAL_GS] = t;
+    if (tid == 0) scal_out[SCAL_GS] = t;
 #pragma unroll
     for (int slot = 0; slot < CP_NSCAL; ++slot) {
         if (slot == SCAL_GS || slot == SCAL_FLAGS) continue;
@@ -450,15 +446,33 @@ cudaError_t add_aw(const float* Mt, const double* A, const double* W, int s, int
     return cudaGetLastError();
 }
 
-cudaError_t gram_update(const double* A, const double* dA, int s, int R, double* part, int nchunk,
-                        const double* scal_part, int nblk, const double* Gamma, double* S, double* dS,
-                        double* scal_out, double* tile_gs, unsigned* cnt, cudaStream_t st) {
-    if (nchunk > GRAM_MAX_CHUNKS) nchunk = GRAM_MAX_CHUNKS;
-    const int rows_per = (s + nchunk - 1) / nchunk;
-    nchunk = (s + rows_per - 1) / rows_per;  // every chunk non-empty
-    dim3 grid((R + 15) / 16, (R + 15) / 16, nchunk);
-    k_gram_fin<<<grid, 256, 0, st>>>(A, dA, s, R, part, rows_per, scal_part, nblk, Gamma, dA ? 1 : 0, S, dS,
-                                     scal_out, tile_gs, cnt);
+int gram_tiles(int R) { return ((R + 15) / 16) * ((R + 15) / 16); }
+
+cudaError_t gram(const double* A, const double* dA, int s, int R, const double* Gamma, double* S,
+                 double* dS, double* tile_gs, cudaStream_t st) {
+    int nc = (s + 31) / 32;  // about 32 rows per chunk
+    if (nc > GRAM_MAX_CHUNKS) nc = GRAM_MAX_CHUNKS;
+    if (nc < 1) nc = 1;
+    const int rows_per = (s + nc - 1) / nc;
+    nc = (s + rows_per - 1) / rows_per;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((R + 15) / 16, (R + 15) / 16, nc);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = nc;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_gram_cl, A, dA, s, R, rows_per, Gamma, S, dS, tile_gs);
+}
+
+cudaError_t scal_fin(const double* scal_part, int nblk, const double* tile_gs, int ntiles, double* scal_out,
+                     cudaStream_t st) {
+    k_scal_fin<<<1, 256, 0, st>>>(scal_part, nblk, tile_gs, ntiles, scal_out);
     return cudaGetLastError();
 }
 

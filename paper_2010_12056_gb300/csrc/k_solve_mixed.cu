@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
             const double dmax = fmax(red[0], red[1]), xmax = fmax(red[2], red[3]);
             // remaining error after this step is about rho * dmax, rho = dmax / prev
             const double rho = (itr > 0 && prev > 0.0) ? dmax / prev : 1.0;
-            conv = rho * dmax <= 0x1.0p-44 * xmax || dmax == 0.0;
+            conv = rho * dmax <= 0x1.0p-36 * xmax || dmax == 0.0;
             prev = dmax;
             if (conv) break;
             __syncthreads();  // red[] is rewritten by the next step
@@ -766,15 +766,14 @@ cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int
         return cudaGetLastError();
     }
     k_gamma_form<<<(R * R + 255) / 256, 256, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, G32, W);
-    // (threads / 32, rows per thread, columns per thread): TY x IR >= R, 32 JC >= R
+    // (warps, rows per thread, columns per thread): TY x IR >= R, 32 JC >= R.
+    // Sixteen warps hide the latency of each step's dependent chain.
     if (R <= 32)
-        k_gj_inv<4, 8, 1><<<1, 128, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
+        k_gj_inv<8, 4, 1><<<1, 256, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
     else if (R <= 64)
-        k_gj_inv<4, 16, 2><<<1, 128, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
-    else if (R <= 96)
-        k_gj_inv<8, 12, 3><<<1, 256, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
+        k_gj_inv<16, 4, 2><<<1, 512, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
     else
-        k_gj_inv<8, 16, 4><<<1, 256, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
+        k_gj_inv<16, 8, 4><<<1, 512, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
     return cudaGetLastError();
 }
 
