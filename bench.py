@@ -48,11 +48,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS) + ["policy"])
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32", "bf16x3", "bf16", "tf32x3"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    # learned PP policy experiment (--workload policy)
+    ap.add_argument("--train-tensors", type=int, default=512)
+    ap.add_argument("--eval-tensors", type=int, default=64)
+    ap.add_argument("--probe-sweeps", type=int, default=40)
+    ap.add_argument("--target-sweeps", type=int, default=60)
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--policy-dims", default="256,256,256")
     return ap.parse_args()
 
 
@@ -183,8 +190,95 @@ def run_reference(args, wl, rank):
     print(json.dumps(line), flush=True)
 
 
+def policy_problem(i, dims, base_seed):
+    """The i-th tensor of the policy study: collinear rank-R factors, R in {16, 32, 64},
+    cosine U[0.5, 0.95], noise log-uniform in [1e-4, 1e-2] (draws from a seeded generator)."""
+    import numpy as np
+    import synth
+    g = np.random.default_rng(base_seed + i)
+    R = (16, 32, 64)[i % 3]
+    C = float(g.uniform(0.5, 0.95))
+    eta = float(10.0 ** g.uniform(-4.0, -2.0))
+    T, _, _ = synth.make_problem_device(base_seed + i, list(dims), R, law="collinear", eta=eta, C=C)
+    return T, R, C, eta
+
+
+def run_policy(args):
+    """Learned PP policy: traces from the training tensors (cp_pp_probe), training with the
+    library's kernels, then device time to reach exact MSDT's fit after --target-sweeps sweeps
+    on held-out tensors for exact MSDT, Alg. 2 with eps = 0.1, and the learned policy."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2010_12056_gb300 import policy as pol
+    import paper_2010_12056_gb300 as pkg
+    dims = tuple(int(x) for x in args.policy_dims.split(","))
+    train_seed, eval_seed = 20101205 + 4000, 20101205 + 5000
+    t0 = time.perf_counter()
+    Xs, ys = [], []
+    for i in range(args.train_tensors):
+        T, R, C, eta = policy_problem(i, dims, train_seed)
+        X, y, _ = pol.collect(T, R, args.probe_sweeps, prec=args.prec, seed=1 + i, min_gain=1e-9)
+        Xs.append(X)
+        ys.append(y)
+        del T
+    X = np.concatenate(Xs)
+    y = np.concatenate(ys)
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    policy = pol.train(X, y, steps=args.train_steps, lr=3e-3, seed=0)
+    t_train = time.perf_counter() - t0
+    acc = pol.accuracy(policy, X, y)
+    res = {"msdt": [], "pp": [], "policy": []}
+    per = []
+    for i in range(args.eval_tensors):
+        T, R, C, eta = policy_problem(i, dims, eval_seed)
+        ctx = pkg.CPContext(T, R, prec=args.prec, seed=7 + i)
+        ctx.sweep_msdt(args.target_sweeps)
+        target = ctx.fit(exact=True)[1] + 1e-6   # equal fit: within 1e-6
+        ctx.close()
+        row = {"R": R, "C": round(C, 3), "eta": eta, "target_resid": target}
+        for m in ("msdt", "pp", "policy"):
+            ms, k, r, tr = pol.time_to_target(T, R, m, target, 3 * args.target_sweeps, prec=args.prec,
+                                              seed=7 + i, eps=0.1, policy=policy if m == "policy" else None)
+            res[m].append(ms)
+            row[m] = {"ms": ms, "sweeps": k,
+                      "approx": sum(t["kind"] == "pp" for t in tr),
+                      "rolled_back": sum(t["rolled_back"] for t in tr)}
+        per.append(row)
+        del T
+    tot = {m: float(np.sum(v)) for m, v in res.items()}
+    reached = {m: int(np.sum(np.isfinite(v))) for m, v in res.items()}
+    both = np.isfinite(res["msdt"]) & np.isfinite(res["pp"]) & np.isfinite(res["policy"])
+    common = {m: float(np.sum(np.asarray(v)[both])) for m, v in res.items()}
+    wins = {m: 0 for m in res}
+    for i in range(len(res["msdt"])):
+        wins[min(res, key=lambda m: res[m][i])] += 1
+    line = {
+        "metric": "device time to exact MSDT's fit after %d sweeps (+1e-6), held-out tensors" % args.target_sweeps,
+        "value": tot["policy"], "unit": "ms (sum over held-out tensors)", "n_gpus": 1,
+        "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "learned PP policy, %s collinear tensors" % "x".join(map(str, dims)),
+                   "train_tensors": args.train_tensors, "eval_tensors": args.eval_tensors,
+                   "probe_sweeps": args.probe_sweeps, "train_steps": args.train_steps, "prec": args.prec},
+        "total_ms": tot, "reached": reached, "wins": wins,
+        "total_ms_where_all_reached": common, "all_reached": int(both.sum()),
+        "policy_vs_pp": tot["pp"] / tot["policy"] if tot["policy"] > 0 else None,
+        "policy_vs_msdt": tot["msdt"] / tot["policy"] if tot["policy"] > 0 else None,
+        "train": {"samples": int(len(y)), "positive": float(np.mean(y)) if len(y) else None,
+                  "accuracy": acc, "collect_s": t_collect, "train_s": t_train},
+        "per_tensor": per,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "policy":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_policy(args)
+        return
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -64,11 +64,13 @@ typedef struct {
     double delta;     /* stopping tolerance on |r - r_old| (Alg. 1); <= 0: never  */
     int max_sweeps;   /* cap used by cp_run (<= 0: no cap)                        */
     int judge_every;  /* policy mode: direct residual every k sweeps (0 = off)    */
-    int use_policy;   /* unused: a policy is passed to cp_sweep_pp directly       */
+    int policy_gate;  /* 1: consult the policy only when approximating pays (see
+                         cp_sweep_pp); 0: before every sweep                  */
     uint64_t seed;    /* Philox4x32-10 seed of the default U[0,1) initial factors */
 } cp_config;
 
-/* Fill *cfg with defaults: bf16x3 TTM, eps 0.1, delta 0, judge every 5 sweeps. */
+/* Fill *cfg with defaults: bf16x3 TTM, eps 0.1, delta 0, judge every 5 sweeps,
+ * policy gate on. */
 void cp_config_default(cp_config *cfg);
 
 /*
@@ -136,13 +138,26 @@ cp_status cp_sweep_msdt(cp_ctx *ctx, int nsweeps);
  *           approximated sweep with the current operators (p_cur) and one with
  *           operators rebuilt now (p_new).  The sweep is approximated with the
  *           current operators if they exist and p_cur >= 0.5, else rebuilt and
- *           approximated if p_new >= 0.5, else regular (MSDT).  Every
- *           cfg.judge_every sweeps (the judge; 0 = never) the direct residual
- *           is computed; if it exceeds (1 + 1e-8) times the previous judged
- *           value, the factors return to their state at that judgement, the
+ *           approximated if p_new >= 0.5, else regular (MSDT).  The network
+ *           is consulted only while an approximated sweep, with its share of
+ *           the query and of the judge, is measured to cost less than the
+ *           cheapest regular sweep seen on this problem; before it has been
+ *           measured, only while the MTTKRP traffic it avoids (at about
+ *           6 TB/s) covers that share.  The first two policy-driven sweeps of a
+ *           context are regular.  cfg.policy_gate = 0 consults the network
+ *           before every sweep instead.  The judge (judge_every
+ *           > 0): before a run of approximated sweeps the state and its direct
+ *           residual are kept as the rollback point; after judge_every
+ *           approximated sweeps, or when a regular sweep is chosen after some,
+ *           the direct residual is computed again.  If it exceeds (1 + 1e-5)
+ *           times the rollback point's (1e-5: above the rounding noise of the
+ *           FP32 model values), the factors return to the rollback point, the
  *           operators are dropped, the undone sweeps stay in the trace with
  *           rolled_back = 1, and the rule above decides the next judge_every
- *           sweeps.  The judge's time is added to the sweep it follows.
+ *           sweeps (twice as many after each further rollback in a row, up to
+ *           64 judge_every).  An approximated sweep whose normal equations
+ *           break down (CP_ENOTSPD) is rolled back the same way.  Query and
+ *           judge time are added to the sweep's trace ms.
  */
 typedef struct cp_policy cp_policy;
 cp_status cp_sweep_pp(cp_ctx *ctx, int nsweeps, double eps, cp_policy *policy);

@@ -35,7 +35,7 @@ class CPError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("pp_eps", ctypes.c_double), ("delta", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int), ("judge_every", ctypes.c_int),
-                ("use_policy", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("policy_gate", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
 class TraceRec(ctypes.Structure):
@@ -131,7 +131,7 @@ class CPContext:
     """One decomposition of a dense CUDA tensor (float32 borrowed, float64 copied once)."""
 
     def __init__(self, T, R, A0=None, prec="bf16x3", seed=20101205, pp_eps=0.1, judge_every=5,
-                 stream=None):
+                 policy_gate=True, stream=None):
         import torch
         if not (isinstance(T, torch.Tensor) and T.is_cuda and T.is_contiguous()):
             raise ValueError("T must be a contiguous CUDA tensor")
@@ -149,6 +149,7 @@ class CPContext:
         cfg.seed = int(seed)
         cfg.pp_eps = float(pp_eps)
         cfg.judge_every = int(judge_every)
+        cfg.policy_gate = 1 if policy_gate else 0
         dims = (ctypes.c_int64 * self.N)(*self.dims)
         a0p = None
         if A0 is not None:

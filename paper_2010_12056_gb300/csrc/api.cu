@@ -137,7 +137,15 @@ struct cp_ctx {
     } snap[2];
     float* pol_io = nullptr;   // device: 16 policy features + 2 scores
     double judge_r = -1.0;     // direct residual at the judge's rollback point
-    int since_judge = 0, fallback_left = 0;
+    int since_judge = 0;       // approximated sweeps since the rollback point
+    int fallback_left = 0;
+    int rollbacks_in_row = 0;  // consecutive rollbacks (the fallback doubles each time)
+    double pending_ms = 0.0;   // policy query / rollback-point time of the coming sweep
+    // measured device time of the choices (exponential averages; < 0: not yet seen)
+    double cost_exact = -1.0, cost_pp = -1.0, cost_init = -1.0, cost_judge = -1.0, cost_query = -1.0;
+    int n_exact_seen = 0;
+    double sweep_mttkrp_bytes = -1.0;  // MTTKRP bytes of the last regular sweep
+    bool snap_current = false;  // the rollback point is the present state
 
     std::vector<cp_trace_rec> trace;
     std::vector<double> last_hist;   // host copy of the last harvested scalars
@@ -846,9 +854,23 @@ cp_status policy_scores(cp_ctx* c, cp_policy* p, float sc[2]) {
 
 enum { CH_EXACT = 0, CH_CUR = 1, CH_NEW = 2 };
 
+// bytes an approximated sweep reads: for every mode n the N-1 pair operators
+// M_p(n,i) (s_n s_i R) plus M_p(n) and writes M~(n) (FP32)
+double pp_sweep_bytes(const cp_ctx* c) {
+    double b = 0.0;
+    for (int n = 0; n < c->N; ++n) {
+        for (int i = 0; i < c->N; ++i)
+            if (i != n) b += (double)c->dims[n] * c->dims[i] * c->R;
+        b += 2.0 * c->dims[n] * c->R;
+    }
+    return 4.0 * b;
+}
+
 // the policy judge's rollback point no longer describes a predecessor state
 void drop_judge(cp_ctx* c) {
     c->snap[1].have = false;
+    c->snap_current = false;
+    c->rollbacks_in_row = 0;
     c->since_judge = 0;
     c->fallback_left = 0;
 }
@@ -866,7 +888,9 @@ cp_status run_choice(cp_ctx* c, int choice) {
         kind = 2;
     } else {
         c->pp_valid = false;
+        const double b0 = c->stats.ttm_bytes + c->stats.mttv_bytes;
         CKST(exact_sweep(c, true, 0));
+        c->sweep_mttkrp_bytes = c->stats.ttm_bytes + c->stats.mttv_bytes - b0;
         kind = 3;
     }
     CKCUDA(c, cudaEventRecord(c->events[1], c->st));
@@ -923,7 +947,7 @@ void cp_config_default(cp_config* cfg) {
     cfg->delta = 0.0;
     cfg->max_sweeps = 0;
     cfg->judge_every = 5;
-    cfg->use_policy = 0;
+    cfg->policy_gate = 1;
     cfg->seed = 20101205ull;
 }
 
@@ -1174,31 +1198,132 @@ cp_status cp_pp_mttkrp(cp_ctx* c, int mode, float* M_dev) {
     return CP_OK;
 }
 
+void ema(double& v, double x) { v = (v < 0.0) ? x : 0.7 * v + 0.3 * x; }
+
+// Running averages of what each choice costs on this problem.
+void note_cost(cp_ctx* c, int kind, int init, double ms) {
+    if (kind == 3) {
+        // the cheapest regular sweep seen: early sweeps (refinement from a
+        // random start) are slower than the steady state
+        c->cost_exact = (c->cost_exact < 0.0) ? ms : std::min(c->cost_exact, ms);
+        c->n_exact_seen++;
+    } else if (kind == 2 && !init) {
+        ema(c->cost_pp, ms);
+    } else if (kind == 2 && init && c->cost_pp > 0.0) {
+        ema(c->cost_init, std::max(0.0, ms - c->cost_pp));
+    }
+}
+
+// undo every sweep since the rollback point (a failed judgement, or an
+// approximated sweep whose normal equations broke down)
+cp_status rollback(cp_ctx* c, int judge) {
+    const size_t from = c->snap[1].trace_len;
+    for (size_t t = from; t < c->trace.size(); ++t) c->trace[t].rolled_back = 1;
+    const int done = c->sweeps_done;
+    CKST(snap_restore(c, c->snap[1], false, false));
+    c->sweeps_done = done;  // the undone sweeps stay in the count and the trace
+    // Alg. 2's rule decides the next judge_every sweeps, twice as many after
+    // each further rollback in a row (at most 64 judge_every)
+    c->rollbacks_in_row = std::min(c->rollbacks_in_row + 1, 7);
+    c->fallback_left = judge << (c->rollbacks_in_row - 1);
+    c->since_judge = 0;
+    c->snap_current = true;
+    c->stats.rollbacks++;
+    return CP_OK;
+}
+
+// The judge: the direct residual at the end of a run of approximated sweeps.  If
+// it rose by more than the residual's own rounding noise (1e-5 relative: the
+// model values are FP32 dot products), the factors return to the rollback point,
+// the operators are dropped, the undone sweeps stay in the trace marked
+// rolled_back, and Alg. 2's rule decides the next judge_every sweeps.
+cp_status judge_now(cp_ctx* c, int judge) {
+    CKCUDA(c, cudaEventRecord(c->events[2], c->st));
+    double r;
+    CKST(direct_resid(c, &r));
+    if (r > c->judge_r * (1.0 + 1e-5)) {
+        CKST(rollback(c, judge));
+    } else {
+        c->judge_r = r;
+        c->rollbacks_in_row = 0;
+        CKST(snap_take(c, c->snap[1]));
+    }
+    c->since_judge = 0;
+    c->snap_current = true;
+    CKCUDA(c, cudaEventRecord(c->events[3], c->st));
+    CKCUDA(c, cudaEventSynchronize(c->events[3]));
+    float jms = 0.f;
+    CKCUDA(c, cudaEventElapsedTime(&jms, c->events[2], c->events[3]));
+    if (!c->trace.empty()) c->trace.back().ms += jms;
+    ema(c->cost_judge, jms);
+    return CP_OK;
+}
+
+// rollback point = the current state (taken before a run of approximated sweeps)
+cp_status judge_mark(cp_ctx* c) {
+    CKCUDA(c, cudaEventRecord(c->events[2], c->st));
+    CKST(direct_resid(c, &c->judge_r));
+    CKST(snap_take(c, c->snap[1]));
+    c->since_judge = 0;
+    c->snap_current = true;
+    CKCUDA(c, cudaEventRecord(c->events[3], c->st));
+    CKCUDA(c, cudaEventSynchronize(c->events[3]));
+    float jms = 0.f;
+    CKCUDA(c, cudaEventElapsedTime(&jms, c->events[2], c->events[3]));
+    c->pending_ms += jms;
+    ema(c->cost_judge, jms);
+    return CP_OK;
+}
+
 cp_status cp_sweep_pp(cp_ctx* c, int nsweeps, double eps, cp_policy* policy) {
     CKST(entry_check(c));
     if (nsweeps < 0 || !(eps > 0.0 && eps < 1.0)) return CP_EINVAL;
     CKST(grow_hist(c, 1));
     CKST(ensure_events(c, 4));
     const int judge = policy ? std::max(0, c->cfg.judge_every) : 0;
-    if (!judge) drop_judge(c);
-    if (judge && !c->snap[1].have) {
-        // rollback point at the start of policy-driven sweeps
-        CKST(direct_resid(c, &c->judge_r));
-        CKST(snap_take(c, c->snap[1]));
-        c->since_judge = 0;
-    }
+    if (!policy) drop_judge(c);
     for (int k = 0; k < nsweeps; ++k) {
-        CKCUDA(c, cudaEventRecord(c->events[0], c->st));
+        c->pending_ms = 0.0;
         float sc[2] = {-1.f, -1.f};
         int by = 0, choice;
         if (policy && c->fallback_left == 0) {
-            // the network's two queries: approximate with the current operators,
-            // or with operators rebuilt now; neither safe -> regular sweep
-            CKST(policy_scores(c, policy, sc));
+            // an approximated sweep is considered only while it is measured (or
+            // not yet known) to cost less than a regular one, counting its share
+            // of the judge and of the network query
+            // (the first sweep is regular, as in Alg. 2 from a random start, and
+            // gives the reference cost)
+            const double extra = std::max(0.0, c->cost_query) + (judge ? std::max(0.0, c->cost_judge) / judge : 0.0);
+            bool pp_pays = c->n_exact_seen >= 2 || !c->cfg.policy_gate;
+            if (!c->cfg.policy_gate) {
+                // consult the network before every sweep
+            } else if (pp_pays && c->cost_pp < 0.0) {
+                // not measured yet: explore only if the MTTKRP traffic an approximated
+                // sweep avoids (at about 6 TB/s) can cover a network query (about
+                // 30 us) and the judge's share (its residual: 2 numel R flops at
+                // about 20 TFLOP/s)
+                const double saved_ms = (c->sweep_mttkrp_bytes - pp_sweep_bytes(c)) / 6e9;
+                const double judge_ms = c->cost_judge >= 0.0 ? c->cost_judge : 2.0 * c->numel * c->R / 20e9;
+                const double over_ms = (c->cost_query >= 0.0 ? c->cost_query : 0.03) + (judge ? judge_ms / judge : 0.0);
+                pp_pays = saved_ms > over_ms;
+            } else if (pp_pays) {
+                pp_pays = c->cost_pp + extra < c->cost_exact;
+            }
             by = 1;
-            if (c->pp_valid && sc[0] >= 0.5f) choice = CH_CUR;
-            else if (sc[1] >= 0.5f) choice = CH_NEW;
-            else choice = CH_EXACT;
+            choice = CH_EXACT;
+            if (pp_pays) {
+                CKCUDA(c, cudaEventRecord(c->events[0], c->st));
+                CKST(policy_scores(c, policy, sc));
+                CKCUDA(c, cudaEventRecord(c->events[1], c->st));
+                CKCUDA(c, cudaEventSynchronize(c->events[1]));
+                float fms = 0.f;
+                CKCUDA(c, cudaEventElapsedTime(&fms, c->events[0], c->events[1]));
+                c->pending_ms += fms;
+                ema(c->cost_query, fms);
+                // the network's two queries: approximate with the current operators,
+                // or with operators rebuilt now; neither safe -> regular sweep
+                if (c->pp_valid && sc[0] >= 0.5f) choice = CH_CUR;
+                else if (sc[1] >= 0.5f) choice = CH_NEW;
+            }
         } else {
             // Alg. 2: enter / stay while every ||dA(i)|| < eps ||A(i)||
             bool small = true;
@@ -1209,37 +1334,39 @@ cp_status cp_sweep_pp(cp_ctx* c, int nsweeps, double eps, cp_policy* policy) {
             else choice = c->pp_valid ? CH_CUR : CH_NEW;
             if (c->fallback_left > 0) c->fallback_left--;
         }
-        CKST(run_choice(c, choice));
+        if (judge) {
+            if (choice == CH_EXACT && c->since_judge > 0) {
+                const int64_t rb0 = c->stats.rollbacks;
+                CKST(judge_now(c, judge));  // judge a run of approximated sweeps before leaving it
+                if (c->stats.rollbacks != rb0) {
+                    by = 2;  // rolled back: Alg. 2's rule decides from the restored state
+                    bool small = true;
+                    for (int i = 0; i < c->N; ++i)
+                        if (!(c->dA_rel[i] < eps)) small = false;
+                    choice = !small ? CH_EXACT : (c->pp_valid ? CH_CUR : CH_NEW);
+                    c->fallback_left--;
+                }
+            }
+            if (choice != CH_EXACT && c->since_judge == 0 && !(c->snap_current && c->snap[1].have))
+                CKST(judge_mark(c));
+        }
+        CKCUDA(c, cudaEventRecord(c->events[0], c->st));
+        const cp_status rs = run_choice(c, choice);
+        if (rs == CP_ENOTSPD && judge && choice != CH_EXACT && c->snap[1].have && !c->poisoned) {
+            // the approximation broke the normal equations: undo the run
+            c->err.clear();
+            CKST(rollback(c, judge));
+            continue;
+        }
+        CKST(rs);
+        c->snap_current = false;
         cp_trace_rec& rec = c->trace.back();
         rec.p_cur = sc[0];
         rec.p_new = sc[1];
         rec.decided_by = by;
-        if (judge && ++c->since_judge >= judge) {
-            // the judge: a direct residual; if it rose since the last judgement,
-            // undo every sweep since then and let Alg. 2's rule decide until the
-            // next judgement
-            CKCUDA(c, cudaEventRecord(c->events[2], c->st));
-            double r;
-            CKST(direct_resid(c, &r));
-            if (r > c->judge_r * (1.0 + 1e-8)) {
-                const size_t from = c->snap[1].trace_len;
-                for (size_t t = from; t < c->trace.size(); ++t) c->trace[t].rolled_back = 1;
-                const int done = c->sweeps_done;
-                CKST(snap_restore(c, c->snap[1], false, false));
-                c->sweeps_done = done;  // the undone sweeps stay in the count and the trace
-                c->fallback_left = judge;
-                c->stats.rollbacks++;
-            } else {
-                c->judge_r = r;
-            }
-            CKST(snap_take(c, c->snap[1]));
-            c->since_judge = 0;
-            CKCUDA(c, cudaEventRecord(c->events[3], c->st));
-            CKCUDA(c, cudaEventSynchronize(c->events[3]));
-            float jms = 0.f;
-            CKCUDA(c, cudaEventElapsedTime(&jms, c->events[2], c->events[3]));
-            c->trace.back().ms += jms;
-        }
+        note_cost(c, rec.kind, rec.pp_init, rec.ms);
+        rec.ms += c->pending_ms;
+        if (judge && rec.kind == 2 && ++c->since_judge >= judge) CKST(judge_now(c, judge));
     }
     return CP_OK;
 }
@@ -1261,7 +1388,15 @@ cp_status cp_pp_probe(cp_ctx* c, int follow, cp_probe_rec* out) {
     CKST(snap_take(c, c->snap[0]));
     auto branch = [&](int ch, double* r, double* ms) -> cp_status {
         CKCUDA(c, cudaEventRecord(c->events[0], c->st));
-        CKST(run_choice(c, ch));
+        const cp_status rs = run_choice(c, ch);
+        if (rs == CP_ENOTSPD && ch != CH_EXACT && !c->poisoned) {
+            // an approximated branch whose normal equations broke down: unsafe
+            c->err.clear();
+            *r = INFINITY;
+            *ms = 0.0;
+            return CP_OK;
+        }
+        CKST(rs);
         *ms = c->trace.back().ms;
         CKST(direct_resid(c, r));
         return CP_OK;
@@ -1282,10 +1417,16 @@ cp_status cp_pp_probe(cp_ctx* c, int follow, cp_probe_rec* out) {
     out->label_new = (out->r_new - out->r_exact <= slack) ? 1 : 0;
     int ch = follow;
     if (ch < 0) ch = out->label_cur ? CH_CUR : (out->label_new ? CH_NEW : CH_EXACT);
+    double rf = out->r_new;
     if (ch != CH_NEW) {
         CKST(snap_restore(c, c->snap[0], true, true));
-        double r, ms;
-        CKST(branch(ch, &r, &ms));
+        double ms;
+        CKST(branch(ch, &rf, &ms));
+    }
+    if (!isfinite(rf)) {
+        // the requested branch broke down: back to the starting state
+        CKST(snap_restore(c, c->snap[0], true, true));
+        return fail(c, CP_ENOTSPD, "the followed PP branch broke the normal equations");
     }
     out->followed = ch;
     c->trace.back().decided_by = 3;

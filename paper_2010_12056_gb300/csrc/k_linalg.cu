@@ -229,73 +229,139 @@ __global__ void k_f64_to_f32(const double* __restrict__ x, float* __restrict__ y
 }
 
 // ------------------------------------------------------------------ direct residual
-// ||T - [[A]]||^2 with T viewed as rows (modes 0..N-2) x cols (mode N-1): per
-// 64 x 64 tile, t~ = KR(row) . A_last(col) over r in chunks of 16 (FP32), then
-// (t - t~)^2 summed in FP32 per thread and FP64 across tiles.
-__global__ void __launch_bounds__(256) k_resid_direct(cpk::ResidArgs a, int64_t nrows,
+// ||T - [[A]]||^2 (Eq. residual-def): T seen as rows (modes
+// 0..N-2, C order) x columns (mode N-1); the model block of a 128 x 128 tile is
+// KR(rows) A_{N-1}(cols)^T with the Khatri-Rao rows formed on the fly.  256
+// threads, 8 x 8 model values per thread (FP32 FMAs over r, in order), the
+// operands staged in shared memory 8 ranks at a time, double-buffered through
+// registers.  Per block: FP64 sum of the per-tile FP32 sums of squares.
+constexpr int RD_T = 128, RD_K = 8;
+
+template <int NF>  // tensor order when fixed at compile time (3, 4), else 0
+__global__ void __launch_bounds__(256, 2) k_resid_direct(cpk::ResidArgs a, int64_t nrows,
                                                       int64_t ncols, int64_t ntile_c,
                                                       double* __restrict__ partials,
                                                       int64_t ntiles) {
-    __shared__ __align__(16) float KR[16][64];
-    __shared__ __align__(16) float Bs[16][64];
-    __shared__ int rowoff[64][CP_MAXN];
+    __shared__ __align__(16) float KR[2][RD_K][RD_T];
+    __shared__ __align__(16) float Bs[2][RD_K][RD_T];
     __shared__ double red[32];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int N = a.N, R = a.R;
+    const int N = NF ? NF : a.N, R = a.R;
+    constexpr int NMAX = NF ? NF : CP_MAXN;
     const float* Alast = a.A32[N - 1];
+    // staging: thread loads ranks sr .. sr + 3 of row / column sm of the tile
+    const int sm = tid & 127, sr = (tid >> 7) * 4;
+    const bool r4 = (R & 3) == 0;  // rows of every factor are 16-byte aligned
     double total = 0.0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t row0 = (tile / ntile_c) * 64, col0 = (tile % ntile_c) * 64;
-        __syncthreads();
-        if (tid < 64) {
-            int64_t row = row0 + tid;
+        const int64_t row0 = (tile / ntile_c) * RD_T, col0 = (tile % ntile_c) * RD_T;
+        // the factor rows of this thread's staging row (multi-index of modes 0..N-2)
+        const float* frow[NMAX];
+        {
+            int64_t row = row0 + sm;
             if (row >= nrows) row = 0;
-            for (int k = N - 2; k >= 0; --k) {
-                rowoff[tid][k] = (int)(row % a.dims[k]);
+#pragma unroll
+            for (int k = NMAX - 2; k >= 0; --k) {
+                if (k > N - 2) continue;
+                frow[k] = a.A32[k] + (size_t)(row % a.dims[k]) * R;
                 row /= a.dims[k];
             }
         }
-        float acc[4][4];
+        const bool rok = row0 + sm < nrows, cok = col0 + sm < ncols;
+        const float* brow = Alast + (size_t)(cok ? col0 + sm : 0) * R;
+        auto stage = [&](int r0, float* kv, float* bv) {
+            const int r = r0 + sr;
+            if (r4 && r + 4 <= R) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f), b = v;
+                if (rok) {
+                    v = __ldg(reinterpret_cast<const float4*>(frow[0] + r));
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        for (int r0 = 0; r0 < R; r0 += 16) {
-            __syncthreads();
-            for (int e = tid; e < 16 * 64; e += 256) {
-                const int rr = e >> 6, m = e & 63;
-                float v = 0.f, b = 0.f;
-                if (r0 + rr < R) {
-                    v = 1.f;
-                    for (int k = 0; k < N - 1; ++k) v *= a.A32[k][(size_t)rowoff[m][k] * R + r0 + rr];
-                    if (col0 + m < ncols) b = Alast[(size_t)(col0 + m) * R + r0 + rr];
+                    for (int k = 1; k < NMAX - 1; ++k) {
+                        if (k >= N - 1) break;
+                        const float4 w = __ldg(reinterpret_cast<const float4*>(frow[k] + r));
+                        v.x *= w.x; v.y *= w.y; v.z *= w.z; v.w *= w.w;
+                    }
                 }
-                KR[rr][m] = v;
-                Bs[rr][m] = b;
+                if (cok) b = __ldg(reinterpret_cast<const float4*>(brow + r));
+                kv[0] = v.x; kv[1] = v.y; kv[2] = v.z; kv[3] = v.w;
+                bv[0] = b.x; bv[1] = b.y; bv[2] = b.z; bv[3] = b.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float v = 0.f, b = 0.f;
+                    if (r + q < R) {
+                        if (rok) {
+                            v = 1.f;
+#pragma unroll
+                            for (int k = 0; k < NMAX - 1; ++k)
+                                if (k < N - 1) v *= __ldg(frow[k] + r + q);
+                        }
+                        if (cok) b = __ldg(brow + r + q);
+                    }
+                    kv[q] = v;
+                    bv[q] = b;
+                }
+            }
+        };
+        float acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        float kv[4], bv[4];
+        stage(0, kv, bv);
+        int buf = 0;
+        for (int r0 = 0; r0 < R; r0 += RD_K) {
+            __syncthreads();  // buffer `buf` is free (its last readers are two barriers back)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                KR[buf][sr + q][sm] = kv[q];
+                Bs[buf][sr + q][sm] = bv[q];
             }
             __syncthreads();
+            if (r0 + RD_K < R) stage(r0 + RD_K, kv, bv);  // next ranks in flight
+            // rows ty*4 + {0..3} and 64 + ty*4 + {0..3}; columns likewise with tx:
+            // a warp's 16 column groups are contiguous 16-byte words (no bank conflicts)
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                float4 av = *reinterpret_cast<const float4*>(&KR[k][ty * 4]);
-                float4 bv = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
-                float aa[4] = {av.x, av.y, av.z, av.w}, bb[4] = {bv.x, bv.y, bv.z, bv.w};
+            for (int k = 0; k < RD_K; ++k) {
+                const float4 a0 = *reinterpret_cast<const float4*>(&KR[buf][k][ty * 4]);
+                const float4 a1 = *reinterpret_cast<const float4*>(&KR[buf][k][64 + ty * 4]);
+                const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
+                const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][64 + tx * 4]);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bw[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(aa[i], bb[j], acc[i][j]);
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bw[j], acc[i][j]);
             }
+            buf ^= 1;
         }
         float part = 0.f;
+        const bool al = (((uintptr_t)a.T & 15) == 0) && ((ncols & 3) == 0);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int64_t row = row0 + ty * 4 + i;
+        for (int i = 0; i < 8; ++i) {
+            const int64_t row = row0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
             if (row >= nrows) continue;
+            const float* trow = a.T + row * ncols;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int64_t col = col0 + tx * 4 + j;
-                if (col < ncols) {
-                    float d = __ldg(a.T + row * ncols + col) - acc[i][j];
-                    part = fmaf(d, d, part);
+            for (int h = 0; h < 2; ++h) {
+                const int64_t c0 = col0 + h * 64 + tx * 4;
+                if (al && c0 + 4 <= ncols) {
+                    const float4 t = __ldg(reinterpret_cast<const float4*>(trow + c0));
+                    const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float d = tv[j] - acc[i][h * 4 + j];
+                        part = fmaf(d, d, part);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (c0 + j < ncols) {
+                            const float d = __ldg(trow + c0 + j) - acc[i][h * 4 + j];
+                            part = fmaf(d, d, part);
+                        }
                 }
             }
         }
@@ -507,10 +573,12 @@ int resid_direct_partials(const ResidArgs& a, double* partials, int max_blocks, 
     int64_t nrows = 1;
     for (int k = 0; k < a.N - 1; ++k) nrows *= a.dims[k];
     const int64_t ncols = a.dims[a.N - 1];
-    const int64_t ntr = (nrows + 63) / 64, ntc = (ncols + 63) / 64;
+    const int64_t ntr = (nrows + RD_T - 1) / RD_T, ntc = (ncols + RD_T - 1) / RD_T;
     const int64_t ntiles = ntr * ntc;
     int blocks = (int)(ntiles < max_blocks ? ntiles : max_blocks);
-    k_resid_direct<<<blocks, 256, 0, st>>>(a, nrows, ncols, ntc, partials, ntiles);
+    if (a.N == 3) k_resid_direct<3><<<blocks, 256, 0, st>>>(a, nrows, ncols, ntc, partials, ntiles);
+    else if (a.N == 4) k_resid_direct<4><<<blocks, 256, 0, st>>>(a, nrows, ncols, ntc, partials, ntiles);
+    else k_resid_direct<0><<<blocks, 256, 0, st>>>(a, nrows, ncols, ntc, partials, ntiles);
     return blocks;
 }
 
