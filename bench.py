@@ -244,8 +244,10 @@ def run_policy(args):
                                               seed=7 + i, eps=0.1, policy=policy if m == "policy" else None)
             res[m].append(ms)
             row[m] = {"ms": ms, "sweeps": k,
-                      "approx": sum(t["kind"] == "pp" for t in tr),
-                      "rolled_back": sum(t["rolled_back"] for t in tr)}
+                      "approx": sum(t.get("kind") == "pp" for t in tr),
+                      "rolled_back": sum(t.get("rolled_back", 0) for t in tr)}
+            if tr and "error" in tr[-1]:
+                row[m]["error"] = tr[-1]["error"]
         per.append(row)
         del T
     tot = {m: float(np.sum(v)) for m, v in res.items()}

@@ -153,11 +153,14 @@ cp_status cp_sweep_msdt(cp_ctx *ctx, int nsweeps);
  *           times the rollback point's (1e-5: above the rounding noise of the
  *           FP32 model values), the factors return to the rollback point, the
  *           operators are dropped, the undone sweeps stay in the trace with
- *           rolled_back = 1, and the rule above decides the next judge_every
- *           sweeps (twice as many after each further rollback in a row, up to
- *           64 judge_every).  An approximated sweep whose normal equations
- *           break down (CP_ENOTSPD) is rolled back the same way.  Query and
- *           judge time are added to the sweep's trace ms.
+ *           rolled_back = 1, and the next judge_every sweeps are regular
+ *           (twice as many after each further rollback in a row, up to 64
+ *           judge_every).  An approximated sweep whose normal equations break
+ *           down (CP_ENOTSPD) is rolled back the same way, and a judged run
+ *           that lowered the residual by less than 1e-7 relative is followed
+ *           by judge_every regular sweeps.  If the network's output is not a
+ *           probability, the rule above decides.  Query and judge time are
+ *           added to the sweep's trace ms.
  */
 typedef struct cp_policy cp_policy;
 cp_status cp_sweep_pp(cp_ctx *ctx, int nsweeps, double eps, cp_policy *policy);
@@ -243,8 +246,9 @@ typedef struct {
                              its operator build and, with a policy, the network
                              query and the judge                               */
     float p_cur, p_new;   /* policy scores before the sweep (-1: not queried)     */
-    int32_t decided_by;   /* 0 eps rule, 1 policy network, 2 eps rule after a
-                             rollback, 3 cp_pp_probe                            */
+    int32_t decided_by;   /* 0 eps rule, 1 policy network, 2 regular sweep after
+                             a rollback or a stalled run, 3 cp_pp_probe, 4 eps
+                             rule because the network's output was invalid    */
     int32_t reserved;
 } cp_trace_rec;
 

@@ -838,7 +838,7 @@ void features(const cp_ctx* c, bool rebuilt, float f[8]) {
 }
 
 // network scores of the two choices: [0] current operators, [1] rebuilt ones
-cp_status policy_scores(cp_ctx* c, cp_policy* p, float sc[2]) {
+cp_status policy_scores(cp_ctx* c, cp_policy* p, float sc[2], bool* valid) {
     if (!c->pol_io) CKST(dalloc(c, &c->pol_io, 32));
     float f[16];
     features(c, false, f);
@@ -847,8 +847,9 @@ cp_status policy_scores(cp_ctx* c, cp_policy* p, float sc[2]) {
     LAUNCH(c, cpk::mlp_forward(p->theta, c->pol_io, 2, c->pol_io + 16, c->st));
     CKCUDA(c, cudaMemcpyAsync(sc, c->pol_io + 16, 2 * sizeof(float), cudaMemcpyDeviceToHost, c->st));
     CKCUDA(c, cudaStreamSynchronize(c->st));
+    *valid = true;
     for (int k = 0; k < 2; ++k)
-        if (!(sc[k] >= 0.f && sc[k] <= 1.f)) sc[k] = 0.f;  // NaN or garbage: not safe
+        if (!(sc[k] >= 0.f && sc[k] <= 1.f)) *valid = false;  // NaN or garbage
     return CP_OK;
 }
 
@@ -1222,8 +1223,8 @@ cp_status rollback(cp_ctx* c, int judge) {
     const int done = c->sweeps_done;
     CKST(snap_restore(c, c->snap[1], false, false));
     c->sweeps_done = done;  // the undone sweeps stay in the count and the trace
-    // Alg. 2's rule decides the next judge_every sweeps, twice as many after
-    // each further rollback in a row (at most 64 judge_every)
+    // regular sweeps for the next judge_every sweeps, twice as many after each
+    // further rollback in a row (at most 64 judge_every)
     c->rollbacks_in_row = std::min(c->rollbacks_in_row + 1, 7);
     c->fallback_left = judge << (c->rollbacks_in_row - 1);
     c->since_judge = 0;
@@ -1244,6 +1245,10 @@ cp_status judge_now(cp_ctx* c, int judge) {
     if (r > c->judge_r * (1.0 + 1e-5)) {
         CKST(rollback(c, judge));
     } else {
+        // a run that no longer lowers the residual (the approximation has
+        // settled above the regular iteration's fixed point) also hands over
+        // to regular sweeps
+        if (c->judge_r - r < 1e-7 * r) c->fallback_left = judge;
         c->judge_r = r;
         c->rollbacks_in_row = 0;
         CKST(snap_take(c, c->snap[1]));
@@ -1286,7 +1291,21 @@ cp_status cp_sweep_pp(cp_ctx* c, int nsweeps, double eps, cp_policy* policy) {
         c->pending_ms = 0.0;
         float sc[2] = {-1.f, -1.f};
         int by = 0, choice;
-        if (policy && c->fallback_left == 0) {
+        auto eps_rule = [&]() {
+            // Alg. 2: enter / stay while every ||dA(i)|| < eps ||A(i)||
+            bool small = true;
+            for (int i = 0; i < c->N; ++i)
+                if (!(c->dA_rel[i] < eps)) small = false;
+            return !small ? CH_EXACT : (c->pp_valid ? CH_CUR : CH_NEW);
+        };
+        if (!policy) {
+            choice = eps_rule();
+        } else if (c->fallback_left > 0) {
+            // after a rollback or a stalled run: regular sweeps
+            choice = CH_EXACT;
+            by = 2;
+            c->fallback_left--;
+        } else {
             // an approximated sweep is considered only while it is measured (or
             // not yet known) to cost less than a regular one, counting its share
             // of the judge and of the network query
@@ -1312,38 +1331,32 @@ cp_status cp_sweep_pp(cp_ctx* c, int nsweeps, double eps, cp_policy* policy) {
             choice = CH_EXACT;
             if (pp_pays) {
                 CKCUDA(c, cudaEventRecord(c->events[0], c->st));
-                CKST(policy_scores(c, policy, sc));
+                bool valid = true;
+                CKST(policy_scores(c, policy, sc, &valid));
                 CKCUDA(c, cudaEventRecord(c->events[1], c->st));
                 CKCUDA(c, cudaEventSynchronize(c->events[1]));
                 float fms = 0.f;
                 CKCUDA(c, cudaEventElapsedTime(&fms, c->events[0], c->events[1]));
                 c->pending_ms += fms;
                 ema(c->cost_query, fms);
-                // the network's two queries: approximate with the current operators,
-                // or with operators rebuilt now; neither safe -> regular sweep
-                if (c->pp_valid && sc[0] >= 0.5f) choice = CH_CUR;
-                else if (sc[1] >= 0.5f) choice = CH_NEW;
+                if (!valid) {
+                    // the network gave no usable score: Alg. 2's rule decides
+                    choice = eps_rule();
+                    by = 4;
+                } else if (c->pp_valid && sc[0] >= 0.5f) {
+                    // the network's two queries: approximate with the current
+                    // operators, or with operators rebuilt now; neither -> regular
+                    choice = CH_CUR;
+                } else if (sc[1] >= 0.5f) {
+                    choice = CH_NEW;
+                }
             }
-        } else {
-            // Alg. 2: enter / stay while every ||dA(i)|| < eps ||A(i)||
-            bool small = true;
-            for (int i = 0; i < c->N; ++i)
-                if (!(c->dA_rel[i] < eps)) small = false;
-            by = policy ? 2 : 0;
-            if (!small) choice = CH_EXACT;
-            else choice = c->pp_valid ? CH_CUR : CH_NEW;
-            if (c->fallback_left > 0) c->fallback_left--;
         }
         if (judge) {
             if (choice == CH_EXACT && c->since_judge > 0) {
-                const int64_t rb0 = c->stats.rollbacks;
                 CKST(judge_now(c, judge));  // judge a run of approximated sweeps before leaving it
-                if (c->stats.rollbacks != rb0) {
-                    by = 2;  // rolled back: Alg. 2's rule decides from the restored state
-                    bool small = true;
-                    for (int i = 0; i < c->N; ++i)
-                        if (!(c->dA_rel[i] < eps)) small = false;
-                    choice = !small ? CH_EXACT : (c->pp_valid ? CH_CUR : CH_NEW);
+                if (c->fallback_left > 0) {
+                    by = 2;
                     c->fallback_left--;
                 }
             }

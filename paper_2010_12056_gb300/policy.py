@@ -111,19 +111,24 @@ def time_to_target(T, R, method, target_resid, max_sweeps, prec="bf16x3", seed=1
     sweep is outside the timed work.  Returns (ms or inf, sweeps, final resid,
     trace).
     """
+    from . import CPError
     ctx = CPContext(T, R, prec=prec, seed=seed, judge_every=judge_every)
     try:
         r = 1.0
         for k in range(max_sweeps):
-            if method == "msdt":
-                ctx.sweep_msdt(1)
-            elif method == "pp":
-                ctx.sweep_pp(1, eps)
-            elif method == "policy":
-                ctx.sweep_pp(1, eps, policy)
-            else:
-                raise ValueError(method)
-            _, r = ctx.fit(exact=True)
+            try:
+                if method == "msdt":
+                    ctx.sweep_msdt(1)
+                elif method == "pp":
+                    ctx.sweep_pp(1, eps)
+                elif method == "policy":
+                    ctx.sweep_pp(1, eps, policy)
+                else:
+                    raise ValueError(method)
+                _, r = ctx.fit(exact=True)
+            except CPError as e:
+                # the iteration broke down (e.g. diverging factors): target not reached
+                return float("inf"), k + 1, float("nan"), ctx.trace() + [{"error": str(e)}]
             if r <= target_resid:
                 tr = ctx.trace()
                 return sum(t["ms"] for t in tr), k + 1, r, tr

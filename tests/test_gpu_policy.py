@@ -198,10 +198,10 @@ def test_policy_judge_never_lets_the_residual_rise(pkg):
     assert st["sweeps_pp"] > 0
     nrb = sum(t["rolled_back"] for t in tr)
     assert (nrb > 0) == (st["rollbacks"] > 0)
-    # after a rollback the next sweep is decided by Alg. 2's rule
+    # after a rollback the next sweep is a regular one
     for i, t in enumerate(tr[:-1]):
         if t["rolled_back"] and not tr[i + 1]["rolled_back"]:
-            assert tr[i + 1]["decided_by"] == 2
+            assert tr[i + 1]["decided_by"] == 2 and tr[i + 1]["kind"] == "pp-regular"
     pol.close()
     a.close()
 
