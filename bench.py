@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--target-sweeps", type=int, default=60)
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--policy-dims", default="256,256,256")
+    ap.add_argument("--pp-sweeps", type=int, default=-1,
+                    help="PP (eps = 0.1) vs exact MSDT over this many sweeps (default: 100 for c4, else 0)")
     return ap.parse_args()
 
 
@@ -398,12 +400,40 @@ def main():
     torch.cuda.synchronize()
     wall_pp = time.perf_counter() - t0
     tr = ctx_pp.trace()[tr0:]
-    pp_ms = [t["ms"] for t in tr if t["kind"] == "pp"]
+    pp_ms = [t["ms"] for t in tr if t["kind"] == "pp" and not t["pp_init"]]
     pp_info = {"approx_sweeps": len(pp_ms),
                "approx_sweep_ms": (sum(pp_ms) / len(pp_ms)) if pp_ms else None,
                "approx_sweeps_per_s_wall": len(tr) / wall_pp,
                "init_count": ctx_pp.stats()["pp_init"]}
     ctx_pp.close()
+
+    # ---------------------------------------------------------------- PP vs exact MSDT (Alg. 2, eps 0.1)
+    npp = args.pp_sweeps if args.pp_sweeps >= 0 else (100 if args.workload == "c4" else 0)
+    pp_vs = None
+    if npp > 0:
+        pp_vs = {"sweeps": npp, "eps": 0.1}
+        for name in ("msdt", "pp"):
+            c2 = pkg.CPContext(T, R, A0=A0, prec=args.prec, stream=stream)
+            barrier()
+            e0.record(stream)
+            if name == "msdt":
+                c2.sweep_msdt(npp)
+            else:
+                c2.sweep_pp(npp, eps=0.1)
+            e1.record(stream)
+            barrier()
+            tr = c2.trace()
+            apx = [t["ms"] for t in tr if t["kind"] == "pp" and not t["pp_init"]]
+            ini = [t["ms"] for t in tr if t["pp_init"]]
+            reg = [t["ms"] for t in tr if t["kind"] in ("msdt", "pp-regular")]
+            pp_vs[name] = {"ms": e0.elapsed_time(e1), "fit_direct": c2.fit(exact=True)[0],
+                           "approx_sweeps": len(apx), "inits": len(ini), "regular_sweeps": len(reg),
+                           "approx_sweep_ms": (sum(apx) / len(apx)) if apx else None,
+                           "sweep_with_init_ms": (sum(ini) / len(ini)) if ini else None,
+                           "regular_sweep_ms": (sum(reg) / len(reg)) if reg else None,
+                           "solves_fp64": int(c2.stats()["solves_fp64"])}
+            c2.close()
+        pp_vs["speedup_pp_over_msdt"] = pp_vs["msdt"]["ms"] / pp_vs["pp"]["ms"]
 
     # ---------------------------------------------------------------- e2e (host buffers)
     e2e = None
@@ -450,6 +480,7 @@ def main():
         "fit": {"formula": fit_formula, "direct": fit_direct, "after_sweeps": args.warmup + args.steps},
         "solves_fp64": int(st1["solves_fp64"]),
         "pp": pp_info,
+        "pp_vs_msdt": pp_vs,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

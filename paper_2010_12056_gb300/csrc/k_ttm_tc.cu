@@ -53,6 +53,8 @@ struct TcArgs {
     int R, Rpad, nk, S_stg, S_op, tmem_cols, x3, b_resident, nsplit, nacc;
     int nsk;          // split-K factor: work item w = (tile w / nsk, k-slice w % nsk)
     int64_t slice;    // floats between split-K output slices
+    int ldx;          // row stride of X in floats (R of the whole factor; this pass writes
+                      // columns 0..R-1 of X, which points at its first column)
     uint32_t idesc;
     unsigned* dev_err;
 };
@@ -208,7 +210,8 @@ __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, in
 
 // ------------------------------------------------------------------ kernel
 // MODE 0: last mode, T rows K-contiguous (2-D map {K, PQ}, boxes {32, 128}, SWIZZLE_128B)
-// MODE 1: other modes, T[p][k][q] with Q % 128 == 0 (3-D map {Q, K, P}, box {128, BK, 1})
+// MODE 1: other modes, T[p][k][q] with Q % 4 == 0 (3-D map {Q, K, P}, box {128, BK, 1}; the
+//         last q-tile of each p is zero-filled past Q by the TMA unit and written up to Q)
 // KIND 0: bf16 parts, BK = 64, kind::f16;  KIND 1: tf32 parts, BK = 32, kind::tf32
 template <int MODE, int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -452,12 +455,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int buf = lt & 1;
             if (!(ok = mbar_wait(acc_full(buf), (uint32_t)((lt >> 1) & 1), abort_flag))) break;
             tc_fence_after();
-            int64_t g0;  // global row of this warp's first row
+            int64_t g0;       // global row of this warp's first row
+            int64_t gend;     // rows g0 + r < gend belong to this tile
             if (MODE == 0) {
                 g0 = tile * BM + quad * 32;
+                gend = a.PQ;
             } else {
                 const int64_t p = tile / a.tiles_per_p;
-                g0 = p * a.Q + (tile % a.tiles_per_p) * BM + quad * 32;
+                const int64_t qb = (tile % a.tiles_per_p) * BM;
+                g0 = p * a.Q + qb + quad * 32;
+                gend = p * a.Q + a.Q;  // the last tile of a p is ragged when BM does not divide Q
             }
             const uint32_t taddr =
                 tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * a.nacc * a.Rpad);
@@ -483,10 +490,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int i = 0; i < 4; ++i) {
                     const int r = (lane >> 2) + 8 * i;
                     const int64_t g = g0 + r;
-                    if (g < a.PQ && col < a.R) {
+                    if (g < gend && col < a.R) {
                         const float4 w = *reinterpret_cast<const float4*>(tb + r * EPI_STRIDE + 4 * q);
-                        float* dst = Xs + g * (int64_t)a.R + col;
-                        if ((a.R & 3) == 0) {
+                        float* dst = Xs + g * (int64_t)a.ldx + col;
+                        if (((a.R | a.ldx) & 3) == 0) {
                             *reinterpret_cast<float4*>(dst) = w;
                         } else {
                             dst[0] = w.x;
@@ -541,19 +548,32 @@ EncodeTiledFn encoder() {
 
 namespace cpk {
 
+// R > 128 runs as column passes of at most 128 (one MMA N and one TMEM layout
+// that fit); pass p multiplies by factor rows 128 p .. and writes those columns.
+constexpr int MAX_PASS = 2, PASS_COLS = 128;
+
+struct TcPass {
+    CUtensorMap tmBhi, tmBlo;
+    int R, Rpad, S_stg, b_resident;
+};
+
 struct TcPlan {
-    CUtensorMap tmT, tmBhi, tmBlo;
+    CUtensorMap tmT;
+    TcPass pass[MAX_PASS];
+    int npass;
     int mode;   // kernel MODE
     int kind;   // kernel KIND
     int64_t P, Q, PQ;
-    int K, R, Rpad, nk, S_stg, S_op, b_resident;
+    int K, R, nk, S_op;
 };
 
 bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R) {
     const int Rpad = (R + 15) / 16 * 16;
-    if (Rpad > 128 || K < 1 || P * Q < 1) return false;
+    if (Rpad > MAX_PASS * PASS_COLS || K < 1 || P * Q < 1) return false;
     if (Q == 1) return K % 4 == 0 && P <= ((int64_t)1 << 31);
-    return Q % BM == 0 && Q <= ((int64_t)1 << 31) && P <= ((int64_t)1 << 31);
+    // ragged Q: the last tile of each p reads past Q (TMA fills zeros) and
+    // writes only its rows q < Q; the row stride Q * 4 bytes must be 16-byte aligned
+    return Q % 4 == 0 && Q <= ((int64_t)1 << 31) && P <= ((int64_t)1 << 31);
 }
 
 TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind, const void* bhi,
@@ -569,21 +589,43 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
     pl->PQ = P * Q;
     pl->K = K;
     pl->R = R;
-    pl->Rpad = Rpad;
     pl->nk = (K + BK - 1) / BK;
     pl->S_op = 2;
-    pl->b_resident = (size_t)pl->nk * 2 * Rpad * 128 <= 64 * 1024 ? 1 : 0;
-    pl->S_stg = 0;
-    for (int s = MAX_STG; s >= 2; --s)
-        if (layout_bytes(s, pl->S_op, Rpad, pl->nk, pl->b_resident, BK) <= SMEM_LIMIT) {
-            pl->S_stg = s;
-            break;
-        }
-    if (pl->S_stg == 0) {
-        delete pl;
-        return nullptr;
-    }
+    pl->npass = (R + PASS_COLS - 1) / PASS_COLS;
+    const int esz = kind == 0 ? 2 : 4;
+    const CUtensorMapDataType bt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint32_t es[3] = {1, 1, 1};
+    for (int q = 0; q < pl->npass; ++q) {
+        TcPass& ps = pl->pass[q];
+        ps.R = std::min(PASS_COLS, R - q * PASS_COLS);
+        ps.Rpad = pl->npass == 1 ? Rpad : (ps.R + 15) / 16 * 16;
+        ps.b_resident = (size_t)pl->nk * 2 * ps.Rpad * 128 <= 64 * 1024 ? 1 : 0;
+        ps.S_stg = 0;
+        for (int st = MAX_STG; st >= 2; --st)
+            if (layout_bytes(st, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK) <= SMEM_LIMIT) {
+                ps.S_stg = st;
+                break;
+            }
+        if (ps.S_stg == 0) {
+            delete pl;
+            return nullptr;
+        }
+        // rows 128 q .. 128 q + Rpad_q - 1 of the [Rpad][Kpad] operand copies
+        const size_t off = (size_t)q * PASS_COLS * Kpad * esz;
+        const cuuint64_t bd[2] = {(cuuint64_t)Kpad, (cuuint64_t)ps.Rpad};
+        const cuuint64_t bs[1] = {(cuuint64_t)Kpad * esz};
+        const cuuint32_t bb[2] = {(cuuint32_t)BK, (cuuint32_t)ps.Rpad};
+        CUresult r2 = enc(&ps.tmBhi, bt, 2, (void*)((const char*)bhi + off), bd, bs, bb, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r3 = enc(&ps.tmBlo, bt, 2, (void*)((const char*)blo + off), bd, bs, bb, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r2 != CUDA_SUCCESS || r3 != CUDA_SUCCESS) {
+            delete pl;
+            return nullptr;
+        }
+    }
     CUresult r1;
     if (Q == 1) {
         pl->mode = 0;
@@ -602,18 +644,7 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
-    const int esz = kind == 0 ? 2 : 4;
-    const CUtensorMapDataType bt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    const cuuint64_t bd[2] = {(cuuint64_t)Kpad, (cuuint64_t)Rpad};
-    const cuuint64_t bs[1] = {(cuuint64_t)Kpad * esz};
-    const cuuint32_t bb[2] = {(cuuint32_t)BK, (cuuint32_t)Rpad};
-    CUresult r2 = enc(&pl->tmBhi, bt, 2, (void*)bhi, bd, bs, bb, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    CUresult r3 = enc(&pl->tmBlo, bt, 2, (void*)blo, bd, bs, bb, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS || r3 != CUDA_SUCCESS) {
+    if (r1 != CUDA_SUCCESS) {
         delete pl;
         return nullptr;
     }
@@ -625,13 +656,13 @@ void ttm_tc_plan_free(TcPlan* p) { delete p; }
 int ttm_tc_kind(const TcPlan* p) { return p ? p->kind : -1; }
 
 static int64_t plan_tiles(const TcPlan* pl) {
-    return pl->mode == 1 ? pl->P * (pl->Q / BM) : (pl->PQ + BM - 1) / BM;
+    return pl->mode == 1 ? pl->P * ((pl->Q + BM - 1) / BM) : (pl->PQ + BM - 1) / BM;
 }
 
 int ttm_tc_splitk(const TcPlan* pl, int num_sms) {
     // split K when the row tiles alone cannot fill the GPU and K is long enough
     const int64_t nt = plan_tiles(pl);
-    if (pl->b_resident || nt >= 2 * (int64_t)num_sms || pl->nk < 8) return 1;
+    if (pl->pass[0].b_resident || nt >= 2 * (int64_t)num_sms || pl->nk < 8) return 1;
     int nsk = (int)((4 * (int64_t)num_sms + nt - 1) / nt);
     if (nsk > pl->nk / 4) nsk = pl->nk / 4;
     if (nsk > 16) nsk = 16;
@@ -641,9 +672,10 @@ int ttm_tc_splitk(const TcPlan* pl, int num_sms) {
 int64_t ttm_tc_rows(const TcPlan* pl) { return pl->PQ; }
 
 template <int MODE, int KIND>
-static cudaError_t launch(const TcPlan* pl, const TcArgs& a, size_t smem, unsigned grid, cudaStream_t st) {
+static cudaError_t launch(const TcPlan* pl, const TcPass& ps, const TcArgs& a, size_t smem, unsigned grid,
+                          cudaStream_t st) {
     cudaFuncSetAttribute(k_ttm_tc<MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ttm_tc<MODE, KIND><<<grid, NTHREADS, smem, st>>>(pl->tmT, pl->tmBhi, pl->tmBlo, a);
+    k_ttm_tc<MODE, KIND><<<grid, NTHREADS, smem, st>>>(pl->tmT, ps.tmBhi, ps.tmBlo, a);
     return cudaGetLastError();
 }
 
@@ -675,54 +707,59 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     const bool tf = (prec == CP_TF32X3 || prec == CP_TF32);
     if ((pl->kind == 0 && !bf) || (pl->kind == 1 && !tf)) return cudaErrorInvalidValue;
     if (((uintptr_t)X & 15) && (pl->R & 3) == 0) return cudaErrorMisalignedAddress;
-    TcArgs a;
-    a.X = X;
-    a.PQ = pl->PQ;
-    a.Q = pl->Q;
-    a.tiles_per_p = pl->mode == 1 ? pl->Q / BM : 1;
-    a.ntiles = pl->mode == 1 ? pl->P * a.tiles_per_p : (pl->PQ + BM - 1) / BM;
-    a.R = pl->R;
-    a.Rpad = pl->Rpad;
-    a.nk = pl->nk;
-    a.S_stg = pl->S_stg;
-    a.S_op = pl->S_op;
-    a.b_resident = pl->b_resident;
-    a.x3 = (prec == CP_BF16X3 || prec == CP_TF32X3) ? 1 : 0;
-    // accumulators per tile: nsplit for hi*hi (by k-chunk) + 1 for the corrections;
-    // two sets must fit the 512 TMEM columns
-    const int per_set = 256 / pl->Rpad;
-    int nsplit = per_set - a.x3;
-    if (nsplit > 4) nsplit = 4;
-    if (nsplit > pl->nk) nsplit = pl->nk;
-    if (nsplit < 1) nsplit = 1;
-    a.nsplit = nsplit;
-    a.nacc = nsplit + a.x3;
-    int cols = 32;
-    while (cols < 2 * a.nacc * pl->Rpad) cols *= 2;
-    a.tmem_cols = cols;
-    const uint32_t fmt = pl->kind == 0 ? 1u : 2u;  // BF16 = 1, TF32 = 2
-    a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(pl->Rpad >> 3) << 17) |
-              ((uint32_t)(BM >> 4) << 24);
-    a.dev_err = dev_err;
-    a.nsk = splitk_ws ? ttm_tc_splitk(pl, num_sms) : 1;
-    a.slice = pl->PQ * (int64_t)pl->R;
-    if (a.nsk > 1) a.X = splitk_ws;
+    const int nsk = splitk_ws ? ttm_tc_splitk(pl, num_sms) : 1;
+    float* out = nsk > 1 ? splitk_ws : X;
     const int BK = pl->kind == 0 ? 64 : 32;
-    const size_t smem = layout_bytes(pl->S_stg, pl->S_op, pl->Rpad, pl->nk, pl->b_resident, BK);
-    const int64_t nwork = a.ntiles * a.nsk;
-    const unsigned grid = (unsigned)(nwork < num_sms ? nwork : num_sms);
-    if (grid == 0) return cudaSuccess;
-    cudaError_t e;
-    if (pl->mode == 0)
-        e = pl->kind == 0 ? launch<0, 0>(pl, a, smem, grid, st) : launch<0, 1>(pl, a, smem, grid, st);
-    else
-        e = pl->kind == 0 ? launch<1, 0>(pl, a, smem, grid, st) : launch<1, 1>(pl, a, smem, grid, st);
-    if (e != cudaSuccess || a.nsk == 1) return e;
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < pl->npass && e == cudaSuccess; ++q) {
+        const TcPass& ps = pl->pass[q];
+        TcArgs a;
+        a.X = out + (size_t)q * PASS_COLS;
+        a.ldx = pl->R;
+        a.PQ = pl->PQ;
+        a.Q = pl->Q;
+        a.tiles_per_p = pl->mode == 1 ? (pl->Q + BM - 1) / BM : 1;
+        a.ntiles = pl->mode == 1 ? pl->P * a.tiles_per_p : (pl->PQ + BM - 1) / BM;
+        a.R = ps.R;
+        a.Rpad = ps.Rpad;
+        a.nk = pl->nk;
+        a.S_stg = ps.S_stg;
+        a.S_op = pl->S_op;
+        a.b_resident = ps.b_resident;
+        a.x3 = (prec == CP_BF16X3 || prec == CP_TF32X3) ? 1 : 0;
+        // accumulators per tile: nsplit for hi*hi (by k-chunk) + 1 for the corrections;
+        // two sets must fit the 512 TMEM columns
+        const int per_set = 256 / ps.Rpad;
+        int nsplit = per_set - a.x3;
+        if (nsplit > 4) nsplit = 4;
+        if (nsplit > pl->nk) nsplit = pl->nk;
+        if (nsplit < 1) nsplit = 1;
+        a.nsplit = nsplit;
+        a.nacc = nsplit + a.x3;
+        int cols = 32;
+        while (cols < 2 * a.nacc * ps.Rpad) cols *= 2;
+        a.tmem_cols = cols;
+        const uint32_t fmt = pl->kind == 0 ? 1u : 2u;  // BF16 = 1, TF32 = 2
+        a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(ps.Rpad >> 3) << 17) |
+                  ((uint32_t)(BM >> 4) << 24);
+        a.dev_err = dev_err;
+        a.nsk = nsk;
+        a.slice = pl->PQ * (int64_t)pl->R;
+        const size_t smem = layout_bytes(ps.S_stg, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK);
+        const int64_t nwork = a.ntiles * a.nsk;
+        const unsigned grid = (unsigned)(nwork < num_sms ? nwork : num_sms);
+        if (grid == 0) return cudaSuccess;
+        if (pl->mode == 0)
+            e = pl->kind == 0 ? launch<0, 0>(pl, ps, a, smem, grid, st) : launch<0, 1>(pl, ps, a, smem, grid, st);
+        else
+            e = pl->kind == 0 ? launch<1, 0>(pl, ps, a, smem, grid, st) : launch<1, 1>(pl, ps, a, smem, grid, st);
+    }
+    if (e != cudaSuccess || nsk == 1) return e;
     const int64_t n = pl->PQ * (int64_t)pl->R;
     int64_t blocks = (n / 4 + 255) / 256;
     if (blocks > 4 * num_sms) blocks = 4 * num_sms;
     if (blocks < 1) blocks = 1;
-    k_splitk_sum<<<(unsigned)blocks, 256, 0, st>>>(splitk_ws, a.nsk, n, X);
+    k_splitk_sum<<<(unsigned)blocks, 256, 0, st>>>(splitk_ws, nsk, n, X);
     return cudaGetLastError();
 }
 

@@ -40,7 +40,8 @@ def relerr(a, b):
 
 SHAPES = [((33, 40, 29), 3), ((64, 64, 64), 16), ((17, 130, 9, 12), 17), ((6, 5, 7, 4, 5), 4),
           ((150, 1, 70), 5), ((128, 96, 140), 100), ((40, 33, 260), 64), ((9, 8, 7), 1),
-          ((300, 200, 64), 64), ((130, 70, 36), 48), ((20, 16, 128, 12), 32)]
+          ((300, 200, 64), 64), ((130, 70, 36), 48), ((20, 16, 128, 12), 32),
+          ((64, 48, 40), 200)]
 
 
 @pytest.mark.parametrize("dims,R", SHAPES)
@@ -54,7 +55,7 @@ def test_mttkrp_parity(pkg, dims, R, prec):
     ctx.close()
 
 
-@pytest.mark.parametrize("dims,R", SHAPES[:6])
+@pytest.mark.parametrize("dims,R", SHAPES[:6] + SHAPES[-1:])
 @pytest.mark.parametrize("prec", PRECS)
 def test_ttm_parity(pkg, dims, R, prec):
     Td, Tref, A0 = problem(dims, R, 12)
@@ -192,10 +193,12 @@ def test_float64_input_and_default_init(pkg):
     ctx.close()
 
 
-@pytest.mark.parametrize("dims,R", [((300, 200, 64), 64), ((128, 96, 140), 100), ((20, 16, 128, 12), 32)])
+@pytest.mark.parametrize("dims,R", [((300, 200, 64), 64), ((128, 96, 140), 100), ((20, 16, 128, 12), 32),
+                                    ((64, 48, 40), 200), ((96, 36, 44), 256)])
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 def test_tensor_core_ttm_used_and_matches_simt(pkg, dims, R, prec):
-    """The tcgen05 TTM runs for supported modes and agrees with the FP32 SIMT kernel."""
+    """The tcgen05 TTM runs for supported modes (ragged last q-tiles and two column
+    passes for R > 128 included) and agrees with the FP32 SIMT kernel."""
     Td, Tref, A0 = problem(dims, R, 13)
     tc = pkg.CPContext(Td, R, A0=A0, prec=prec)
     sm = pkg.CPContext(Td, R, A0=A0, prec="fp32")
@@ -203,7 +206,7 @@ def test_tensor_core_ttm_used_and_matches_simt(pkg, dims, R, prec):
         Xt = tc.ttm(m).cpu().numpy()
         Xs = sm.ttm(m).cpu().numpy()
         assert relerr(Xt, Xs.astype(np.float64)) <= 2e-6
-    assert tc.stats()["ttm_tensor_core"] >= 1
+    assert tc.stats()["ttm_tensor_core"] == len(dims)   # every mode here has Q % 4 == 0
     assert sm.stats()["ttm_tensor_core"] == 0
     tc.close()
     sm.close()
