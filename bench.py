@@ -381,10 +381,22 @@ def main():
                     "unit": "TFLOP/s", "frac": None, "traffic": None,
                     "kernel": "ttm_simt", "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz} MHz"}
     else:
-        ach = ttm_bytes / (ttm_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": None, "traffic": None, "kernel": "ttm_tc",
-                    "peak_source": f"hbm_gbs of {peak_kind}"}
+        # tensor peak for the algorithmic flops of this mode: x3 modes issue three
+        # products per term; tf32 runs at half the bf16 rate (nominal ratio)
+        nprod = 3 if args.prec in ("bf16x3", "tf32x3") else 1
+        rate = 1.0 if args.prec in ("bf16x3", "bf16") else 0.5
+        tpeak = peaks["bf16_tflops"] * rate / nprod
+        t_hbm = ttm_bytes / (peaks["hbm_gbs"] * 1e9)
+        t_tc = ttm_flops / (tpeak * 1e12)
+        if t_tc > t_hbm:
+            roofline = {"bound": "tensor", "achieved": ttm_flops / (ttm_ms / 1e3) / 1e12, "peak": tpeak,
+                        "unit": "TFLOP/s", "frac": None, "traffic": None, "kernel": "ttm_tc",
+                        "peak_source": f"bf16_tflops of {peak_kind} x {rate} / {nprod} products per term"}
+        else:
+            ach = ttm_bytes / (ttm_ms / 1e3) / 1e9
+            roofline = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": None, "traffic": None, "kernel": "ttm_tc",
+                        "peak_source": f"hbm_gbs of {peak_kind}"}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
     roofline["ms_per_launch"] = ttm_ms
     roofline["algorithmic_bytes"] = ttm_bytes

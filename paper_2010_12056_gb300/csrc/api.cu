@@ -72,6 +72,7 @@ struct cp_ctx {
     double *Gamma = nullptr, *L = nullptr, *invd = nullptr, *W = nullptr;
     float* Ginv = nullptr;      // FP32 Gamma^{-1} for iterative refinement
     float* G32 = nullptr;       // FP32 copy of Gamma (input of the inverse)
+    float* schur_ws = nullptr;  // blocked inverse workspace (R > 128)
     cudaStream_t side = nullptr;            // normal-equation factorisation runs here,
     cudaEvent_t ev_ready = nullptr, ev_chol = nullptr;  // overlapped with the MTTKRP
     bool chol_pending = false;
@@ -389,7 +390,7 @@ cp_status launch_chol(cp_ctx* c, int u, bool pp, double* scal) {
     CKCUDA(c, cudaEventRecord(c->ev_ready, c->st));
     CKCUDA(c, cudaStreamWaitEvent(c->side, c->ev_ready, 0));
     LAUNCH(c, cpk::chol_mixed(c->d_Slist, c->d_dSlist, c->N, u, c->R, pp ? 1 : 0, c->Gamma, c->G32, c->Ginv,
-                              c->L, c->invd, c->W, scal, c->d_mode, c->side));
+                              c->L, c->invd, c->W, scal, c->d_mode, c->schur_ws, c->side));
     CKCUDA(c, cudaEventRecord(c->ev_chol, c->side));
     c->chol_pending = true;
     return CP_OK;
@@ -921,7 +922,7 @@ void free_all(cp_ctx* c) {
         c->kr_plan[i] = nullptr;
     }
     F(c->kr_hi); F(c->kr_lo); F(c->splitk_ws);
-    F(c->Ginv); F(c->G32); F(c->d_mode);
+    F(c->Ginv); F(c->G32); F(c->schur_ws); F(c->d_mode);
     if (c->side) { cudaStreamSynchronize(c->side); cudaStreamDestroy(c->side); c->side = nullptr; }
     if (c->ev_ready) { cudaEventDestroy(c->ev_ready); c->ev_ready = nullptr; }
     if (c->ev_chol) { cudaEventDestroy(c->ev_chol); c->ev_chol = nullptr; }
@@ -1041,6 +1042,7 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
     TRY(dalloc(c, &c->Gamma, RR + 2));
     TRY(dalloc(c, &c->Ginv, RR + 4));
     TRY(dalloc(c, &c->G32, RR + 4));
+    if (cpk::schur_ws_floats(R)) TRY(dalloc(c, &c->schur_ws, cpk::schur_ws_floats(R)));
     TRYC(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     TRYC(cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming));
     TRYC(cudaEventCreateWithFlags(&c->ev_chol, cudaEventDisableTiming));

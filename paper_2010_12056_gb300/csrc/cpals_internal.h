@@ -104,7 +104,9 @@ struct SolveOut {
 // substitution).  Gamma and Ginv must have 16 spare bytes after R*R entries.
 cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
                        double* Gamma, float* G32, float* Ginv, double* L64, double* invd64, double* W,
-                       double* scal, int* mode, cudaStream_t st);
+                       double* scal, int* mode, float* ws, cudaStream_t st);
+// floats of the workspace chol_mixed needs for R > 128 (blocked inverse), else 0
+size_t schur_ws_floats(int R);
 cudaError_t solve_mixed(const float* M, const double* W, const double* Gamma, const float* Ginv,
                         const double* L64, const double* invd64, const int* mode, const SolveOut& o,
                         int s, int R, double* scal, double* scal_part, int* nblk, unsigned* dev_err,

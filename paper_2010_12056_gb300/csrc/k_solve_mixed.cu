@@ -144,42 +144,6 @@ __device__ __forceinline__ double gamma_entry(const double* const* Sp, const dou
     return g;
 }
 
-// R > 128: Gamma, W and the FP64 factorisation only.
-__global__ void __launch_bounds__(1024) k_chol_fp64only(double* const* __restrict__ S_list,
-                                                        double* const* __restrict__ dS_list, int N, int n,
-                                                        int R, int pp, double* __restrict__ G,
-                                                        double* __restrict__ L64,
-                                                        double* __restrict__ invd64,
-                                                        double* __restrict__ W,
-                                                        double* __restrict__ scal,
-                                                        int* __restrict__ mode) {
-    __shared__ double red[32];
-    __shared__ double sinv[CP_MAXR], srs[CP_MAXR];
-    __shared__ int sfail;
-    const int RR = R * R;
-    const double* Sp[CP_MAXN];
-    const double* dSp[CP_MAXN];
-    for (int k = 0; k < N; ++k) {
-        Sp[k] = S_list[k];
-        dSp[k] = pp ? dS_list[k] : nullptr;
-    }
-    double tr = 0.0;
-    for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-        double w = 0.0;
-        const double g = gamma_entry(Sp, dSp, N, n, pp, (size_t)e, &w);
-        G[e] = g;
-        if (pp) W[e] = w;
-        if (e / R == e % R) tr += g;
-    }
-    tr = block_sum_d(tr, red);
-    const double flag = chol_fp64(G, R, tr, L64, L64 + RR, invd64, sinv, srs, &sfail);
-    if (threadIdx.x == 0) {
-        scal[SCAL_FLAGS] = 10.0 + flag;
-        scal[SCAL_GS] = 0.0;
-        *mode = 1;
-    }
-}
-
 // Gamma (FP64), its FP32 copy and PP's W, one entry per thread over many
 // blocks: FP64 throughput per SM is low, so this work is spread over the GPU.
 __global__ void __launch_bounds__(256) k_gamma_form(double* const* __restrict__ S_list,
@@ -217,6 +181,85 @@ __global__ void __launch_bounds__(256) k_gamma_form(double* const* __restrict__ 
 // condition number ||Gt||_inf ||Gt^{-1}||_inf exceeds 2e5 (refinement would
 // contract too slowly) or a pivot is not positive, Gamma is factored in FP64
 // (LDL^T) instead.
+// The R Gauss-Jordan steps on register tiles a (an n x n SPD matrix with unit
+// diagonal, padded with zeros) with the layout described above.  Returns false
+// if a pivot is not positive.  Ends with a barrier.
+template <int TY, int IR, int JC>
+__device__ __forceinline__ bool gj_steps(float (&a)[IR][JC], int n, float (*prow)[MIXED_MAXR],
+                                         float (*pcol)[MIXED_MAXR]) {
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int r0 = ty * IR, c0 = tx * JC;
+    // publish row 0 and column 0
+    if (ty == 0)
+#pragma unroll
+        for (int j = 0; j < JC; ++j) prow[0][c0 + j] = a[0][j];
+    if (tx == 0)
+#pragma unroll
+        for (int i = 0; i < IR; ++i) pcol[0][r0 + i] = a[i][0];
+    __syncthreads();
+    bool bad = false;
+    for (int kb = 0; kb < n && !bad; kb += IR) {
+        const bool own_rows = ty == kb / IR;  // this warp holds rows kb .. kb + IR - 1
+#pragma unroll
+        for (int kk = 0; kk < IR; ++kk) {
+            const int k = kb + kk;
+            if (k >= n) break;
+            const int cur = k & 1;
+            const float p = prow[cur][k];
+            if (!(p > 0.f) || !isfinite(p)) {
+                bad = true;
+                break;
+            }
+            const float inv = __frcp_rn(p);
+            const int jk = kk % JC;  // register slot of column k (constant once unrolled)
+            const bool kcol = tx == k / JC;
+            float rp[JC];
+#pragma unroll
+            for (int j = 0; j < JC; ++j) rp[j] = prow[cur][c0 + j];
+            if (kcol) rp[jk] = 1.f;
+            float f[IR];
+#pragma unroll
+            for (int i = 0; i < IR; i += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(&pcol[cur][r0 + i]);
+                f[i] = v.x * inv;
+                f[i + 1] = v.y * inv;
+                f[i + 2] = v.z * inv;
+                f[i + 3] = v.w * inv;
+            }
+#pragma unroll
+            for (int i = 0; i < IR; ++i) {
+                if (own_rows && i == kk) {
+#pragma unroll
+                    for (int j = 0; j < JC; ++j) a[i][j] = rp[j] * inv;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < JC; ++j) {
+                        const float g = fmaf(-f[i], rp[j], a[i][j]);
+                        a[i][j] = (j == jk && kcol) ? -f[i] : g;
+                    }
+                }
+            }
+            // owners of row / column k + 1 publish them for the next step
+            const int k1 = k + 1;
+            if (k1 < n) {
+                const int nxt = cur ^ 1;
+                const int i1 = (kk + 1) % IR, j1 = (kk + 1) % JC;
+                if (ty == k1 / IR)
+#pragma unroll
+                    for (int j = 0; j < JC; ++j) prow[nxt][c0 + j] = a[i1][j];
+                if (tx == k1 / JC)
+#pragma unroll
+                    for (int i = 0; i < IR; i += 4)
+                        *reinterpret_cast<float4*>(&pcol[nxt][r0 + i]) =
+                            make_float4(a[i][j1], a[i + 1][j1], a[i + 2][j1], a[i + 3][j1]);
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    return !bad;
+}
+
 template <int TY, int IR, int JC>
 __global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(const float* __restrict__ G32, int R,
                                                        const double* __restrict__ G,
@@ -273,75 +316,8 @@ __global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(const float* __restrict__
         for (int o = 16; o; o >>= 1) rs += __shfl_xor_sync(FULL, rs, o);
         if (tx == 0 && r0 + i < R) atomicMax(&gmax_bits, __float_as_uint(rs));
     }
-    // publish row 0 and column 0
-    if (ty == 0)
-#pragma unroll
-        for (int j = 0; j < JC; ++j) prow[0][c0 + j] = a[0][j];
-    if (tx == 0)
-#pragma unroll
-        for (int i = 0; i < IR; ++i) pcol[0][r0 + i] = a[i][0];
-    __syncthreads();
-    bool bad = sfail != 0;
-    for (int kb = 0; kb < R && !bad; kb += IR) {
-        const bool own_rows = ty == kb / IR;  // this warp holds rows kb .. kb + IR - 1
-#pragma unroll
-        for (int kk = 0; kk < IR; ++kk) {
-            const int k = kb + kk;
-            if (k >= R) break;
-            const int cur = k & 1;
-            const float p = prow[cur][k];
-            if (!(p > 0.f) || !isfinite(p)) {
-                bad = true;
-                break;
-            }
-            const float inv = __frcp_rn(p);
-            const int jk = kk % JC;  // register slot of column k (constant once unrolled)
-            const bool kcol = tx == k / JC;
-            float rp[JC];
-#pragma unroll
-            for (int j = 0; j < JC; ++j) rp[j] = prow[cur][c0 + j];
-            if (kcol) rp[jk] = 1.f;
-            float f[IR];
-#pragma unroll
-            for (int i = 0; i < IR; i += 4) {
-                const float4 v = *reinterpret_cast<const float4*>(&pcol[cur][r0 + i]);
-                f[i] = v.x * inv;
-                f[i + 1] = v.y * inv;
-                f[i + 2] = v.z * inv;
-                f[i + 3] = v.w * inv;
-            }
-#pragma unroll
-            for (int i = 0; i < IR; ++i) {
-                if (own_rows && i == kk) {
-#pragma unroll
-                    for (int j = 0; j < JC; ++j) a[i][j] = rp[j] * inv;
-                } else {
-#pragma unroll
-                    for (int j = 0; j < JC; ++j) {
-                        const float g = fmaf(-f[i], rp[j], a[i][j]);
-                        a[i][j] = (j == jk && kcol) ? -f[i] : g;
-                    }
-                }
-            }
-            // owners of row / column k + 1 publish them for the next step
-            const int k1 = k + 1;
-            if (k1 < R) {
-                const int nxt = cur ^ 1;
-                const int i1 = (kk + 1) % IR, j1 = (kk + 1) % JC;
-                if (ty == k1 / IR)
-#pragma unroll
-                    for (int j = 0; j < JC; ++j) prow[nxt][c0 + j] = a[i1][j];
-                if (tx == k1 / JC)
-#pragma unroll
-                    for (int i = 0; i < IR; i += 4)
-                        *reinterpret_cast<float4*>(&pcol[nxt][r0 + i]) =
-                            make_float4(a[i][j1], a[i + 1][j1], a[i + 2][j1], a[i + 3][j1]);
-            }
-            __syncthreads();
-        }
-    }
-    __syncthreads();
-    bool use64 = bad;
+    bool use64 = sfail != 0;
+    if (!use64) use64 = !gj_steps<TY, IR, JC>(a, R, prow, pcol);
     if (!use64) {
 #pragma unroll
         for (int i = 0; i < IR; ++i) {
@@ -385,6 +361,198 @@ __global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(const float* __restrict__
     }
 }
 
+// ------------------------------------------------------------------ 128 < R <= 256
+// Gt = D Gamma D is inverted by blocks (n1 = 128, n2 = R - 128):
+//   Gt = [[A, B], [B^T, C]],  S = C - B^T A^{-1} B (Schur complement, SPD),
+//   Gt^{-1} = [[A^{-1} + T2 T1^T, -T2], [-T2^T, S^{-1}]],  T1 = A^{-1} B,  T2 = T1 S^{-1},
+// with the two block inverses by the Gauss-Jordan kernel above (each scales its
+// own block) and four small FP32 GEMMs.  If a block pivot fails or the scaled
+// condition number exceeds 2e5, the FP64 factorisation runs instead.
+
+// Gt = D G32 D (FP32, row stride R) and ||Gt||_inf; flags[0] = 0
+__global__ void __launch_bounds__(256) k_scale_big(const float* __restrict__ G32, int R, float* __restrict__ Gt,
+                                                   float* __restrict__ dvec, unsigned* __restrict__ flags) {
+    __shared__ float dsc[CP_MAXR];
+    const int tid = threadIdx.x;
+    for (int r = tid; r < R; r += blockDim.x) {
+        const float g = G32[(size_t)r * R + r];
+        const float d = (g > 0.f && isfinite(g)) ? rsqrtf(g) : 0.f;
+        dsc[r] = d;
+        dvec[r] = d;
+        if (!(d > 0.f)) atomicOr(flags, 1u);
+    }
+    __syncthreads();
+    for (int r = blockIdx.x; r < R; r += gridDim.x) {
+        float rs = 0.f;
+        for (int c = tid; c < R; c += blockDim.x) {
+            const float v = G32[(size_t)r * R + c] * (dsc[r] * dsc[c]);
+            Gt[(size_t)r * R + c] = v;
+            rs += fabsf(v);
+        }
+        for (int o = 16; o; o >>= 1) rs += __shfl_xor_sync(FULL, rs, o);
+        __shared__ float wsum[8];
+        if ((tid & 31) == 0) wsum[tid >> 5] = rs;
+        __syncthreads();
+        if (tid == 0) {
+            float t = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+            atomicMax(flags + 1, __float_as_uint(t));
+        }
+        __syncthreads();
+    }
+}
+
+// inverse of an n x n block (n <= 128) of an SPD matrix: src row stride lds,
+// dst row stride ldd; flags[0] |= 2 if a pivot fails
+template <int TY, int IR, int JC>
+__global__ void __launch_bounds__(32 * TY, 1) k_gj_block(const float* __restrict__ src, int lds, int n,
+                                                         float* __restrict__ dst, int ldd,
+                                                         unsigned* __restrict__ flags) {
+    __shared__ __align__(16) float prow[2][MIXED_MAXR];
+    __shared__ __align__(16) float pcol[2][MIXED_MAXR];
+    __shared__ float dsc[MIXED_MAXR];
+    __shared__ int sfail;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int r0 = ty * IR, c0 = tx * JC;
+    if (tid == 0) sfail = 0;
+    __syncthreads();
+    for (int r = tid; r < MIXED_MAXR; r += 32 * TY) {
+        float d = 0.f;
+        if (r < n) {
+            const float g = src[(size_t)r * lds + r];
+            d = (g > 0.f && isfinite(g)) ? rsqrtf(g) : 0.f;
+            if (!(d > 0.f)) sfail = 1;
+        }
+        dsc[r] = d;
+    }
+    __syncthreads();
+    float a[IR][JC];
+#pragma unroll
+    for (int i = 0; i < IR; ++i)
+#pragma unroll
+        for (int j = 0; j < JC; ++j) {
+            const int r = r0 + i, c = c0 + j;
+            a[i][j] = (r < n && c < n) ? src[(size_t)r * lds + c] * (dsc[r] * dsc[c]) : 0.f;
+        }
+    bool ok = sfail == 0;
+    if (ok) ok = gj_steps<TY, IR, JC>(a, n, prow, pcol);
+    if (!ok) {
+        if (tid == 0) atomicOr(flags, 2u);
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < IR; ++i)
+#pragma unroll
+        for (int j = 0; j < JC; ++j) {
+            const int r = r0 + i, c = c0 + j;
+            if (r < n && c < n) dst[(size_t)r * ldd + c] = a[i][j] * (dsc[r] * dsc[c]);
+        }
+}
+
+// C = beta Cin + alpha op(A) op(B) (FP32), op(X) = X or X^T; 32 x 32 output tile
+// per block of 256 threads (2 x 2 per thread)
+__global__ void __launch_bounds__(256) k_gemm_small(int M, int N, int K, float alpha, const float* __restrict__ A,
+                                                    int lda, int ta, const float* __restrict__ B, int ldb, int tb,
+                                                    float beta, const float* __restrict__ Cin, int ldci,
+                                                    float* __restrict__ C, int ldc) {
+    __shared__ float As[32][33], Bs[32][33];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int i = e >> 5, kk = e & 31;
+            const int gm = m0 + i, gk = k0 + kk;
+            As[i][kk] = (gm < M && gk < K) ? (ta ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : 0.f;
+            const int gn = n0 + i;
+            Bs[kk][i] = (gn < N && gk < K) ? (tb ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            const float a0 = As[ty][kk], a1 = As[ty + 16][kk];
+            const float b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+            acc[0][0] = fmaf(a0, b0, acc[0][0]);
+            acc[0][1] = fmaf(a0, b1, acc[0][1]);
+            acc[1][0] = fmaf(a1, b0, acc[1][0]);
+            acc[1][1] = fmaf(a1, b1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+            if (gm < M && gn < N)
+                C[(size_t)gm * ldc + gn] = alpha * acc[i][j] + (Cin ? beta * Cin[(size_t)gm * ldci + gn] : 0.f);
+        }
+}
+
+// assemble D Gt^{-1} D into Ginv, check the scaled condition number, choose the path
+__global__ void __launch_bounds__(256) k_schur_finish(int R, const float* __restrict__ B11,
+                                                      const float* __restrict__ T2, const float* __restrict__ Si,
+                                                      const float* __restrict__ dvec, float* __restrict__ Ginv,
+                                                      unsigned* __restrict__ flags, double* __restrict__ scal,
+                                                      int* __restrict__ mode) {
+    __shared__ float wsum[8];
+    __shared__ unsigned imax_bits;
+    const int tid = threadIdx.x, n1 = 128, n2 = R - 128;
+    if (tid == 0) imax_bits = 0u;
+    __syncthreads();
+    for (int r = blockIdx.x; r < R; r += gridDim.x) {
+        float rs = 0.f;
+        for (int c = tid; c < R; c += blockDim.x) {
+            float v;
+            if (r < n1 && c < n1) v = B11[(size_t)r * n1 + c];
+            else if (r < n1) v = -T2[(size_t)r * n2 + (c - n1)];
+            else if (c < n1) v = -T2[(size_t)c * n2 + (r - n1)];
+            else v = Si[(size_t)(r - n1) * n2 + (c - n1)];
+            rs += fabsf(v);
+            Ginv[(size_t)r * R + c] = v * (dvec[r] * dvec[c]);
+        }
+        for (int o = 16; o; o >>= 1) rs += __shfl_xor_sync(FULL, rs, o);
+        if ((tid & 31) == 0) wsum[tid >> 5] = rs;
+        __syncthreads();
+        if (tid == 0) {
+            float t = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+            atomicMax(&imax_bits, __float_as_uint(t));
+        }
+        __syncthreads();
+    }
+    if (tid == 0) atomicMax(flags + 2, imax_bits);
+    // the last block decides (blocks count themselves in flags[3])
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned done = atomicAdd(flags + 3, 1u);
+        if (done == gridDim.x - 1) {
+            __threadfence();
+            const float kappa = __uint_as_float(atomicOr(flags + 1, 0u)) * __uint_as_float(atomicOr(flags + 2, 0u));
+            const bool ok = atomicOr(flags, 0u) == 0u && kappa <= 2e5f;
+            *mode = ok ? 0 : 1;
+            scal[SCAL_FLAGS] = 0.0;
+            scal[SCAL_GS] = 0.0;
+        }
+    }
+}
+
+// FP64 LDL^T of Gamma when the blocked FP32 inverse was not usable (*mode == 1)
+__global__ void __launch_bounds__(1024) k_chol_fp64_if(const double* __restrict__ G, int R,
+                                                       double* __restrict__ L64, double* __restrict__ invd64,
+                                                       double* __restrict__ scal, const int* __restrict__ mode) {
+    __shared__ double red[32];
+    __shared__ double sinv[CP_MAXR], srs[CP_MAXR];
+    __shared__ int sfail;
+    if (*mode == 0) return;
+    double tr = 0.0;
+    for (int j = threadIdx.x; j < R; j += blockDim.x) tr += G[(size_t)j * R + j];
+    tr = block_sum_d(tr, red);
+    const double flag = chol_fp64(G, R, tr, L64, L64 + (size_t)R * R, invd64, sinv, srs, &sfail);
+    if (threadIdx.x == 0) scal[SCAL_FLAGS] = 10.0 + flag;
+}
+
 // ------------------------------------------------------------------ row solves
 __device__ __forceinline__ void bf16_split(float x, uint16_t& hi, uint16_t& lo) {
     __nv_bfloat16 h = __float2bfloat16_rn(x);
@@ -419,7 +587,7 @@ __host__ __device__ inline SolveSmem solve_smem(int R) {
 // One row x per block of 64 threads; in the refinement path thread t owns the
 // columns t + 64 c (c < CT) and computes every dot product of those columns by
 // itself (four partial sums, no reductions across threads).  Per iteration:
-//   r = m - x Gamma   (FP64, Gamma staged in shared memory)
+//   r = m - x Gamma   (FP64; Gamma staged in shared memory for R <= 128, else read from L2)
 //   d = r G32         (FP32; r is small, so FP32 carries it to full accuracy)
 //   x += d
 // and two barriers.  It stops once the error left after the step, estimated as
@@ -459,11 +627,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
     }
 
     if (path == 0) {
-        // stage Gamma and G32 with two bulk copies (sizes rounded up to 16 bytes;
-        // the sources have 16 spare bytes)
+        // R <= 128: stage Gamma and G32 with two bulk copies (sizes rounded up to
+        // 16 bytes; the sources have 16 spare bytes).  Larger R reads both from L2.
+        const bool staged = R <= MIXED_MAXR;
+        const double* Gm = staged ? sG : G;
+        const float* Gim = staged ? sGi : Ginv;
         const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
         const uint32_t bytesG = (uint32_t)((RR * 8 + 15) & ~15), bytesGi = (uint32_t)((RR * 4 + 15) & ~15);
-        if (tid == 0) {
+        if (tid == 0 && staged) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytesG + bytesGi)
@@ -509,7 +680,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
             if (j < R) rv[j] = (float)mj[c];
         }
         // bounded wait for the staged matrices (about 1 s)
-        {
+        if (staged) {
             const long long t0 = clock64();
             uint32_t ok = 0;
             int give_up = 0;
@@ -540,12 +711,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
                 if (j < R) {
                     int k = 0;
                     for (; k + 3 < R; k += 4) {
-                        a0 = fmaf(rv[k], sGi[k * R + j], a0);
-                        a1 = fmaf(rv[k + 1], sGi[(k + 1) * R + j], a1);
-                        a2 = fmaf(rv[k + 2], sGi[(k + 2) * R + j], a2);
-                        a3 = fmaf(rv[k + 3], sGi[(k + 3) * R + j], a3);
+                        a0 = fmaf(rv[k], Gim[k * R + j], a0);
+                        a1 = fmaf(rv[k + 1], Gim[(k + 1) * R + j], a1);
+                        a2 = fmaf(rv[k + 2], Gim[(k + 2) * R + j], a2);
+                        a3 = fmaf(rv[k + 3], Gim[(k + 3) * R + j], a3);
                     }
-                    for (; k < R; ++k) a0 = fmaf(rv[k], sGi[k * R + j], a0);
+                    for (; k < R; ++k) a0 = fmaf(rv[k], Gim[k * R + j], a0);
                 }
                 d[c] = (a0 + a1) + (a2 + a3);
             }
@@ -571,12 +742,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
                 double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
                 int k = 0;
                 for (; k + 3 < R; k += 4) {
-                    r0 = fma(xv[k], sG[(size_t)k * R + j], r0);
-                    r1 = fma(xv[k + 1], sG[(size_t)(k + 1) * R + j], r1);
-                    r2 = fma(xv[k + 2], sG[(size_t)(k + 2) * R + j], r2);
-                    r3 = fma(xv[k + 3], sG[(size_t)(k + 3) * R + j], r3);
+                    r0 = fma(xv[k], Gm[(size_t)k * R + j], r0);
+                    r1 = fma(xv[k + 1], Gm[(size_t)(k + 1) * R + j], r1);
+                    r2 = fma(xv[k + 2], Gm[(size_t)(k + 2) * R + j], r2);
+                    r3 = fma(xv[k + 3], Gm[(size_t)(k + 3) * R + j], r3);
                 }
-                for (; k < R; ++k) r0 = fma(xv[k], sG[(size_t)k * R + j], r0);
+                for (; k < R; ++k) r0 = fma(xv[k], Gm[(size_t)k * R + j], r0);
                 rv[j] = (float)(mj[c] - ((r0 + r1) + (r2 + r3)));
             }
             __syncthreads();
@@ -758,14 +929,43 @@ cudaError_t launch_solve_mixed(const float* M, const double* W, const double* G,
 
 namespace cpk {
 
+size_t schur_ws_floats(int R) {
+    return R <= MIXED_MAXR ? 0 : (size_t)R * R + 6 * 128 * 128 + R + 4;
+}
+
 cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
                        double* Gamma, float* G32, float* Ginv, double* L64, double* invd64, double* W,
-                       double* scal, int* mode, cudaStream_t st) {
+                       double* scal, int* mode, float* ws, cudaStream_t st) {
+    k_gamma_form<<<(R * R + 255) / 256, 256, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, G32, W);
     if (R > MIXED_MAXR) {
-        k_chol_fp64only<<<1, 1024, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, L64, invd64, W, scal, mode);
+        if (!ws) return cudaErrorInvalidValue;
+        const int n1 = 128, n2 = R - 128;
+        float* Gt = ws;
+        float* Ai = Gt + (size_t)R * R;
+        float* T1 = Ai + 128 * 128;
+        float* Sm = T1 + 128 * 128;
+        float* Si = Sm + 128 * 128;
+        float* T2 = Si + 128 * 128;
+        float* B11 = T2 + 128 * 128;
+        float* dvec = B11 + 128 * 128;
+        unsigned* flags = reinterpret_cast<unsigned*>(dvec + R);
+        cudaError_t e = cudaMemsetAsync(flags, 0, 4 * sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+        auto grid = [](int M, int Nn) { return dim3((unsigned)((Nn + 31) / 32), (unsigned)((M + 31) / 32)); };
+        k_scale_big<<<64, 256, 0, st>>>(G32, R, Gt, dvec, flags);
+        k_gj_block<16, 8, 4><<<1, 512, 0, st>>>(Gt, R, n1, Ai, n1, flags);
+        k_gemm_small<<<grid(n1, n2), 256, 0, st>>>(n1, n2, n1, 1.f, Ai, n1, 0, Gt + n1, R, 0, 0.f, nullptr, 0,
+                                                     T1, n2);
+        k_gemm_small<<<grid(n2, n2), 256, 0, st>>>(n2, n2, n1, -1.f, Gt + n1, R, 1, T1, n2, 0, 1.f,
+                                                     Gt + (size_t)n1 * R + n1, R, Sm, n2);
+        k_gj_block<16, 8, 4><<<1, 512, 0, st>>>(Sm, n2, n2, Si, n2, flags);
+        k_gemm_small<<<grid(n1, n2), 256, 0, st>>>(n1, n2, n2, 1.f, T1, n2, 0, Si, n2, 0, 0.f, nullptr, 0, T2,
+                                                     n2);
+        k_gemm_small<<<grid(n1, n1), 256, 0, st>>>(n1, n1, n2, 1.f, T2, n2, 0, T1, n2, 1, 1.f, Ai, n1, B11, n1);
+        k_schur_finish<<<64, 256, 0, st>>>(R, B11, T2, Si, dvec, Ginv, flags, scal, mode);
+        k_chol_fp64_if<<<1, 1024, 0, st>>>(Gamma, R, L64, invd64, scal, mode);
         return cudaGetLastError();
     }
-    k_gamma_form<<<(R * R + 255) / 256, 256, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, G32, W);
     // (warps, rows per thread, columns per thread): TY x IR >= R, 32 JC >= R.
     // Sixteen warps hide the latency of each step's dependent chain.
     if (R <= 32)
