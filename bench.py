@@ -129,6 +129,40 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(mhz)}
 
 
+class Ranks:
+    """Rank bookkeeping of the replica benchmark: every rank decomposes its own
+    tensor; timing takes a barrier on both sides and the maximum over ranks.
+    `dist` is torch.distributed (initialised) or None for one process."""
+
+    def __init__(self, dist=None, device="cuda"):
+        self.dist = dist
+        self.device = device
+
+    def _sync(self):
+        if self.device == "cuda":
+            import torch
+            torch.cuda.synchronize()
+
+    def barrier(self):
+        self._sync()
+        if self.dist is not None:
+            self.dist.barrier()
+        self._sync()
+
+    def max(self, x):
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def replica_rate(steps, ms_max, world):
+    """Whole-job sweeps/s: every rank ran `steps` sweeps; the slowest rank's time counts."""
+    return world * steps / (ms_max / 1e3)
+
+
 def cpu_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -299,18 +333,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    def barrier():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(dist, "cuda")
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     import paper_2010_12056_gb300 as pkg
     import __graft_entry__ as ge
@@ -340,7 +364,7 @@ def main():
     launches = int(st1["launches"] - st0["launches"])
     flops = (st1["ttm_flops"] - st0["ttm_flops"]) + (st1["mttv_flops"] - st0["mttv_flops"])
     msdt_sps = args.steps / (ms / 1e3)
-    value = msdt_sps * world
+    value = replica_rate(args.steps, ms, world)
     mttkrp_tflops = flops / (ms / 1e3) / 1e12
     fit_formula = ctx.fit(exact=False)[0]
     fit_direct = ctx.fit(exact=True)[0]

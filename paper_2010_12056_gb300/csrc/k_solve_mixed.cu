@@ -9,7 +9,7 @@
 //   k_gamma_form  Gamma = *_{k != n} S(k) and PP's W in FP64 (many blocks)
 //   k_gj_inv      (one CTA) the FP32 inverse of the diagonally scaled Gamma by
 //                 Gauss-Jordan elimination; if the scaled condition number is
-//                 above 2e5 or a pivot is not positive, an FP64 LDL^T of Gamma
+//                 above 1e6 or a pivot is not positive, an FP64 LDL^T of Gamma
 //                 instead, and the solve kernel substitutes in FP64.
 //   k_solve_mixed (one warp per row) m = M(x,:) [+ A_old(x,:) W];
 //                 x0 = m G32;  repeat  r = m - x Gamma (FP64),  d = r G32,  x += d
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(256) k_gamma_form(double* const* __restrict__ 
 // Row i != k: a_ij <- a_ij - (a_ik / p) a_kj for j != k, a_ik <- -a_ik / p;
 // row k: a_kj <- a_kj / p, a_kk <- 1 / p.  Scaling removes the part of Gamma's
 // condition number that comes from unequal column norms; if the scaled
-// condition number ||Gt||_inf ||Gt^{-1}||_inf exceeds 2e5 (refinement would
+// condition number ||Gt||_inf ||Gt^{-1}||_inf exceeds 1e6 (refinement would
 // contract too slowly) or a pivot is not positive, Gamma is factored in FP64
 // (LDL^T) instead.
 // The R Gauss-Jordan steps on register tiles a (an n x n SPD matrix with unit
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(const float* __restrict__
         }
         __syncthreads();
         const float kappa = __uint_as_float(gmax_bits) * __uint_as_float(imax_bits);
-        use64 = !(kappa <= 2e5f);
+        use64 = !(kappa <= 1e6f);
     }
     if (use64) {
         double tr = 0.0;
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(const float* __restrict__
 //   Gt^{-1} = [[A^{-1} + T2 T1^T, -T2], [-T2^T, S^{-1}]],  T1 = A^{-1} B,  T2 = T1 S^{-1},
 // with the two block inverses by the Gauss-Jordan kernel above (each scales its
 // own block) and four small FP32 GEMMs.  If a block pivot fails or the scaled
-// condition number exceeds 2e5, the FP64 factorisation runs instead.
+// condition number exceeds 1e6, the FP64 factorisation runs instead.
 
 // Gt = D G32 D (FP32, row stride R) and ||Gt||_inf; flags[0] = 0
 __global__ void __launch_bounds__(256) k_scale_big(const float* __restrict__ G32, int R, float* __restrict__ Gt,
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(256) k_schur_finish(int R, const float* __rest
         if (done == gridDim.x - 1) {
             __threadfence();
             const float kappa = __uint_as_float(atomicOr(flags + 1, 0u)) * __uint_as_float(atomicOr(flags + 2, 0u));
-            const bool ok = atomicOr(flags, 0u) == 0u && kappa <= 2e5f;
+            const bool ok = atomicOr(flags, 0u) == 0u && kappa <= 1e6f;
             *mode = ok ? 0 : 1;
             scal[SCAL_FLAGS] = 0.0;
             scal[SCAL_GS] = 0.0;
@@ -734,21 +734,42 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
         double prev = 0.0;
         bool conv = false;
         for (int itr = 0; itr < 30; ++itr) {
-            // r = m - x Gamma (FP64, four partial sums)
+            // r = m - x Gamma (FP64).  Eight partial sums per column, the thread's
+            // columns interleaved: 8 CT independent chains cover the FP64 FMA
+            // latency (64 cycles) with the few warps a row has.
+            {
+                double ra[CT][8];
+                int jj[CT];
 #pragma unroll
-            for (int c = 0; c < CT; ++c) {
-                const int j = tid + SOLVE_THREADS * c;
-                if (j >= R) continue;
-                double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
-                int k = 0;
-                for (; k + 3 < R; k += 4) {
-                    r0 = fma(xv[k], Gm[(size_t)k * R + j], r0);
-                    r1 = fma(xv[k + 1], Gm[(size_t)(k + 1) * R + j], r1);
-                    r2 = fma(xv[k + 2], Gm[(size_t)(k + 2) * R + j], r2);
-                    r3 = fma(xv[k + 3], Gm[(size_t)(k + 3) * R + j], r3);
+                for (int c = 0; c < CT; ++c) {
+                    const int j = tid + SOLVE_THREADS * c;
+                    jj[c] = j < R ? j : 0;  // idle columns read column 0 and are dropped
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) ra[c][q] = 0.0;
                 }
-                for (; k < R; ++k) r0 = fma(xv[k], Gm[(size_t)k * R + j], r0);
-                rv[j] = (float)(mj[c] - ((r0 + r1) + (r2 + r3)));
+                int k = 0;
+                for (; k + 7 < R; k += 8) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const double xk = xv[k + q];
+                        const double* grow = Gm + (size_t)(k + q) * R;
+#pragma unroll
+                        for (int c = 0; c < CT; ++c) ra[c][q] = fma(xk, grow[jj[c]], ra[c][q]);
+                    }
+                }
+                for (; k < R; ++k) {
+#pragma unroll
+                    for (int c = 0; c < CT; ++c) ra[c][0] = fma(xv[k], Gm[(size_t)k * R + jj[c]], ra[c][0]);
+                }
+#pragma unroll
+                for (int c = 0; c < CT; ++c) {
+                    const int j = tid + SOLVE_THREADS * c;
+                    if (j < R) {
+                        const double t = ((ra[c][0] + ra[c][1]) + (ra[c][2] + ra[c][3])) +
+                                         ((ra[c][4] + ra[c][5]) + (ra[c][6] + ra[c][7]));
+                        rv[j] = (float)(mj[c] - t);
+                    }
+                }
             }
             __syncthreads();
             float dd[CT];
