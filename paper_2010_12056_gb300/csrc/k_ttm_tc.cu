@@ -53,8 +53,14 @@ struct TcArgs {
     int R, Rpad, nk, S_stg, S_op, tmem_cols, x3, b_resident, nsplit, nacc;
     int nsk;          // split-K factor: work item w = (tile w / nsk, k-slice w % nsk)
     int64_t slice;    // floats between split-K output slices
-    int ldx;          // row stride of X in floats (R of the whole factor; this pass writes
-                      // columns 0..R-1 of X, which points at its first column)
+    int ldx;          // row stride of X in floats (R of the whole factor)
+    // column passes (R > 128): work item w = (tile, k-slice, pass) with the pass
+    // innermost, so a tile's second pass finds its T chunks in L2.  R / Rpad above
+    // are the largest pass's (they size the shared-memory slots and TMEM sets).
+    int npass;
+    int Rp[2], Rpadp[2];   // columns of pass p (written at column 128 p of X), padded
+    uint32_t idescp[2];    // MMA instruction descriptor of pass p (N = Rpadp[p])
+    int set_cols;          // TMEM columns of one accumulator set
     uint32_t idesc;
     unsigned* dev_err;
 };
@@ -216,7 +222,8 @@ __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, in
 template <int MODE, int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_ttm_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmBhi,
-             const __grid_constant__ CUtensorMap tmBlo, const TcArgs a) {
+             const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmBhi1,
+             const __grid_constant__ CUtensorMap tmBlo1, const TcArgs a) {
     constexpr int BK = KIND == 0 ? 64 : 32;
     constexpr uint32_t STG = BM * BK * 4;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -280,6 +287,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmT) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBhi) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBlo) : "memory");
+            if (a.npass > 1) {
+                asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBhi1) : "memory");
+                asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBlo1) : "memory");
+            }
             if (a.b_resident) {
                 mbar_expect_tx(b_full, (uint32_t)a.nk * bchunk);
                 for (int kc = 0; kc < a.nk; ++kc) {
@@ -290,10 +301,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             int64_t it = 0;
             bool ok = true;
-            const int64_t nwork = a.ntiles * a.nsk;
+            const int64_t nwork = a.ntiles * a.nsk * a.npass;
             for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
-                const int64_t tile = w / a.nsk;
-                const int ks = (int)(w % a.nsk);
+                const int64_t tile = w / ((int64_t)a.nsk * a.npass);
+                const int ks = (int)((w / a.npass) % a.nsk);
+                const int pass = (int)(w % a.npass);
+                const CUtensorMap* mhi = pass ? &tmBhi1 : &tmBhi;
+                const CUtensorMap* mlo = pass ? &tmBlo1 : &tmBlo;
                 const int kc0 = ks * a.nk / a.nsk, kc1 = (ks + 1) * a.nk / a.nsk;
                 for (int kc = kc0; kc < kc1 && ok; ++kc, ++it) {
                     const int s = (int)(it % S_stg);
@@ -315,10 +329,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         const int j = (int)(it % S_op);
                         const uint32_t uj = (uint32_t)(it / S_op);
                         if (!(ok = mbar_wait(op_empty(j), (uj & 1u) ^ 1u, abort_flag))) break;
-                        mbar_expect_tx(op_full(j), bchunk);
+                        // this pass's operand rows only (a smaller last pass leaves the
+                        // rest of the slot unused)
+                        mbar_expect_tx(op_full(j), 2u * (uint32_t)a.Rpadp[pass] * 128u);
                         const uint32_t bdst = b0 + (uint32_t)j * bchunk;
-                        tma_load_2d(bdst, &tmBhi, kc * BK, 0, op_full(j));
-                        tma_load_2d(bdst + bpart, &tmBlo, kc * BK, 0, op_full(j));
+                        tma_load_2d(bdst, mhi, kc * BK, 0, op_full(j));
+                        tma_load_2d(bdst + bpart, mlo, kc * BK, 0, op_full(j));
                     }
                 }
             }
@@ -337,15 +353,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int lt = 0;
             bool ok = true;
             if (a.b_resident) ok = mbar_wait(b_full, 0u, abort_flag);
-            const int64_t nwork = a.ntiles * a.nsk;
+            const int64_t nwork = a.ntiles * a.nsk * a.npass;
             for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++lt) {
-                const int ks = (int)(w % a.nsk);
+                const int ks = (int)((w / a.npass) % a.nsk);
+                const int pass = (int)(w % a.npass);
+                const uint32_t idesc = a.idescp[pass];
                 const int kc0 = ks * a.nk / a.nsk, kc1 = (ks + 1) * a.nk / a.nsk;
                 const int buf = lt & 1;
                 const uint32_t ub = (uint32_t)(lt >> 1);
                 if (!(ok = mbar_wait(acc_empty(buf), (ub & 1u) ^ 1u, abort_flag))) break;
                 tc_fence_after();
-                const uint32_t dt = tmem_base + (uint32_t)(buf * a.nacc * a.Rpad);
+                const uint32_t dt = tmem_base + (uint32_t)(buf * a.set_cols);
                 const uint32_t dcorr = dt + (uint32_t)(a.nsplit * a.Rpad);
                 for (int kc = kc0; kc < kc1; ++kc, ++it) {
                     const int rc = kc - kc0;  // chunk index within this work item
@@ -359,11 +377,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     for (int kk = 0; kk < 4; ++kk) {  // 4 k-steps of 32 bytes per 128-byte row
                         const uint32_t off = (uint32_t)kk * 32u;
                         const uint32_t accm = (rc >= a.nsplit || kk > 0) ? 1u : 0u;
-                        tc_mma<KIND>(dmain, sw128_desc(ahi + off), sw128_desc(bhi + off), a.idesc, accm);
+                        tc_mma<KIND>(dmain, sw128_desc(ahi + off), sw128_desc(bhi + off), idesc, accm);
                         if (a.x3) {
                             const uint32_t accc = (rc > 0 || kk > 0) ? 1u : 0u;
-                            tc_mma<KIND>(dcorr, sw128_desc(ahi + off), sw128_desc(blo + off), a.idesc, accc);
-                            tc_mma<KIND>(dcorr, sw128_desc(alo + off), sw128_desc(bhi + off), a.idesc, 1u);
+                            tc_mma<KIND>(dcorr, sw128_desc(ahi + off), sw128_desc(blo + off), idesc, accc);
+                            tc_mma<KIND>(dcorr, sw128_desc(alo + off), sw128_desc(bhi + off), idesc, 1u);
                         }
                     }
                     tc_commit(op_empty(j));
@@ -384,9 +402,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int sw = m & 7;
         int64_t it = 0;
         bool ok = true;
-        const int64_t nwork = a.ntiles * a.nsk;
+        const int64_t nwork = a.ntiles * a.nsk * a.npass;
         for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
-            const int ks = (int)(w % a.nsk);
+            const int ks = (int)((w / a.npass) % a.nsk);
             const int kc0 = ks * a.nk / a.nsk, kc1 = (ks + 1) * a.nk / a.nsk;
             for (int kc = kc0; kc < kc1; ++kc, ++it) {
                 const int s = (int)(it % S_stg);
@@ -448,10 +466,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         float* tb = reinterpret_cast<float*>(gbase + (epi0 - base)) + quad * 32 * EPI_STRIDE;
         int lt = 0;
         bool ok = true;
-        const int64_t nwork = a.ntiles * a.nsk;
+        const int64_t nwork = a.ntiles * a.nsk * a.npass;
         for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++lt) {
-            const int64_t tile = w / a.nsk;
-            float* Xs = a.X + (int64_t)(w % a.nsk) * a.slice;
+            const int64_t tile = w / ((int64_t)a.nsk * a.npass);
+            const int pass = (int)(w % a.npass);
+            const int Rw = a.Rp[pass], Rpw = a.Rpadp[pass];
+            float* Xs = a.X + (int64_t)((w / a.npass) % a.nsk) * a.slice + 128 * pass;
             const int buf = lt & 1;
             if (!(ok = mbar_wait(acc_full(buf), (uint32_t)((lt >> 1) & 1), abort_flag))) break;
             tc_fence_after();
@@ -467,8 +487,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 gend = p * a.Q + a.Q;  // the last tile of a p is ragged when BM does not divide Q
             }
             const uint32_t taddr =
-                tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * a.nacc * a.Rpad);
-            for (int c0 = 0; c0 < a.Rpad; c0 += 16) {
+                tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * a.set_cols);
+            for (int c0 = 0; c0 < Rpw; c0 += 16) {
                 float v[16];
                 // corrections first (last accumulator), then the hi*hi partial sums
                 tmem_ld16(taddr + (uint32_t)((a.nacc - 1) * a.Rpad + c0), v);
@@ -490,16 +510,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int i = 0; i < 4; ++i) {
                     const int r = (lane >> 2) + 8 * i;
                     const int64_t g = g0 + r;
-                    if (g < gend && col < a.R) {
+                    if (g < gend && col < Rw) {
                         const float4 w = *reinterpret_cast<const float4*>(tb + r * EPI_STRIDE + 4 * q);
                         float* dst = Xs + g * (int64_t)a.ldx + col;
-                        if (((a.R | a.ldx) & 3) == 0) {
+                        if (((Rw | a.ldx) & 3) == 0) {
                             *reinterpret_cast<float4*>(dst) = w;
                         } else {
                             dst[0] = w.x;
-                            if (col + 1 < a.R) dst[1] = w.y;
-                            if (col + 2 < a.R) dst[2] = w.z;
-                            if (col + 3 < a.R) dst[3] = w.w;
+                            if (col + 1 < Rw) dst[1] = w.y;
+                            if (col + 2 < Rw) dst[2] = w.z;
+                            if (col + 3 < Rw) dst[3] = w.w;
                         }
                     }
                 }
@@ -599,7 +619,8 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
         TcPass& ps = pl->pass[q];
         ps.R = std::min(PASS_COLS, R - q * PASS_COLS);
         ps.Rpad = pl->npass == 1 ? Rpad : (ps.R + 15) / 16 * 16;
-        ps.b_resident = (size_t)pl->nk * 2 * ps.Rpad * 128 <= 64 * 1024 ? 1 : 0;
+        // with two passes the operand slots are refilled per work item
+        ps.b_resident = (pl->npass == 1 && (size_t)pl->nk * 2 * ps.Rpad * 128 <= 64 * 1024) ? 1 : 0;
         ps.S_stg = 0;
         for (int st = MAX_STG; st >= 2; --st)
             if (layout_bytes(st, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK) <= SMEM_LIMIT) {
@@ -672,10 +693,11 @@ int ttm_tc_splitk(const TcPlan* pl, int num_sms) {
 int64_t ttm_tc_rows(const TcPlan* pl) { return pl->PQ; }
 
 template <int MODE, int KIND>
-static cudaError_t launch(const TcPlan* pl, const TcPass& ps, const TcArgs& a, size_t smem, unsigned grid,
+static cudaError_t launch(const TcPlan* pl, const TcPass& p1, const TcArgs& a, size_t smem, unsigned grid,
                           cudaStream_t st) {
     cudaFuncSetAttribute(k_ttm_tc<MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ttm_tc<MODE, KIND><<<grid, NTHREADS, smem, st>>>(pl->tmT, ps.tmBhi, ps.tmBlo, a);
+    k_ttm_tc<MODE, KIND><<<grid, NTHREADS, smem, st>>>(pl->tmT, pl->pass[0].tmBhi, pl->pass[0].tmBlo, p1.tmBhi,
+                                                       p1.tmBlo, a);
     return cudaGetLastError();
 }
 
@@ -708,52 +730,58 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     if ((pl->kind == 0 && !bf) || (pl->kind == 1 && !tf)) return cudaErrorInvalidValue;
     if (((uintptr_t)X & 15) && (pl->R & 3) == 0) return cudaErrorMisalignedAddress;
     const int nsk = splitk_ws ? ttm_tc_splitk(pl, num_sms) : 1;
-    float* out = nsk > 1 ? splitk_ws : X;
     const int BK = pl->kind == 0 ? 64 : 32;
-    cudaError_t e = cudaSuccess;
-    for (int q = 0; q < pl->npass && e == cudaSuccess; ++q) {
-        const TcPass& ps = pl->pass[q];
-        TcArgs a;
-        a.X = out + (size_t)q * PASS_COLS;
-        a.ldx = pl->R;
-        a.PQ = pl->PQ;
-        a.Q = pl->Q;
-        a.tiles_per_p = pl->mode == 1 ? (pl->Q + BM - 1) / BM : 1;
-        a.ntiles = pl->mode == 1 ? pl->P * a.tiles_per_p : (pl->PQ + BM - 1) / BM;
-        a.R = ps.R;
-        a.Rpad = ps.Rpad;
-        a.nk = pl->nk;
-        a.S_stg = ps.S_stg;
-        a.S_op = pl->S_op;
-        a.b_resident = ps.b_resident;
-        a.x3 = (prec == CP_BF16X3 || prec == CP_TF32X3) ? 1 : 0;
-        // accumulators per tile: nsplit for hi*hi (by k-chunk) + 1 for the corrections;
-        // two sets must fit the 512 TMEM columns
-        const int per_set = 256 / ps.Rpad;
-        int nsplit = per_set - a.x3;
-        if (nsplit > 4) nsplit = 4;
-        if (nsplit > pl->nk) nsplit = pl->nk;
-        if (nsplit < 1) nsplit = 1;
-        a.nsplit = nsplit;
-        a.nacc = nsplit + a.x3;
-        int cols = 32;
-        while (cols < 2 * a.nacc * ps.Rpad) cols *= 2;
-        a.tmem_cols = cols;
-        const uint32_t fmt = pl->kind == 0 ? 1u : 2u;  // BF16 = 1, TF32 = 2
-        a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(ps.Rpad >> 3) << 17) |
-                  ((uint32_t)(BM >> 4) << 24);
-        a.dev_err = dev_err;
-        a.nsk = nsk;
-        a.slice = pl->PQ * (int64_t)pl->R;
-        const size_t smem = layout_bytes(ps.S_stg, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK);
-        const int64_t nwork = a.ntiles * a.nsk;
-        const unsigned grid = (unsigned)(nwork < num_sms ? nwork : num_sms);
-        if (grid == 0) return cudaSuccess;
-        if (pl->mode == 0)
-            e = pl->kind == 0 ? launch<0, 0>(pl, ps, a, smem, grid, st) : launch<0, 1>(pl, ps, a, smem, grid, st);
-        else
-            e = pl->kind == 0 ? launch<1, 0>(pl, ps, a, smem, grid, st) : launch<1, 1>(pl, ps, a, smem, grid, st);
+    const TcPass& p0 = pl->pass[0];  // the widest pass: it sizes the slots and TMEM sets
+    TcArgs a;
+    a.X = nsk > 1 ? splitk_ws : X;
+    a.ldx = pl->R;
+    a.PQ = pl->PQ;
+    a.Q = pl->Q;
+    a.tiles_per_p = pl->mode == 1 ? (pl->Q + BM - 1) / BM : 1;
+    a.ntiles = pl->mode == 1 ? pl->P * a.tiles_per_p : (pl->PQ + BM - 1) / BM;
+    a.R = p0.R;
+    a.Rpad = p0.Rpad;
+    a.nk = pl->nk;
+    a.S_stg = p0.S_stg;
+    a.S_op = pl->S_op;
+    a.b_resident = p0.b_resident;
+    a.x3 = (prec == CP_BF16X3 || prec == CP_TF32X3) ? 1 : 0;
+    // accumulators per tile: nsplit for hi*hi (by k-chunk) + 1 for the corrections;
+    // two sets must fit the 512 TMEM columns
+    const int per_set = 256 / p0.Rpad;
+    int nsplit = per_set - a.x3;
+    if (nsplit > 4) nsplit = 4;
+    if (nsplit > pl->nk) nsplit = pl->nk;
+    if (nsplit < 1) nsplit = 1;
+    a.nsplit = nsplit;
+    a.nacc = nsplit + a.x3;
+    a.set_cols = a.nacc * p0.Rpad;
+    int cols = 32;
+    while (cols < 2 * a.set_cols) cols *= 2;
+    a.tmem_cols = cols;
+    const uint32_t fmt = pl->kind == 0 ? 1u : 2u;  // BF16 = 1, TF32 = 2
+    a.npass = pl->npass;
+    for (int q = 0; q < 2; ++q) {
+        const TcPass& ps = pl->pass[q < pl->npass ? q : 0];
+        a.Rp[q] = ps.R;
+        a.Rpadp[q] = ps.Rpad;
+        a.idescp[q] = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(ps.Rpad >> 3) << 17) |
+                      ((uint32_t)(BM >> 4) << 24);
     }
+    a.idesc = a.idescp[0];
+    a.dev_err = dev_err;
+    a.nsk = nsk;
+    a.slice = pl->PQ * (int64_t)pl->R;
+    const size_t smem = layout_bytes(p0.S_stg, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK);
+    const int64_t nwork = a.ntiles * a.nsk * a.npass;
+    const unsigned grid = (unsigned)(nwork < num_sms ? nwork : num_sms);
+    if (grid == 0) return cudaSuccess;
+    const TcPass& p1 = pl->pass[pl->npass > 1 ? 1 : 0];
+    cudaError_t e;
+    if (pl->mode == 0)
+        e = pl->kind == 0 ? launch<0, 0>(pl, p1, a, smem, grid, st) : launch<0, 1>(pl, p1, a, smem, grid, st);
+    else
+        e = pl->kind == 0 ? launch<1, 0>(pl, p1, a, smem, grid, st) : launch<1, 1>(pl, p1, a, smem, grid, st);
     if (e != cudaSuccess || nsk == 1) return e;
     const int64_t n = pl->PQ * (int64_t)pl->R;
     int64_t blocks = (n / 4 + 255) / 256;
