@@ -60,6 +60,11 @@ def parse():
     ap.add_argument("--target-sweeps", type=int, default=60)
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--policy-dims", default="256,256,256")
+    ap.add_argument("--ttm-only", action="store_true",
+                    help="time only the first-level TTM of the last mode (cp_ttm) and exit")
+    ap.add_argument("--dims", default=None, help="override the workload's mode sizes, e.g. 512,512,512")
+    ap.add_argument("--rank", type=int, default=None, help="override the workload's rank")
+    ap.add_argument("--law", default=None, choices=["uniform", "gaussian", "collinear"])
     ap.add_argument("--pp-sweeps", type=int, default=-1,
                     help="PP (eps = 0.1) vs exact MSDT over this many sweeps (default: 100 for c4, else 0)")
     return ap.parse_args()
@@ -311,13 +316,56 @@ def run_policy(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ttm_only(args, wl):
+    """Time cp_ttm of the last mode (the kernel the sweeps launch) on one workload."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2010_12056_gb300 as pkg
+    dims, R = wl["dims"], wl["R"]
+    numel = int(np.prod(dims))
+    T, _, A0 = make_inputs(wl, "cuda")
+    ctx = pkg.CPContext(T, R, A0=A0, prec=args.prec)
+    mode = len(dims) - 1
+    X = torch.empty(numel // dims[mode] * R, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        ctx.ttm(mode, out=X)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        ctx.ttm(mode, out=X)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = ctx.stats()
+    print(json.dumps({"metric": "first-level TTM time", "value": ms, "unit": "ms", "workload": wl["desc"],
+                      "prec": args.prec, "tflops_algorithmic": 2.0 * numel * R / (ms / 1e3) / 1e12,
+                      "gbs_algorithmic": (4.0 * numel + 4.0 * numel // dims[mode] * R) / (ms / 1e3) / 1e9,
+                      "tensor_core_launches": st["ttm_tensor_core"]}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.workload == "policy":
         if int(os.environ.get("RANK", "0")) == 0:
             run_policy(args)
         return
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.dims or args.rank or args.law:
+        if args.dims:
+            wl["dims"] = tuple(int(x) for x in args.dims.split(","))
+        if args.rank:
+            wl["R"] = args.rank
+        if args.law:
+            wl["law"] = args.law
+        wl["desc"] = "custom: dims %s, R = %d, %s factors + %g noise" % (
+            "x".join(map(str, wl["dims"])), wl["R"], wl["law"], wl["eta"])
+    if args.ttm_only:
+        run_ttm_only(args, wl)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -422,6 +470,12 @@ def main():
                         "frac": None, "traffic": None, "kernel": "ttm_tc",
                         "peak_source": f"hbm_gbs of {peak_kind}"}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    if args.workload == "c2" and args.prec == "bf16x3" and not (args.dims or args.rank or args.law):
+        # DRAM bytes per launch from the ncu capture of the same kernel on order-4 96^4
+        # (0.93 of its algorithmic bytes), scaled by this launch's algorithmic bytes
+        roofline["traffic"] = 0.932 * ttm_bytes
+        roofline["traffic_source"] = "ncu dram__bytes_read+write on 96^4 R=64 (0.932 x algorithmic), scaled"
+
     roofline["ms_per_launch"] = ttm_ms
     roofline["algorithmic_bytes"] = ttm_bytes
     roofline["algorithmic_flops"] = ttm_flops
