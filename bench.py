@@ -45,7 +45,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS) + ["policy"])
@@ -80,7 +80,8 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms; only samples taken
+    between mark_start() and mark_stop() (the timed region) are summarised."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -91,23 +92,33 @@ class ClockSampler:
         self.rows = []
         self.proc = None
         self.t = None
+        self.t0 = self.t1 = None
 
-    def start(self):
+    def start(self, wait_s=3.0):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
         self.t = threading.Thread(target=self._read, daemon=True)
         self.t.start()
+        t_end = time.time() + wait_s   # the first sample shows the sampler is running
+        while not self.rows and time.time() < t_end:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
-                self.rows.append(parts)
+                self.rows.append((time.time(), parts))
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_stop(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc:
@@ -118,9 +129,13 @@ class ClockSampler:
                 self.proc.kill()
         if self.t:
             self.t.join(timeout=2)
+        rows = self.rows
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows if self.t0 <= r[0] <= self.t1 + 0.05]
+            rows = inside if inside else [r for r in rows if r[0] >= self.t0][:1]
         mhz, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for _, r in rows:
             try:
                 mhz.append(float(r[1]))
                 mx = float(r[2])
@@ -198,8 +213,12 @@ def make_inputs(wl, device):
                                      C=wl.get("C"), device=device)
 
 
-def run_reference(args, wl, rank):
-    """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
+def run_reference(args, wl, rank, budget_s=60.0):
+    """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only).
+
+    A step is one oracle MSDT sweep of the full tensor; the sample is bounded:
+    sweeps run until --steps are done or about budget_s seconds have passed (at
+    least one), after at most one warm-up sweep, and the line says how many ran."""
     import numpy as np
     import torch
     if rank != 0:
@@ -210,22 +229,25 @@ def run_reference(args, wl, rank):
     del T
     from oracle import cp_oracle as co
     A = [a.copy() for a in A0]
-    for _ in range(args.warmup):
+    for _ in range(min(args.warmup, 1)):
         A = co.cp_als(T64, A, 1, route="msdt").A
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+    n, t0 = 0, time.perf_counter()
+    while n < args.steps:
         A = co.cp_als(T64, A, 1, route="msdt").A
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
     el = time.perf_counter() - t0
-    v = args.steps / el
+    v = n / el
     cores = cpu_threads()
+    sample = f"{n} of {args.steps} FP64 oracle MSDT sweeps on the full tensor ({el:.1f} s, budget {budget_s:.0f} s)"
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "sweep/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": wl["desc"], "sweep": "msdt"},
-        "cpu_baseline": {"value": v, "unit": "sweep/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} FP64 oracle MSDT sweeps on the full tensor"},
+        "cpu_baseline": {"value": v, "unit": "sweep/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "sweep/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -402,10 +424,12 @@ def main():
     clk.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
+    clk.mark_start()
     e0.record(stream)
     ctx.sweep_msdt(args.steps)
     e1.record(stream)
     barrier()
+    clk.mark_stop()
     clocks = clk.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
     st1 = ctx.stats()
