@@ -505,20 +505,27 @@ def main():
     roofline["algorithmic_flops"] = ttm_flops
 
     # ---------------------------------------------------------------- PP (approximated sweeps)
+    # operators built explicitly after the warm-up, then a bounded run of Alg. 2
+    # with a loose tolerance (0.5) so that most sweeps are approximated
     ctx_pp = pkg.CPContext(T, R, A0=A0, prec=args.prec, stream=stream)
     ctx_pp.sweep_msdt(max(2, args.warmup))
-    ctx_pp.sweep_pp(3, eps=0.99)           # regular sweep, PP init, first approximated sweep
-    tr0 = len(ctx_pp.trace())
-    t0 = time.perf_counter()
-    ctx_pp.sweep_pp(args.steps, eps=0.99)
-    torch.cuda.synchronize()
-    wall_pp = time.perf_counter() - t0
-    tr = ctx_pp.trace()[tr0:]
-    pp_ms = [t["ms"] for t in tr if t["kind"] == "pp" and not t["pp_init"]]
-    pp_info = {"approx_sweeps": len(pp_ms),
-               "approx_sweep_ms": (sum(pp_ms) / len(pp_ms)) if pp_ms else None,
-               "approx_sweeps_per_s_wall": len(tr) / wall_pp,
-               "init_count": ctx_pp.stats()["pp_init"]}
+    npp_run = min(args.steps, 20)
+    pp_info = {"eps": 0.5, "sweeps": npp_run}
+    try:
+        ctx_pp.pp_init()
+        tr0 = len(ctx_pp.trace())
+        t0 = time.perf_counter()
+        ctx_pp.sweep_pp(npp_run, eps=0.5)
+        torch.cuda.synchronize()
+        wall_pp = time.perf_counter() - t0
+        tr = ctx_pp.trace()[tr0:]
+        pp_ms = [t["ms"] for t in tr if t["kind"] == "pp" and not t["pp_init"]]
+        pp_info.update({"approx_sweeps": len(pp_ms),
+                        "approx_sweep_ms": (sum(pp_ms) / len(pp_ms)) if pp_ms else None,
+                        "sweeps_per_s_wall": len(tr) / wall_pp,
+                        "init_count": ctx_pp.stats()["pp_init"]})
+    except pkg.CPError as e:
+        pp_info["error"] = str(e)
     ctx_pp.close()
 
     # ---------------------------------------------------------------- PP vs exact MSDT (Alg. 2, eps 0.1)

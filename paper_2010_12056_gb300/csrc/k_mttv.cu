@@ -9,8 +9,11 @@
 
 namespace {
 
-// Block = TX outputs (vectors of VEC along r) x KS partial sums over k.
-template <int VEC>
+// Block = TX outputs (vectors of VEC along r) x KS partial sums over k.  With
+// float4 outputs each thread keeps U loads of X in flight: the kernel is bound by
+// how many bytes the SMs have outstanding (measured on 128^4 R = 64 roots: 4 in
+// flight gave 3.2-3.6 TB/s, 16 in flight with a 4-way k-split 5.4-5.5 TB/s).
+template <int VEC, int U>
 __global__ void __launch_bounds__(256) k_mttv(const float* __restrict__ X,
                                               const float* __restrict__ A,
                                               float* __restrict__ Y, int64_t P, int K, int64_t Q,
@@ -30,23 +33,18 @@ __global__ void __launch_bounds__(256) k_mttv(const float* __restrict__ X,
         const float* ap = A + rv * VEC;
         int k = ty;
         if (VEC == 4) {
-            for (; k + 3 * KS < K; k += 4 * KS) {
-                float4 x0 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)k * strideK));
-                float4 x1 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)(k + KS) * strideK));
-                float4 x2 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)(k + 2 * KS) * strideK));
-                float4 x3 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)(k + 3 * KS) * strideK));
-                float4 a0 = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)k * R));
-                float4 a1 = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)(k + KS) * R));
-                float4 a2 = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)(k + 2 * KS) * R));
-                float4 a3 = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)(k + 3 * KS) * R));
-                acc.x = fmaf(x0.x, a0.x, acc.x); acc.y = fmaf(x0.y, a0.y, acc.y);
-                acc.z = fmaf(x0.z, a0.z, acc.z); acc.w = fmaf(x0.w, a0.w, acc.w);
-                acc.x = fmaf(x1.x, a1.x, acc.x); acc.y = fmaf(x1.y, a1.y, acc.y);
-                acc.z = fmaf(x1.z, a1.z, acc.z); acc.w = fmaf(x1.w, a1.w, acc.w);
-                acc.x = fmaf(x2.x, a2.x, acc.x); acc.y = fmaf(x2.y, a2.y, acc.y);
-                acc.z = fmaf(x2.z, a2.z, acc.z); acc.w = fmaf(x2.w, a2.w, acc.w);
-                acc.x = fmaf(x3.x, a3.x, acc.x); acc.y = fmaf(x3.y, a3.y, acc.y);
-                acc.z = fmaf(x3.z, a3.z, acc.z); acc.w = fmaf(x3.w, a3.w, acc.w);
+            for (; k + (U - 1) * KS < K; k += U * KS) {
+                float4 x[U], a[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    x[u] = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)(k + u * KS) * strideK));
+                    a[u] = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)(k + u * KS) * R));
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    acc.x = fmaf(x[u].x, a[u].x, acc.x); acc.y = fmaf(x[u].y, a[u].y, acc.y);
+                    acc.z = fmaf(x[u].z, a[u].z, acc.z); acc.w = fmaf(x[u].w, a[u].w, acc.w);
+                }
             }
             for (; k < K; k += KS) {
                 float4 x0 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)k * strideK));
@@ -81,16 +79,19 @@ cudaError_t mttv(const float* X, const float* A, float* Y, int64_t P, int K, int
     const bool v4 = (R % 4 == 0) && (((uintptr_t)X | (uintptr_t)A | (uintptr_t)Y) & 15) == 0;
     const int VEC = v4 ? 4 : 1;
     const int64_t nout = P * Q * (R / VEC);
-    // choose the k-split so that the grid covers the GPU at least twice
+    // k-split: enough blocks to cover the GPU twice, and (float4 path) at least
+    // two rounds of 16 loads per thread where K allows a split
     int KS = 1;
     while (KS < 32 && KS < K && (nout * KS) < (int64_t)num_sms * 2 * 256) KS *= 2;
+    if (v4)
+        while (KS < 8 && K / (2 * KS) >= 32) KS *= 2;
     int TX = 256 / KS;
     unsigned nblk = (unsigned)((nout + TX - 1) / TX);
     size_t smem = sizeof(float4) * 256;
     if (v4)
-        k_mttv<4><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
+        k_mttv<4, 16><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
     else
-        k_mttv<1><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
+        k_mttv<1, 1><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
     return cudaGetLastError();
 }
 
