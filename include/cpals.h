@@ -62,7 +62,7 @@ typedef struct {
     int prec;         /* cp_prec of the first-level TTM                           */
     double pp_eps;    /* PP tolerance epsilon of Alg. 2 (0 < eps < 1)             */
     double delta;     /* stopping tolerance on |r - r_old| (Alg. 1); <= 0: never  */
-    int max_sweeps;   /* cap used by cp_run (<= 0: no cap)                        */
+    int max_sweeps;   /* sweep cap of cp_run (<= 0: no cap)                       */
     int judge_every;  /* policy mode: direct residual every k sweeps (0 = off)    */
     int policy_gate;  /* 1: consult the policy only when approximating pays (see
                          cp_sweep_pp); 0: before every sweep                  */
@@ -139,11 +139,13 @@ cp_status cp_sweep_msdt(cp_ctx *ctx, int nsweeps);
  *           operators rebuilt now (p_new).  The sweep is approximated with the
  *           current operators if they exist and p_cur >= 0.5, else rebuilt and
  *           approximated if p_new >= 0.5, else regular (MSDT).  The network
- *           is consulted only while an approximated sweep, with its share of
- *           the query and of the judge, is measured to cost less than the
- *           cheapest regular sweep seen on this problem; before it has been
- *           measured, only while the MTTKRP traffic it avoids (at about
- *           6 TB/s) covers that share.  The first two policy-driven sweeps of a
+ *           is consulted only while approximated sweeps are measured to cost,
+ *           all in (operator builds, judge and queries included), less than 0.9
+ *           of the cheapest regular sweep seen on this problem (a safe
+ *           approximated sweep keeps at least 90% of a regular sweep's
+ *           progress); before three have been measured, only while the MTTKRP
+ *           traffic an approximated sweep avoids (at about 6 TB/s) covers its
+ *           share of the query and the judge.  The first two policy-driven sweeps of a
  *           context are regular.  cfg.policy_gate = 0 consults the network
  *           before every sweep instead.  The judge (judge_every
  *           > 0): before a run of approximated sweeps the state and its direct
@@ -164,6 +166,17 @@ cp_status cp_sweep_msdt(cp_ctx *ctx, int nsweeps);
  */
 typedef struct cp_policy cp_policy;
 cp_status cp_sweep_pp(cp_ctx *ctx, int nsweeps, double eps, cp_policy *policy);
+
+/*
+ * cp_run - the outer loop of Alg. 1 (route 0 DT, 1 MSDT) or Alg. 2 (route 2: PP
+ * with cfg.pp_eps and `policy`, which may be NULL): sweeps until the relative
+ * residual of Eq. (residual) changes by at most cfg.delta between consecutive
+ * sweeps (the first sweep of a context compares with r = 1), or cfg.max_sweeps
+ * sweeps have run in this call.  At least one of the two must be set (delta > 0
+ * or max_sweeps > 0), else CP_EINVAL.  *nsweeps (may be NULL) returns the sweeps
+ * run.  Synchronises after every sweep.
+ */
+cp_status cp_run(cp_ctx *ctx, int route, cp_policy *policy, int *nsweeps);
 
 /*
  * cp_policy_features - the 8 inputs of the PP policy network for the current

@@ -78,6 +78,7 @@ _SIGS = {
     "cp_sweep_msdt": (_I, [_P, _I]),
     "cp_sweep_pp": (_I, [_P, _I, _D, _P]),
     "cp_pp_init": (_I, [_P]),
+    "cp_run": (_I, [_P, _I, _P, ctypes.POINTER(_I)]),
     "cp_pp_probe": (_I, [_P, _I, ctypes.POINTER(ProbeRec)]),
     "cp_policy_features": (_I, [_P, ctypes.POINTER(ctypes.c_float)]),
     "cp_pp_mttkrp": (_I, [_P, _I, _P]),
@@ -131,7 +132,7 @@ class CPContext:
     """One decomposition of a dense CUDA tensor (float32 borrowed, float64 copied once)."""
 
     def __init__(self, T, R, A0=None, prec="bf16x3", seed=20101205, pp_eps=0.1, judge_every=5,
-                 policy_gate=True, stream=None):
+                 policy_gate=True, delta=0.0, max_sweeps=0, stream=None):
         import torch
         if not (isinstance(T, torch.Tensor) and T.is_cuda and T.is_contiguous()):
             raise ValueError("T must be a contiguous CUDA tensor")
@@ -150,6 +151,8 @@ class CPContext:
         cfg.pp_eps = float(pp_eps)
         cfg.judge_every = int(judge_every)
         cfg.policy_gate = 1 if policy_gate else 0
+        cfg.delta = float(delta)
+        cfg.max_sweeps = int(max_sweeps)
         dims = (ctypes.c_int64 * self.N)(*self.dims)
         a0p = None
         if A0 is not None:
@@ -211,6 +214,13 @@ class CPContext:
 
     def pp_init(self):
         self._ck(self._L.cp_pp_init(self._h))
+
+    def run(self, route="msdt", policy=None):
+        """cp_run: sweeps until |r - r_old| <= delta or max_sweeps (given at construction)."""
+        n = ctypes.c_int(0)
+        rt = {"dt": 0, "msdt": 1, "pp": 2}[route]
+        self._ck(self._L.cp_run(self._h, rt, policy._h if policy else None, ctypes.byref(n)))
+        return n.value
 
     def pp_mttkrp(self, mode, out=None):
         import torch

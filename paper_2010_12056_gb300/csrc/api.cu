@@ -145,6 +145,8 @@ struct cp_ctx {
     // measured device time of the choices (exponential averages; < 0: not yet seen)
     double cost_exact = -1.0, cost_pp = -1.0, cost_init = -1.0, cost_judge = -1.0, cost_query = -1.0;
     int n_exact_seen = 0;
+    double pp_ms_total = 0.0;   // all-in time of the approximated sweeps (builds, judge, queries)
+    int pp_n = 0;
     double sweep_mttkrp_bytes = -1.0;  // MTTKRP bytes of the last regular sweep
     bool snap_current = false;  // the rollback point is the present state
 
@@ -1327,7 +1329,12 @@ cp_status cp_sweep_pp(cp_ctx* c, int nsweeps, double eps, cp_policy* policy) {
                 const double over_ms = (c->cost_query >= 0.0 ? c->cost_query : 0.03) + (judge ? judge_ms / judge : 0.0);
                 pp_pays = saved_ms > over_ms;
             } else if (pp_pays) {
-                pp_pays = c->cost_pp + extra < c->cost_exact;
+                // measured: the approximated sweeps' all-in time per sweep (their
+                // operator builds, judge and queries included) against 0.9 of the
+                // cheapest regular sweep (a safe approximated sweep keeps at least
+                // 90% of a regular sweep's progress)
+                pp_pays = c->pp_n >= 3 ? c->pp_ms_total / c->pp_n < 0.9 * c->cost_exact
+                                       : c->cost_pp + extra < c->cost_exact;
             }
             by = 1;
             choice = CH_EXACT;
@@ -1381,7 +1388,12 @@ cp_status cp_sweep_pp(cp_ctx* c, int nsweeps, double eps, cp_policy* policy) {
         rec.decided_by = by;
         note_cost(c, rec.kind, rec.pp_init, rec.ms);
         rec.ms += c->pending_ms;
+        const size_t rec_i = c->trace.size() - 1;
         if (judge && rec.kind == 2 && ++c->since_judge >= judge) CKST(judge_now(c, judge));
+        if (policy && c->trace[rec_i].kind == 2) {
+            c->pp_ms_total += c->trace[rec_i].ms;  // judge time lands on this record
+            c->pp_n++;
+        }
     }
     return CP_OK;
 }
@@ -1445,6 +1457,25 @@ cp_status cp_pp_probe(cp_ctx* c, int follow, cp_probe_rec* out) {
     }
     out->followed = ch;
     c->trace.back().decided_by = 3;
+    return CP_OK;
+}
+
+cp_status cp_run(cp_ctx* c, int route, cp_policy* policy, int* nsweeps) {
+    CKST(entry_check(c));
+    if (nsweeps) *nsweeps = 0;
+    const double delta = c->cfg.delta;
+    const int cap = c->cfg.max_sweeps;
+    if (route < 0 || route > 2 || (!(delta > 0.0) && cap <= 0)) return CP_EINVAL;
+    double r = c->have_last ? c->last_resid : 1.0;
+    for (int k = 0; cap <= 0 || k < cap; ++k) {
+        if (route == 0) CKST(cp_sweep_dt(c, 1));
+        else if (route == 1) CKST(cp_sweep_msdt(c, 1));
+        else CKST(cp_sweep_pp(c, 1, c->cfg.pp_eps, policy));
+        if (nsweeps) *nsweeps = k + 1;
+        const double r_old = r;
+        r = c->trace.back().resid;
+        if (delta > 0.0 && fabs(r - r_old) <= delta) break;
+    }
     return CP_OK;
 }
 

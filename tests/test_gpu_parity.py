@@ -286,3 +286,20 @@ def test_mixed_solve_no_fallback_on_well_conditioned(pkg):
     for n in range(3):
         assert relerr(ctx.get_factor(n), ref.A[n]) <= 1e-4
     ctx.close()
+
+
+@pytest.mark.parametrize("route", ["dt", "msdt"])
+def test_run_stops_like_alg1(pkg, route):
+    """cp_run: sweeps until |r - r_old| <= delta (Alg. 1), like the oracle's loop."""
+    Td, Tref, A0 = problem((40, 36, 44), 6, 36, eta=1e-2)
+    ctx = pkg.CPContext(Td, 6, A0=A0, prec="fp32", delta=1e-4, max_sweeps=200)
+    n = ctx.run(route)
+    ref = co.cp_als(Tref, A0, 200, route=route, delta=1e-4)
+    assert abs(n - len(ref.resid)) <= 1
+    assert n < 200
+    _, r = ctx.fit(exact=True)
+    assert abs(r - ref.resid[-1]) <= 1e-4
+    ctx.close()
+    with pytest.raises(pkg.CPError):
+        bad = pkg.CPContext(Td, 6, A0=A0, prec="fp32")   # neither delta nor a cap
+        bad.run("msdt")
