@@ -441,17 +441,34 @@ def main():
     fit_formula = ctx.fit(exact=False)[0]
     fit_direct = ctx.fit(exact=True)[0]
 
-    # ---------------------------------------------------------------- DT on the same problem
-    ctx_dt = pkg.CPContext(T, R, A0=A0, prec=args.prec, stream=stream)
-    ctx_dt.sweep_dt(args.warmup)
-    barrier()
-    e0.record(stream)
-    ctx_dt.sweep_dt(args.steps)
-    e1.record(stream)
-    barrier()
-    ms_dt = max_over_ranks(e0.elapsed_time(e1))
-    dt_sps = args.steps / (ms_dt / 1e3)
-    ctx_dt.close()
+    # ---------------------------------------------------------------- other schedules, same problem
+    def timed_sweeps(route, **options):
+        """sweeps/s of `route` from the same start, with cp_set_option switches."""
+        c2 = pkg.CPContext(T, R, A0=A0, prec=args.prec, stream=stream)
+        for k, v in options.items():
+            c2.set_option(k, v)
+        run = c2.sweep_dt if route == "dt" else c2.sweep_msdt
+        run(args.warmup)
+        barrier()
+        e0.record(stream)
+        run(args.steps)
+        e1.record(stream)
+        barrier()
+        t = max_over_ranks(e0.elapsed_time(e1))
+        c2.close()
+        return args.steps / (t / 1e3)
+
+    dt_sps = timed_sweeps("dt")
+    schedules = {
+        "msdt": msdt_sps,
+        "dt_fused": dt_sps,
+        # Fig. 1a literally: first-level TTM, then one multi-TTV per level
+        "dt_unfused": timed_sweeps("dt", fuse_dt=False),
+        # the TTM epilogue also forms the first child of roots T x_0 and T x_{N-1}
+        "msdt_fused_child": timed_sweeps("msdt", fuse_child=True),
+        # second child contracted on a side stream during the next update (6 blocks/SM)
+        "msdt_lookahead": timed_sweeps("msdt", lookahead=6),
+    }
 
     # ---------------------------------------------------------------- TTM roofline
     peaks, peak_kind = load_peaks()
@@ -597,7 +614,9 @@ def main():
                    if args.workload == "c2" else "see dims"},
         "mttkrp_tflops": mttkrp_tflops,
         "dt_sweeps_per_s": dt_sps * world,
-        "msdt_time_over_dt": (ms / args.steps) / (ms_dt / args.steps),
+        "msdt_time_over_dt": dt_sps / msdt_sps,
+        "msdt_time_over_dt_unfused": schedules["dt_unfused"] / msdt_sps,
+        "schedules_sweeps_per_s": schedules,
         "fit": {"formula": fit_formula, "direct": fit_direct, "after_sweeps": args.warmup + args.steps},
         "solves_fp64": int(st1["solves_fp64"]),
         "pp": pp_info,

@@ -287,8 +287,34 @@ typedef struct {
     int64_t solves_fp64;    /* updates whose normal equations needed the FP64
                                factorisation (ill-conditioned Gamma)          */
     int64_t rollbacks;      /* policy judge rollbacks                         */
+    int64_t lookahead;      /* multi-sweep nodes contracted ahead, overlapped
+                               with the next update (cp_set_option)           */
+    int64_t ttm_child;      /* first-level TTMs whose epilogue also produced
+                               the first child node (cp_set_option)           */
 } cp_stats;
 cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
+
+/*
+ * cp_set_option - schedule switches that change the order or fusion of the
+ * tree's contractions, never which nodes are formed from which factor values
+ * (Fig. 1a, Fig. 2): results agree to FP32 rounding.
+ *   CP_OPT_FUSE_DT    (default 1) standard tree: contract a half's first two
+ *                     modes from T in one pass with their Khatri-Rao product (no
+ *                     s^(N-1) R node); 0 runs Fig. 1a literally (first-level TTM,
+ *                     then one multi-TTV per level).
+ *   CP_OPT_LOOKAHEAD  (default 0) multi-sweep tree, N >= 4: contract the level-2
+ *                     node of the update after next on a second stream while the
+ *                     next update runs; value 1..8 = blocks per SM that
+ *                     contraction may hold (the rest is left to the next update's
+ *                     kernels); results are bit-identical to 0.
+ *   CP_OPT_FUSE_CHILD (default 0) multi-sweep tree: when the first child of a
+ *                     root contracts the root's innermost mode (roots T x_0 and
+ *                     T x_{N-1}), the tensor-core TTM's epilogue forms it too and
+ *                     the root is read once instead of twice.
+ * CP_EINVAL for an unknown option or value.  Takes effect at the next call.
+ */
+enum { CP_OPT_FUSE_DT = 1, CP_OPT_LOOKAHEAD = 2, CP_OPT_FUSE_CHILD = 3 };
+cp_status cp_set_option(cp_ctx *ctx, int option, int value);
 
 /*
  * cp_resid_noalloc - the direct residual of cp_fit(exact = 1) for callers that

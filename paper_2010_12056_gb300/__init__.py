@@ -62,8 +62,11 @@ class Stats(ctypes.Structure):
                 ("mttv_flops", ctypes.c_double), ("pp_flops", ctypes.c_double),
                 ("ttm_bytes", ctypes.c_double), ("mttv_bytes", ctypes.c_double),
                 ("ttm_tensor_core", ctypes.c_int64), ("ttm_fused", ctypes.c_int64),
-                ("solves_fp64", ctypes.c_int64), ("rollbacks", ctypes.c_int64)]
+                ("solves_fp64", ctypes.c_int64), ("rollbacks", ctypes.c_int64),
+                ("lookahead", ctypes.c_int64), ("ttm_child", ctypes.c_int64)]
 
+
+OPTIONS = {"fuse_dt": 1, "lookahead": 2, "fuse_child": 3}
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -87,6 +90,7 @@ _SIGS = {
     "cp_set_factor": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "cp_get_trace": (_I, [_P, ctypes.POINTER(TraceRec), ctypes.POINTER(ctypes.c_size_t)]),
     "cp_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
+    "cp_set_option": (_I, [_P, _I, _I]),
     "cp_last_error": (ctypes.c_char_p, [_P]),
     "cp_free": (None, [_P]),
     "cp_policy_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_float), _P]),
@@ -278,6 +282,14 @@ class CPContext:
                 "r0": r.r0, "r_exact": r.r_exact, "r_cur": r.r_cur, "r_new": r.r_new,
                 "ms_exact": r.ms_exact, "ms_cur": r.ms_cur, "ms_new": r.ms_new, "has_ops": r.has_ops,
                 "label_cur": r.label_cur, "label_new": r.label_new, "followed": r.followed}
+
+    def set_option(self, option, value):
+        """cp_set_option: option in OPTIONS ('fuse_dt', 'lookahead', 'fuse_child'); value a
+        bool, or for 'lookahead' the blocks per SM of the look-ahead contraction (1..8)."""
+        v = int(value) if not isinstance(value, bool) else (1 if value else 0)
+        if option == "lookahead" and value is True:
+            v = 3
+        self._ck(self._L.cp_set_option(self._h, OPTIONS[option], v))
 
     def stats(self):
         s = Stats()

@@ -91,6 +91,18 @@ struct cp_ctx {
     double normT2 = 0.0;
 
     Slot slot[CP_MAXN + 1];
+    // Multi-sweep look-ahead: a node of the update after next whose inputs are
+    // already final is contracted on `ahead` into alt[k] while the next update's
+    // MTTKRP and normal equations run on the main stream (same nodes, same
+    // arithmetic as Fig. 2; only the order of independent work changes).
+    Slot alt[CP_MAXN + 1];
+    int64_t alt_busy[CP_MAXN + 1] = {0};  // update index that still reads alt[k]
+    cudaStream_t ahead = nullptr;
+    cudaEvent_t ev_x = nullptr, ev_ahead = nullptr;
+    bool ahead_pending = false;
+    int64_t ahead_target = -1;
+    bool lookahead = false;
+    int ahead_blocks_per_sm = 3;  // leaves every SM room for the normal-equation kernels
     cpk::TcPlan* tc_plan[CP_MAXN] = {0};   // tensor-core TTM per mode (NULL: SIMT)
     // fused two-mode contraction T x_{a,a+1} KR(A_a, A_{a+1}) per adjacent pair a
     cpk::TcPlan* kr_plan[CP_MAXN] = {0};
@@ -99,6 +111,9 @@ struct cp_ctx {
     void* kr_lo = nullptr;
     float* splitk_ws = nullptr;
     bool fuse_dt = true;
+    bool fuse_child = false;  // TTM epilogue forms the first child (multi-sweep tree)
+    float* child_ws = nullptr;  // pieces of first-child segments that cross TTM tiles
+    size_t child_ws_cap = 0;
 
     // PP state.  An operator set is A_p with the M_p(i,j) and M_p(n) built from
     // it; pair/Mp/Ap64 point into the current set.  A second set is allocated
@@ -249,6 +264,7 @@ cp_status launch_ttm(cp_ctx* c, int mode, float* X) {
     const int prec = c->cfg.prec;
     if (prec != CP_FP32_SIMT && c->tc_plan[mode]) {
         LAUNCH(c, cpk::ttm_tc_run(c->tc_plan[mode], X, prec, c->num_sms, c->dev_err, c->st, c->splitk_ws));
+        if (c->splitk_ws && cpk::ttm_tc_splitk(c->tc_plan[mode], c->num_sms) > 1) c->stats.launches++;  // partial-sum kernel
         c->stats.ttm_tensor_core++;
     } else {
         LAUNCH(c, cpk::ttm_simt(c->T, c->A32[mode], X, P, K, Q, c->R, c->st));
@@ -259,12 +275,13 @@ cp_status launch_ttm(cp_ctx* c, int mode, float* X) {
     return CP_OK;
 }
 
-cp_status launch_mttv(cp_ctx* c, const float* X, uint32_t contracted, int mode, float* Y) {
+cp_status launch_mttv(cp_ctx* c, const float* X, uint32_t contracted, int mode, float* Y,
+                      cudaStream_t st = nullptr, int max_blocks_per_sm = 0) {
     int64_t P, Q;
     contract_dims(c, contracted, mode, &P, &Q);
     const int K = (int)c->dims[mode];
     if (P * Q == 0) return CP_OK;
-    LAUNCH(c, cpk::mttv(X, c->A32[mode], Y, P, K, Q, c->R, c->num_sms, c->st));
+    LAUNCH(c, cpk::mttv(X, c->A32[mode], Y, P, K, Q, c->R, c->num_sms, st ? st : c->st, max_blocks_per_sm));
     const double nin = (double)P * K * Q * c->R;
     c->stats.mttv++;
     c->stats.mttv_flops += 2.0 * nin;
@@ -280,6 +297,7 @@ cp_status launch_fused2(cp_ctx* c, int a, float* X) {
     LAUNCH(c, cpk::kr_operand(c->A64[a], c->A64[a + 1], sa, sb, R, c->kr_Kpad[a], bf ? 0 : 1, c->kr_hi,
                               c->kr_lo, c->st));
     LAUNCH(c, cpk::ttm_tc_run(c->kr_plan[a], X, c->cfg.prec, c->num_sms, c->dev_err, c->st, c->splitk_ws));
+    if (c->splitk_ws && cpk::ttm_tc_splitk(c->kr_plan[a], c->num_sms) > 1) c->stats.launches++;  // partial-sum kernel
     const double rows = (double)c->numel / ((double)sa * sb);
     c->stats.ttm++;
     c->stats.ttm_tensor_core++;
@@ -289,29 +307,91 @@ cp_status launch_fused2(cp_ctx* c, int a, float* X) {
     return CP_OK;
 }
 
+// A cached node equal to the contraction of `mask` with the current factors:
+// the slot of its level or the look-ahead slot, else NULL.
+Slot* find_node(cp_ctx* c, uint32_t mask) {
+    const int k = c->N - __builtin_popcount(mask);
+    for (Slot* s : {&c->slot[k], &c->alt[k]}) {
+        if (!s->buf || !s->valid || s->contracted != mask) continue;
+        bool ok = true;
+        for (int m = 0; ok && m < c->N; ++m)
+            if ((mask >> m & 1u) && s->ver[m] != c->ver[m]) ok = false;
+        if (ok) return s;
+    }
+    return nullptr;
+}
+
+// The main stream waits for the look-ahead contraction in flight, if any.
+cp_status ahead_join(cp_ctx* c) {
+    if (!c->ahead_pending) return CP_OK;
+    CKCUDA(c, cudaStreamWaitEvent(c->st, c->ev_ahead, 0));
+    c->ahead_pending = false;
+    return CP_OK;
+}
+
+// Multi-sweep root T x_m A(m) whose first child contracts cm: the TTM epilogue
+// can form the child too when cm is the root's innermost kept mode.
+bool child_fusable(const cp_ctx* c, int m, int cm) {
+    if (!c->fuse_child || c->cfg.prec == CP_FP32_SIMT || !c->tc_plan[m]) return false;
+    const int N = c->N;
+    const int inner = (m == N - 1) ? N - 2 : N - 1;
+    if (cm != inner || !(m == 0 || m == N - 1)) return false;
+    const int sc = (int)c->dims[cm];
+    if (!cpk::ttm_tc_child_ok(c->tc_plan[m], sc)) return false;
+    return (size_t)cpk::ttm_tc_child_ws_floats(c->tc_plan[m], sc) <= c->child_ws_cap;
+}
+
+// Root X = T x_m A(m) and its first child Y = X x_cm A(cm) in one pass over T.
+cp_status launch_ttm_child(cp_ctx* c, int m, int cm, float* X, float* Y) {
+    cpk::TcChild ch;
+    ch.Y = Y;
+    ch.Ac = c->A32[cm];
+    ch.sc = (int)c->dims[cm];
+    ch.ws = c->child_ws;
+    LAUNCH(c, cpk::ttm_tc_run(c->tc_plan[m], X, c->cfg.prec, c->num_sms, c->dev_err, c->st, nullptr, &ch));
+    if (cpk::ttm_tc_child_ws_floats(c->tc_plan[m], ch.sc) > 0) c->stats.launches++;  // cross-tile segments
+    const int64_t rows = c->numel / c->dims[m];
+    c->stats.ttm++;
+    c->stats.ttm_tensor_core++;
+    c->stats.ttm_child++;
+    c->stats.ttm_flops += 2.0 * (double)c->numel * c->R;
+    c->stats.ttm_bytes += 4.0 * ((double)c->numel + (double)rows * c->R);
+    // the child is the multi-TTV the epilogue replaced (its input is not re-read)
+    c->stats.mttv_flops += 2.0 * (double)rows * c->R;
+    c->stats.mttv_bytes += 4.0 * (double)(rows / ch.sc) * c->R;
+    return CP_OK;
+}
+
 // Ensure the node reached by contracting path[0..d-1] is in its slot; returns it.
 // fuse2: the level-1 node of this path has no other use, so the level-2 node may
 // be computed from T directly when its two modes are adjacent.
-cp_status ensure_node(cp_ctx* c, const int* path, int d, float** out, bool fuse2 = false) {
+// child: multi-sweep path; a level-2 node whose root is missing may come from
+// the root's TTM epilogue (child_fusable).
+cp_status ensure_node(cp_ctx* c, const int* path, int d, float** out, bool fuse2 = false,
+                      bool child = false) {
     uint32_t mask = 0;
     for (int i = 0; i < d; ++i) mask |= 1u << path[i];
-    Slot& s = c->slot[c->N - d];
-    bool hit = s.valid && s.contracted == mask;
-    for (int i = 0; hit && i < d; ++i)
-        if (s.ver[path[i]] != c->ver[path[i]]) hit = false;
-    if (hit) {
-        *out = s.buf;
+    if (Slot* h = find_node(c, mask)) {
+        *out = h->buf;
         return CP_OK;
     }
+    Slot& s = c->slot[c->N - d];
     s.valid = false;
     const int lo_m = d >= 2 ? std::min(path[0], path[1]) : -1;
-    if (d == 1) {
+    if (d == 2 && child && !find_node(c, 1u << path[0]) && child_fusable(c, path[0], path[1])) {
+        Slot& root = c->slot[c->N - 1];
+        root.valid = false;
+        CKST(launch_ttm_child(c, path[0], path[1], root.buf, s.buf));
+        root.valid = true;
+        root.contracted = 1u << path[0];
+        for (int k = 0; k < c->N; ++k) root.ver[k] = c->ver[k];
+    } else if (d == 1) {
         CKST(launch_ttm(c, path[0], s.buf));
     } else if (d == 2 && fuse2 && c->fuse_dt && std::abs(path[0] - path[1]) == 1 && c->kr_plan[lo_m]) {
         CKST(launch_fused2(c, lo_m, s.buf));
     } else {
         float* parent = nullptr;
-        CKST(ensure_node(c, path, d - 1, &parent, fuse2));
+        CKST(ensure_node(c, path, d - 1, &parent, fuse2, child));
         CKST(launch_mttv(c, parent, mask & ~(1u << path[d - 1]), path[d - 1], s.buf));
     }
     s.valid = true;
@@ -367,8 +447,9 @@ std::vector<int> msdt_path(int N, int64_t t, int* u_out) {
     return seq;
 }
 
-cp_status mttkrp_leaf(cp_ctx* c, const std::vector<int>& path, float** M, bool fuse2 = false) {
-    return ensure_node(c, path.data(), (int)path.size(), M, fuse2);
+cp_status mttkrp_leaf(cp_ctx* c, const std::vector<int>& path, float** M, bool fuse2 = false,
+                      bool child = false) {
+    return ensure_node(c, path.data(), (int)path.size(), M, fuse2, child);
 }
 
 double* scal_slot(cp_ctx* c, int k, int mode) {
@@ -511,23 +592,68 @@ cp_status entry_check(cp_ctx* c) {
     return CP_OK;
 }
 
+// After update t of the multi-sweep tree (Sec. III), when update t+2 belongs to
+// the same subtree: the level-2 node on its path (root with one more mode
+// contracted) is final once it contracts no factor that update t+1 changes.  If
+// it is not on update t+1's path and not cached, contract it now on the `ahead`
+// stream, on a capped grid, so that it overlaps update t+1.  For N = 4 this is
+// the second child X x_a A(a) of Fig. 2 (root mode m, leaves a, b, c), computed
+// while b is updated.
+cp_status msdt_lookahead(cp_ctx* c, int64_t t) {
+    const int N = c->N;
+    if (!c->lookahead || N < 4 || !c->ahead) return CP_OK;
+    if (t / (N - 1) != (t + 2) / (N - 1)) return CP_OK;
+    int u1 = 0, u2 = 0;
+    const std::vector<int> p1 = msdt_path(N, t + 1, &u1), p2 = msdt_path(N, t + 2, &u2);
+    if (p2.size() < 3) return CP_OK;
+    const uint32_t root = 1u << p2[0];
+    const uint32_t mask = root | (1u << p2[1]);
+    if (mask & (1u << u1)) return CP_OK;                               // changes at t+1
+    if (p1.size() >= 2 && ((1u << p1[0]) | (1u << p1[1])) == mask) return CP_OK;  // next update builds it
+    if (find_node(c, mask)) return CP_OK;
+    Slot* parent = find_node(c, root);
+    const int k = N - 2;
+    if (!parent || parent == &c->alt[N - 1] || !c->alt[k].buf || c->alt_busy[k] > t) return CP_OK;
+    Slot& s = c->alt[k];
+    s.valid = false;
+    CKCUDA(c, cudaEventRecord(c->ev_x, c->st));
+    CKCUDA(c, cudaStreamWaitEvent(c->ahead, c->ev_x, 0));
+    CKST(launch_mttv(c, parent->buf, root, p2[1], s.buf, c->ahead, c->ahead_blocks_per_sm));
+    CKCUDA(c, cudaEventRecord(c->ev_ahead, c->ahead));
+    s.valid = true;
+    s.contracted = mask;
+    for (int m = 0; m < N; ++m) s.ver[m] = c->ver[m];
+    c->alt_busy[k] = t + 2;
+    c->ahead_pending = true;
+    c->ahead_target = t + 2;
+    c->stats.lookahead++;
+    return CP_OK;
+}
+
 // One exact sweep: DT (kind 0) or MSDT (kind 1/3).  Records into scal_hist[k].
-cp_status exact_sweep(cp_ctx* c, bool msdt, int k) {
+// keep_ahead: the caller continues with another MSDT sweep, so a look-ahead
+// contraction may stay in flight across the sweep boundary.
+cp_status exact_sweep(cp_ctx* c, bool msdt, int k, bool keep_ahead = false) {
     for (int u0 = 0; u0 < c->N; ++u0) {
         int u = u0;
         std::vector<int> path;
         bool fuse2 = false;
+        const int64_t t = c->t_msdt;
         if (msdt) {
-            path = msdt_path(c->N, c->t_msdt, &u);
+            path = msdt_path(c->N, t, &u);
             c->t_msdt++;
+            if (c->ahead_pending && t >= c->ahead_target) CKST(ahead_join(c));
         } else {
+            CKST(ahead_join(c));
             path = dt_path(c->N, u0, &fuse2);
         }
         CKST(launch_chol(c, u, false, scal_slot(c, k, u)));
         float* M = nullptr;
-        CKST(mttkrp_leaf(c, path, &M, fuse2));
+        CKST(mttkrp_leaf(c, path, &M, fuse2, msdt));
         CKST(update_mode(c, u, M, false, scal_slot(c, k, u)));
+        if (msdt) CKST(msdt_lookahead(c, t));
     }
+    if (!keep_ahead) CKST(ahead_join(c));
     c->stats.sweeps_exact++;
     return CP_OK;
 }
@@ -917,13 +1043,17 @@ void free_all(cp_ctx* c) {
     }
     F(c->pol_io);
     for (int k = 0; k <= CP_MAXN; ++k) F(c->slot[k].buf);
+    for (int k = 0; k <= CP_MAXN; ++k) F(c->alt[k].buf);
+    if (c->ahead) { cudaStreamSynchronize(c->ahead); cudaStreamDestroy(c->ahead); c->ahead = nullptr; }
+    for (cudaEvent_t* e : {&c->ev_x, &c->ev_ahead})
+        if (*e) { cudaEventDestroy(*e); *e = nullptr; }
     for (int i = 0; i < CP_MAXN; ++i) {
         cpk::ttm_tc_plan_free(c->tc_plan[i]);
         c->tc_plan[i] = nullptr;
         cpk::ttm_tc_plan_free(c->kr_plan[i]);
         c->kr_plan[i] = nullptr;
     }
-    F(c->kr_hi); F(c->kr_lo); F(c->splitk_ws);
+    F(c->kr_hi); F(c->kr_lo); F(c->splitk_ws); F(c->child_ws);
     F(c->Ginv); F(c->G32); F(c->schur_ws); F(c->d_mode);
     if (c->side) { cudaStreamSynchronize(c->side); cudaStreamDestroy(c->side); c->side = nullptr; }
     if (c->ev_ready) { cudaEventDestroy(c->ev_ready); c->ev_ready = nullptr; }
@@ -1036,7 +1166,14 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
         for (int i = 0; i < k; ++i) cap *= sd[i];
         TRY(dalloc(c, &c->slot[k].buf, (size_t)cap));
         c->slot[k].cap = (size_t)cap;
+        if (N >= 4 && k == N - 2) {  // look-ahead slot of the multi-sweep tree
+            TRY(dalloc(c, &c->alt[k].buf, (size_t)cap));
+            c->alt[k].cap = (size_t)cap;
+        }
     }
+    TRYC(cudaStreamCreateWithFlags(&c->ahead, cudaStreamNonBlocking));
+    TRYC(cudaEventCreateWithFlags(&c->ev_x, cudaEventDisableTiming));
+    TRYC(cudaEventCreateWithFlags(&c->ev_ahead, cudaEventDisableTiming));
     TRY(dalloc(c, &c->d_Slist, N));
     TRY(dalloc(c, &c->d_dSlist, N));
     TRYC(cudaMemcpyAsync(c->d_Slist, c->S, sizeof(double*) * N, cudaMemcpyHostToDevice, c->st));
@@ -1123,6 +1260,16 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
         for (int m = 0; m < N; ++m) need(c->tc_plan[m]);
         for (int a = 0; a + 1 < N; ++a) need(c->kr_plan[a]);
         if (ws) TRY(dalloc(c, &c->splitk_ws, ws));
+        // first-child pieces of the multi-sweep roots T x_0 and T x_{N-1}
+        if (N >= 3) {
+            size_t cw = 0;
+            const int roots[2][2] = {{0, N - 1}, {N - 1, N - 2}};
+            for (const auto& rc : roots)
+                if (c->tc_plan[rc[0]] && cpk::ttm_tc_child_ok(c->tc_plan[rc[0]], (int)dims[rc[1]]))
+                    cw = std::max(cw, (size_t)cpk::ttm_tc_child_ws_floats(c->tc_plan[rc[0]], (int)dims[rc[1]]));
+            if (cw) TRY(dalloc(c, &c->child_ws, cw));
+            c->child_ws_cap = cw;
+        }
     }
     // ||T||_F^2
     int nb = cpk::norm2_partials(c->T, numel, c->red_part, 4096, c->st);
@@ -1173,12 +1320,32 @@ static cp_status sweeps_exact(cp_ctx* c, int nsweeps, bool msdt) {
     std::vector<int> kinds(nsweeps, msdt ? 1 : 0);
     CKCUDA(c, cudaEventRecord(c->events[0], c->st));
     for (int k = 0; k < nsweeps; ++k) {
-        CKST(exact_sweep(c, msdt, k));
+        CKST(exact_sweep(c, msdt, k, msdt && k + 1 < nsweeps));
         CKCUDA(c, cudaEventRecord(c->events[k + 1], c->st));
     }
     CKST(harvest(c, nsweeps, kinds.data(), nullptr, 0));
     // regular sweeps: dA(i) = this sweep's change (Alg. 2 line 14)
     return CP_OK;
+}
+
+cp_status cp_set_option(cp_ctx* c, int option, int value) {
+    CKST(entry_check(c));
+    switch (option) {
+        case CP_OPT_FUSE_DT:
+            if (value != 0 && value != 1) return CP_EINVAL;
+            c->fuse_dt = value != 0;
+            return CP_OK;
+        case CP_OPT_LOOKAHEAD:
+            if (value < 0 || value > 8) return CP_EINVAL;
+            c->lookahead = value != 0;
+            if (value) c->ahead_blocks_per_sm = value;
+            return CP_OK;
+        case CP_OPT_FUSE_CHILD:
+            if (value != 0 && value != 1) return CP_EINVAL;
+            c->fuse_child = value != 0;
+            return CP_OK;
+        default: return CP_EINVAL;
+    }
 }
 
 cp_status cp_sweep_dt(cp_ctx* c, int nsweeps) { return sweeps_exact(c, nsweeps, false); }

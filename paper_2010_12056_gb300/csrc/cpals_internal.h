@@ -53,8 +53,19 @@ void ttm_tc_plan_free(TcPlan* p);
 // splitk_ws: NULL, or a workspace of ttm_tc_splitk() * rows * R floats that lets
 // the kernel split K across CTAs when the row tiles alone cannot fill the GPU
 // (partial sums are then added in a fixed order by a second kernel).
+// child: NULL, or the first child of a multi-sweep root formed in the epilogue:
+//   Y[y][r] = sum_{j < sc} X[y sc + j][r] Ac[j][r]   (X's innermost kept mode, size sc)
+// Needs ttm_tc_child_ok(); ws holds ttm_tc_child_ws_floats() floats (NULL if 0).
+struct TcChild {
+    float* Y;
+    const float* Ac;   // FP32 factor of the contracted mode, sc x R row-major
+    int sc;
+    float* ws;
+};
+bool ttm_tc_child_ok(const TcPlan* p, int sc);
+int64_t ttm_tc_child_ws_floats(const TcPlan* p, int sc);
 cudaError_t ttm_tc_run(const TcPlan* p, float* X, int prec, int num_sms, unsigned* dev_err,
-                       cudaStream_t st, float* splitk_ws);
+                       cudaStream_t st, float* splitk_ws, const TcChild* child = nullptr);
 int ttm_tc_splitk(const TcPlan* p, int num_sms);
 int64_t ttm_tc_rows(const TcPlan* p);
 // Khatri-Rao operand of two adjacent modes a, a+1 for a fused two-mode contraction:
@@ -64,8 +75,10 @@ cudaError_t kr_operand(const double* Aa, const double* Ab, int sa, int sb, int R
                        int kind, void* hi, void* lo, cudaStream_t st);
 
 // multi-TTV: Y[p][q][r] = sum_k X[p][k][q][r] * A[k][r]
+// max_blocks_per_sm > 0 caps the grid (blocks loop over the outputs) so that the
+// whole launch is resident at once and leaves room for kernels of other streams.
 cudaError_t mttv(const float* X, const float* A, float* Y, int64_t P, int K, int64_t Q, int R,
-                 int num_sms, cudaStream_t st);
+                 int num_sms, cudaStream_t st, int max_blocks_per_sm = 0);
 
 // PP first-order corrections for one mode n (Eq. U_ni):
 //   Mt[x][r] = Mp[x][r] + sum_i sum_y Op_i(x, y, r) dA_i[y][r]

@@ -13,7 +13,9 @@ namespace {
 // float4 outputs each thread keeps U loads of X in flight: the kernel is bound by
 // how many bytes the SMs have outstanding (measured on 128^4 R = 64 roots: 4 in
 // flight gave 3.2-3.6 TB/s, 16 in flight with a 4-way k-split 5.4-5.5 TB/s).
-template <int VEC, int U>
+// STRIDE: blocks loop over the chunks of TX outputs (a capped grid); else one
+// chunk per block.
+template <int VEC, int U, bool STRIDE>
 __global__ void __launch_bounds__(256) k_mttv(const float* __restrict__ X,
                                               const float* __restrict__ A,
                                               float* __restrict__ Y, int64_t P, int K, int64_t Q,
@@ -22,51 +24,57 @@ __global__ void __launch_bounds__(256) k_mttv(const float* __restrict__ X,
     const int RV = R / VEC;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int64_t nout = P * Q * RV;
-    const int64_t o = (int64_t)blockIdx.x * TX + tx;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (o < nout) {
-        const int64_t pq = o / RV;
-        const int rv = (int)(o - pq * RV);
-        const int64_t p = pq / Q, q = pq - p * Q;
-        const int64_t strideK = Q * R;
-        const float* xp = X + (p * K) * strideK + q * R + rv * VEC;
-        const float* ap = A + rv * VEC;
-        int k = ty;
-        if (VEC == 4) {
-            for (; k + (U - 1) * KS < K; k += U * KS) {
-                float4 x[U], a[U];
+    const int64_t nchunks = (nout + TX - 1) / TX;
+    // grid-stride over chunks of TX outputs: a launch may use fewer blocks than
+    // chunks to leave room on every SM for concurrent kernels
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += (STRIDE ? gridDim.x : nchunks)) {
+        const int64_t o = ch * TX + tx;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (o < nout) {
+            const int64_t pq = o / RV;
+            const int rv = (int)(o - pq * RV);
+            const int64_t p = pq / Q, q = pq - p * Q;
+            const int64_t strideK = Q * R;
+            const float* xp = X + (p * K) * strideK + q * R + rv * VEC;
+            const float* ap = A + rv * VEC;
+            int k = ty;
+            if (VEC == 4) {
+                for (; k + (U - 1) * KS < K; k += U * KS) {
+                    float4 x[U], a[U];
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    x[u] = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)(k + u * KS) * strideK));
-                    a[u] = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)(k + u * KS) * R));
-                }
+                    for (int u = 0; u < U; ++u) {
+                        x[u] = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)(k + u * KS) * strideK));
+                        a[u] = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)(k + u * KS) * R));
+                    }
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    acc.x = fmaf(x[u].x, a[u].x, acc.x); acc.y = fmaf(x[u].y, a[u].y, acc.y);
-                    acc.z = fmaf(x[u].z, a[u].z, acc.z); acc.w = fmaf(x[u].w, a[u].w, acc.w);
+                    for (int u = 0; u < U; ++u) {
+                        acc.x = fmaf(x[u].x, a[u].x, acc.x); acc.y = fmaf(x[u].y, a[u].y, acc.y);
+                        acc.z = fmaf(x[u].z, a[u].z, acc.z); acc.w = fmaf(x[u].w, a[u].w, acc.w);
+                    }
                 }
+                for (; k < K; k += KS) {
+                    float4 x0 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)k * strideK));
+                    float4 a0 = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)k * R));
+                    acc.x = fmaf(x0.x, a0.x, acc.x); acc.y = fmaf(x0.y, a0.y, acc.y);
+                    acc.z = fmaf(x0.z, a0.z, acc.z); acc.w = fmaf(x0.w, a0.w, acc.w);
+                }
+            } else {
+                for (; k < K; k += KS) acc.x = fmaf(__ldg(xp + (int64_t)k * strideK), __ldg(ap + (int64_t)k * R), acc.x);
             }
-            for (; k < K; k += KS) {
-                float4 x0 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)k * strideK));
-                float4 a0 = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)k * R));
-                acc.x = fmaf(x0.x, a0.x, acc.x); acc.y = fmaf(x0.y, a0.y, acc.y);
-                acc.z = fmaf(x0.z, a0.z, acc.z); acc.w = fmaf(x0.w, a0.w, acc.w);
+        }
+        red[ty * TX + tx] = acc;
+        __syncthreads();
+        if (ty == 0 && o < nout) {
+            for (int j = 1; j < KS; ++j) {
+                float4 v = red[j * TX + tx];
+                acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
             }
-        } else {
-            for (; k < K; k += KS) acc.x = fmaf(__ldg(xp + (int64_t)k * strideK), __ldg(ap + (int64_t)k * R), acc.x);
+            if (VEC == 4)
+                *reinterpret_cast<float4*>(Y + o * 4) = acc;
+            else
+                Y[o] = acc.x;
         }
-    }
-    red[ty * TX + tx] = acc;
-    __syncthreads();
-    if (ty == 0 && o < nout) {
-        for (int j = 1; j < KS; ++j) {
-            float4 v = red[j * TX + tx];
-            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
-        }
-        if (VEC == 4)
-            *reinterpret_cast<float4*>(Y + o * 4) = acc;
-        else
-            Y[o] = acc.x;
+        if (STRIDE) __syncthreads();  // red is rewritten by the next chunk
     }
 }
 
@@ -75,7 +83,7 @@ __global__ void __launch_bounds__(256) k_mttv(const float* __restrict__ X,
 namespace cpk {
 
 cudaError_t mttv(const float* X, const float* A, float* Y, int64_t P, int K, int64_t Q, int R,
-                 int num_sms, cudaStream_t st) {
+                 int num_sms, cudaStream_t st, int max_blocks_per_sm) {
     const bool v4 = (R % 4 == 0) && (((uintptr_t)X | (uintptr_t)A | (uintptr_t)Y) & 15) == 0;
     const int VEC = v4 ? 4 : 1;
     const int64_t nout = P * Q * (R / VEC);
@@ -86,12 +94,22 @@ cudaError_t mttv(const float* X, const float* A, float* Y, int64_t P, int K, int
     if (v4)
         while (KS < 8 && K / (2 * KS) >= 32) KS *= 2;
     int TX = 256 / KS;
-    unsigned nblk = (unsigned)((nout + TX - 1) / TX);
+    int64_t nchunks = (nout + TX - 1) / TX;
+    const bool stride = max_blocks_per_sm > 0 && nchunks > (int64_t)max_blocks_per_sm * num_sms;
+    if (stride) nchunks = (int64_t)max_blocks_per_sm * num_sms;
+    const unsigned nblk = (unsigned)nchunks;
     size_t smem = sizeof(float4) * 256;
-    if (v4)
-        k_mttv<4, 16><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
-    else
-        k_mttv<1, 1><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
+    if (v4) {
+        if (stride)
+            k_mttv<4, 16, true><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
+        else
+            k_mttv<4, 16, false><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
+    } else {
+        if (stride)
+            k_mttv<1, 1, true><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
+        else
+            k_mttv<1, 1, false><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
+    }
     return cudaGetLastError();
 }
 

@@ -24,7 +24,15 @@
 //               adds them with round-to-nearest.  Two sets of accumulators let
 //               the epilogue overlap the next tile.
 //   warps 8-11  epilogue: tcgen05.ld 32x32b -> registers -> a warp-private smem
-//               transpose -> full-sector coalesced stores of X.
+//               transpose -> full-sector coalesced stores of X.  Optionally (the
+//               multi-sweep tree's first child, Fig. 2) it also forms
+//                 Y[y][r] = sum_{j < sc} X[y sc + j][r] Ac[j][r]
+//               (X's innermost kept mode contracted) from the accumulators.
+//               sc a multiple of 32: each warp's 32 rows lie in one segment; the
+//               warp writes its column sums and a second kernel adds the sc / 32
+//               pieces of each segment in order.  Other sc: segmented warp sums,
+//               boundary pieces combined per tile by warp 8, pieces of segments
+//               that cross tiles added by a second kernel in a fixed order.
 // Every mbarrier wait is bounded; on expiry the CTA sets DEVERR_TIMEOUT, drains
 // what it issued (bounded), frees TMEM and exits.
 #include <cuda.h>
@@ -39,7 +47,9 @@ constexpr int NTHREADS = 384;
 constexpr int OPA_BYTES = BM * 128;        // one split part of a 128-row chunk: 16 KB
 constexpr int EPI_STRIDE = 20;             // floats per row of the epilogue transpose buffer
 constexpr int EPI_BYTES = 4 * 32 * EPI_STRIDE * 4;
-constexpr int BAR_BYTES = 256;
+constexpr int BAR_BYTES = 512;
+// first-child pieces: [2 tiles in flight][4 warps][2 pieces][128 columns] floats + keys
+constexpr int CHILD_BYTES = 2 * 4 * 2 * 128 * 4 + 2 * 4 * 2 * 8;
 constexpr int MAX_STG = 8, MAX_OP = 4;
 constexpr long long WAIT_LIMIT = 2000000000LL;  // cycles (about 1 s)
 constexpr size_t SMEM_LIMIT = 232448;
@@ -63,6 +73,14 @@ struct TcArgs {
     int set_cols;          // TMEM columns of one accumulator set
     uint32_t idesc;
     unsigned* dev_err;
+    // first child (NULL Yc: off): Yc[(g / sc)][r] += X[g][r] Ac[g % sc][r].  Pieces:
+    // sc % 32 == 0 (sc > 32): cws[(g0 / 32) * R + r] per warp of rows g0..g0+31;
+    // else segments that cross a tile: cws[(tile * 2 + piece) * R + r]
+    float* Yc;
+    const float* Ac;
+    float* cws;
+    int sc;
+    int ac_bytes;   // > 0: Ac (sc x R floats) is copied to shared memory once per CTA
 };
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -207,11 +225,12 @@ struct Layout {
 };
 
 __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, int nk, int b_resident,
-                                               int BK) {
+                                               int BK, bool child = false, int ac_bytes = 0) {
     const size_t stg = (size_t)BM * BK * 4;
     const size_t bchunk = 2 * (size_t)Rpad * 128;
     const size_t nb = b_resident ? (size_t)nk : (size_t)S_op;
-    return 1024 + (size_t)S_stg * stg + (size_t)S_op * 2 * OPA_BYTES + nb * bchunk + EPI_BYTES + BAR_BYTES;
+    return 1024 + (size_t)S_stg * stg + (size_t)S_op * 2 * OPA_BYTES + nb * bchunk + EPI_BYTES +
+           (child ? CHILD_BYTES + (size_t)ac_bytes : 0) + BAR_BYTES;
 }
 
 // ------------------------------------------------------------------ kernel
@@ -219,7 +238,10 @@ __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, in
 // MODE 1: other modes, T[p][k][q] with Q % 4 == 0 (3-D map {Q, K, P}, box {128, BK, 1}; the
 //         last q-tile of each p is zero-filled past Q by the TMA unit and written up to Q)
 // KIND 0: bf16 parts, BK = 64, kind::f16;  KIND 1: tf32 parts, BK = 32, kind::tf32
-template <int MODE, int KIND>
+// CHILD: 0 plain; 1 the epilogue also forms the first child (a.Yc) for sc a
+// multiple of 32; 2 for other sc.  Separate instantiations keep each kernel's
+// code, registers and shared memory to what it runs.
+template <int MODE, int KIND, int CHILD>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_ttm_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmBhi,
              const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmBhi1,
@@ -236,7 +258,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t op0 = stg0 + (uint32_t)S_stg * STG;
     const uint32_t b0 = op0 + (uint32_t)S_op * 2u * OPA_BYTES;
     const uint32_t epi0 = b0 + (uint32_t)(a.b_resident ? a.nk : S_op) * bchunk;
-    const uint32_t bar0 = epi0 + EPI_BYTES;
+    const uint32_t child0 = epi0 + EPI_BYTES;
+    const uint32_t ac0 = child0 + (CHILD ? CHILD_BYTES : 0);
+    const uint32_t bar0 = ac0 + (CHILD ? (uint32_t)a.ac_bytes : 0u);
     auto stg_full = [&](int s) { return bar0 + 8u * s; };
     auto stg_empty = [&](int s) { return bar0 + 8u * (MAX_STG + s); };
     auto op_full = [&](int j) { return bar0 + 8u * (2 * MAX_STG + j); };
@@ -247,6 +271,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t drain_bar = bar0 + 8u * (2 * MAX_STG + 2 * MAX_OP + 5);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + (bar0 - base) + 8 * 30);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bar0 - base) + 8 * 31);
+    auto epi_bar = [&](int b) { return bar0 + 8u * (32 + b); };  // first child: the 4 epilogue warps
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -264,6 +289,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         mbar_init(b_full, 1);
         mbar_init(drain_bar, 1);
+        mbar_init(epi_bar(0), 128);
+        mbar_init(epi_bar(1), 128);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
@@ -274,6 +301,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                      "r"(a.tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (CHILD && a.ac_bytes > 0) {
+        // the contracted factor, read by the epilogue for every tile
+        float* sAc = reinterpret_cast<float*>(gbase + (ac0 - base));
+        const int n = a.sc * a.R;
+        for (int i = threadIdx.x; i < n; i += NTHREADS) sAc[i] = __ldg(a.Ac + i);
     }
     tc_fence_before();
     __syncthreads();
@@ -464,6 +497,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------ epilogue (thread = TMEM lane = row)
         const int quad = warp & 3;
         float* tb = reinterpret_cast<float*>(gbase + (epi0 - base)) + quad * 32 * EPI_STRIDE;
+        // first-child pieces and their segment keys (-1: none), double-buffered by tile
+        float* cpart = reinterpret_cast<float*>(gbase + (child0 - base));           // [2][4][2][128]
+        long long* ckey = reinterpret_cast<long long*>(gbase + (child0 - base) + 2 * 4 * 2 * 128 * 4);
+        const int sc = CHILD ? a.sc : 1;
+        // sc a multiple of 32: every warp's 32 rows lie in one segment (tiles and
+        // warps start at multiples of 32), so a warp's share is a plain column sum
+        constexpr bool aligned = CHILD == 1;
+        const int qq = lane & 3, rr = lane >> 2;  // transposed layout: rows rr + 8i, columns 4qq..4qq+3
+        const bool avec = CHILD && (a.R % 4 == 0);
         int lt = 0;
         bool ok = true;
         const int64_t nwork = a.ntiles * a.nsk * a.npass;
@@ -486,6 +528,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 g0 = p * a.Q + qb + quad * 32;
                 gend = p * a.Q + a.Q;  // the last tile of a p is ragged when BM does not divide Q
             }
+            // first child: rows of the transposed layout and their factor rows
+            int jt[4] = {0, 0, 0, 0};
+            long long key = -1;           // general path: this lane's row segment
+            bool head = false, head_complete = false;
+            int piece = 0;
+            int64_t glast = g0;
+            if (CHILD) {
+                if (aligned) {
+                    // g0 % 32 == 0 and sc % 32 == 0: the warp's rows are consecutive in one segment
+                    const int j0 = (int)(g0 % sc);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) jt[i] = j0 + rr + 8 * i;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) jt[i] = (int)((g0 + rr + 8 * i) % sc);
+                }
+                glast = (gend - 1 < g0 + 31) ? gend - 1 : g0 + 31;
+                if (!aligned) {
+                    const int64_t gme = g0 + lane;
+                    const bool vme = gme < gend;
+                    key = vme ? (long long)(gme / sc) : -1ll;
+                    const long long kprev = __shfl_up_sync(0xffffffffu, key, 1);
+                    head = vme && (lane == 0 || kprev != key);
+                    if (head) {
+                        const int64_t S = (int64_t)key * sc, E = S + sc - 1;
+                        head_complete = S >= g0 && E <= glast;
+                        piece = lane == 0 ? 0 : 1;
+                    }
+                }
+            }
+            float* cpart = reinterpret_cast<float*>(gbase + (child0 - base));           // [2][4][2][128]
+            long long* ckey = reinterpret_cast<long long*>(gbase + (child0 - base) + 2 * 4 * 2 * 128 * 4);
+            float* mypart = cpart + (((lt & 1) * 4 + quad) * 2 + piece) * 128;
             const uint32_t taddr =
                 tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * a.set_cols);
             for (int c0 = 0; c0 < Rpw; c0 += 16) {
@@ -504,11 +579,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                 __syncwarp();
                 // lanes 4i..4i+3 write the 64 bytes of row i (+8, +16, +24): full sectors
-                const int q = lane & 3;
+                const int q = qq;
                 const int col = c0 + 4 * q;
+                float4 csum = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const int r = (lane >> 2) + 8 * i;
+                    const int r = rr + 8 * i;
                     const int64_t g = g0 + r;
                     if (g < gend && col < Rw) {
                         const float4 w = *reinterpret_cast<const float4*>(tb + r * EPI_STRIDE + 4 * q);
@@ -521,12 +597,151 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             if (col + 2 < Rw) dst[2] = w.z;
                             if (col + 3 < Rw) dst[3] = w.w;
                         }
+                        if (CHILD) {
+                            // weight by the contracted factor's row (coalesced: 4 lanes
+                            // read one 64-byte piece of it)
+                            const int64_t ao = (int64_t)jt[i] * a.R + col;
+                            float4 f;
+                            if (a.ac_bytes > 0) {
+                                const float* ap = reinterpret_cast<const float*>(gbase + (ac0 - base)) + ao;
+                                if (avec) {
+                                    f = *reinterpret_cast<const float4*>(ap);
+                                } else {
+                                    f.x = ap[0];
+                                    f.y = col + 1 < Rw ? ap[1] : 0.f;
+                                    f.z = col + 2 < Rw ? ap[2] : 0.f;
+                                    f.w = col + 3 < Rw ? ap[3] : 0.f;
+                                }
+                            } else {
+                                const float* ap = a.Ac + ao;
+                                if (avec) {
+                                    f = __ldg(reinterpret_cast<const float4*>(ap));
+                                } else {
+                                    f.x = __ldg(ap);
+                                    f.y = col + 1 < Rw ? __ldg(ap + 1) : 0.f;
+                                    f.z = col + 2 < Rw ? __ldg(ap + 2) : 0.f;
+                                    f.w = col + 3 < Rw ? __ldg(ap + 3) : 0.f;
+                                }
+                            }
+                            if (aligned) {
+                                csum.x = fmaf(w.x, f.x, csum.x); csum.y = fmaf(w.y, f.y, csum.y);
+                                csum.z = fmaf(w.z, f.z, csum.z); csum.w = fmaf(w.w, f.w, csum.w);
+                            } else {
+                                *reinterpret_cast<float4*>(tb + r * EPI_STRIDE + 4 * q) =
+                                    make_float4(w.x * f.x, w.y * f.y, w.z * f.z, w.w * f.w);
+                            }
+                        }
+                    } else if (CHILD && !aligned) {
+                        *reinterpret_cast<float4*>(tb + r * EPI_STRIDE + 4 * q) = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
                 __syncwarp();
+                if (CHILD && aligned) {
+                    // the 8 lanes of each column quad hold 4 rows each: add them up
+#pragma unroll
+                    for (int off = 4; off < 32; off <<= 1) {
+                        csum.x += __shfl_xor_sync(0xffffffffu, csum.x, off);
+                        csum.y += __shfl_xor_sync(0xffffffffu, csum.y, off);
+                        csum.z += __shfl_xor_sync(0xffffffffu, csum.z, off);
+                        csum.w += __shfl_xor_sync(0xffffffffu, csum.w, off);
+                    }
+                    if (rr == 0 && g0 < gend && col < Rw) {
+                        // sc == 32: the warp is the whole segment; else its piece
+                        float* dst = (sc == 32 ? a.Yc : a.cws) + (g0 >> 5) * (int64_t)a.ldx + col;
+                        if (((Rw | a.ldx) & 3) == 0) {
+                            *reinterpret_cast<float4*>(dst) = csum;
+                        } else {
+                            dst[0] = csum.x;
+                            if (col + 1 < Rw) dst[1] = csum.y;
+                            if (col + 2 < Rw) dst[2] = csum.z;
+                            if (col + 3 < Rw) dst[3] = csum.w;
+                        }
+                    }
+                } else if (CHILD) {
+                    // general segments: this lane's row of weighted values back from
+                    // the buffer, then segmented suffix sums over the lanes; the first
+                    // lane of every segment ends with the warp's part of it
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const float4 t4 = *reinterpret_cast<const float4*>(tb + lane * EPI_STRIDE + 4 * q4);
+                        v[4 * q4] = t4.x; v[4 * q4 + 1] = t4.y; v[4 * q4 + 2] = t4.z; v[4 * q4 + 3] = t4.w;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const long long kp = __shfl_down_sync(0xffffffffu, key, off);
+                        const bool take = lane + off < 32 && kp == key;
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float t = __shfl_down_sync(0xffffffffu, v[i], off);
+                            if (take) v[i] += t;
+                        }
+                    }
+                    if (head) {
+                        if (head_complete) {
+                            float* yrow = a.Yc + (int64_t)key * a.ldx + c0;
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                if (c0 + i < Rw) yrow[i] = v[i];
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) mypart[c0 + i] = v[i];
+                        }
+                    }
+                }
             }
             tc_fence_before();
             mbar_arrive(acc_empty(buf));
+            if (CHILD && !aligned) {
+                // keys of this warp's two boundary pieces: 0 = the segment of its first
+                // row, 1 = a later segment that runs past its last row
+                if (lane == 0) {
+                    long long k0 = -1, k1 = -1;
+                    if (g0 < gend) {
+                        const int64_t a0 = g0 / sc;
+                        if (!(a0 * sc >= g0 && a0 * sc + sc - 1 <= glast)) k0 = a0;
+                        const int64_t al = glast / sc;
+                        if (al * sc > g0 && al * sc + sc - 1 > glast) k1 = al;
+                    }
+                    ckey[((lt & 1) * 4 + quad) * 2 + 0] = k0;
+                    ckey[((lt & 1) * 4 + quad) * 2 + 1] = k1;
+                }
+                __syncwarp();
+                mbar_arrive(epi_bar(lt & 1));
+                if (!(ok = mbar_wait(epi_bar(lt & 1), (uint32_t)((lt >> 1) & 1), abort_flag))) break;
+                if (quad == 0) {
+                    // warp 8 adds the pieces of each segment in row order; a segment
+                    // inside the tile is final, one that crosses the tile's first row
+                    // (piece 0) or last row (piece 1) waits for the cross-tile sum
+                    const int64_t t0 = g0;
+                    const int64_t tl = (gend - 1 < t0 + 127) ? gend - 1 : t0 + 127;
+                    const float* pb = cpart + (lt & 1) * 4 * 2 * 128;
+                    const long long* kb = ckey + (lt & 1) * 4 * 2;
+                    for (int col = lane; col < Rw; col += 32) {
+                        long long ck = -1;
+                        float acc = 0.f;
+                        for (int e = 0; e <= 8; ++e) {
+                            const long long k = e < 8 ? kb[e] : -2ll;
+                            if (e < 8 && k < 0) continue;
+                            if (e < 8 && k == ck) {
+                                acc += pb[e * 128 + col];
+                                continue;
+                            }
+                            if (ck >= 0) {
+                                const int64_t S = (int64_t)ck * sc, E = S + sc - 1;
+                                if (S >= t0 && E <= tl)
+                                    a.Yc[(int64_t)ck * a.ldx + col] = acc;
+                                else
+                                    a.cws[(tile * 2 + (S <= t0 ? 0 : 1)) * (int64_t)a.ldx + col] = acc;
+                            }
+                            if (e < 8) {
+                                ck = k;
+                                acc = pb[e * 128 + col];
+                            }
+                        }
+                    }
+                }
+            }
         }
     }
     tc_fence_before();
@@ -692,12 +907,12 @@ int ttm_tc_splitk(const TcPlan* pl, int num_sms) {
 
 int64_t ttm_tc_rows(const TcPlan* pl) { return pl->PQ; }
 
-template <int MODE, int KIND>
+template <int MODE, int KIND, int CHILD>
 static cudaError_t launch(const TcPlan* pl, const TcPass& p1, const TcArgs& a, size_t smem, unsigned grid,
                           cudaStream_t st) {
-    cudaFuncSetAttribute(k_ttm_tc<MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ttm_tc<MODE, KIND><<<grid, NTHREADS, smem, st>>>(pl->tmT, pl->pass[0].tmBhi, pl->pass[0].tmBlo, p1.tmBhi,
-                                                       p1.tmBlo, a);
+    cudaFuncSetAttribute(k_ttm_tc<MODE, KIND, CHILD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ttm_tc<MODE, KIND, CHILD><<<grid, NTHREADS, smem, st>>>(pl->tmT, pl->pass[0].tmBhi, pl->pass[0].tmBlo,
+                                                              p1.tmBhi, p1.tmBlo, a);
     return cudaGetLastError();
 }
 
@@ -722,9 +937,60 @@ __global__ void k_splitk_sum(const float* __restrict__ ws, int nsk, int64_t n, f
 }
 }  // namespace
 
+bool ttm_tc_child_ok(const TcPlan* pl, int sc) {
+    // one column pass, rows = one run of X's row index (last mode, or first mode
+    // with nothing before it), and the contracted mode innermost in that index
+    if (!pl || pl->npass != 1 || sc < 1) return false;
+    if (!(pl->mode == 0 || pl->P == 1)) return false;
+    return pl->PQ % sc == 0;
+}
+
+int64_t ttm_tc_child_ws_floats(const TcPlan* pl, int sc) {
+    if (!ttm_tc_child_ok(pl, sc)) return 0;
+    if (sc % 32 == 0) return sc == 32 ? 0 : (pl->PQ / 32) * (int64_t)pl->R;  // one piece per warp
+    if (BM % sc == 0) return 0;  // no segment crosses a tile
+    return plan_tiles(pl) * 2 * (int64_t)pl->R;
+}
+
+namespace {
+// sc % 32 == 0: Y[y] = sum of the sc / 32 warp pieces of segment y, in row order.
+__global__ void k_child_warpsum(const float* __restrict__ ws, float* __restrict__ Y, int64_t nseg, int nw, int R) {
+    const int64_t n = nseg * R;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t y = i / R;
+        const int col = (int)(i - y * R);
+        const float* p = ws + (y * nw) * R + col;
+        float acc = p[0];
+        for (int k = 1; k < nw; ++k) acc += p[(int64_t)k * R];
+        Y[i] = acc;
+    }
+}
+// Segments of the first child that cross tiles: piece 0 of every tile they cover
+// (piece 1 of the tile where they start, unless they start on its first row),
+// added in tile order.
+__global__ void k_child_cross(const float* __restrict__ ws, float* __restrict__ Y, int64_t nseg, int sc, int R) {
+    const int64_t n = nseg * R;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t y = i / R;
+        const int col = (int)(i - y * R);
+        const int64_t S = y * sc, E = S + sc - 1;
+        const int64_t tf = S / BM, tl = E / BM;
+        if (tf == tl) continue;
+        float acc = ws[(tf * 2 + (S == tf * BM ? 0 : 1)) * R + col];
+        for (int64_t t = tf + 1; t <= tl; ++t) acc += ws[(t * 2) * R + col];
+        Y[y * R + col] = acc;
+    }
+}
+}  // namespace
+
 cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsigned* dev_err,
-                       cudaStream_t st, float* splitk_ws) {
+                       cudaStream_t st, float* splitk_ws, const TcChild* child) {
     if (!pl) return cudaErrorInvalidValue;
+    if (child) {
+        if (!ttm_tc_child_ok(pl, child->sc) || !child->Y || !child->Ac) return cudaErrorInvalidValue;
+        if (ttm_tc_child_ws_floats(pl, child->sc) > 0 && !child->ws) return cudaErrorInvalidValue;
+        splitk_ws = nullptr;  // the epilogue needs complete sums
+    }
     const bool bf = (prec == CP_BF16X3 || prec == CP_BF16);
     const bool tf = (prec == CP_TF32X3 || prec == CP_TF32);
     if ((pl->kind == 0 && !bf) || (pl->kind == 1 && !tf)) return cudaErrorInvalidValue;
@@ -742,7 +1008,29 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     a.R = p0.R;
     a.Rpad = p0.Rpad;
     a.nk = pl->nk;
-    a.S_stg = p0.S_stg;
+    // the first child's buffers, and its factor in shared memory when that fits
+    // with at least two staging stages (else the epilogue reads it from L2), may
+    // cost staging stages
+    int S_stg = p0.S_stg;
+    int ac_bytes = 0;
+    if (child) {
+        auto fit = [&](int acb) {
+            int st2 = p0.S_stg;
+            while (st2 > 2 && layout_bytes(st2, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, true, acb) > SMEM_LIMIT)
+                --st2;
+            return layout_bytes(st2, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, true, acb) <= SMEM_LIMIT ? st2 : 0;
+        };
+        const int acb = (child->sc * pl->R * 4 + 15) / 16 * 16;
+        if (int st2 = fit(acb)) {
+            S_stg = st2;
+            ac_bytes = acb;
+        } else if (int st3 = fit(0)) {
+            S_stg = st3;
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+    a.S_stg = S_stg;
     a.S_op = pl->S_op;
     a.b_resident = p0.b_resident;
     a.x3 = (prec == CP_BF16X3 || prec == CP_TF32X3) ? 1 : 0;
@@ -772,17 +1060,42 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     a.dev_err = dev_err;
     a.nsk = nsk;
     a.slice = pl->PQ * (int64_t)pl->R;
-    const size_t smem = layout_bytes(p0.S_stg, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK);
+    a.Yc = child ? child->Y : nullptr;
+    a.Ac = child ? child->Ac : nullptr;
+    a.cws = child ? child->ws : nullptr;
+    a.sc = child ? child->sc : 1;
+    a.ac_bytes = ac_bytes;
+    const size_t smem = layout_bytes(S_stg, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, child != nullptr, ac_bytes);
     const int64_t nwork = a.ntiles * a.nsk * a.npass;
     const unsigned grid = (unsigned)(nwork < num_sms ? nwork : num_sms);
     if (grid == 0) return cudaSuccess;
     const TcPass& p1 = pl->pass[pl->npass > 1 ? 1 : 0];
     cudaError_t e;
-    if (pl->mode == 0)
-        e = pl->kind == 0 ? launch<0, 0>(pl, p1, a, smem, grid, st) : launch<0, 1>(pl, p1, a, smem, grid, st);
+    const int ck = child ? (child->sc % 32 == 0 ? 1 : 2) : 0;
+#define CP_TTM_LAUNCH(C)                                                                                  \
+    (pl->mode == 0 ? (pl->kind == 0 ? launch<0, 0, C>(pl, p1, a, smem, grid, st)                        \
+                                    : launch<0, 1, C>(pl, p1, a, smem, grid, st))                       \
+                   : (pl->kind == 0 ? launch<1, 0, C>(pl, p1, a, smem, grid, st)                        \
+                                    : launch<1, 1, C>(pl, p1, a, smem, grid, st)))
+    if (ck == 1)
+        e = CP_TTM_LAUNCH(1);
+    else if (ck == 2)
+        e = CP_TTM_LAUNCH(2);
     else
-        e = pl->kind == 0 ? launch<1, 0>(pl, p1, a, smem, grid, st) : launch<1, 1>(pl, p1, a, smem, grid, st);
-    if (e != cudaSuccess || nsk == 1) return e;
+        e = CP_TTM_LAUNCH(0);
+#undef CP_TTM_LAUNCH
+    if (e != cudaSuccess) return e;
+    if (child && ttm_tc_child_ws_floats(pl, child->sc) > 0) {
+        const int64_t nseg = pl->PQ / child->sc;
+        int64_t blocks = (nseg * pl->R + 255) / 256;
+        if (blocks > 4 * num_sms) blocks = 4 * num_sms;
+        if (child->sc % 32 == 0)
+            k_child_warpsum<<<(unsigned)blocks, 256, 0, st>>>(child->ws, child->Y, nseg, child->sc / 32, pl->R);
+        else
+            k_child_cross<<<(unsigned)blocks, 256, 0, st>>>(child->ws, child->Y, nseg, child->sc, pl->R);
+        return cudaGetLastError();
+    }
+    if (nsk == 1) return cudaSuccess;
     const int64_t n = pl->PQ * (int64_t)pl->R;
     int64_t blocks = (n / 4 + 255) / 256;
     if (blocks > 4 * num_sms) blocks = 4 * num_sms;

@@ -53,6 +53,7 @@ def test_invalid_arguments_rejected_before_device_use(lib):
     assert lib.cp_init(ctypes.byref(h), 3, dims, 3, fake, 0, None, ctypes.byref(cfg), None) == 1
     # NULL contexts
     assert lib.cp_sweep_dt(None, 1) == 1
+    assert lib.cp_set_option(None, 2, 1) == 1
     assert lib.cp_fit(None, 0, None, None) == 1
     lib.cp_free(None)
     assert lib.cp_last_error(None) == b"null context"

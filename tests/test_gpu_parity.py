@@ -303,3 +303,67 @@ def test_run_stops_like_alg1(pkg, route):
     with pytest.raises(pkg.CPError):
         bad = pkg.CPContext(Td, 6, A0=A0, prec="fp32")   # neither delta nor a cap
         bad.run("msdt")
+
+
+# Schedules of the multi-sweep tree with its execution options.  Shapes cover
+# first-child segments that divide the 128-row TTM tile (16, 128), that cross
+# tiles (22..36), that span several tiles (256), and N = 3, 4, 5.
+SCHED_SHAPES = [((24, 20, 36, 28), 8), ((40, 32, 256, 16), 16), ((16, 16, 128, 128), 16),
+                ((64, 48, 40), 16), ((8, 6, 7, 8, 12), 4)]
+
+
+@pytest.mark.parametrize("dims,R", SCHED_SHAPES)
+def test_msdt_schedule_options(pkg, dims, R):
+    """Look-ahead and the fused first child reorder work on the nodes of Fig. 2 and
+    change no node: look-ahead leaves every bit unchanged (same kernel, same
+    arithmetic per output); the first child formed in the TTM epilogue sums the
+    same products in another order (FP32 rounding), and every variant follows the
+    oracle's MSDT trajectory to the bf16x3 fit tolerance."""
+    N = len(dims)
+    Td, Tref, A0 = problem(dims, R, 37, eta=0.05)
+    nsw = 2 * (N - 1)
+    runs = {}
+    for la in (False, True):
+        for fc in (False, True):
+            ctx = pkg.CPContext(Td, R, A0=A0, prec="bf16x3")
+            ctx.set_option("lookahead", la)
+            ctx.set_option("fuse_child", fc)
+            ctx.sweep_msdt(nsw)
+            runs[la, fc] = ([ctx.get_factor(n) for n in range(N)], ctx.stats(), ctx.fit(exact=True)[1])
+            ctx.close()
+    for fc in (False, True):
+        for n in range(N):
+            assert np.array_equal(runs[False, fc][0][n], runs[True, fc][0][n]), (fc, n)
+    for key, (_, st, _) in runs.items():
+        assert st["ttm"] == 2 * N                       # N roots per N-1 sweeps (Sec. III)
+        assert st["ttm_child"] == (4 if key[1] else 0)  # roots T x_0 and T x_{N-1}, twice each
+        # one level-2 node per subtree of N-1 updates is contracted ahead (N >= 4)
+        # (2 (N-1) sweeps of N updates = 2N subtrees)
+        assert st["lookahead"] == (2 * N if key[0] and N >= 4 else 0)
+    # the child's FP32 sums differ in order only (about 1e-7 relative); over 2(N-1)
+    # sweeps ALS amplifies that by the conditioning of Gamma (U[0,1) factors:
+    # kappa ~ 3R), measured about 1e-4 on these shapes
+    for n in range(N):
+        assert relerr(runs[True, True][0][n], runs[False, False][0][n]) <= 1e-3, n
+    ref = co.cp_als(Tref, A0, nsw, route="msdt")
+    r_ref = co.residual_direct(Tref, ref.A)
+    for key, (_, _, r) in runs.items():
+        assert abs(r - r_ref) <= FIT_TOL["bf16x3"], key
+
+
+def test_dt_unfused_follows_fig1a(pkg):
+    """CP_OPT_FUSE_DT off: each half starts from a first-level TTM and descends by
+    multi-TTVs (Fig. 1a literally); 2 first-level TTMs per sweep, none fused."""
+    dims, R = (24, 20, 36, 28), 8
+    Td, Tref, A0 = problem(dims, R, 38, eta=0.05)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec="bf16x3")
+    ctx.set_option("fuse_dt", False)
+    ctx.sweep_dt(3)
+    st = ctx.stats()
+    assert st["ttm"] == 6 and st["ttm_fused"] == 0 and st["ttm_child"] == 0
+    ref = co.cp_als(Tref, A0, 3, route="dt")
+    _, r = ctx.fit(exact=True)
+    assert abs(r - co.residual_direct(Tref, ref.A)) <= FIT_TOL["bf16x3"]
+    with pytest.raises(KeyError):
+        ctx.set_option("nonsense", True)
+    ctx.close()
