@@ -192,6 +192,41 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+// 2 loads of 16 columns behind one tcgen05.wait::ld (outputs are defined only
+// after the wait, so loads and wait are one asm statement)
+__device__ __forceinline__ void tmem_ld16x2(uint32_t t0, uint32_t t1, float* d0, float* d1) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(t0), "r"(t1)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) d0[i] = __uint_as_float(r[0 + i]);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) d1[i] = __uint_as_float(r[16 + i]);
+}
+// 3 loads of 16 columns behind one tcgen05.wait::ld (outputs are defined only
+// after the wait, so loads and wait are one asm statement)
+__device__ __forceinline__ void tmem_ld16x3(uint32_t t0, uint32_t t1, uint32_t t2, float* d0, float* d1, float* d2) {
+    uint32_t r[48];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%48];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%49];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%50];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+        : "r"(t0), "r"(t1), "r"(t2)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) d0[i] = __uint_as_float(r[0 + i]);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) d1[i] = __uint_as_float(r[16 + i]);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) d2[i] = __uint_as_float(r[32 + i]);
+}
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -565,11 +600,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * a.set_cols);
             for (int c0 = 0; c0 < Rpw; c0 += 16) {
                 float v[16];
-                // corrections first (last accumulator), then the hi*hi partial sums
-                tmem_ld16(taddr + (uint32_t)((a.nacc - 1) * a.Rpad + c0), v);
-                for (int ac = a.nacc - 2; ac >= 0; --ac) {
+                // corrections first (last accumulator), then the hi*hi partial sums;
+                // up to three accumulators per TMEM round trip
+                const uint32_t tcol = taddr + (uint32_t)c0;
+                const uint32_t rp = (uint32_t)a.Rpad;
+                int ac = a.nacc - 1;
+                if (ac >= 2) {
+                    float w1[16], w2[16];
+                    tmem_ld16x3(tcol + ac * rp, tcol + (ac - 1) * rp, tcol + (ac - 2) * rp, v, w1, w2);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += w1[i];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += w2[i];
+                    ac -= 3;
+                } else if (ac == 1) {
+                    float w1[16];
+                    tmem_ld16x2(tcol + rp, tcol, v, w1);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += w1[i];
+                    ac = -1;
+                } else {
+                    tmem_ld16(tcol, v);
+                    ac = -1;
+                }
+                for (; ac >= 0; --ac) {
                     float w[16];
-                    tmem_ld16(taddr + (uint32_t)(ac * a.Rpad + c0), w);
+                    tmem_ld16(tcol + ac * rp, w);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] += w[i];
                 }
