@@ -512,10 +512,10 @@ def main():
                         "peak_source": f"hbm_gbs of {peak_kind}"}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
     if args.workload == "c2" and args.prec == "bf16x3" and not (args.dims or args.rank or args.law):
-        # DRAM bytes per launch from the ncu capture of the same kernel on order-4 96^4
-        # (0.93 of its algorithmic bytes), scaled by this launch's algorithmic bytes
-        roofline["traffic"] = 0.932 * ttm_bytes
-        roofline["traffic_source"] = "ncu dram__bytes_read+write on 96^4 R=64 (0.932 x algorithmic), scaled"
+        # DRAM bytes per launch of this kernel on this workload, from one ncu capture
+        # (dram__bytes_read.sum 1.0738 GB + dram__bytes_write.sum 0.5035 GB)
+        roofline["traffic"] = 1.0738e9 + 0.5035e9
+        roofline["traffic_source"] = "ncu dram__bytes_read+write of k_ttm_tc on 128^4 R=64, one launch"
 
     roofline["ms_per_launch"] = ttm_ms
     roofline["algorithmic_bytes"] = ttm_bytes
