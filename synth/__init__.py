@@ -175,11 +175,24 @@ def make_problem_device(seed: int, dims, R: int, law: str = "uniform", eta: floa
     else:
         raise ValueError(law)
     Ft = [torch.from_numpy(f).to(device) for f in F]
-    rows = Ft[0]
-    for f in Ft[1:-1]:
-        rows = (rows[:, None, :] * f[None, :, :]).reshape(-1, R)
-    T = rows @ Ft[-1].T
-    del rows
+
+    def slab(first):
+        # rows of the Khatri-Rao product of modes 0..N-2 for the given mode-0 rows
+        rows = first
+        for f in Ft[1:-1]:
+            rows = (rows[:, None, :] * f[None, :, :]).reshape(-1, R)
+        return rows @ Ft[-1].T
+
+    inner = 1
+    for d in dims[1:-1]:
+        inner *= d
+    # slices of mode 0 keep the FP64 Khatri-Rao rows near 1 GB (uneven shapes
+    # with a small last mode would otherwise need many times the tensor's size)
+    step = max(1, int((1 << 27) // max(1, inner * R)))
+    if step >= dims[0]:
+        T = slab(Ft[0])
+    else:
+        T = torch.cat([slab(Ft[0][i:i + step]) for i in range(0, dims[0], step)])
     if eta > 0.0:
         g = torch.Generator(device=device)
         g.manual_seed(int(seed))

@@ -367,3 +367,41 @@ def test_dt_unfused_follows_fig1a(pkg):
     with pytest.raises(KeyError):
         ctx.set_option("nonsense", True)
     ctx.close()
+
+
+# Reduced shapes with the small modes of the application-tensor stand-ins of the
+# benchmark (Sec. V-A): a mode of 3 between large ones and a long last mode, a small
+# last mode (9: no tensor-core plan, the SIMT kernel runs), an order-3 shape with one
+# long mode.  A mode smaller than R makes the normal equations of the other modes
+# ill-conditioned: with 1e-6 relative noise in every MTTKRP the oracle's own residual
+# after 3 sweeps moves by up to 3.5e-6 on the first shape, so the fit bar here is
+# 1e-5 (FP32) and 1e-4 (bf16x3); the MTTKRP bar stays 1e-5.
+STANDIN_SHAPES = [((32, 32, 3, 480), 20), ((64, 84, 33, 9), 16), ((452, 28, 28), 32)]
+STANDIN_FIT_TOL = {"fp32": 1e-5, "bf16x3": 1e-4}
+
+
+@pytest.mark.parametrize("dims,R", STANDIN_SHAPES)
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_uneven_modes(pkg, dims, R, prec):
+    Td, Tref, A0 = problem(dims, R, 39, eta=1e-3)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    for n in range(len(dims)):
+        assert relerr(ctx.mttkrp(n).cpu().numpy(), co.mttkrp(Tref, A0, n)) <= 1e-5, n
+    ctx.close()
+    for route in ("dt", "msdt"):
+        ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+        (ctx.sweep_dt if route == "dt" else ctx.sweep_msdt)(3)
+        ref = co.cp_als(Tref, A0, 3, route=route)
+        _, r = ctx.fit(exact=True)
+        assert abs(r - co.residual_direct(Tref, ref.A)) <= STANDIN_FIT_TOL[prec], route
+        ctx.close()
+
+
+@pytest.mark.parametrize("dims,R", STANDIN_SHAPES)
+def test_uneven_modes_pp_mttkrp(pkg, dims, R):
+    """Approximated MTTKRP (Eq. ppupdate) with pair operators of very uneven sizes."""
+    ctx, Tref, A, pairs, Mp, dA, S = _pp_case(pkg, dims, R, 51, 0.05)
+    for n in range(len(dims)):
+        got = ctx.pp_mttkrp(n).cpu().numpy()
+        assert relerr(got, co.pp_mttkrp(pairs, Mp, A, dA, S, n)) <= 1e-5, n
+    ctx.close()
