@@ -377,6 +377,20 @@ struct PPArgs {
     int nterms;
 };
 
+// VEC consecutive floats (4, 2 or 1) as the low lanes of a float4
+template <int VEC>
+__device__ __forceinline__ float4 ldv_pp(const float* p) {
+    if (VEC == 4) return __ldg(reinterpret_cast<const float4*>(p));
+    if (VEC == 2) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        return make_float4(v.x, v.y, 0.f, 0.f);
+    }
+    return make_float4(__ldg(p), 0.f, 0.f, 0.f);
+}
+
+// U operator rows in flight per thread (the operators are read once per update)
+constexpr int PPU_U = 8;
+
 template <int VEC>
 __global__ void __launch_bounds__(256) k_pp_u(const float* __restrict__ Mp, PPArgs a,
                                               float* __restrict__ Mt, int sx, int R, int TX,
@@ -395,16 +409,30 @@ __global__ void __launch_bounds__(256) k_pp_u(const float* __restrict__ Mp, PPAr
             const float* dA = a.t[i].dA;
             const int sy = a.t[i].sy;
             const bool tr = a.t[i].trans;
-            for (int y = ty; y < sy; y += KS) {
-                const size_t e = tr ? ((size_t)y * sx + x) * R + r : ((size_t)x * sy + y) * R + r;
-                if (VEC == 4) {
-                    float4 v = __ldg(reinterpret_cast<const float4*>(op + e));
-                    float4 d = __ldg(reinterpret_cast<const float4*>(dA + (size_t)y * R + r));
-                    acc.x = fmaf(v.x, d.x, acc.x); acc.y = fmaf(v.y, d.y, acc.y);
-                    acc.z = fmaf(v.z, d.z, acc.z); acc.w = fmaf(v.w, d.w, acc.w);
-                } else {
-                    acc.x = fmaf(__ldg(op + e), __ldg(dA + (size_t)y * R + r), acc.x);
+            // element (x, y, r) of the operator: [y][x][r] (trans) or [x][y][r]
+            const size_t ystep = tr ? (size_t)sx * R : (size_t)R;
+            const float* opx = op + (tr ? (size_t)x * R : (size_t)x * sy * R) + r;
+            int y = ty;
+            for (; y + (PPU_U - 1) * KS < sy; y += PPU_U * KS) {
+                float4 v[PPU_U], d[PPU_U];
+#pragma unroll
+                for (int u = 0; u < PPU_U; ++u) {
+                    v[u] = ldv_pp<VEC>(opx + (size_t)(y + u * KS) * ystep);
+                    d[u] = ldv_pp<VEC>(dA + (size_t)(y + u * KS) * R + r);
                 }
+#pragma unroll
+                for (int u = 0; u < PPU_U; ++u) {
+                    acc.x = fmaf(v[u].x, d[u].x, acc.x);
+                    if (VEC > 1) acc.y = fmaf(v[u].y, d[u].y, acc.y);
+                    if (VEC > 2) { acc.z = fmaf(v[u].z, d[u].z, acc.z); acc.w = fmaf(v[u].w, d[u].w, acc.w); }
+                }
+            }
+            for (; y < sy; y += KS) {
+                const float4 v = ldv_pp<VEC>(opx + (size_t)y * ystep);
+                const float4 d = ldv_pp<VEC>(dA + (size_t)y * R + r);
+                acc.x = fmaf(v.x, d.x, acc.x);
+                if (VEC > 1) acc.y = fmaf(v.y, d.y, acc.y);
+                if (VEC > 2) { acc.z = fmaf(v.z, d.z, acc.z); acc.w = fmaf(v.w, d.w, acc.w); }
             }
         }
     }
@@ -419,6 +447,9 @@ __global__ void __launch_bounds__(256) k_pp_u(const float* __restrict__ Mp, PPAr
             float4 m = __ldg(reinterpret_cast<const float4*>(Mp) + o);
             *reinterpret_cast<float4*>(Mt + o * 4) =
                 make_float4(m.x + acc.x, m.y + acc.y, m.z + acc.z, m.w + acc.w);
+        } else if (VEC == 2) {
+            float2 m = __ldg(reinterpret_cast<const float2*>(Mp) + o);
+            *reinterpret_cast<float2*>(Mt + o * 2) = make_float2(m.x + acc.x, m.y + acc.y);
         } else {
             Mt[o] = Mp[o] + acc.x;
         }
@@ -591,8 +622,9 @@ cudaError_t pp_u(const float* Mp, const PPTerm* terms, int nterms, float* Mt, in
         a.t[i] = terms[i];
         al = al && (((uintptr_t)terms[i].op | (uintptr_t)terms[i].dA) % 16 == 0);
     }
-    const bool v4 = (R % 4 == 0) && al;
-    const int VEC = v4 ? 4 : 1;
+    bool al8 = ((uintptr_t)Mp | (uintptr_t)Mt) % 8 == 0;
+    for (int i = 0; i < nterms; ++i) al8 = al8 && (((uintptr_t)terms[i].op | (uintptr_t)terms[i].dA) % 8 == 0);
+    const int VEC = (R % 4 == 0 && al) ? 4 : (R % 2 == 0 && al8) ? 2 : 1;
     const int64_t nout = (int64_t)sx * (R / VEC);
     int maxs = 1;
     for (int i = 0; i < nterms; ++i) maxs = terms[i].sy > maxs ? terms[i].sy : maxs;
@@ -601,8 +633,10 @@ cudaError_t pp_u(const float* Mp, const PPTerm* terms, int nterms, float* Mt, in
     const int TX = 256 / KS;
     const unsigned blocks = (unsigned)((nout + TX - 1) / TX);
     if (blocks == 0) return cudaSuccess;
-    if (v4)
+    if (VEC == 4)
         k_pp_u<4><<<blocks, 256, 256 * sizeof(float4), st>>>(Mp, a, Mt, sx, R, TX, KS);
+    else if (VEC == 2)
+        k_pp_u<2><<<blocks, 256, 256 * sizeof(float4), st>>>(Mp, a, Mt, sx, R, TX, KS);
     else
         k_pp_u<1><<<blocks, 256, 256 * sizeof(float4), st>>>(Mp, a, Mt, sx, R, TX, KS);
     return cudaGetLastError();

@@ -9,10 +9,22 @@
 
 namespace {
 
-// Block = TX outputs (vectors of VEC along r) x KS partial sums over k.  With
-// float4 outputs each thread keeps U loads of X in flight: the kernel is bound by
-// how many bytes the SMs have outstanding (measured on 128^4 R = 64 roots: 4 in
-// flight gave 3.2-3.6 TB/s, 16 in flight with a 4-way k-split 5.4-5.5 TB/s).
+// VEC consecutive floats (VEC = 4, 2 or 1) as the low lanes of a float4
+template <int VEC>
+__device__ __forceinline__ float4 ldv(const float* p) {
+    if (VEC == 4) return __ldg(reinterpret_cast<const float4*>(p));
+    if (VEC == 2) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        return make_float4(v.x, v.y, 0.f, 0.f);
+    }
+    return make_float4(__ldg(p), 0.f, 0.f, 0.f);
+}
+
+// Block = TX outputs (vectors of VEC along r) x KS partial sums over k.  Each
+// thread keeps U loads of X in flight: the kernel is bound by how many bytes the
+// SMs have outstanding (measured on 128^4 R = 64 roots: 4 in flight gave
+// 3.2-3.6 TB/s, 16 in flight with a 4-way k-split 5.4-5.5 TB/s).  R not a multiple
+// of 4 uses float2 or float vectors with the same unrolling.
 // STRIDE: blocks loop over the chunks of TX outputs (a capped grid); else one
 // chunk per block.
 template <int VEC, int U, bool STRIDE>
@@ -38,28 +50,26 @@ __global__ void __launch_bounds__(256) k_mttv(const float* __restrict__ X,
             const float* xp = X + (p * K) * strideK + q * R + rv * VEC;
             const float* ap = A + rv * VEC;
             int k = ty;
-            if (VEC == 4) {
-                for (; k + (U - 1) * KS < K; k += U * KS) {
-                    float4 x[U], a[U];
+            for (; k + (U - 1) * KS < K; k += U * KS) {
+                float4 x[U], a[U];
 #pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        x[u] = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)(k + u * KS) * strideK));
-                        a[u] = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)(k + u * KS) * R));
-                    }
+                for (int u = 0; u < U; ++u) {
+                    x[u] = ldv<VEC>(xp + (int64_t)(k + u * KS) * strideK);
+                    a[u] = ldv<VEC>(ap + (int64_t)(k + u * KS) * R);
+                }
 #pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        acc.x = fmaf(x[u].x, a[u].x, acc.x); acc.y = fmaf(x[u].y, a[u].y, acc.y);
-                        acc.z = fmaf(x[u].z, a[u].z, acc.z); acc.w = fmaf(x[u].w, a[u].w, acc.w);
-                    }
+                for (int u = 0; u < U; ++u) {
+                    acc.x = fmaf(x[u].x, a[u].x, acc.x);
+                    if (VEC > 1) acc.y = fmaf(x[u].y, a[u].y, acc.y);
+                    if (VEC > 2) { acc.z = fmaf(x[u].z, a[u].z, acc.z); acc.w = fmaf(x[u].w, a[u].w, acc.w); }
                 }
-                for (; k < K; k += KS) {
-                    float4 x0 = __ldg(reinterpret_cast<const float4*>(xp + (int64_t)k * strideK));
-                    float4 a0 = __ldg(reinterpret_cast<const float4*>(ap + (int64_t)k * R));
-                    acc.x = fmaf(x0.x, a0.x, acc.x); acc.y = fmaf(x0.y, a0.y, acc.y);
-                    acc.z = fmaf(x0.z, a0.z, acc.z); acc.w = fmaf(x0.w, a0.w, acc.w);
-                }
-            } else {
-                for (; k < K; k += KS) acc.x = fmaf(__ldg(xp + (int64_t)k * strideK), __ldg(ap + (int64_t)k * R), acc.x);
+            }
+            for (; k < K; k += KS) {
+                const float4 x0 = ldv<VEC>(xp + (int64_t)k * strideK);
+                const float4 a0 = ldv<VEC>(ap + (int64_t)k * R);
+                acc.x = fmaf(x0.x, a0.x, acc.x);
+                if (VEC > 1) acc.y = fmaf(x0.y, a0.y, acc.y);
+                if (VEC > 2) { acc.z = fmaf(x0.z, a0.z, acc.z); acc.w = fmaf(x0.w, a0.w, acc.w); }
             }
         }
         red[ty * TX + tx] = acc;
@@ -71,6 +81,8 @@ __global__ void __launch_bounds__(256) k_mttv(const float* __restrict__ X,
             }
             if (VEC == 4)
                 *reinterpret_cast<float4*>(Y + o * 4) = acc;
+            else if (VEC == 2)
+                *reinterpret_cast<float2*>(Y + o * 2) = make_float2(acc.x, acc.y);
             else
                 Y[o] = acc.x;
         }
@@ -84,32 +96,30 @@ namespace cpk {
 
 cudaError_t mttv(const float* X, const float* A, float* Y, int64_t P, int K, int64_t Q, int R,
                  int num_sms, cudaStream_t st, int max_blocks_per_sm) {
-    const bool v4 = (R % 4 == 0) && (((uintptr_t)X | (uintptr_t)A | (uintptr_t)Y) & 15) == 0;
-    const int VEC = v4 ? 4 : 1;
+    const uintptr_t al = (uintptr_t)X | (uintptr_t)A | (uintptr_t)Y;
+    const int VEC = (R % 4 == 0 && al % 16 == 0) ? 4 : (R % 2 == 0 && al % 8 == 0) ? 2 : 1;
     const int64_t nout = P * Q * (R / VEC);
-    // k-split: enough blocks to cover the GPU twice, and (float4 path) at least
-    // two rounds of 16 loads per thread where K allows a split
+    // k-split: enough blocks to cover the GPU twice, and at least two rounds of 16
+    // loads per thread where K allows a split
     int KS = 1;
     while (KS < 32 && KS < K && (nout * KS) < (int64_t)num_sms * 2 * 256) KS *= 2;
-    if (v4)
-        while (KS < 8 && K / (2 * KS) >= 32) KS *= 2;
+    while (KS < 8 && K / (2 * KS) >= 32) KS *= 2;
     int TX = 256 / KS;
     int64_t nchunks = (nout + TX - 1) / TX;
     const bool stride = max_blocks_per_sm > 0 && nchunks > (int64_t)max_blocks_per_sm * num_sms;
     if (stride) nchunks = (int64_t)max_blocks_per_sm * num_sms;
     const unsigned nblk = (unsigned)nchunks;
-    size_t smem = sizeof(float4) * 256;
-    if (v4) {
-        if (stride)
-            k_mttv<4, 16, true><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
-        else
-            k_mttv<4, 16, false><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
-    } else {
-        if (stride)
-            k_mttv<1, 1, true><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
-        else
-            k_mttv<1, 1, false><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS);
-    }
+    const size_t smem = sizeof(float4) * 256;
+#define CP_MTTV_LAUNCH(V)                                                                    \
+    (stride ? k_mttv<V, 16, true><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS)      \
+            : k_mttv<V, 16, false><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS))
+    if (VEC == 4)
+        CP_MTTV_LAUNCH(4);
+    else if (VEC == 2)
+        CP_MTTV_LAUNCH(2);
+    else
+        CP_MTTV_LAUNCH(1);
+#undef CP_MTTV_LAUNCH
     return cudaGetLastError();
 }
 

@@ -17,9 +17,12 @@ constexpr int APAD = 4;                                     // As row padding (f
 // Tile loaders fill As[BK][BM + APAD] with As[k][m] = T(row g0 + m, k0 + k).
 enum { LOAD_QTILE = 0, LOAD_ROWK = 1, LOAD_GENERIC = 2 };
 
+// rowoff (LOAD_GENERIC): offset of T[p][0][q] for this thread's row m = tid & 127
+// (fixed for the whole tile), or -1 past the last row
 template <int MODE>
 __device__ __forceinline__ void load_a(float (*As)[BM + APAD], const float* __restrict__ T,
-                                       int64_t g0, int k0, int64_t P, int K, int64_t Q, int tid) {
+                                       int64_t g0, int k0, int64_t P, int K, int64_t Q, int tid,
+                                       int64_t rowoff) {
     const int64_t PQ = P * Q;
     if (MODE == LOAD_QTILE) {
         // whole tile inside one p-slice, contiguous along m; Q % BM == 0, Q % 4 == 0
@@ -49,18 +52,16 @@ __device__ __forceinline__ void load_a(float (*As)[BM + APAD], const float* __re
             As[4 * k4 + 3][m] = v.w;
         }
     } else {
+        // row m = tid & 127 for every j; k = (tid >> 7) + 2 j
+        const int m = tid & 127;
+        float v[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            int idx = tid + 256 * j;
-            int k = idx >> 7, m = idx & 127;
-            int64_t g = g0 + m;
-            float v = 0.f;
-            if (g < PQ && k0 + k < K) {
-                int64_t p = g / Q, q = g - p * Q;
-                v = __ldg(T + (p * K + k0 + k) * Q + q);
-            }
-            As[k][m] = v;
+            const int k = (tid >> 7) + 2 * j;
+            v[j] = (rowoff >= 0 && k0 + k < K) ? __ldg(T + rowoff + (int64_t)(k0 + k) * Q) : 0.f;
         }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) As[(tid >> 7) + 2 * j][m] = v[j];
     }
 }
 
@@ -68,7 +69,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_ttm_simt(const float* __restrict__ T,
                                                   const float* __restrict__ A,
                                                   float* __restrict__ X, int64_t P, int K,
-                                                  int64_t Q, int R) {
+                                                  int64_t Q, int R, int xvec) {
     __shared__ __align__(16) float As[BK][BM + APAD];
     __shared__ __align__(16) float Bs[BK][BN];
     const int tid = threadIdx.x;
@@ -83,8 +84,16 @@ __global__ void __launch_bounds__(256) k_ttm_simt(const float* __restrict__ T,
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
 
+    int64_t rowoff = -1;
+    if (MODE == LOAD_GENERIC) {
+        const int64_t g = g0 + (tid & 127);
+        if (g < PQ) {
+            const int64_t p = g / Q, q = g - p * Q;
+            rowoff = p * K * Q + q;
+        }
+    }
     for (int k0 = 0; k0 < K; k0 += BK) {
-        load_a<MODE>(As, T, g0, k0, P, K, Q, tid);
+        load_a<MODE>(As, T, g0, k0, P, K, Q, tid, rowoff);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             int idx = tid + 256 * j;
@@ -115,8 +124,12 @@ __global__ void __launch_bounds__(256) k_ttm_simt(const float* __restrict__ T,
         int64_t g = g0 + ty * TM + i;
         if (g >= PQ) break;
         float* dst = X + g * R + c0;
-        if ((R & 3) == 0 && c0 + 3 < R) {
+        // xvec: widest store every row start allows (R and the base address)
+        if (xvec == 4 && c0 + 3 < R) {
             *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        } else if (xvec == 2 && c0 + 3 < R) {
+            *reinterpret_cast<float2*>(dst) = make_float2(acc[i][0], acc[i][1]);
+            *reinterpret_cast<float2*>(dst + 2) = make_float2(acc[i][2], acc[i][3]);
         } else {
 #pragma unroll
             for (int j = 0; j < TN; ++j)
@@ -134,12 +147,13 @@ cudaError_t ttm_simt(const float* T, const float* A, float* X, int64_t P, int K,
     const int64_t PQ = P * Q;
     dim3 grid((unsigned)((PQ + BM - 1) / BM), (unsigned)((R + BN - 1) / BN));
     bool al16 = ((uintptr_t)T & 15) == 0;
+    const int xvec = ((R & 3) == 0 && ((uintptr_t)X & 15) == 0) ? 4 : ((R & 1) == 0 && ((uintptr_t)X & 7) == 0) ? 2 : 1;
     if (Q > 1 && Q % BM == 0 && al16)
-        k_ttm_simt<LOAD_QTILE><<<grid, 256, 0, st>>>(T, A, X, P, K, Q, R);
+        k_ttm_simt<LOAD_QTILE><<<grid, 256, 0, st>>>(T, A, X, P, K, Q, R, xvec);
     else if (Q == 1 && K % 4 == 0 && al16)
-        k_ttm_simt<LOAD_ROWK><<<grid, 256, 0, st>>>(T, A, X, P, K, Q, R);
+        k_ttm_simt<LOAD_ROWK><<<grid, 256, 0, st>>>(T, A, X, P, K, Q, R, xvec);
     else
-        k_ttm_simt<LOAD_GENERIC><<<grid, 256, 0, st>>>(T, A, X, P, K, Q, R);
+        k_ttm_simt<LOAD_GENERIC><<<grid, 256, 0, st>>>(T, A, X, P, K, Q, R, xvec);
     return cudaGetLastError();
 }
 

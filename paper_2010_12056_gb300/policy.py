@@ -103,16 +103,16 @@ def accuracy(pol, X, y):
 
 
 def time_to_target(T, R, method, target_resid, max_sweeps, prec="bf16x3", seed=1, eps=0.1,
-                   policy=None, judge_every=5):
+                   policy=None, judge_every=5, A0=None):
     """Device milliseconds until the direct residual first drops to target_resid.
 
     method: "msdt" (regular sweeps), "pp" (Alg. 2 with tolerance eps) or
     "policy" (cp_sweep_pp with the network).  The residual check after each
     sweep is outside the timed work.  Returns (ms or inf, sweeps, final resid,
-    trace).
+    trace).  A0: initial factors (default: U[0,1) from `seed`).
     """
     from . import CPError
-    ctx = CPContext(T, R, prec=prec, seed=seed, judge_every=judge_every)
+    ctx = CPContext(T, R, A0=A0, prec=prec, seed=seed, judge_every=judge_every)
     try:
         r = 1.0
         for k in range(max_sweeps):
