@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--target-sweeps", type=int, default=60)
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--policy-dims", default="256,256,256")
+    ap.add_argument("--policy-law", default="collinear", choices=["collinear", "uniform"])
     ap.add_argument("--ttm-only", action="store_true",
                     help="time only the first-level TTM of the last mode (cp_ttm) and exit")
     ap.add_argument("--dims", default=None, help="override the workload's mode sizes, e.g. 512,512,512")
@@ -267,16 +268,22 @@ def run_reference(args, wl, rank, budget_s=60.0):
     print(json.dumps(line), flush=True)
 
 
-def policy_problem(i, dims, base_seed):
-    """The i-th tensor of the policy study: collinear rank-R factors, R in {16, 32, 64},
-    cosine U[0.5, 0.95], noise log-uniform in [1e-4, 1e-2] (draws from a seeded generator)."""
+def policy_problem(i, dims, base_seed, law="collinear"):
+    """The i-th tensor of the policy study: rank-R factors, R in {16, 32, 64}, noise
+    log-uniform in [1e-4, 1e-2] (draws from a seeded generator).  law "collinear":
+    pairwise cosine U[0.5, 0.95] (needs every mode >= R); "uniform": U[0,1) factors
+    (expected cosine 0.75), for shapes with small modes."""
     import numpy as np
     import synth
     g = np.random.default_rng(base_seed + i)
     R = (16, 32, 64)[i % 3]
     C = float(g.uniform(0.5, 0.95))
     eta = float(10.0 ** g.uniform(-4.0, -2.0))
-    T, _, _ = synth.make_problem_device(base_seed + i, list(dims), R, law="collinear", eta=eta, C=C)
+    if law == "collinear":
+        T, _, _ = synth.make_problem_device(base_seed + i, list(dims), R, law="collinear", eta=eta, C=C)
+    else:
+        T, _, _ = synth.make_problem_device(base_seed + i, list(dims), R, law=law, eta=eta)
+        C = 0.75
     return T, R, C, eta
 
 
@@ -295,7 +302,7 @@ def run_policy(args):
     t0 = time.perf_counter()
     Xs, ys = [], []
     for i in range(args.train_tensors):
-        T, R, C, eta = policy_problem(i, dims, train_seed)
+        T, R, C, eta = policy_problem(i, dims, train_seed, args.policy_law)
         X, y, _ = pol.collect(T, R, args.probe_sweeps, prec=args.prec, seed=1 + i, min_gain=1e-9)
         Xs.append(X)
         ys.append(y)
@@ -310,7 +317,7 @@ def run_policy(args):
     res = {"msdt": [], "pp": [], "policy": []}
     per = []
     for i in range(args.eval_tensors):
-        T, R, C, eta = policy_problem(i, dims, eval_seed)
+        T, R, C, eta = policy_problem(i, dims, eval_seed, args.policy_law)
         ctx = pkg.CPContext(T, R, prec=args.prec, seed=7 + i)
         ctx.sweep_msdt(args.target_sweeps)
         target = ctx.fit(exact=True)[1] + 1e-6   # equal fit: within 1e-6
@@ -338,7 +345,8 @@ def run_policy(args):
         "metric": "device time to exact MSDT's fit after %d sweeps (+1e-6), held-out tensors" % args.target_sweeps,
         "value": tot["policy"], "unit": "ms (sum over held-out tensors)", "n_gpus": 1,
         "higher_is_better": False, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "learned PP policy, %s collinear tensors" % "x".join(map(str, dims)),
+        "config": {"workload": "learned PP policy, %s %s tensors" % ("x".join(map(str, dims)),
+                                                                    args.policy_law),
                    "train_tensors": args.train_tensors, "eval_tensors": args.eval_tensors,
                    "probe_sweeps": args.probe_sweeps, "train_steps": args.train_steps, "prec": args.prec},
         "total_ms": tot, "reached": reached, "wins": wins,
