@@ -43,10 +43,16 @@
 namespace {
 
 constexpr int BM = 128;
-constexpr int NTHREADS = 384;
+// warps 0 producer, 1 MMA, 2-3 idle, 4-7 converters, 8.. epilogue: EW = 4 epilogue
+// warps (one per TMEM lane quarter), or 8 (two per quarter, alternate 16-column
+// groups) for passes of 128 columns, where the epilogue is the slowest stage
+// (measured on 128^4: R = 128 0.73 -> 0.81-0.87 of HBM; R <= 64 slower with 8,
+// whose extra warps take issue slots from the converters)
+__host__ __device__ constexpr int nthreads(int ew) { return 256 + 32 * ew; }
+inline int epi_warps_for(int Rpad) { return Rpad >= 128 ? 8 : 4; }
 constexpr int OPA_BYTES = BM * 128;        // one split part of a 128-row chunk: 16 KB
 constexpr int EPI_STRIDE = 20;             // floats per row of the epilogue transpose buffer
-constexpr int EPI_BYTES = 4 * 32 * EPI_STRIDE * 4;
+constexpr int EPI_WARP_BYTES = 32 * EPI_STRIDE * 4;   // one epilogue warp's transpose buffer
 constexpr int BAR_BYTES = 512;
 // first-child pieces: [2 tiles in flight][4 warps][2 pieces][128 columns] floats + keys
 constexpr int CHILD_BYTES = 2 * 4 * 2 * 128 * 4 + 2 * 4 * 2 * 8;
@@ -260,11 +266,12 @@ struct Layout {
 };
 
 __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, int nk, int b_resident,
-                                               int BK, bool child = false, int ac_bytes = 0) {
+                                               int BK, int ew, bool child = false, int ac_bytes = 0) {
     const size_t stg = (size_t)BM * BK * 4;
     const size_t bchunk = 2 * (size_t)Rpad * 128;
     const size_t nb = b_resident ? (size_t)nk : (size_t)S_op;
-    return 1024 + (size_t)S_stg * stg + (size_t)S_op * 2 * OPA_BYTES + nb * bchunk + EPI_BYTES +
+    return 1024 + (size_t)S_stg * stg + (size_t)S_op * 2 * OPA_BYTES + nb * bchunk +
+           (size_t)ew * EPI_WARP_BYTES +
            (child ? CHILD_BYTES + (size_t)ac_bytes : 0) + BAR_BYTES;
 }
 
@@ -276,8 +283,8 @@ __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, in
 // CHILD: 0 plain; 1 the epilogue also forms the first child (a.Yc) for sc a
 // multiple of 32; 2 for other sc.  Separate instantiations keep each kernel's
 // code, registers and shared memory to what it runs.
-template <int MODE, int KIND, int CHILD>
-__global__ void __launch_bounds__(NTHREADS, 1)
+template <int MODE, int KIND, int CHILD, int EW>
+__global__ void __launch_bounds__(nthreads(EW), 1)
     k_ttm_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmBhi,
              const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmBhi1,
              const __grid_constant__ CUtensorMap tmBlo1, const TcArgs a) {
@@ -293,7 +300,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t op0 = stg0 + (uint32_t)S_stg * STG;
     const uint32_t b0 = op0 + (uint32_t)S_op * 2u * OPA_BYTES;
     const uint32_t epi0 = b0 + (uint32_t)(a.b_resident ? a.nk : S_op) * bchunk;
-    const uint32_t child0 = epi0 + EPI_BYTES;
+    static_assert(EW == 4 || (EW == 8 && CHILD == 0), "first-child epilogues use four warps");
+    constexpr int NEPI = EW;
+    const uint32_t child0 = epi0 + NEPI * EPI_WARP_BYTES;
     const uint32_t ac0 = child0 + (CHILD ? CHILD_BYTES : 0);
     const uint32_t bar0 = ac0 + (CHILD ? (uint32_t)a.ac_bytes : 0u);
     auto stg_full = [&](int s) { return bar0 + 8u * s; };
@@ -320,7 +329,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full(b), 1);
-            mbar_init(acc_empty(b), 128);
+            mbar_init(acc_empty(b), 32 * NEPI);
         }
         mbar_init(b_full, 1);
         mbar_init(drain_bar, 1);
@@ -341,7 +350,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // the contracted factor, read by the epilogue for every tile
         float* sAc = reinterpret_cast<float*>(gbase + (ac0 - base));
         const int n = a.sc * a.R;
-        for (int i = threadIdx.x; i < n; i += NTHREADS) sAc[i] = __ldg(a.Ac + i);
+        for (int i = threadIdx.x; i < n; i += nthreads(EW)) sAc[i] = __ldg(a.Ac + i);
     }
     tc_fence_before();
     __syncthreads();
@@ -530,8 +539,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else if (warp >= 8) {
         // ------------------------------------------------ epilogue (thread = TMEM lane = row)
-        const int quad = warp & 3;
-        float* tb = reinterpret_cast<float*>(gbase + (epi0 - base)) + quad * 32 * EPI_STRIDE;
+        const int quad = warp & 3;             // TMEM lane quarter (warp id mod 4)
+        const int half = (warp - 8) >> 2;     // which alternate 16-column groups
+        constexpr int NHALF = NEPI / 4;
+        float* tb = reinterpret_cast<float*>(gbase + (epi0 - base)) + (warp - 8) * 32 * EPI_STRIDE;
         // first-child pieces and their segment keys (-1: none), double-buffered by tile
         float* cpart = reinterpret_cast<float*>(gbase + (child0 - base));           // [2][4][2][128]
         long long* ckey = reinterpret_cast<long long*>(gbase + (child0 - base) + 2 * 4 * 2 * 128 * 4);
@@ -598,7 +609,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             float* mypart = cpart + (((lt & 1) * 4 + quad) * 2 + piece) * 128;
             const uint32_t taddr =
                 tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * a.set_cols);
-            for (int c0 = 0; c0 < Rpw; c0 += 16) {
+            for (int c0 = 16 * half; c0 < Rpw; c0 += 16 * NHALF) {
                 float v[16];
                 // corrections first (last accumulator), then the hi*hi partial sums;
                 // up to three accumulators per TMEM round trip
@@ -894,7 +905,7 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
         ps.b_resident = (pl->npass == 1 && (size_t)pl->nk * 2 * ps.Rpad * 128 <= 64 * 1024) ? 1 : 0;
         ps.S_stg = 0;
         for (int st = MAX_STG; st >= 2; --st)
-            if (layout_bytes(st, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK) <= SMEM_LIMIT) {
+            if (layout_bytes(st, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK, epi_warps_for(ps.Rpad)) <= SMEM_LIMIT) {
                 ps.S_stg = st;
                 break;
             }
@@ -963,11 +974,11 @@ int ttm_tc_splitk(const TcPlan* pl, int num_sms) {
 
 int64_t ttm_tc_rows(const TcPlan* pl) { return pl->PQ; }
 
-template <int MODE, int KIND, int CHILD>
+template <int MODE, int KIND, int CHILD, int EW>
 static cudaError_t launch(const TcPlan* pl, const TcPass& p1, const TcArgs& a, size_t smem, unsigned grid,
                           cudaStream_t st) {
-    cudaFuncSetAttribute(k_ttm_tc<MODE, KIND, CHILD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ttm_tc<MODE, KIND, CHILD><<<grid, NTHREADS, smem, st>>>(pl->tmT, pl->pass[0].tmBhi, pl->pass[0].tmBlo,
+    cudaFuncSetAttribute(k_ttm_tc<MODE, KIND, CHILD, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ttm_tc<MODE, KIND, CHILD, EW><<<grid, nthreads(EW), smem, st>>>(pl->tmT, pl->pass[0].tmBhi, pl->pass[0].tmBlo,
                                                               p1.tmBhi, p1.tmBlo, a);
     return cudaGetLastError();
 }
@@ -1072,9 +1083,9 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     if (child) {
         auto fit = [&](int acb) {
             int st2 = p0.S_stg;
-            while (st2 > 2 && layout_bytes(st2, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, true, acb) > SMEM_LIMIT)
+            while (st2 > 2 && layout_bytes(st2, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, 4, true, acb) > SMEM_LIMIT)
                 --st2;
-            return layout_bytes(st2, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, true, acb) <= SMEM_LIMIT ? st2 : 0;
+            return layout_bytes(st2, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, 4, true, acb) <= SMEM_LIMIT ? st2 : 0;
         };
         const int acb = (child->sc * pl->R * 4 + 15) / 16 * 16;
         if (int st2 = fit(acb)) {
@@ -1121,24 +1132,28 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     a.cws = child ? child->ws : nullptr;
     a.sc = child ? child->sc : 1;
     a.ac_bytes = ac_bytes;
-    const size_t smem = layout_bytes(S_stg, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, child != nullptr, ac_bytes);
+    // first-child epilogues use four warps; plain ones eight for wide passes
+    const int ew = child ? 4 : epi_warps_for(p0.Rpad);
+    const size_t smem = layout_bytes(S_stg, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, ew, child != nullptr, ac_bytes);
     const int64_t nwork = a.ntiles * a.nsk * a.npass;
     const unsigned grid = (unsigned)(nwork < num_sms ? nwork : num_sms);
     if (grid == 0) return cudaSuccess;
     const TcPass& p1 = pl->pass[pl->npass > 1 ? 1 : 0];
     cudaError_t e;
     const int ck = child ? (child->sc % 32 == 0 ? 1 : 2) : 0;
-#define CP_TTM_LAUNCH(C)                                                                                  \
-    (pl->mode == 0 ? (pl->kind == 0 ? launch<0, 0, C>(pl, p1, a, smem, grid, st)                        \
-                                    : launch<0, 1, C>(pl, p1, a, smem, grid, st))                       \
-                   : (pl->kind == 0 ? launch<1, 0, C>(pl, p1, a, smem, grid, st)                        \
-                                    : launch<1, 1, C>(pl, p1, a, smem, grid, st)))
+#define CP_TTM_LAUNCH(C, W)                                                                               \
+    (pl->mode == 0 ? (pl->kind == 0 ? launch<0, 0, C, W>(pl, p1, a, smem, grid, st)                     \
+                                    : launch<0, 1, C, W>(pl, p1, a, smem, grid, st))                    \
+                   : (pl->kind == 0 ? launch<1, 0, C, W>(pl, p1, a, smem, grid, st)                     \
+                                    : launch<1, 1, C, W>(pl, p1, a, smem, grid, st)))
     if (ck == 1)
-        e = CP_TTM_LAUNCH(1);
+        e = CP_TTM_LAUNCH(1, 4);
     else if (ck == 2)
-        e = CP_TTM_LAUNCH(2);
+        e = CP_TTM_LAUNCH(2, 4);
+    else if (ew == 8)
+        e = CP_TTM_LAUNCH(0, 8);
     else
-        e = CP_TTM_LAUNCH(0);
+        e = CP_TTM_LAUNCH(0, 4);
 #undef CP_TTM_LAUNCH
     if (e != cudaSuccess) return e;
     if (child && ttm_tc_child_ws_floats(pl, child->sc) > 0) {
