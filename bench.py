@@ -546,8 +546,8 @@ def main():
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
     if args.workload == "c2" and args.prec == "bf16x3" and not (args.dims or args.rank or args.law):
         # DRAM bytes per launch of this kernel on this workload, from one ncu capture
-        # (dram__bytes_read.sum 1.0738 GB + dram__bytes_write.sum 0.5035 GB)
-        roofline["traffic"] = 1.0738e9 + 0.5035e9
+        # (dram__bytes_read.sum 1.0739 GB + dram__bytes_write.sum 0.5036 GB)
+        roofline["traffic"] = 1.0739e9 + 0.5036e9
         roofline["traffic_source"] = "ncu dram__bytes_read+write of k_ttm_tc on 128^4 R=64, one launch"
 
     roofline["mode"] = mode
