@@ -154,14 +154,16 @@ def make_problem(seed: int, dims, R: int, law: str = "uniform", eta: float = 0.0
 
 
 def make_problem_device(seed: int, dims, R: int, law: str = "uniform", eta: float = 0.0,
-                        C: float | None = None, device="cuda", init_seed: int | None = None):
+                        C: float | None = None, device="cuda", init_seed: int | None = None,
+                        slab_elems: int = 1 << 27):
     """Large-tensor variant of make_problem, assembled with torch on `device`.
 
     Factors come from the same Philox streams as make_problem; the dense product
     is formed in FP64 with a torch matmul, the noise from torch's own seeded
     generator (N(0,1), scaled to eta ||T||_F), and the result is returned as a
     contiguous FP32 tensor.  Returns (T float32 on device, true factors, initial
-    factors); the host oracle reads back exactly these FP32 bytes.
+    factors); the host oracle reads back exactly these FP32 bytes.  slab_elems bounds
+    the FP64 Khatri-Rao rows formed at once (the product is built in mode-0 slices).
     """
     import torch
 
@@ -188,7 +190,7 @@ def make_problem_device(seed: int, dims, R: int, law: str = "uniform", eta: floa
         inner *= d
     # slices of mode 0 keep the FP64 Khatri-Rao rows near 1 GB (uneven shapes
     # with a small last mode would otherwise need many times the tensor's size)
-    step = max(1, int((1 << 27) // max(1, inner * R)))
+    step = max(1, int(slab_elems // max(1, inner * R)))
     if step >= dims[0]:
         T = slab(Ft[0])
     else:

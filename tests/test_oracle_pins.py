@@ -50,6 +50,21 @@ def test_noise_ratio_exact():
     assert abs(ratio - 1e-2) < 1e-12
 
 
+@pytest.mark.parametrize("dims,R", [((9, 5, 4, 3), 4), ((7, 6, 5), 3)])
+def test_device_generator_slices_equal_one_product(dims, R):
+    """The large-tensor generator builds [[A]] in mode-0 slices when its Khatri-Rao rows
+    would be large; slices of 1, 2 and 3 mode-0 indices give the tensor of one product,
+    and that tensor is the definition sum_r prod_n A(n)[i_n, r] (no noise)."""
+    torch = pytest.importorskip("torch")
+    whole, F, _ = synth.make_problem_device(31, dims, R, device="cpu")
+    ref = synth.cp_full(F).astype(np.float32)
+    assert np.array_equal(whole.numpy(), ref) or np.abs(whole.numpy() - ref).max() <= 1e-6 * np.abs(ref).max()
+    inner = int(np.prod(dims[1:-1]))
+    for rows in (1, 2, 3):
+        sliced, _, _ = synth.make_problem_device(31, dims, R, device="cpu", slab_elems=rows * inner * R)
+        assert np.array_equal(sliced.numpy(), whole.numpy())
+
+
 # ----------------------------------------------------------------------------- MTTKRP
 
 
