@@ -76,6 +76,7 @@ struct cp_ctx {
     cudaStream_t side = nullptr;            // normal-equation factorisation runs here,
     cudaEvent_t ev_ready = nullptr, ev_chol = nullptr;  // overlapped with the MTTKRP
     bool chol_pending = false;
+    int chol_mode = -1;         // mode whose factorisation is pending
     int* d_mode = nullptr;      // 0: refinement path, 1: FP64 substitution path
     double* tile_gs = nullptr;     // per mode: tile shares of <Gamma, S>
     int ntiles = 1;
@@ -476,6 +477,7 @@ cp_status launch_chol(cp_ctx* c, int u, bool pp, double* scal) {
                               c->L, c->invd, c->W, scal, c->d_mode, c->schur_ws, c->side));
     CKCUDA(c, cudaEventRecord(c->ev_chol, c->side));
     c->chol_pending = true;
+    c->chol_mode = u;
     return CP_OK;
 }
 
@@ -647,10 +649,17 @@ cp_status exact_sweep(cp_ctx* c, bool msdt, int k, bool keep_ahead = false) {
             CKST(ahead_join(c));
             path = dt_path(c->N, u0, &fuse2);
         }
-        CKST(launch_chol(c, u, false, scal_slot(c, k, u)));
+        if (!(c->chol_pending && c->chol_mode == u)) CKST(launch_chol(c, u, false, scal_slot(c, k, u)));
         float* M = nullptr;
         CKST(mttkrp_leaf(c, path, &M, fuse2, msdt));
         CKST(update_mode(c, u, M, false, scal_slot(c, k, u)));
+        if (msdt && c->lookahead && u0 + 1 < c->N) {
+            // the next update's factorisation goes first, so that its one-CTA inverse
+            // finds an SM before the look-ahead contraction fills them
+            int un = 0;
+            msdt_path(c->N, c->t_msdt, &un);
+            CKST(launch_chol(c, un, false, scal_slot(c, k, un)));
+        }
         if (msdt) CKST(msdt_lookahead(c, t));
     }
     if (!keep_ahead) CKST(ahead_join(c));
