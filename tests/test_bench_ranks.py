@@ -58,3 +58,23 @@ def test_single_process_is_a_pass_through():
     r.barrier()
     assert r.max(3.5) == 3.5
     assert bench.replica_rate(10, 5.0, 1) == pytest.approx(2000.0)
+
+
+def test_reference_arm_line_on_cpu():
+    """bench.py --impl reference (the FP64 oracle on the host cores) prints one JSON
+    line with the contract's keys; the 64^3 workload keeps it to seconds."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "c1", "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "cpu_baseline", "e2e", "config"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
