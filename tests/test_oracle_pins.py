@@ -338,6 +338,110 @@ def test_pp_loop_enters_and_tracks_als():
     assert abs(b.resid[-1] - a.resid[-1]) < 1e-3
 
 
+def _scripted_pp(monkeypatch, steps, eps=0.1, dims=(5, 6, 7), R=2):
+    """Run the oracle's Alg. 2 loop with the normal-equation solve replaced by a
+    script: update n of sweep k returns A(n) * (1 + steps[k]).  Every factor then
+    changes by exactly steps[k] / (1 + steps[k]) relative in a sweep, so the
+    regime tests of Alg. 2 see prescribed values, whatever the contractions
+    compute.  Returns the result and the factors each operator build started from."""
+    T = synth.normal(300, 0, int(np.prod(dims))).reshape(dims)
+    A0 = synth.uniform_factors(301, dims, R)
+    N = len(dims)
+    cur = [a.copy() for a in A0]
+    calls = {"k": 0}
+
+    def fake_solve(M, G):
+        k, n = divmod(calls["k"], N)
+        calls["k"] += 1
+        cur[n] = cur[n] * (1.0 + steps[k])
+        return cur[n].copy()
+
+    builds = []
+    real_ops = co.pp_operators
+
+    def spy_ops(Tt, Ap):
+        builds.append([a.copy() for a in Ap])
+        return real_ops(Tt, Ap)
+
+    monkeypatch.setattr(co, "solve_normal", fake_solve)
+    monkeypatch.setattr(co, "pp_operators", spy_ops)
+    res = co.pp_cp_als(T, A0, len(steps), eps=eps)
+    return res, builds, A0
+
+
+def _grow(A0, factor):
+    return [a * factor for a in A0]
+
+
+def test_pp_control_follows_alg2_on_a_script(monkeypatch):
+    """Alg. 2's regime logic, sweep by sweep, on scripted relative changes (eps 0.1):
+      0  dA = A (line 2): regular                      step 0.5  -> change 0.333
+      1  0.333 >= eps: regular                         step 0.05 -> change 0.048
+      2  0.048 < eps: build operators (A_p = A), PP    step 0.04 -> A - A_p 0.038
+      3  0.038 < eps: stay in PP                       step 0.04 -> 0.075
+      4  0.075 < eps: stay in PP                       step 0.04 -> 0.111
+      5  0.111 >= eps: leave, one regular sweep        step 0.02 -> change 0.0196
+      6  that sweep's change 0.0196 < eps: rebuild, PP step 0.3  -> 0.231
+      7  0.231 >= eps: leave, regular                  step 0.2  -> change 0.167
+      8  0.167 >= eps: regular again                   step 0.01 -> change 0.0099
+      9  rebuild, PP
+    A PP initialization is not a sweep: ten sweeps, three builds."""
+    steps = [0.5, 0.05, 0.04, 0.04, 0.04, 0.02, 0.3, 0.2, 0.01, 0.01]
+    res, builds, A0 = _scripted_pp(monkeypatch, steps)
+    assert res.kinds == ["als", "als", "pp", "pp", "pp", "als", "pp", "als", "als", "pp"]
+    assert len(res.kinds) == len(res.resid) == len(steps)
+    assert res.n_pp_init == 3 == len(builds)
+    # each build starts from the factors of that moment (A_p = A, Alg. 2 line 6)
+    for b, k in zip(builds, (2, 6, 9)):
+        g = float(np.prod([1.0 + x for x in steps[:k]]))
+        for n in range(3):
+            assert np.allclose(b[n], A0[n] * g, rtol=1e-14, atol=0)
+    # the final factors are the scripted ones (PP sweeps write A(n), dA = A - A_p)
+    g = float(np.prod([1.0 + x for x in steps]))
+    for n in range(3):
+        assert np.allclose(res.A[n], A0[n] * g, rtol=1e-14, atol=0)
+
+
+def test_pp_control_reentry_uses_the_regular_sweeps_change(monkeypatch):
+    """After leaving PP, the entry test uses the change made by the regular sweep
+    (Alg. 2 line 14), not A - A_p of the old operators: here the accumulated
+    A - A_p (0.3 after the regular sweep) would keep it out, the sweep's own change
+    (0.01) lets it back in with new operators."""
+    steps = [0.5, 0.05, 0.09, 0.09, 0.01, 0.01]
+    res, builds, _ = _scripted_pp(monkeypatch, steps)
+    # 0 als (dA = A), 1 als (0.333), 2 build + pp (0.048), 3 pp (A - A_p 0.083),
+    # 4 leave: als (A - A_p 0.158), 5 re-enter on the regular change 0.0099: build + pp
+    assert res.kinds == ["als", "als", "pp", "pp", "als", "pp"]
+    assert res.n_pp_init == 2
+
+
+def test_pp_control_tests_every_factor(monkeypatch):
+    """The test is ||dA(i)|| < eps ||A(i)|| for every i: one factor above eps keeps
+    the sweep regular (entry) or ends the approximation (stay)."""
+    dims, R, N = (5, 6, 7), 2, 3
+    T = synth.normal(302, 0, int(np.prod(dims))).reshape(dims)
+    A0 = synth.uniform_factors(303, dims, R)
+    # relative step of factor n in sweep k (new = old (1 + step))
+    steps = [[1.0, 1.0, 1.0],          # 0 regular (dA = A)
+             [0.01, 0.25, 0.01],       # 1 regular (0.5 >= eps); factor 1 changes 0.2
+             [0.01, 0.01, 0.01],       # 2 regular: factor 1 alone is above eps
+             [0.001, 0.001, 0.2],      # 3 build + PP; factor 2 drifts 0.167 from A_p
+             [0.01, 0.01, 0.01]]       # 4 regular: factor 2 alone is above eps
+    cur = [a.copy() for a in A0]
+    calls = {"k": 0}
+
+    def fake_solve(M, G):
+        k, n = divmod(calls["k"], N)
+        calls["k"] += 1
+        cur[n] = cur[n] * (1.0 + steps[k][n])
+        return cur[n].copy()
+
+    monkeypatch.setattr(co, "solve_normal", fake_solve)
+    res = co.pp_cp_als(T, A0, len(steps), eps=0.1)
+    assert res.kinds == ["als", "als", "als", "pp", "als"]
+    assert res.n_pp_init == 1
+
+
 # ----------------------------------------------------------------------------- MLP
 
 
