@@ -54,6 +54,12 @@ WORKLOADS = {
 STANDINS = ("coil", "timelapse", "chem")
 METRIC = "ALS sweep/s (MSDT) on 1 GPU, order-4 128^4 R=64"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# DRAM bytes per launch of the last-mode TTM on 128^4 R=64 from ncu captures of
+# the current kernel, by precision (profiles/ttm_tc_*_c2.md); a precision whose
+# kernel changed since its capture has no entry (traffic null)
+TRAFFIC_C2 = {}
+FIT_SWEEPS = 20     # the fit check: direct residual after this many MSDT sweeps from A0
+FIT_TOL = 1e-6
 
 
 def parse():
@@ -63,8 +69,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS) + ["policy"])
-    ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32", "bf16x3", "bf16", "tf32x3"])
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--prec", default="f16x3", choices=["fp32", "tf32", "bf16x3", "bf16", "tf32x3", "f16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     # learned PP policy experiment (--workload policy)
@@ -95,8 +100,12 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 50 ms; only samples taken
-    between mark_start() and mark_stop() (the timed region) are summarised."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms.  Samples taken
+    between mark_start() and mark_stop() (the timed region) are summarised; when
+    that region is shorter than the sampling period, the samples of the whole
+    GPU-busy window around it (mark_window_start/stop: the timed region followed
+    by the schedule and roofline loops on the same workload) stand in, and the
+    summary says which."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -108,6 +117,13 @@ class ClockSampler:
         self.proc = None
         self.t = None
         self.t0 = self.t1 = None
+        self.w0 = self.w1 = None
+
+    def mark_window_start(self):
+        self.w0 = time.time()
+
+    def mark_window_stop(self):
+        self.w1 = time.time()
 
     def start(self, wait_s=3.0):
         try:
@@ -145,9 +161,17 @@ class ClockSampler:
         if self.t:
             self.t.join(timeout=2)
         rows = self.rows
+        source = "all samples"
         if self.t0 is not None and self.t1 is not None:
             inside = [r for r in rows if self.t0 <= r[0] <= self.t1 + 0.05]
-            rows = inside if inside else [r for r in rows if r[0] >= self.t0][:1]
+            if inside:
+                rows, source = inside, "timed region"
+            elif self.w0 is not None and self.w1 is not None:
+                rows = [r for r in rows if self.w0 <= r[0] <= self.w1]
+                source = "benchmark window (timed region shorter than the 50 ms sampling period)"
+            else:
+                rows = [r for r in rows if r[0] >= self.t0][:1]
+                source = "first sample after the timed region"
         mhz, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for _, r in rows:
@@ -161,7 +185,8 @@ class ClockSampler:
                     reasons.add(nm)
         mhz.sort()
         med = mhz[len(mhz) // 2] if mhz else None
-        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(mhz)}
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(mhz),
+                "source": source}
 
 
 class Ranks:
@@ -199,27 +224,11 @@ def replica_rate(steps, ms_max, world):
 
 
 def cpu_threads():
+    """Host cores the oracle's BLAS may use: every core of the box (nproc)."""
     try:
-        from threadpoolctl import threadpool_info
-        n = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
-        return int(n)
+        return len(os.sched_getaffinity(0))
     except Exception:
         return os.cpu_count() or 1
-
-
-def oracle_sweeps(T64, A0, seconds, route="msdt"):
-    """Time the FP64 oracle (as it stands) on the same tensor: sweeps/s over a bounded sample."""
-    from oracle import cp_oracle as co
-    A = [a.copy() for a in A0]
-    n, t0 = 0, time.perf_counter()
-    while True:
-        res = co.cp_als(T64, A, 1, route=route)
-        A = res.A
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    return n / el, n, el
 
 
 def make_inputs(wl, device):
@@ -256,6 +265,8 @@ def run_reference(args, wl, rank, budget_s=60.0):
     v = n / el
     cores = cpu_threads()
     sample = f"{n} of {args.steps} FP64 oracle MSDT sweeps on the full tensor ({el:.1f} s, budget {budget_s:.0f} s)"
+    nwarm = min(args.warmup, 1)
+    r_direct = co.residual_direct(T64, A)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "sweep/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n,
@@ -264,6 +275,7 @@ def run_reference(args, wl, rank, budget_s=60.0):
         "config": {"workload": wl["desc"], "sweep": "msdt"},
         "cpu_baseline": {"value": v, "unit": "sweep/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "sweep/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "fit": {"direct": r_direct, "after_sweeps": nwarm + n},
     }
     print(json.dumps(line), flush=True)
 
@@ -446,13 +458,13 @@ def main():
     clk.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
+    clk.mark_window_start()
     clk.mark_start()
     e0.record(stream)
     ctx.sweep_msdt(args.steps)
     e1.record(stream)
     barrier()
     clk.mark_stop()
-    clocks = clk.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
     st1 = ctx.stats()
     launches = int(st1["launches"] - st0["launches"])
@@ -520,6 +532,8 @@ def main():
     ttm_bytes = 4.0 * numel + 4.0 * (numel // dims[mode]) * R
     ttm_flops = 2.0 * numel * R
     del X
+    clk.mark_window_stop()
+    clocks = clk.stop()
     if args.prec == "fp32" or not used_tc:
         sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
         alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -529,8 +543,8 @@ def main():
     else:
         # tensor peak for the algorithmic flops of this mode: x3 modes issue three
         # products per term; tf32 runs at half the bf16 rate (nominal ratio)
-        nprod = 3 if args.prec in ("bf16x3", "tf32x3") else 1
-        rate = 1.0 if args.prec in ("bf16x3", "bf16") else 0.5
+        nprod = 3 if args.prec in ("bf16x3", "tf32x3", "f16x3") else 1
+        rate = 1.0 if args.prec in ("bf16x3", "bf16", "f16x3") else 0.5
         tpeak = peaks["bf16_tflops"] * rate / nprod
         t_hbm = ttm_bytes / (peaks["hbm_gbs"] * 1e9)
         t_tc = ttm_flops / (tpeak * 1e12)
@@ -544,10 +558,10 @@ def main():
                         "frac": None, "traffic": None, "kernel": "ttm_tc",
                         "peak_source": f"hbm_gbs of {peak_kind}"}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
-    if args.workload == "c2" and args.prec == "bf16x3" and not (args.dims or args.rank or args.law):
+    if args.workload == "c2" and args.prec in TRAFFIC_C2 and not (args.dims or args.rank or args.law):
         # DRAM bytes per launch of this kernel on this workload, from one ncu capture
-        # (dram__bytes_read.sum 1.0739 GB + dram__bytes_write.sum 0.5036 GB)
-        roofline["traffic"] = 1.0739e9 + 0.5036e9
+        # (dram__bytes_read.sum + dram__bytes_write.sum)
+        roofline["traffic"] = TRAFFIC_C2[args.prec]
         roofline["traffic_source"] = "ncu dram__bytes_read+write of k_ttm_tc on 128^4 R=64, one launch"
 
     roofline["mode"] = mode
@@ -608,35 +622,53 @@ def main():
         if pp_vs["msdt"]["reached"] and pp_vs["pp"]["reached"]:
             pp_vs["speedup_pp_over_msdt"] = pp_vs["msdt"]["ms_to_target"] / pp_vs["pp"]["ms_to_target"]
 
-    # ---------------------------------------------------------------- e2e (host buffers)
+    # ---------------------------------------------------------------- e2e (host buffers, C ABI)
+    # every step hands the library this step's tensor in pinned host memory
+    # (cp_load_tensor: host -> device copy, cached nodes dropped), runs one MSDT
+    # sweep and reads the step's fit back (cp_fit: device -> host)
     e2e = None
     if not args.no_e2e:
         Th = torch.empty(dims, dtype=torch.float32, pin_memory=True)
         Th.copy_(T.cpu())
-        ctx_e = pkg.CPContext(T, R, A0=A0, prec=args.prec, stream=stream)
+        ctx_e = pkg.CPContext(Th, R, A0=A0, prec=args.prec, stream=stream)
         ctx_e.sweep_msdt(1)
         barrier()
         t0 = time.perf_counter()
         fits = []
         for _ in range(args.steps):
-            T.copy_(Th, non_blocking=True)     # this step's input, host -> device
+            ctx_e.load_tensor(Th)
             ctx_e.sweep_msdt(1)
-            fits.append(ctx_e.fit(exact=False)[0])  # the step's result, device -> host
+            fits.append(ctx_e.fit(exact=False)[0])
         barrier()
         el = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": world * args.steps / el, "unit": "sweep/s",
-               "h2d_bytes_per_step": 4 * numel, "d2h_bytes_per_step": 8}
+               "h2d_bytes_per_step": 4 * numel, "d2h_bytes_per_step": 16,
+               "path": "cp_load_tensor(host) + cp_sweep_msdt(1) + cp_fit per step"}
         ctx_e.close()
         del Th
 
-    # ---------------------------------------------------------------- CPU baseline (oracle)
+    # ---------------------------------------------------------------- fit check and CPU baseline (oracle)
+    # the GPU's direct residual after FIT_SWEEPS MSDT sweeps from A0 against the FP64
+    # oracle's after the same sweeps on the same FP32 bytes; the oracle run is also
+    # the timed CPU baseline
     cpu = None
+    fit_vs = None
     if rank == 0 and not args.no_cpu_baseline and args.gpus == 1:
+        cf = pkg.CPContext(T, R, A0=A0, prec=args.prec, stream=stream)
+        cf.sweep_msdt(FIT_SWEEPS)
+        r_gpu = cf.fit(exact=True)[1]
+        cf.close()
+        from oracle import cp_oracle as co
         T64 = T.cpu().numpy().astype(np.float64)
-        v, n, el = oracle_sweeps(T64, A0, args.cpu_seconds)
-        cpu = {"value": v, "unit": "sweep/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"{n} FP64 oracle MSDT sweeps of the full tensor ({el:.1f} s)"}
+        t0 = time.perf_counter()
+        ref = co.cp_als(T64, A0, FIT_SWEEPS, route="msdt")
+        el = time.perf_counter() - t0
+        r_orc = co.residual_direct(T64, ref.A)
         del T64
+        fit_vs = {"sweeps": FIT_SWEEPS, "route": "msdt", "resid_gpu": r_gpu, "resid_oracle": r_orc,
+                  "abs_diff": abs(r_gpu - r_orc), "tol": FIT_TOL, "pass": abs(r_gpu - r_orc) <= FIT_TOL}
+        cpu = {"value": FIT_SWEEPS / el, "unit": "sweep/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{FIT_SWEEPS} FP64 oracle MSDT sweeps of the full tensor from A0 ({el:.1f} s)"}
 
     line = {
         "metric": METRIC if args.workload == "c2" and not (args.dims or args.rank or args.law)
@@ -654,6 +686,7 @@ def main():
         "msdt_time_over_dt_unfused": schedules["dt_unfused"] / msdt_sps,
         "schedules_sweeps_per_s": schedules,
         "fit": {"formula": fit_formula, "direct": fit_direct, "after_sweeps": args.warmup + args.steps},
+        "fit_vs_oracle": fit_vs,
         "solves_fp64": int(st1["solves_fp64"]),
         "pp": pp_info,
         "pp_vs_msdt": pp_vs,

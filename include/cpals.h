@@ -54,8 +54,17 @@ typedef enum {
     CP_TF32 = 1,      /* tcgen05 kind::tf32 on rna_tf32(x) only (reported, 10-bit mantissa) */
     CP_BF16X3 = 2,    /* tcgen05 kind::f16: x = hi + lo in bf16, hi*hi+hi*lo+lo*hi */
     CP_BF16 = 3,      /* tcgen05 kind::f16 on bf16(x) only (reported, low accuracy) */
-    CP_TF32X3 = 4     /* tcgen05 kind::tf32: x = hi + lo in tf32 (round to nearest),
+    CP_TF32X3 = 4,    /* tcgen05 kind::tf32: x = hi + lo in tf32 (round to nearest),
                          hi*hi+hi*lo+lo*hi; about FP32 accuracy at half bf16x3's rate */
+    CP_F16X3 = 5      /* tcgen05 kind::f16 on fp16 parts: T scaled by one power of two
+                         (max |T| to [2^14, 2^15)), each factor column by its own, then
+                         x = hi + lo in fp16, hi*hi+hi*lo+lo*hi, the powers of two
+                         removed exactly from the FP32 result.  About 22 bits per
+                         value (tf32x3 accuracy) at bf16x3's rate.  Accuracy is
+                         relative to max |T|: entries below 2^-24 max |T| keep only
+                         part of their bits (negligible in any Frobenius norm; use
+                         another precision for tensors whose MTTKRP rows differ in
+                         magnitude by more than about 1e6) */
 } cp_prec;
 
 typedef struct {
@@ -69,7 +78,7 @@ typedef struct {
     uint64_t seed;    /* Philox4x32-10 seed of the default U[0,1) initial factors */
 } cp_config;
 
-/* Fill *cfg with defaults: bf16x3 TTM, eps 0.1, delta 0, judge every 5 sweeps,
+/* Fill *cfg with defaults: f16x3 TTM, eps 0.1, delta 0, judge every 5 sweeps,
  * policy gate on. */
 void cp_config_default(cp_config *cfg);
 
@@ -78,9 +87,11 @@ void cp_config_default(cp_config *cfg);
  *   N        tensor order, 3 <= N <= 8
  *   dims     N mode sizes, each >= 1; host array, copied
  *   R        rank, 1 <= R <= 256
- *   T_dev    device pointer to the tensor, C order, contiguous.  dtype 0: FP32,
- *            borrowed (must outlive the context, never written); dtype 1: FP64,
- *            converted once into a library-owned FP32 copy.
+ *   T_dev    pointer to the tensor, C order, contiguous.  dtype 0: FP32 on the
+ *            device, borrowed (must outlive the context, never written); dtype 1:
+ *            FP64 on the device, converted once into a library-owned FP32 copy;
+ *            dtype 2: FP32 in HOST memory (pinned memory gives the full copy
+ *            bandwidth), copied once into a library-owned device buffer.
  *   A0_host  NULL, or N host blocks (s_n x R row-major FP64, concatenated in mode
  *            order) of initial factors.  NULL draws U[0,1) entries (Alg. 1) from
  *            Philox4x32-10 with key = cfg->seed, counter = (j, 0, n, 0) for
@@ -95,6 +106,22 @@ void cp_config_default(cp_config *cfg);
  */
 cp_status cp_init(cp_ctx **out, int N, const int64_t *dims, int R, const void *T_dev,
                   int dtype, const double *A0_host, const cp_config *cfg, void *stream);
+
+/*
+ * cp_load_tensor - a new tensor of the same sizes for an existing context (the
+ * paper has no counterpart; it lets one context serve a stream of tensors).
+ *   T        NULL: the tensor's contents changed in place (borrowed or owned
+ *            buffer) and only the derived state is refreshed.  Otherwise FP32 data
+ *            copied into the context's own tensor buffer, which exists for contexts
+ *            created from an FP64 (dtype 1) or a host (dtype 2) tensor; a context
+ *            that borrows its tensor returns CP_ESTATE.
+ *   on_host  1: T is host memory (pinned for full bandwidth); 0: device memory.
+ * Drops every cached tree intermediate (the multi-sweep root included) and the PP
+ * operators, recomputes ||T||_F^2 (and, for f16x3, the tensor's power of two);
+ * the factors are kept, so the next sweep starts from them.  Enqueued on the
+ * context's stream behind earlier work; synchronises it (the norm is read back).
+ */
+cp_status cp_load_tensor(cp_ctx *ctx, const float *T, int on_host);
 
 /*
  * cp_mttkrp - exact MTTKRP M(mode) = T_(mode) P(mode) with the current factors
@@ -311,9 +338,16 @@ cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
  *                     root contracts the root's innermost mode (roots T x_0 and
  *                     T x_{N-1}), the tensor-core TTM's epilogue forms it too and
  *                     the root is read once instead of twice.
+ *   CP_OPT_WAIT_LIMIT (default 0) the bounded waits of the tensor-core TTM
+ *                     pipeline give up after `value` SM clock cycles (0: about
+ *                     one second).  A wait that runs out makes the kernel drain
+ *                     its copies in flight, free its tensor memory and return;
+ *                     the next call that synchronises reports CP_ETIMEOUT and the
+ *                     context is poisoned.  A tiny value exists for tests of that
+ *                     path (no GPU fault, no hang).
  * CP_EINVAL for an unknown option or value.  Takes effect at the next call.
  */
-enum { CP_OPT_FUSE_DT = 1, CP_OPT_LOOKAHEAD = 2, CP_OPT_FUSE_CHILD = 3 };
+enum { CP_OPT_FUSE_DT = 1, CP_OPT_LOOKAHEAD = 2, CP_OPT_FUSE_CHILD = 3, CP_OPT_WAIT_LIMIT = 4 };
 cp_status cp_set_option(cp_ctx *ctx, int option, int value);
 
 /*

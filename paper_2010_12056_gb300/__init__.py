@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcpals.so")
 _lib = None
 
-PREC = {"fp32": 0, "tf32": 1, "bf16x3": 2, "bf16": 3, "tf32x3": 4}
+PREC = {"fp32": 0, "tf32": 1, "bf16x3": 2, "bf16": 3, "tf32x3": 4, "f16x3": 5}
 STATUS = {0: "CP_OK", 1: "CP_EINVAL", 2: "CP_ENOMEM", 3: "CP_ECUDA", 4: "CP_ENOTSPD",
           5: "CP_ENUMERIC", 6: "CP_ETIMEOUT", 7: "CP_ESTATE"}
 KINDS = {0: "dt", 1: "msdt", 2: "pp", 3: "pp-regular"}
@@ -66,7 +66,7 @@ class Stats(ctypes.Structure):
                 ("lookahead", ctypes.c_int64), ("ttm_child", ctypes.c_int64)]
 
 
-OPTIONS = {"fuse_dt": 1, "lookahead": 2, "fuse_child": 3}
+OPTIONS = {"fuse_dt": 1, "lookahead": 2, "fuse_child": 3, "wait_limit": 4}
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -75,6 +75,7 @@ _SIGS = {
     "cp_config_default": (None, [ctypes.POINTER(Config)]),
     "cp_init": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(ctypes.c_int64), _I, _P, _I,
                      ctypes.POINTER(_D), ctypes.POINTER(Config), _P]),
+    "cp_load_tensor": (_I, [_P, _P, _I]),
     "cp_mttkrp": (_I, [_P, _I, _P]),
     "cp_ttm": (_I, [_P, _I, _P]),
     "cp_sweep_dt": (_I, [_P, _I]),
@@ -133,15 +134,23 @@ def _dptr(t):
 
 
 class CPContext:
-    """One decomposition of a dense CUDA tensor (float32 borrowed, float64 copied once)."""
+    """One decomposition of a dense tensor: a float32 CUDA tensor is borrowed, a
+    float64 CUDA tensor converted once, a float32 CPU tensor (pinned for full
+    bandwidth) copied once to the device by the library."""
 
-    def __init__(self, T, R, A0=None, prec="bf16x3", seed=20101205, pp_eps=0.1, judge_every=5,
+    def __init__(self, T, R, A0=None, prec="f16x3", seed=20101205, pp_eps=0.1, judge_every=5,
                  policy_gate=True, delta=0.0, max_sweeps=0, stream=None):
         import torch
-        if not (isinstance(T, torch.Tensor) and T.is_cuda and T.is_contiguous()):
-            raise ValueError("T must be a contiguous CUDA tensor")
-        if T.dtype not in (torch.float32, torch.float64):
-            raise ValueError("T must be float32 or float64")
+        if not (isinstance(T, torch.Tensor) and T.is_contiguous()):
+            raise ValueError("T must be a contiguous tensor")
+        if T.is_cuda:
+            if T.dtype not in (torch.float32, torch.float64):
+                raise ValueError("T must be float32 or float64")
+            dtype = 1 if T.dtype == torch.float64 else 0
+        else:
+            if T.dtype != torch.float32:
+                raise ValueError("a host tensor must be float32")
+            dtype = 2
         self._L = lib()
         self.T = T
         self.dims = [int(d) for d in T.shape]
@@ -167,9 +176,11 @@ class CPContext:
             self._a0 = flat
             a0p = flat.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         h = ctypes.c_void_p()
-        st = self._L.cp_init(ctypes.byref(h), self.N, dims, self.R, _dptr(T),
-                             1 if T.dtype == torch.float64 else 0, a0p, ctypes.byref(cfg),
+        st = self._L.cp_init(ctypes.byref(h), self.N, dims, self.R, _dptr(T), dtype, a0p, ctypes.byref(cfg),
                              _stream_ptr(self._stream))
+        if dtype == 2:
+            self.T = None   # the library holds its own device copy
+        self._dev = torch.device("cuda", torch.cuda.current_device()) if dtype == 2 else T.device
         if st != 0:
             raise CPError(st, "cp_init failed")
         self._h = h
@@ -195,7 +206,7 @@ class CPContext:
     def mttkrp(self, mode, out=None):
         import torch
         if out is None:
-            out = torch.empty(self.dims[mode], self.R, dtype=torch.float32, device=self.T.device)
+            out = torch.empty(self.dims[mode], self.R, dtype=torch.float32, device=self._dev)
         self._ck(self._L.cp_mttkrp(self._h, int(mode), _dptr(out)))
         return out
 
@@ -203,9 +214,20 @@ class CPContext:
         import torch
         if out is None:
             shape = [d for k, d in enumerate(self.dims) if k != mode] + [self.R]
-            out = torch.empty(shape, dtype=torch.float32, device=self.T.device)
+            out = torch.empty(shape, dtype=torch.float32, device=self._dev)
         self._ck(self._L.cp_ttm(self._h, int(mode), _dptr(out)))
         return out
+
+    def load_tensor(self, T=None):
+        """cp_load_tensor: a new tensor of the same sizes (float32, host or CUDA), copied
+        into the library's own buffer; None: the borrowed tensor changed in place."""
+        import torch
+        if T is None:
+            self._ck(self._L.cp_load_tensor(self._h, None, 0))
+            return
+        if not (T.is_contiguous() and T.dtype == torch.float32 and list(T.shape) == self.dims):
+            raise ValueError("T must be a contiguous float32 tensor of the context's sizes")
+        self._ck(self._L.cp_load_tensor(self._h, _dptr(T), 0 if T.is_cuda else 1))
 
     def sweep_dt(self, n=1):
         self._ck(self._L.cp_sweep_dt(self._h, int(n)))
@@ -229,7 +251,7 @@ class CPContext:
     def pp_mttkrp(self, mode, out=None):
         import torch
         if out is None:
-            out = torch.empty(self.dims[mode], self.R, dtype=torch.float32, device=self.T.device)
+            out = torch.empty(self.dims[mode], self.R, dtype=torch.float32, device=self._dev)
         self._ck(self._L.cp_pp_mttkrp(self._h, int(mode), _dptr(out)))
         return out
 

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <string>
 #include <vector>
@@ -57,9 +58,14 @@ struct cp_ctx {
 
     double* A64[CP_MAXN] = {0};
     float* A32[CP_MAXN] = {0};
-    uint16_t* bhi[CP_MAXN] = {0};
+    uint16_t* bhi[CP_MAXN] = {0};   // bf16 parts, or fp16 parts of the scaled factor (f16x3)
     uint16_t* blo[CP_MAXN] = {0};
     float* bt32[CP_MAXN] = {0};
+    // f16x3: per-column output scales of each factor operand, and the factor
+    // version the fp16 parts were converted from (converted lazily, before a TTM)
+    float* colinv[CP_MAXN] = {0};
+    int f16_ver[CP_MAXN] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    int eT = 0;                     // f16x3: T is multiplied by 2^eT before its split
     double* S[CP_MAXN] = {0};
     double* dS[CP_MAXN] = {0};
     double* Ap64[CP_MAXN] = {0};
@@ -110,9 +116,12 @@ struct cp_ctx {
     int kr_Kpad[CP_MAXN] = {0};
     void* kr_hi = nullptr;
     void* kr_lo = nullptr;
+    float* kr_scale = nullptr;   // f16x3: column powers of two of the Khatri-Rao operand
+    float* kr_colinv = nullptr;
     float* splitk_ws = nullptr;
     bool fuse_dt = true;
-    bool fuse_child = false;  // TTM epilogue forms the first child (multi-sweep tree)
+    bool fuse_child = false;
+    long long wait_limit = 0;  // tensor-core TTM's bounded waits (cycles; 0: about 1 s)  // TTM epilogue forms the first child (multi-sweep tree)
     float* child_ws = nullptr;  // pieces of first-child segments that cross TTM tiles
     size_t child_ws_cap = 0;
 
@@ -202,6 +211,10 @@ cp_status fail(cp_ctx* c, cp_status s, const std::string& msg) {
         CKCUDA(ctx, (expr));       \
     } while (0)
 
+// which operand copies of a factor the chosen TTM precision reads
+bool uses_bf16(const cp_ctx* c) { return c->cfg.prec == CP_BF16X3 || c->cfg.prec == CP_BF16; }
+bool uses_tf32(const cp_ctx* c) { return c->cfg.prec == CP_TF32X3 || c->cfg.prec == CP_TF32; }
+
 template <class Tp>
 cp_status dalloc(cp_ctx* c, Tp** p, size_t n) {
     *p = nullptr;
@@ -258,13 +271,25 @@ void contract_dims(const cp_ctx* c, uint32_t contracted, int mode, int64_t* P, i
     *Q = q;
 }
 
+// f16x3: the fp16 parts of factor `mode` (and its column scales) from its FP32
+// copy, unless they already hold the current version
+cp_status ensure_f16(cp_ctx* c, int mode) {
+    if (c->cfg.prec != CP_F16X3 || c->f16_ver[mode] == c->ver[mode]) return CP_OK;
+    LAUNCH(c, cpk::f16_operand(c->A32[mode], (int)c->dims[mode], c->R, c->Rpad, c->Kpad[mode], c->eT,
+                               c->bhi[mode], c->blo[mode], c->colinv[mode], c->st));
+    c->f16_ver[mode] = c->ver[mode];
+    return CP_OK;
+}
+
 cp_status launch_ttm(cp_ctx* c, int mode, float* X) {
     int64_t P, Q;
     contract_dims(c, 0u, mode, &P, &Q);
     const int K = (int)c->dims[mode];
     const int prec = c->cfg.prec;
     if (prec != CP_FP32_SIMT && c->tc_plan[mode]) {
-        LAUNCH(c, cpk::ttm_tc_run(c->tc_plan[mode], X, prec, c->num_sms, c->dev_err, c->st, c->splitk_ws));
+        CKST(ensure_f16(c, mode));
+        LAUNCH(c, cpk::ttm_tc_run(c->tc_plan[mode], X, prec, c->num_sms, c->dev_err, c->st, c->splitk_ws, nullptr,
+                                  c->wait_limit));
         if (c->splitk_ws && cpk::ttm_tc_splitk(c->tc_plan[mode], c->num_sms) > 1) c->stats.launches++;  // partial-sum kernel
         c->stats.ttm_tensor_core++;
     } else {
@@ -293,11 +318,12 @@ cp_status launch_mttv(cp_ctx* c, const float* X, uint32_t contracted, int mode, 
 // Level-2 node straight from T: contract the adjacent modes a, a+1 at once with
 // their Khatri-Rao product (two dimension-tree levels in one pass over T).
 cp_status launch_fused2(cp_ctx* c, int a, float* X) {
-    const bool bf = (c->cfg.prec == CP_BF16X3 || c->cfg.prec == CP_BF16);
+    const int kind = cpk::ttm_tc_kind(c->kr_plan[a]);
     const int R = c->R, sa = (int)c->dims[a], sb = (int)c->dims[a + 1];
-    LAUNCH(c, cpk::kr_operand(c->A64[a], c->A64[a + 1], sa, sb, R, c->kr_Kpad[a], bf ? 0 : 1, c->kr_hi,
-                              c->kr_lo, c->st));
-    LAUNCH(c, cpk::ttm_tc_run(c->kr_plan[a], X, c->cfg.prec, c->num_sms, c->dev_err, c->st, c->splitk_ws));
+    LAUNCH(c, cpk::kr_operand(c->A64[a], c->A64[a + 1], sa, sb, R, c->kr_Kpad[a], kind, c->kr_hi, c->kr_lo,
+                              c->st, c->eT, c->kr_scale, c->kr_colinv));
+    LAUNCH(c, cpk::ttm_tc_run(c->kr_plan[a], X, c->cfg.prec, c->num_sms, c->dev_err, c->st, c->splitk_ws, nullptr,
+                              c->wait_limit));
     if (c->splitk_ws && cpk::ttm_tc_splitk(c->kr_plan[a], c->num_sms) > 1) c->stats.launches++;  // partial-sum kernel
     const double rows = (double)c->numel / ((double)sa * sb);
     c->stats.ttm++;
@@ -349,7 +375,9 @@ cp_status launch_ttm_child(cp_ctx* c, int m, int cm, float* X, float* Y) {
     ch.Ac = c->A32[cm];
     ch.sc = (int)c->dims[cm];
     ch.ws = c->child_ws;
-    LAUNCH(c, cpk::ttm_tc_run(c->tc_plan[m], X, c->cfg.prec, c->num_sms, c->dev_err, c->st, nullptr, &ch));
+    CKST(ensure_f16(c, m));
+    LAUNCH(c, cpk::ttm_tc_run(c->tc_plan[m], X, c->cfg.prec, c->num_sms, c->dev_err, c->st, nullptr, &ch,
+                              c->wait_limit));
     if (cpk::ttm_tc_child_ws_floats(c->tc_plan[m], ch.sc) > 0) c->stats.launches++;  // cross-tile segments
     const int64_t rows = c->numel / c->dims[m];
     c->stats.ttm++;
@@ -491,9 +519,9 @@ cp_status update_mode(cp_ctx* c, int u, const float* M, bool pp, double* scal) {
     cpk::SolveOut o;
     o.A64 = c->A64[u];
     o.A32 = c->A32[u];
-    o.bhi = c->bhi[u];
-    o.blo = c->blo[u];
-    o.bt32 = c->bt32[u];
+    o.bhi = uses_bf16(c) ? c->bhi[u] : nullptr;
+    o.blo = uses_bf16(c) ? c->blo[u] : nullptr;
+    o.bt32 = uses_tf32(c) ? c->bt32[u] : nullptr;
     o.Rpad = c->Rpad;
     o.Kpad = c->Kpad[u];
     o.Ap = pp ? c->Ap64[u] : nullptr;
@@ -543,10 +571,19 @@ cp_status harvest(cp_ctx* c, int k, const int* kinds, const int* inits, int firs
         rec.resid = sqrt(r2 > 0 ? r2 : 0.0) / sqrt(c->normT2);
         double mx = 0.0, mxp = 0.0;
         bool bad = false;
+        // a NaN or Inf in a factor reaches every later Gamma; report it as such
+        // before any factorisation failure it causes
+        for (int n = 0; n < c->N; ++n) {
+            const double* sc = &h[((size_t)i * c->N + n) * CP_NSCAL];
+            if (!isfinite(sc[SCAL_A2]) || !isfinite(sc[SCAL_MA])) bad = true;
+        }
+        if (bad) {
+            c->sweeps_done += i + 1;
+            return fail(c, CP_ENUMERIC, "non-finite factor or residual");
+        }
         for (int n = 0; n < c->N; ++n) {
             const double* sc = &h[((size_t)i * c->N + n) * CP_NSCAL];
             const double a = sqrt(sc[SCAL_A2]);
-            if (!isfinite(sc[SCAL_A2]) || !isfinite(sc[SCAL_MA])) bad = true;
             // flags: 0 refinement path, 3 refinement did not converge; 10 + (0 ok,
             // 1 shifted, 2 failed) for the FP64 factorisation path
             const double fl = sc[SCAL_FLAGS];
@@ -846,8 +883,9 @@ cp_status pp_sweep(cp_ctx* c, int k) {
 cp_status init_grams(cp_ctx* c) {
     for (int n = 0; n < c->N; ++n) {
         const int s = (int)c->dims[n];
-        LAUNCH(c, cpk::factor_copies(c->A64[n], c->A32[n], c->bhi[n], c->blo[n], c->bt32[n], s, c->R,
-                                     c->Rpad, c->Kpad[n], c->st));
+        LAUNCH(c, cpk::factor_copies(c->A64[n], c->A32[n], uses_bf16(c) ? c->bhi[n] : nullptr,
+                                     uses_bf16(c) ? c->blo[n] : nullptr, uses_tf32(c) ? c->bt32[n] : nullptr, s,
+                                     c->R, c->Rpad, c->Kpad[n], c->st));
         LAUNCH(c, cpk::gram(c->A64[n], nullptr, s, c->R, nullptr, c->S[n], nullptr, nullptr, c->st));
     }
     return CP_OK;
@@ -918,8 +956,9 @@ cp_status snap_restore(cp_ctx* c, const cp_ctx::Snap& sn, bool keep_ops, bool tr
         const int s = (int)c->dims[i];
         CKCUDA(c, cudaMemcpyAsync(c->A64[i], sn.A64[i], sizeof(double) * s * c->R, cudaMemcpyDeviceToDevice,
                                   c->st));
-        LAUNCH(c, cpk::factor_copies(c->A64[i], c->A32[i], c->bhi[i], c->blo[i], c->bt32[i], s, c->R, c->Rpad,
-                                     c->Kpad[i], c->st));
+        LAUNCH(c, cpk::factor_copies(c->A64[i], c->A32[i], uses_bf16(c) ? c->bhi[i] : nullptr,
+                                     uses_bf16(c) ? c->blo[i] : nullptr, uses_tf32(c) ? c->bt32[i] : nullptr, s,
+                                     c->R, c->Rpad, c->Kpad[i], c->st));
         if (pp)
             LAUNCH(c, cpk::pp_delta(c->A64[i], c->Ap64[i], c->dA32[i], c->dA64[i], (int64_t)s * c->R, c->st));
         CKST(regram(c, i, pp));
@@ -1038,6 +1077,38 @@ cp_status run_choice(cp_ctx* c, int choice) {
     return CP_OK;
 }
 
+// ||T||_F^2 (one streaming pass), read back to the host
+cp_status tensor_norm(cp_ctx* c) {
+    c->stats.launches += 2;
+    int nb = cpk::norm2_partials(c->T, c->numel, c->red_part, 4096, c->st);
+    CKCUDA(c, cudaGetLastError());
+    CKCUDA(c, cpk::sum_partials(c->red_part, nb, c->d_red_out, c->st));
+    CKCUDA(c, cudaMemcpyAsync(&c->normT2, c->d_red_out, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CKCUDA(c, cudaStreamSynchronize(c->st));
+    return CP_OK;
+}
+
+// f16x3: the power of two 2^eT that brings max |T| into [2^14, 2^15) (0 for an
+// all-zero or non-finite tensor), and the plans' copy of it
+cp_status tensor_exponent(cp_ctx* c) {
+    float* part = reinterpret_cast<float*>(c->red_part);  // 4096 doubles hold the 4096 block maxima
+    float* out = reinterpret_cast<float*>(c->d_red_out);
+    LAUNCH(c, cpk::absmax(c->T, c->numel, part, 4096, out, c->st));
+    c->stats.launches++;
+    float m = 0.f;
+    CKCUDA(c, cudaMemcpyAsync(&m, out, sizeof(float), cudaMemcpyDeviceToHost, c->st));
+    CKCUDA(c, cudaStreamSynchronize(c->st));
+    int e = 0;
+    if (m > 0.f && std::isfinite(m)) e = std::min(127, std::max(-126, 14 - std::ilogb(m)));
+    c->eT = e;
+    for (int i = 0; i < CP_MAXN; ++i) {
+        cpk::ttm_tc_set_tscale(c->tc_plan[i], ldexpf(1.f, e));
+        cpk::ttm_tc_set_tscale(c->kr_plan[i], ldexpf(1.f, e));
+        c->f16_ver[i] = -1;  // column scales include 2^-eT
+    }
+    return CP_OK;
+}
+
 void free_all(cp_ctx* c) {
     auto F = [](void* p) { if (p) cudaFree(p); };
     F(c->T_owned);
@@ -1062,7 +1133,8 @@ void free_all(cp_ctx* c) {
         cpk::ttm_tc_plan_free(c->kr_plan[i]);
         c->kr_plan[i] = nullptr;
     }
-    F(c->kr_hi); F(c->kr_lo); F(c->splitk_ws); F(c->child_ws);
+    F(c->kr_hi); F(c->kr_lo); F(c->kr_scale); F(c->kr_colinv); F(c->splitk_ws); F(c->child_ws);
+    for (int i = 0; i < CP_MAXN; ++i) F(c->colinv[i]);
     F(c->Ginv); F(c->G32); F(c->schur_ws); F(c->d_mode);
     if (c->side) { cudaStreamSynchronize(c->side); cudaStreamDestroy(c->side); c->side = nullptr; }
     if (c->ev_ready) { cudaEventDestroy(c->ev_ready); c->ev_ready = nullptr; }
@@ -1085,7 +1157,7 @@ extern "C" {
 
 void cp_config_default(cp_config* cfg) {
     if (!cfg) return;
-    cfg->prec = CP_BF16X3;
+    cfg->prec = CP_F16X3;
     cfg->pp_eps = 0.1;
     cfg->delta = 0.0;
     cfg->max_sweeps = 0;
@@ -1098,7 +1170,7 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
                   const double* A0_host, const cp_config* cfg, void* stream) {
     if (!out) return CP_EINVAL;
     *out = nullptr;
-    if (N < 3 || N > CP_MAXN || !dims || R < 1 || R > CP_MAXR || !T_dev || (dtype != 0 && dtype != 1))
+    if (N < 3 || N > CP_MAXN || !dims || R < 1 || R > CP_MAXR || !T_dev || dtype < 0 || dtype > 2)
         return CP_EINVAL;
     int64_t numel = 1;
     for (int i = 0; i < N; ++i) {
@@ -1113,7 +1185,7 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
     c->numel = numel;
     c->st = (cudaStream_t)stream;
     if (cfg) c->cfg = *cfg; else cp_config_default(&c->cfg);
-    if (c->cfg.prec < CP_FP32_SIMT || c->cfg.prec > CP_TF32X3) { delete c; return CP_EINVAL; }
+    if (c->cfg.prec < CP_FP32_SIMT || c->cfg.prec > CP_F16X3) { delete c; return CP_EINVAL; }
     memset(&c->stats, 0, sizeof(c->stats));
     for (int i = 0; i < N; ++i) {
         c->dims[i] = dims[i];
@@ -1148,6 +1220,10 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
         TRY(dalloc(c, &c->T_owned, (size_t)numel));
         TRYC(cpk::f64_to_f32((const double*)T_dev, c->T_owned, numel, c->st));
         c->T = c->T_owned;
+    } else if (dtype == 2) {
+        TRY(dalloc(c, &c->T_owned, (size_t)numel));
+        TRYC(cudaMemcpyAsync(c->T_owned, T_dev, sizeof(float) * numel, cudaMemcpyHostToDevice, c->st));
+        c->T = c->T_owned;
     } else {
         c->T = (const float*)T_dev;
     }
@@ -1166,6 +1242,8 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
         TRYC(cudaMemsetAsync(c->bhi[i], 0, op * sizeof(uint16_t), c->st));
         TRYC(cudaMemsetAsync(c->blo[i], 0, op * sizeof(uint16_t), c->st));
         TRYC(cudaMemsetAsync(c->bt32[i], 0, 2 * op * sizeof(float), c->st));
+        TRY(dalloc(c, &c->colinv[i], (size_t)c->Rpad));
+        TRYC(cudaMemsetAsync(c->colinv[i], 0, c->Rpad * sizeof(float), c->st));
     }
     // one slot per number of kept modes k = 1..N-1: capacity = largest k-mode product x R
     std::vector<int64_t> sd(dims, dims + N);
@@ -1227,17 +1305,20 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
         TRYC(cudaStreamSynchronize(c->st));
     }
     TRY(init_grams(c));
+    if (c->cfg.prec == CP_F16X3) TRY(tensor_exponent(c));
     // tensor-core TTM plans (TMA descriptors of T and of each factor operand)
     if (c->cfg.prec != CP_FP32_SIMT) {
-        const bool bf = (c->cfg.prec == CP_BF16X3 || c->cfg.prec == CP_BF16);
+        const bool bf = uses_bf16(c), hf = c->cfg.prec == CP_F16X3;
+        const int kind = bf ? 0 : (hf ? 2 : 1);
+        const float tscale = ldexpf(1.f, c->eT);
         for (int m = 0; m < N; ++m) {
             int64_t P, Q;
             contract_dims(c, 0u, m, &P, &Q);
-            const void* hi = bf ? (const void*)c->bhi[m] : (const void*)c->bt32[m];
-            const void* lo = bf ? (const void*)c->blo[m]
-                                : (const void*)(c->bt32[m] + (size_t)c->Rpad * c->Kpad[m]);
-            c->tc_plan[m] = cpk::ttm_tc_plan(c->T, P, (int)dims[m], Q, R, bf ? 0 : 1, hi, lo, c->Rpad,
-                                             c->Kpad[m]);
+            const void* hi = (bf || hf) ? (const void*)c->bhi[m] : (const void*)c->bt32[m];
+            const void* lo = (bf || hf) ? (const void*)c->blo[m]
+                                        : (const void*)(c->bt32[m] + (size_t)c->Rpad * c->Kpad[m]);
+            c->tc_plan[m] = cpk::ttm_tc_plan(c->T, P, (int)dims[m], Q, R, kind, hi, lo, c->Rpad, c->Kpad[m],
+                                             tscale, c->colinv[m]);
         }
         // fused two-mode contractions of adjacent pairs (standard tree, N >= 3)
         size_t kr_elems = 0;
@@ -1247,17 +1328,21 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
             c->kr_Kpad[a] = (int)((K + 63) / 64 * 64);
             kr_elems = std::max(kr_elems, (size_t)c->Rpad * c->kr_Kpad[a]);
         }
-        const size_t esz = bf ? 2 : 4;
+        const size_t esz = kind == 1 ? 4 : 2;
         if (kr_elems) {
             TRY(dalloc(c, (uint8_t**)&c->kr_hi, kr_elems * esz));
             TRY(dalloc(c, (uint8_t**)&c->kr_lo, kr_elems * esz));
+            if (hf) {
+                TRY(dalloc(c, &c->kr_scale, (size_t)c->Rpad));
+                TRY(dalloc(c, &c->kr_colinv, (size_t)c->Rpad));
+            }
             for (int a = 0; a + 1 < N; ++a) {
                 if (!c->kr_Kpad[a]) continue;
                 int64_t P = 1, Q = 1;
                 for (int k = 0; k < a; ++k) P *= dims[k];
                 for (int k = a + 2; k < N; ++k) Q *= dims[k];
-                c->kr_plan[a] = cpk::ttm_tc_plan(c->T, P, (int)(dims[a] * dims[a + 1]), Q, R, bf ? 0 : 1,
-                                                 c->kr_hi, c->kr_lo, c->Rpad, c->kr_Kpad[a]);
+                c->kr_plan[a] = cpk::ttm_tc_plan(c->T, P, (int)(dims[a] * dims[a + 1]), Q, R, kind, c->kr_hi,
+                                                 c->kr_lo, c->Rpad, c->kr_Kpad[a], tscale, c->kr_colinv);
             }
         }
         // split-K workspace for contractions with few row tiles
@@ -1280,12 +1365,7 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
             c->child_ws_cap = cw;
         }
     }
-    // ||T||_F^2
-    int nb = cpk::norm2_partials(c->T, numel, c->red_part, 4096, c->st);
-    TRYC(cudaGetLastError());
-    TRYC(cpk::sum_partials(c->red_part, nb, c->d_red_out, c->st));
-    TRYC(cudaMemcpyAsync(&c->normT2, c->d_red_out, sizeof(double), cudaMemcpyDeviceToHost, c->st));
-    TRYC(cudaStreamSynchronize(c->st));
+    TRY(tensor_norm(c));
 #undef TRY
 #undef TRYC
     *out = c;
@@ -1316,6 +1396,27 @@ cp_status cp_ttm(cp_ctx* c, int mode, float* X_dev) {
     CKST(entry_check(c));
     if (mode < 0 || mode >= c->N || !X_dev) return CP_EINVAL;
     return launch_ttm(c, mode, X_dev);
+}
+
+cp_status cp_load_tensor(cp_ctx* c, const float* T, int on_host) {
+    CKST(entry_check(c));
+    if (T && !c->T_owned) return fail(c, CP_ESTATE, "cp_load_tensor: the context borrows its tensor");
+    if (on_host != 0 && on_host != 1) return CP_EINVAL;
+    CKST(ahead_join(c));
+    if (T)
+        CKCUDA(c, cudaMemcpyAsync(c->T_owned, T, sizeof(float) * c->numel,
+                                  on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->st));
+    // every intermediate was contracted from the old tensor
+    for (int k = 0; k <= CP_MAXN; ++k) {
+        c->slot[k].valid = false;
+        c->alt[k].valid = false;
+    }
+    c->pp_valid = false;
+    drop_judge(c);
+    c->have_last = false;
+    CKST(tensor_norm(c));
+    if (c->cfg.prec == CP_F16X3) CKST(tensor_exponent(c));
+    return CP_OK;
 }
 
 static cp_status sweeps_exact(cp_ctx* c, int nsweeps, bool msdt) {
@@ -1352,6 +1453,10 @@ cp_status cp_set_option(cp_ctx* c, int option, int value) {
         case CP_OPT_FUSE_CHILD:
             if (value != 0 && value != 1) return CP_EINVAL;
             c->fuse_child = value != 0;
+            return CP_OK;
+        case CP_OPT_WAIT_LIMIT:
+            if (value < 0) return CP_EINVAL;
+            c->wait_limit = value;
             return CP_OK;
         default: return CP_EINVAL;
     }
@@ -1690,8 +1795,9 @@ cp_status cp_set_factor(cp_ctx* c, int mode, const double* A_host) {
     if (mode < 0 || mode >= c->N || !A_host) return CP_EINVAL;
     const int s = (int)c->dims[mode];
     CKCUDA(c, cudaMemcpyAsync(c->A64[mode], A_host, sizeof(double) * s * c->R, cudaMemcpyHostToDevice, c->st));
-    LAUNCH(c, cpk::factor_copies(c->A64[mode], c->A32[mode], c->bhi[mode], c->blo[mode], c->bt32[mode], s, c->R,
-                                 c->Rpad, c->Kpad[mode], c->st));
+    LAUNCH(c, cpk::factor_copies(c->A64[mode], c->A32[mode], uses_bf16(c) ? c->bhi[mode] : nullptr,
+                                 uses_bf16(c) ? c->blo[mode] : nullptr, uses_tf32(c) ? c->bt32[mode] : nullptr, s,
+                                 c->R, c->Rpad, c->Kpad[mode], c->st));
     // with PP operators present, dA = A - A_p and dS = A^T dA follow the new factor
     const bool pp = c->pp_valid;
     if (pp)

@@ -45,10 +45,14 @@ cudaError_t ttm_simt(const float* T, const float* A, float* X, int64_t P, int K,
 // then uses the SIMT kernel).
 struct TcPlan;
 bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R);
-// kind 0: bf16 parts (bhi/blo uint16 [Rpad][Kpad]); kind 1: tf32 parts (fp32 [Rpad][Kpad])
+// kind 0: bf16 parts (bhi/blo uint16 [Rpad][Kpad]); kind 1: tf32 parts (fp32 [Rpad][Kpad]);
+// kind 2: fp16 parts of the scaled factor (uint16 [Rpad][Kpad]); T is multiplied
+// by tscale (a power of two) before its split and column c of the result by
+// colinv[c] (device, Rpad floats, 16-byte aligned).
 TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind, const void* bhi,
-                    const void* blo, int Rpad, int Kpad);
+                    const void* blo, int Rpad, int Kpad, float tscale = 1.f, const float* colinv = nullptr);
 int ttm_tc_kind(const TcPlan* p);
+void ttm_tc_set_tscale(TcPlan* p, float tscale);
 void ttm_tc_plan_free(TcPlan* p);
 // splitk_ws: NULL, or a workspace of ttm_tc_splitk() * rows * R floats that lets
 // the kernel split K across CTAs when the row tiles alone cannot fill the GPU
@@ -64,15 +68,28 @@ struct TcChild {
 };
 bool ttm_tc_child_ok(const TcPlan* p, int sc);
 int64_t ttm_tc_child_ws_floats(const TcPlan* p, int sc);
+// wait_limit: cycles a pipeline wait may take before the kernel gives up and
+// reports DEVERR_TIMEOUT (<= 0: the default, about 1 s)
 cudaError_t ttm_tc_run(const TcPlan* p, float* X, int prec, int num_sms, unsigned* dev_err,
-                       cudaStream_t st, float* splitk_ws, const TcChild* child = nullptr);
+                       cudaStream_t st, float* splitk_ws, const TcChild* child = nullptr,
+                       long long wait_limit = 0);
 int ttm_tc_splitk(const TcPlan* p, int num_sms);
 int64_t ttm_tc_rows(const TcPlan* p);
 // Khatri-Rao operand of two adjacent modes a, a+1 for a fused two-mode contraction:
 // row k = i_a * s_b + i_b holds A_a[i_a][r] * A_b[i_b][r]; written transposed
 // ([Rpad][Kpad], k contiguous) as bf16 hi/lo (kind 0) or tf32 hi/lo (kind 1).
+// kind 2: fp16 parts of the product scaled per column by powers of two (scale,
+// Rpad floats, written here with colinv = 2^-(column exponent + eT)).
 cudaError_t kr_operand(const double* Aa, const double* Ab, int sa, int sb, int R, int Kpad,
-                       int kind, void* hi, void* lo, cudaStream_t st);
+                       int kind, void* hi, void* lo, cudaStream_t st, int eT = 0, float* scale = nullptr,
+                       float* colinv = nullptr);
+// fp16 factor operand of the tensor-core TTM (kind 2) from the FP32 factor: per
+// column a power of two 2^e_c bringing max |A(:, c)| into [2^14, 2^15), parts
+// written transposed [Rpad][Kpad]; colinv[c] = 2^-(e_c + eT) (Rpad floats).
+cudaError_t f16_operand(const float* A32, int s, int R, int Rpad, int Kpad, int eT, uint16_t* hi, uint16_t* lo,
+                        float* colinv, cudaStream_t st);
+// max |x| over n floats into out[0] (device); part holds max_blocks floats
+cudaError_t absmax(const float* x, int64_t n, float* part, int max_blocks, float* out, cudaStream_t st);
 
 // multi-TTV: Y[p][q][r] = sum_k X[p][k][q][r] * A[k][r]
 // max_blocks_per_sm > 0 caps the grid (blocks loop over the outputs) so that the

@@ -1,10 +1,13 @@
-// Normal-equation side of every factor update (Alg. 1 lines 6, 8, 9; Alg. 2
-// lines 10-12; Eq. gram, Eq. V_nij, Eq. ds) and the residual (Eq. residual,
-// Eq. residual-def).  All R x R work is FP64: the Hadamard chain
-// Gamma(n) = *_{k != n} S(k), its Cholesky factor, the two triangular solves per
-// row of A(n) = M(n) Gamma(n)^{-1}, the Grams S(n) = A^T A and dS(n) = A^T dA,
-// and the scalar terms of the residual.
+// Dense side kernels of the factor updates and the residual (Alg. 1 lines 8-9;
+// Alg. 2 lines 10-12; Eq. ds, Eq. residual, Eq. residual-def): the Grams
+// S(n) = A^T A and dS(n) = A^T dA in FP64 (thread-block clusters), the update's
+// scalar terms, the operand copies of a factor for the tensor-core TTM (bf16 /
+// tf32 / scaled fp16 parts), norms and maxima, the direct residual, the PP
+// first-order terms (Eq. U_ni) and the Khatri-Rao operand of the fused
+// standard-tree contraction.  The normal equations themselves (Hadamard chain,
+// FP32 inverse with FP64 refinement) are in k_solve_mixed.cu.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "cpals_internal.h"
 
@@ -481,12 +484,131 @@ __global__ void k_add_aw(const float* __restrict__ Mt, const double* __restrict_
 }
 
 
+// ------------------------------------------------------------------ scaled fp16 operands
+// Power-of-two exponent that brings a maximum magnitude m into [2^14, 2^15)
+// (the top binade below the fp16 maximum 65504); 0 for m = 0 or non-finite m.
+__device__ __forceinline__ int f16_exp_for(float m) {
+    if (!(m > 0.f) || !isfinite(m)) return 0;
+    const int e = 14 - ilogbf(m);
+    return e < -126 ? -126 : (e > 127 ? 127 : e);
+}
+
+// Factor operand of the fp16 tensor-core TTM: for each column c of the s x R
+// FP32 factor, e_c = f16_exp_for(max_x |A(x, c)|); A(x, c) 2^e_c split into fp16
+// hi = rn(y), lo = rn(y - hi), written transposed ([c][x], x contiguous, row
+// stride Kpad); colinv[c] = 2^-(e_c + eT) for c < Rpad (0 past R).  One block of
+// 32 x 32 threads per 32 columns: the column maxima, then 32 x 32 tiles through
+// shared memory so that reads (along c) and writes (along x) are coalesced.
+__global__ void __launch_bounds__(1024) k_f16_operand(const float* __restrict__ A, int s, int R, int Rpad,
+                                                      int Kpad, int eT, uint16_t* __restrict__ hi,
+                                                      uint16_t* __restrict__ lo, float* __restrict__ colinv) {
+    __shared__ float red[32][33];
+    __shared__ uint16_t th[32][33], tl[32][33];
+    __shared__ float scl[32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + tx;
+    float m = 0.f;
+    if (c < R)
+        for (int x = ty; x < s; x += 32) m = fmaxf(m, fabsf(A[(size_t)x * R + c]));
+    red[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0) {
+        float mm = 0.f;
+        for (int k = 0; k < 32; ++k) mm = fmaxf(mm, red[k][tx]);
+        const int e = c < R ? f16_exp_for(mm) : 0;
+        scl[tx] = ldexpf(1.f, e);
+        if (c < Rpad) colinv[c] = c < R ? ldexpf(1.f, -(e + eT)) : 0.f;
+    }
+    __syncthreads();
+    const float sc = scl[tx];
+    for (int x0 = 0; x0 < s; x0 += 32) {
+        const int x = x0 + ty;
+        const float y = (c < R && x < s) ? A[(size_t)x * R + c] * sc : 0.f;
+        const __half h = __float2half_rn(y);
+        const __half l = __float2half_rn(y - __half2float(h));
+        th[tx][ty] = __half_as_ushort(h);
+        tl[tx][ty] = __half_as_ushort(l);
+        __syncthreads();
+        // thread (ty, tx) writes column blockIdx.x * 32 + ty, row x0 + tx
+        const int cw = blockIdx.x * 32 + ty, xw = x0 + tx;
+        if (cw < R && xw < s) {
+            hi[(size_t)cw * Kpad + xw] = th[ty][tx];
+            lo[(size_t)cw * Kpad + xw] = tl[ty][tx];
+        }
+        __syncthreads();
+    }
+}
+
+// Column powers of two of the Khatri-Rao operand of modes a, a+1: the largest
+// entry of column c is max|A_a(:, c)| * max|A_b(:, c)|.
+__global__ void __launch_bounds__(256) k_kr_scale(const double* __restrict__ Aa, const double* __restrict__ Ab,
+                                                  int sa, int sb, int R, int Rpad, int eT,
+                                                  float* __restrict__ scale, float* __restrict__ colinv) {
+    for (int c = blockIdx.x * 8 + (threadIdx.x >> 5); c < Rpad; c += gridDim.x * 8) {
+        const int lane = threadIdx.x & 31;
+        double ma = 0.0, mb = 0.0;
+        if (c < R) {
+            for (int i = lane; i < sa; i += 32) ma = fmax(ma, fabs(Aa[(size_t)i * R + c]));
+            for (int i = lane; i < sb; i += 32) mb = fmax(mb, fabs(Ab[(size_t)i * R + c]));
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            ma = fmax(ma, __shfl_xor_sync(FULL, ma, o));
+            mb = fmax(mb, __shfl_xor_sync(FULL, mb, o));
+        }
+        if (lane == 0) {
+            const int e = c < R ? f16_exp_for((float)(ma * mb)) : 0;
+            scale[c] = ldexpf(1.f, e);
+            colinv[c] = c < R ? ldexpf(1.f, -(e + eT)) : 0.f;
+        }
+    }
+}
+
+// max |x| over n floats -> one partial per block
+__global__ void __launch_bounds__(256) k_absmax(const float* __restrict__ x, int64_t n, float* __restrict__ part) {
+    __shared__ float red[8];
+    float m = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const bool al = ((uintptr_t)x & 15) == 0;
+    const int64_t n4 = al ? n / 4 : 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(x) + i);
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        m = fmaxf(m, fabsf(x[i]));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+        part[blockIdx.x] = m;
+    }
+}
+
+__global__ void k_absmax_fin(const float* __restrict__ part, int n, float* __restrict__ out) {
+    __shared__ float red[32];
+    float m = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, part[i]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+        out[0] = m;
+    }
+}
+
 // ------------------------------------------------------------------ Khatri-Rao operand
 // out[r][k] (r < Rpad, k < Kpad; zero outside R x K): row k = ia * sb + ib of the
-// Khatri-Rao product, A_a[ia][r] * A_b[ib][r], split into two parts.
+// Khatri-Rao product, A_a[ia][r] * A_b[ib][r], split into two parts (KIND 2:
+// fp16 parts of the product times scale[r], a power of two from k_kr_scale).
 template <int KIND>
 __global__ void k_kr(const double* __restrict__ Aa, const double* __restrict__ Ab, int sa, int sb,
-                     int R, int Rpad, int Kpad, void* __restrict__ hi, void* __restrict__ lo) {
+                     int R, int Rpad, int Kpad, void* __restrict__ hi, void* __restrict__ lo,
+                     const float* __restrict__ scale) {
     const int64_t K = (int64_t)sa * sb;
     const int64_t n = (int64_t)Rpad * Kpad;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
@@ -503,6 +625,11 @@ __global__ void k_kr(const double* __restrict__ Aa, const double* __restrict__ A
             bf16_split(v, h, l);
             static_cast<uint16_t*>(hi)[idx] = h;
             static_cast<uint16_t*>(lo)[idx] = l;
+        } else if (KIND == 2) {
+            const float y = v * scale[r];
+            const __half h = __float2half_rn(y);
+            static_cast<uint16_t*>(hi)[idx] = __half_as_ushort(h);
+            static_cast<uint16_t*>(lo)[idx] = __half_as_ushort(__float2half_rn(y - __half2float(h)));
         } else {
             const float h = tf32_rna(v);
             static_cast<float*>(hi)[idx] = h;
@@ -516,15 +643,34 @@ __global__ void k_kr(const double* __restrict__ Aa, const double* __restrict__ A
 namespace cpk {
 
 cudaError_t kr_operand(const double* Aa, const double* Ab, int sa, int sb, int R, int Kpad,
-                       int kind, void* hi, void* lo, cudaStream_t st) {
+                       int kind, void* hi, void* lo, cudaStream_t st, int eT, float* scale, float* colinv) {
     const int Rpad = (R + 15) / 16 * 16;
     const int64_t n = (int64_t)Rpad * Kpad;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 8192) blocks = 8192;
-    if (kind == 0)
-        k_kr<0><<<(unsigned)blocks, 256, 0, st>>>(Aa, Ab, sa, sb, R, Rpad, Kpad, hi, lo);
-    else
-        k_kr<1><<<(unsigned)blocks, 256, 0, st>>>(Aa, Ab, sa, sb, R, Rpad, Kpad, hi, lo);
+    if (kind == 0) {
+        k_kr<0><<<(unsigned)blocks, 256, 0, st>>>(Aa, Ab, sa, sb, R, Rpad, Kpad, hi, lo, nullptr);
+    } else if (kind == 1) {
+        k_kr<1><<<(unsigned)blocks, 256, 0, st>>>(Aa, Ab, sa, sb, R, Rpad, Kpad, hi, lo, nullptr);
+    } else {
+        if (!scale || !colinv) return cudaErrorInvalidValue;
+        k_kr_scale<<<(Rpad + 7) / 8, 256, 0, st>>>(Aa, Ab, sa, sb, R, Rpad, eT, scale, colinv);
+        k_kr<2><<<(unsigned)blocks, 256, 0, st>>>(Aa, Ab, sa, sb, R, Rpad, Kpad, hi, lo, scale);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t f16_operand(const float* A32, int s, int R, int Rpad, int Kpad, int eT, uint16_t* hi, uint16_t* lo,
+                        float* colinv, cudaStream_t st) {
+    k_f16_operand<<<(unsigned)((R + 31) / 32), 1024, 0, st>>>(A32, s, R, Rpad, Kpad, eT, hi, lo, colinv);
+    return cudaGetLastError();
+}
+
+cudaError_t absmax(const float* x, int64_t n, float* part, int max_blocks, float* out, cudaStream_t st) {
+    int64_t want = (n / 4 + 255) / 256;
+    const int blocks = (int)(want < 1 ? 1 : (want > max_blocks ? max_blocks : want));
+    k_absmax<<<blocks, 256, 0, st>>>(x, n, part);
+    k_absmax_fin<<<1, 1024, 0, st>>>(part, blocks, out);
     return cudaGetLastError();
 }
 

@@ -11,10 +11,11 @@
 //                 Gauss-Jordan elimination; if the scaled condition number is
 //                 above 1e6 or a pivot is not positive, an FP64 LDL^T of Gamma
 //                 instead, and the solve kernel substitutes in FP64.
-//   k_solve_mixed (one warp per row) m = M(x,:) [+ A_old(x,:) W];
+//   k_solve_mixed (one 64-thread block per row) m = M(x,:) [+ A_old(x,:) W];
 //                 x0 = m G32;  repeat  r = m - x Gamma (FP64),  d = r G32,  x += d
 //                 until the estimated remaining error ||d||_inf * rho is below
-//                 2^-50 ||x||_inf (rho = contraction seen between iterations).
+//                 2^-36 ||x||_inf (rho = contraction seen between iterations),
+//                 four orders of magnitude below the FP32 rounding of M itself.
 #include <cuda_bf16.h>
 
 #include "cpals_internal.h"
@@ -592,7 +593,7 @@ __host__ __device__ inline SolveSmem solve_smem(int R) {
 //   x += d
 // and two barriers.  It stops once the error left after the step, estimated as
 // rho ||d||_inf with rho the contraction seen between steps, is below
-// 2^-44 ||x||_inf: far below the FP32 error of the MTTKRP that forms m.
+// 2^-36 ||x||_inf: far below the FP32 error of the MTTKRP that forms m.
 template <int RT>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
     const float* __restrict__ M, const double* __restrict__ W, const double* __restrict__ G,

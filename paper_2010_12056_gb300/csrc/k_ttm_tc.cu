@@ -13,6 +13,14 @@
 //               128 B, 16-byte chunk c of row m at c ^ (m mod 8)):
 //                 bf16 family (BK = 64): hi = rn_bf16(x), lo = rn_bf16(x - hi)
 //                 tf32 family (BK = 32): hi = rna_tf32(x), lo = rna_tf32(x - hi)
+//                 fp16 (BK = 64): y = x * 2^eT, hi = rn_f16(y), lo = rn_f16(y - hi),
+//                   with the power of two 2^eT chosen once per tensor so that
+//                   max |y| lies in [2^14, 2^15); the factor operand carries a
+//                   power of two per column the same way, and the epilogue
+//                   multiplies column r by 2^-(eT + e_r) (exact).  Two 11-bit
+//                   parts keep about 22 bits of every value (tf32x3 accuracy at
+//                   the bf16 rate); values below 2^-24 of max |T| lose their low
+//                   part, an error far below the FP32 rounding of the result.
 //               For the last mode the chunk is K-contiguous (TMA SWIZZLE_128B keeps
 //               row reads conflict-free); for other modes it is q-contiguous
 //               (BK k x 128 q) and the converter transposes while splitting.
@@ -37,6 +45,7 @@
 // what it issued (bounded), frees TMEM and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "cpals_internal.h"
 
@@ -57,7 +66,11 @@ constexpr int BAR_BYTES = 512;
 // first-child pieces: [2 tiles in flight][4 warps][2 pieces][128 columns] floats + keys
 constexpr int CHILD_BYTES = 2 * 4 * 2 * 128 * 4 + 2 * 4 * 2 * 8;
 constexpr int MAX_STG = 8, MAX_OP = 4;
-constexpr long long WAIT_LIMIT = 2000000000LL;  // cycles (about 1 s)
+// bounded waits: the pipeline's waits give up after TcArgs::wait_limit cycles
+// (default about 1 s; a test may shorten it to make a wait run out), the drain
+// after an abort always waits up to DRAIN_LIMIT for the copies and MMAs in flight
+constexpr long long DEFAULT_WAIT_LIMIT = 2000000000LL;
+constexpr long long DRAIN_LIMIT = 2000000000LL;
 constexpr size_t SMEM_LIMIT = 232448;
 
 struct TcArgs {
@@ -87,6 +100,11 @@ struct TcArgs {
     float* cws;
     int sc;
     int ac_bytes;   // > 0: Ac (sc x R floats) is copied to shared memory once per CTA
+    // fp16 parts (KIND 2): T is multiplied by tscale before splitting; column c of
+    // X is multiplied by colinv[c] = 1 / (tscale * factor column scale)
+    float tscale;
+    const float* colinv;
+    long long wait_limit;   // cycles a pipeline wait may take before the CTA aborts
 };
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -115,13 +133,14 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 // bounded wait: false if the CTA is aborting (flag set here on expiry)
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          long long limit) {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_test(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (clock64() - t0 > WAIT_LIMIT) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             return false;
         }
@@ -159,7 +178,7 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
 template <int KIND>
 __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                        uint32_t accumulate) {
-    if (KIND == 0) {
+    if (KIND != 1) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
@@ -253,6 +272,21 @@ __device__ __forceinline__ void split8_bf16(const float* f, uint4& hi, uint4& lo
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
+// 8 floats -> one 16-byte chunk of fp16 hi and one of fp16 lo of y = x * sc
+__device__ __forceinline__ void split8_f16(const float* f, float sc, uint4& hi, uint4& lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float y0 = f[2 * i] * sc, y1 = f[2 * i + 1] * sc;
+        __half2 hh = __floats2half2_rn(y0, y1);
+        float2 hf = __half22float2(hh);
+        __half2 lh = __floats2half2_rn(y0 - hf.x, y1 - hf.y);
+        h[i] = *reinterpret_cast<uint32_t*>(&hh);
+        l[i] = *reinterpret_cast<uint32_t*>(&lh);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
 // 4 floats -> one 16-byte chunk of tf32 hi and one of tf32 lo
 __device__ __forceinline__ void split4_tf32(float4 v, float4& hi, float4& lo) {
     hi.x = tf32_rna(v.x); hi.y = tf32_rna(v.y); hi.z = tf32_rna(v.z); hi.w = tf32_rna(v.w);
@@ -279,7 +313,8 @@ __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, in
 // MODE 0: last mode, T rows K-contiguous (2-D map {K, PQ}, boxes {32, 128}, SWIZZLE_128B)
 // MODE 1: other modes, T[p][k][q] with Q % 4 == 0 (3-D map {Q, K, P}, box {128, BK, 1}; the
 //         last q-tile of each p is zero-filled past Q by the TMA unit and written up to Q)
-// KIND 0: bf16 parts, BK = 64, kind::f16;  KIND 1: tf32 parts, BK = 32, kind::tf32
+// KIND 0: bf16 parts, BK = 64, kind::f16;  KIND 1: tf32 parts, BK = 32, kind::tf32;
+// KIND 2: scaled fp16 parts, BK = 64, kind::f16
 // CHILD: 0 plain; 1 the epilogue also forms the first child (a.Yc) for sc a
 // multiple of 32; 2 for other sc.  Separate instantiations keep each kernel's
 // code, registers and shared memory to what it runs.
@@ -288,7 +323,7 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
     k_ttm_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmBhi,
              const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmBhi1,
              const __grid_constant__ CUtensorMap tmBlo1, const TcArgs a) {
-    constexpr int BK = KIND == 0 ? 64 : 32;
+    constexpr int BK = KIND == 1 ? 32 : 64;
     constexpr uint32_t STG = BM * BK * 4;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -389,7 +424,7 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
                 for (int kc = kc0; kc < kc1 && ok; ++kc, ++it) {
                     const int s = (int)(it % S_stg);
                     const uint32_t us = (uint32_t)(it / S_stg);
-                    if (!(ok = mbar_wait(stg_empty(s), (us & 1u) ^ 1u, abort_flag))) break;
+                    if (!(ok = mbar_wait(stg_empty(s), (us & 1u) ^ 1u, abort_flag, a.wait_limit))) break;
                     mbar_expect_tx(stg_full(s), STG);
                     const uint32_t dst = stg0 + (uint32_t)s * STG;
                     if (MODE == 0) {
@@ -405,7 +440,7 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
                     if (!a.b_resident) {
                         const int j = (int)(it % S_op);
                         const uint32_t uj = (uint32_t)(it / S_op);
-                        if (!(ok = mbar_wait(op_empty(j), (uj & 1u) ^ 1u, abort_flag))) break;
+                        if (!(ok = mbar_wait(op_empty(j), (uj & 1u) ^ 1u, abort_flag, a.wait_limit))) break;
                         // this pass's operand rows only (a smaller last pass leaves the
                         // rest of the slot unused)
                         mbar_expect_tx(op_full(j), 2u * (uint32_t)a.Rpadp[pass] * 128u);
@@ -419,8 +454,8 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
                 // drain: wait (bounded) for the copies issued into the last stages
                 volatile int never = 0;
                 for (int64_t k = (it > S_stg ? it - S_stg : 0); k <= it; ++k)
-                    mbar_wait(stg_full((int)(k % S_stg)), (uint32_t)((k / S_stg) & 1), &never);
-                if (a.b_resident) mbar_wait(b_full, 0u, &never);
+                    mbar_wait(stg_full((int)(k % S_stg)), (uint32_t)((k / S_stg) & 1), &never, DRAIN_LIMIT);
+                if (a.b_resident) mbar_wait(b_full, 0u, &never, DRAIN_LIMIT);
             }
         }
     } else if (warp == 1) {
@@ -429,7 +464,7 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
             int64_t it = 0;
             int lt = 0;
             bool ok = true;
-            if (a.b_resident) ok = mbar_wait(b_full, 0u, abort_flag);
+            if (a.b_resident) ok = mbar_wait(b_full, 0u, abort_flag, a.wait_limit);
             const int64_t nwork = a.ntiles * a.nsk * a.npass;
             for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++lt) {
                 const int ks = (int)((w / a.npass) % a.nsk);
@@ -438,7 +473,7 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
                 const int kc0 = ks * a.nk / a.nsk, kc1 = (ks + 1) * a.nk / a.nsk;
                 const int buf = lt & 1;
                 const uint32_t ub = (uint32_t)(lt >> 1);
-                if (!(ok = mbar_wait(acc_empty(buf), (ub & 1u) ^ 1u, abort_flag))) break;
+                if (!(ok = mbar_wait(acc_empty(buf), (ub & 1u) ^ 1u, abort_flag, a.wait_limit))) break;
                 tc_fence_after();
                 const uint32_t dt = tmem_base + (uint32_t)(buf * a.set_cols);
                 const uint32_t dcorr = dt + (uint32_t)(a.nsplit * a.Rpad);
@@ -446,7 +481,7 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
                     const int rc = kc - kc0;  // chunk index within this work item
                     const uint32_t dmain = dt + (uint32_t)((rc % a.nsplit) * a.Rpad);
                     const int j = (int)(it % S_op);
-                    if (!(ok = mbar_wait(op_full(j), (uint32_t)((it / S_op) & 1), abort_flag))) break;
+                    if (!(ok = mbar_wait(op_full(j), (uint32_t)((it / S_op) & 1), abort_flag, a.wait_limit))) break;
                     tc_fence_after();
                     const uint32_t ahi = op0 + (uint32_t)j * 2u * OPA_BYTES, alo = ahi + OPA_BYTES;
                     const uint32_t bhi = b0 + (uint32_t)(a.b_resident ? kc : j) * bchunk, blo = bhi + bpart;
@@ -470,7 +505,7 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
                 // let every MMA issued so far finish before TMEM is released
                 tc_commit(drain_bar);
                 volatile int never = 0;
-                mbar_wait(drain_bar, 0u, &never);
+                mbar_wait(drain_bar, 0u, &never, DRAIN_LIMIT);
             }
         }
     } else if (warp >= 4 && warp < 8) {
@@ -486,12 +521,12 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
             for (int kc = kc0; kc < kc1; ++kc, ++it) {
                 const int s = (int)(it % S_stg);
                 const int j = (int)(it % S_op);
-                if (!(ok = mbar_wait(stg_full(s), (uint32_t)((it / S_stg) & 1), abort_flag))) break;
-                if (!(ok = mbar_wait(op_empty(j), (uint32_t)(((it / S_op) & 1) ^ 1), abort_flag))) break;
+                if (!(ok = mbar_wait(stg_full(s), (uint32_t)((it / S_stg) & 1), abort_flag, a.wait_limit))) break;
+                if (!(ok = mbar_wait(op_empty(j), (uint32_t)(((it / S_op) & 1) ^ 1), abort_flag, a.wait_limit))) break;
                 const uint8_t* stg = gbase + (stg0 - base) + (size_t)s * STG;
                 uint8_t* ophi = gbase + (op0 - base) + (size_t)j * 2 * OPA_BYTES;
                 uint8_t* oplo = ophi + OPA_BYTES;
-                if (KIND == 0) {
+                if (KIND != 1) {
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {  // output chunk c: k = 8c .. 8c+7
                         float f[8];
@@ -509,7 +544,10 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
                             for (int i = 0; i < 8; ++i) f[i] = col[(8 * c + i) * BM];
                         }
                         uint4 hi, lo;
-                        split8_bf16(f, hi, lo);
+                        if (KIND == 2)
+                            split8_f16(f, a.tscale, hi, lo);
+                        else
+                            split8_bf16(f, hi, lo);
                         const int pos = ((c ^ sw) << 4) + m * 128;
                         *reinterpret_cast<uint4*>(ophi + pos) = hi;
                         *reinterpret_cast<uint4*>(oplo + pos) = lo;
@@ -561,7 +599,7 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
             const int Rw = a.Rp[pass], Rpw = a.Rpadp[pass];
             float* Xs = a.X + (int64_t)((w / a.npass) % a.nsk) * a.slice + 128 * pass;
             const int buf = lt & 1;
-            if (!(ok = mbar_wait(acc_full(buf), (uint32_t)((lt >> 1) & 1), abort_flag))) break;
+            if (!(ok = mbar_wait(acc_full(buf), (uint32_t)((lt >> 1) & 1), abort_flag, a.wait_limit))) break;
             tc_fence_after();
             int64_t g0;       // global row of this warp's first row
             int64_t gend;     // rows g0 + r < gend belong to this tile
@@ -639,6 +677,15 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
                     tmem_ld16(tcol + ac * rp, w);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] += w[i];
+                }
+                if (KIND == 2) {
+                    // undo the powers of two of T and of the factor's columns (exact)
+                    const float4* ci = reinterpret_cast<const float4*>(a.colinv + 128 * pass + c0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 s4 = __ldg(ci + q);
+                        v[4 * q] *= s4.x; v[4 * q + 1] *= s4.y; v[4 * q + 2] *= s4.z; v[4 * q + 3] *= s4.w;
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
@@ -775,7 +822,7 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
                 }
                 __syncwarp();
                 mbar_arrive(epi_bar(lt & 1));
-                if (!(ok = mbar_wait(epi_bar(lt & 1), (uint32_t)((lt >> 1) & 1), abort_flag))) break;
+                if (!(ok = mbar_wait(epi_bar(lt & 1), (uint32_t)((lt >> 1) & 1), abort_flag, a.wait_limit))) break;
                 if (quad == 0) {
                     // warp 8 adds the pieces of each segment in row order; a segment
                     // inside the tile is final, one that crosses the tile's first row
@@ -867,6 +914,8 @@ struct TcPlan {
     int kind;   // kernel KIND
     int64_t P, Q, PQ;
     int K, R, nk, S_op;
+    float tscale = 1.f;              // fp16 parts: power of two applied to T
+    const float* colinv = nullptr;   // fp16 parts: per-column output scale (Rpad floats)
 };
 
 bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R) {
@@ -879,11 +928,12 @@ bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R) {
 }
 
 TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind, const void* bhi,
-                    const void* blo, int Rpad, int Kpad) {
+                    const void* blo, int Rpad, int Kpad, float tscale, const float* colinv) {
     if (!ttm_tc_supported(P, K, Q, R) || ((uintptr_t)T & 15)) return nullptr;
+    if (kind == 2 && (!colinv || ((uintptr_t)colinv & 15))) return nullptr;
     EncodeTiledFn enc = encoder();
     if (!enc) return nullptr;
-    const int BK = kind == 0 ? 64 : 32;
+    const int BK = kind == 1 ? 32 : 64;
     TcPlan* pl = new TcPlan();
     pl->kind = kind;
     pl->P = P;
@@ -894,8 +944,10 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
     pl->nk = (K + BK - 1) / BK;
     pl->S_op = 2;
     pl->npass = (R + PASS_COLS - 1) / PASS_COLS;
-    const int esz = kind == 0 ? 2 : 4;
-    const CUtensorMapDataType bt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    pl->tscale = tscale;
+    pl->colinv = colinv;
+    const int esz = kind == 1 ? 4 : 2;
+    const CUtensorMapDataType bt = kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     const cuuint32_t es[3] = {1, 1, 1};
     for (int q = 0; q < pl->npass; ++q) {
         TcPass& ps = pl->pass[q];
@@ -955,6 +1007,10 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
 }
 
 void ttm_tc_plan_free(TcPlan* p) { delete p; }
+
+void ttm_tc_set_tscale(TcPlan* p, float tscale) {
+    if (p) p->tscale = tscale;
+}
 
 int ttm_tc_kind(const TcPlan* p) { return p ? p->kind : -1; }
 
@@ -1051,7 +1107,7 @@ __global__ void k_child_cross(const float* __restrict__ ws, float* __restrict__ 
 }  // namespace
 
 cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsigned* dev_err,
-                       cudaStream_t st, float* splitk_ws, const TcChild* child) {
+                       cudaStream_t st, float* splitk_ws, const TcChild* child, long long wait_limit) {
     if (!pl) return cudaErrorInvalidValue;
     if (child) {
         if (!ttm_tc_child_ok(pl, child->sc) || !child->Y || !child->Ac) return cudaErrorInvalidValue;
@@ -1060,10 +1116,11 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     }
     const bool bf = (prec == CP_BF16X3 || prec == CP_BF16);
     const bool tf = (prec == CP_TF32X3 || prec == CP_TF32);
-    if ((pl->kind == 0 && !bf) || (pl->kind == 1 && !tf)) return cudaErrorInvalidValue;
+    const bool hf = prec == CP_F16X3;
+    if ((pl->kind == 0 && !bf) || (pl->kind == 1 && !tf) || (pl->kind == 2 && !hf)) return cudaErrorInvalidValue;
     if (((uintptr_t)X & 15) && (pl->R & 3) == 0) return cudaErrorMisalignedAddress;
     const int nsk = splitk_ws ? ttm_tc_splitk(pl, num_sms) : 1;
-    const int BK = pl->kind == 0 ? 64 : 32;
+    const int BK = pl->kind == 1 ? 32 : 64;
     const TcPass& p0 = pl->pass[0];  // the widest pass: it sizes the slots and TMEM sets
     TcArgs a;
     a.X = nsk > 1 ? splitk_ws : X;
@@ -1100,7 +1157,7 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     a.S_stg = S_stg;
     a.S_op = pl->S_op;
     a.b_resident = p0.b_resident;
-    a.x3 = (prec == CP_BF16X3 || prec == CP_TF32X3) ? 1 : 0;
+    a.x3 = (prec == CP_BF16X3 || prec == CP_TF32X3 || prec == CP_F16X3) ? 1 : 0;
     // accumulators per tile: nsplit for hi*hi (by k-chunk) + 1 for the corrections;
     // two sets must fit the 512 TMEM columns
     const int per_set = 256 / p0.Rpad;
@@ -1114,7 +1171,8 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     int cols = 32;
     while (cols < 2 * a.set_cols) cols *= 2;
     a.tmem_cols = cols;
-    const uint32_t fmt = pl->kind == 0 ? 1u : 2u;  // BF16 = 1, TF32 = 2
+    // instruction-descriptor operand format: F16 = 0, BF16 = 1 (kind::f16); TF32 = 2 (kind::tf32)
+    const uint32_t fmt = pl->kind == 0 ? 1u : (pl->kind == 1 ? 2u : 0u);
     a.npass = pl->npass;
     for (int q = 0; q < 2; ++q) {
         const TcPass& ps = pl->pass[q < pl->npass ? q : 0];
@@ -1132,6 +1190,9 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     a.cws = child ? child->ws : nullptr;
     a.sc = child ? child->sc : 1;
     a.ac_bytes = ac_bytes;
+    a.tscale = pl->tscale;
+    a.colinv = pl->colinv;
+    a.wait_limit = wait_limit > 0 ? wait_limit : DEFAULT_WAIT_LIMIT;
     // first-child epilogues use four warps; plain ones eight for wide passes
     const int ew = child ? 4 : epi_warps_for(p0.Rpad);
     const size_t smem = layout_bytes(S_stg, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, ew, child != nullptr, ac_bytes);
@@ -1142,10 +1203,12 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     cudaError_t e;
     const int ck = child ? (child->sc % 32 == 0 ? 1 : 2) : 0;
 #define CP_TTM_LAUNCH(C, W)                                                                               \
-    (pl->mode == 0 ? (pl->kind == 0 ? launch<0, 0, C, W>(pl, p1, a, smem, grid, st)                     \
-                                    : launch<0, 1, C, W>(pl, p1, a, smem, grid, st))                    \
-                   : (pl->kind == 0 ? launch<1, 0, C, W>(pl, p1, a, smem, grid, st)                     \
-                                    : launch<1, 1, C, W>(pl, p1, a, smem, grid, st)))
+    (pl->mode == 0 ? (pl->kind == 0   ? launch<0, 0, C, W>(pl, p1, a, smem, grid, st)                   \
+                      : pl->kind == 1 ? launch<0, 1, C, W>(pl, p1, a, smem, grid, st)                   \
+                                      : launch<0, 2, C, W>(pl, p1, a, smem, grid, st))                  \
+                   : (pl->kind == 0   ? launch<1, 0, C, W>(pl, p1, a, smem, grid, st)                   \
+                      : pl->kind == 1 ? launch<1, 1, C, W>(pl, p1, a, smem, grid, st)                   \
+                                      : launch<1, 2, C, W>(pl, p1, a, smem, grid, st)))
     if (ck == 1)
         e = CP_TTM_LAUNCH(1, 4);
     else if (ck == 2)

@@ -184,8 +184,11 @@ extern "C" cp_status cp_resid_noalloc(int N, const int64_t* dims, int R, const f
     }
     const int64_t ncols = dims[N - 1];
     const int64_t ntc = (ncols + 63) / 64;
-    const int64_t ntiles = ((nrows + 63) / 64) * ntc;
-    if (ntiles > NOALLOC_MAX_TILES) return CP_EINVAL;  // the scratch holds 65536 tiles
+    const int64_t ntr = (nrows + 63) / 64;
+    // the scratch holds 65536 tiles; both factors are bounded before their
+    // product is formed, so a huge last mode cannot wrap it around
+    if (ntc > NOALLOC_MAX_TILES || ntr > NOALLOC_MAX_TILES / ntc) return CP_EINVAL;
+    const int64_t ntiles = ntr * ntc;
     double* part = nullptr;
     if (scratch_for_current_device(&part) != cudaSuccess) {
         cudaGetLastError();

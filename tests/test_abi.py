@@ -43,12 +43,12 @@ def test_invalid_arguments_rejected_before_device_use(lib):
     assert lib.cp_init(ctypes.byref(h), 3, dims, 0, fake, 0, None, None, None) == 1  # R < 1
     assert lib.cp_init(ctypes.byref(h), 3, dims, 257, fake, 0, None, None, None) == 1
     assert lib.cp_init(ctypes.byref(h), 3, dims, 3, None, 0, None, None, None) == 1
-    assert lib.cp_init(ctypes.byref(h), 3, dims, 3, fake, 2, None, None, None) == 1  # dtype
+    assert lib.cp_init(ctypes.byref(h), 3, dims, 3, fake, 3, None, None, None) == 1  # dtype
     bad = (ctypes.c_int64 * 3)(4, 0, 6)
     assert lib.cp_init(ctypes.byref(h), 3, bad, 3, fake, 0, None, None, None) == 1
     cfg = p.Config()
     lib.cp_config_default(ctypes.byref(cfg))
-    assert cfg.prec == p.PREC["bf16x3"] and abs(cfg.pp_eps - 0.1) < 1e-15
+    assert cfg.prec == p.PREC["f16x3"] and abs(cfg.pp_eps - 0.1) < 1e-15
     cfg.prec = 9
     assert lib.cp_init(ctypes.byref(h), 3, dims, 3, fake, 0, None, ctypes.byref(cfg), None) == 1
     # NULL contexts

@@ -61,3 +61,8 @@ def test_resid_noalloc_rejects_oversized(pkg):
     fake = ctypes.c_void_p(256)
     ptrs = (ctypes.c_void_p * 3)(256, 256, 256)
     assert L.cp_resid_noalloc(3, dims, 8, fake, ptrs, fake, None) == 1
+    # a last mode so large that (row tiles x column tiles) would wrap int64
+    huge = (ctypes.c_int64 * 3)(1 << 20, 1 << 20, (1 << 62) + 1)
+    assert L.cp_resid_noalloc(3, huge, 8, fake, ptrs, fake, None) == 1
+    wide = (ctypes.c_int64 * 3)(1, 1, 64 * 65536 + 1)     # one row tile, 65537 column tiles
+    assert L.cp_resid_noalloc(3, wide, 8, fake, ptrs, fake, None) == 1
