@@ -575,7 +575,7 @@ cp_status harvest(cp_ctx* c, int k, const int* kinds, const int* inits, int firs
         // before any factorisation failure it causes
         for (int n = 0; n < c->N; ++n) {
             const double* sc = &h[((size_t)i * c->N + n) * CP_NSCAL];
-            if (!isfinite(sc[SCAL_A2]) || !isfinite(sc[SCAL_MA])) bad = true;
+            if (!isfinite(sc[SCAL_A2]) || !isfinite(sc[SCAL_MA]) || !isfinite(sc[SCAL_GS])) bad = true;
         }
         if (bad) {
             c->sweeps_done += i + 1;
@@ -909,6 +909,8 @@ cp_status direct_resid(cp_ctx* c, double* r) {
     double s2 = 0.0;
     CKCUDA(c, cudaMemcpyAsync(&s2, c->d_red_out, sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CKCUDA(c, cudaStreamSynchronize(c->st));
+    // a NaN must not be clamped away with the rounding-level negatives
+    if (!std::isfinite(s2)) return fail(c, CP_ENUMERIC, "non-finite residual");
     *r = sqrt(s2 > 0 ? s2 : 0.0) / sqrt(c->normT2);
     if (!isfinite(*r)) return fail(c, CP_ENUMERIC, "non-finite residual");
     return CP_OK;
