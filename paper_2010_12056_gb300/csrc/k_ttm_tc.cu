@@ -8,7 +8,8 @@
 //               ring; the factor operand (stored [r][k], K-major, split in two
 //               parts) either once for the whole kernel (when all of K fits) or
 //               one chunk per k-step.
-//   warps 4-7   converters, thread = tile row: split every FP32 value into two
+//   warps 4..    converters (eight warps, each thread half of a tile row, or four
+//               warps of whole rows), thread = tile row: split every FP32 value into two
 //               parts in the canonical K-major 128-byte-swizzled layout (rows of
 //               128 B, 16-byte chunk c of row m at c ^ (m mod 8)):
 //                 bf16 family (BK = 64): hi = rn_bf16(x), lo = rn_bf16(x - hi)
@@ -31,7 +32,7 @@
 //               (2^-8 or 2^-11 smaller) corrections to one more; the epilogue
 //               adds them with round-to-nearest.  Two sets of accumulators let
 //               the epilogue overlap the next tile.
-//   warps 8-11  epilogue: tcgen05.ld 32x32b -> registers -> a warp-private smem
+//   epilogue    (the last EW warps) tcgen05.ld 32x32b -> registers -> a warp-private smem
 //               transpose -> full-sector coalesced stores of X.  Optionally (the
 //               multi-sweep tree's first child, Fig. 2) it also forms
 //                 Y[y][r] = sum_{j < sc} X[y sc + j][r] Ac[j][r]
@@ -39,7 +40,7 @@
 //               sc a multiple of 32: each warp's 32 rows lie in one segment; the
 //               warp writes its column sums and a second kernel adds the sc / 32
 //               pieces of each segment in order.  Other sc: segmented warp sums,
-//               boundary pieces combined per tile by warp 8, pieces of segments
+//               boundary pieces combined per tile by the first epilogue warp, pieces of segments
 //               that cross tiles added by a second kernel in a fixed order.
 // Every mbarrier wait is bounded; on expiry the CTA sets DEVERR_TIMEOUT, drains
 // what it issued (bounded), frees TMEM and exits.
@@ -52,12 +53,15 @@
 namespace {
 
 constexpr int BM = 128;
-// warps 0 producer, 1 MMA, 2-3 idle, 4-7 converters, 8.. epilogue: EW = 4 epilogue
-// warps (one per TMEM lane quarter), or 8 (two per quarter, alternate 16-column
-// groups) for passes of 128 columns, where the epilogue is the slowest stage
-// (measured on 128^4: R = 128 0.73 -> 0.81-0.87 of HBM; R <= 64 slower with 8,
-// whose extra warps take issue slots from the converters)
-__host__ __device__ constexpr int nthreads(int ew) { return 256 + 32 * ew; }
+// warps 0 producer, 1 MMA, 2-3 idle, 4.. converters, then the epilogue: EW = 4
+// epilogue warps (one per TMEM lane quarter), or 8 (two per quarter, alternate
+// 16-column groups) for passes of 128 columns, where the epilogue is the slowest
+// stage (measured on 128^4: R = 128 0.73 -> 0.81-0.87 of HBM; R <= 64 slower with
+// 8, whose extra warps take issue slots from the converters)
+// converter warps: eight (two per SM sub-partition, each half of a tile row's
+// k-chunk) when the register budget of 512 threads allows it, else four
+__host__ __device__ constexpr int conv_warps(int ew, int child) { return (child == 0 && ew == 4) ? 8 : 4; }
+__host__ __device__ constexpr int nthreads(int ew, int child) { return 128 + 32 * conv_warps(ew, child) + 32 * ew; }
 inline int epi_warps_for(int Rpad) { return Rpad >= 128 ? 8 : 4; }
 constexpr int OPA_BYTES = BM * 128;        // one split part of a 128-row chunk: 16 KB
 constexpr int EPI_STRIDE = 20;             // floats per row of the epilogue transpose buffer
@@ -319,7 +323,7 @@ __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, in
 // multiple of 32; 2 for other sc.  Separate instantiations keep each kernel's
 // code, registers and shared memory to what it runs.
 template <int MODE, int KIND, int CHILD, int EW>
-__global__ void __launch_bounds__(nthreads(EW), 1)
+__global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
     k_ttm_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmBhi,
              const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmBhi1,
              const __grid_constant__ CUtensorMap tmBlo1, const TcArgs a) {
@@ -337,6 +341,8 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
     const uint32_t epi0 = b0 + (uint32_t)(a.b_resident ? a.nk : S_op) * bchunk;
     static_assert(EW == 4 || (EW == 8 && CHILD == 0), "first-child epilogues use four warps");
     constexpr int NEPI = EW;
+    constexpr int NCONV = conv_warps(EW, CHILD);
+    constexpr int EPI0 = 4 + NCONV;   // first epilogue warp (a multiple of 4: TMEM lane quarters)
     const uint32_t child0 = epi0 + NEPI * EPI_WARP_BYTES;
     const uint32_t ac0 = child0 + (CHILD ? CHILD_BYTES : 0);
     const uint32_t bar0 = ac0 + (CHILD ? (uint32_t)a.ac_bytes : 0u);
@@ -356,10 +362,10 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < S_stg; ++s) {
             mbar_init(stg_full(s), 1);
-            mbar_init(stg_empty(s), 128);
+            mbar_init(stg_empty(s), 32 * NCONV);
         }
         for (int j = 0; j < S_op; ++j) {
-            mbar_init(op_full(j), a.b_resident ? 128 : 129);
+            mbar_init(op_full(j), a.b_resident ? 32 * NCONV : 32 * NCONV + 1);
             mbar_init(op_empty(j), 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -385,7 +391,7 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
         // the contracted factor, read by the epilogue for every tile
         float* sAc = reinterpret_cast<float*>(gbase + (ac0 - base));
         const int n = a.sc * a.R;
-        for (int i = threadIdx.x; i < n; i += nthreads(EW)) sAc[i] = __ldg(a.Ac + i);
+        for (int i = threadIdx.x; i < n; i += nthreads(EW, CHILD)) sAc[i] = __ldg(a.Ac + i);
     }
     tc_fence_before();
     __syncthreads();
@@ -508,9 +514,15 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
                 mbar_wait(drain_bar, 0u, &never, DRAIN_LIMIT);
             }
         }
-    } else if (warp >= 4 && warp < 8) {
+    } else if (warp >= 4 && warp < EPI0) {
         // ------------------------------------------------ converters (thread = tile row)
-        const int m = threadIdx.x - 128;
+        // NCONV = 8: warps 4-7 take output chunks 0-3 of their row, warps 8-11 chunks
+        // 4-7; NCONV = 4: every chunk.  Chunks are handled four at a time with all
+        // their shared-memory loads issued before the first store (the compiler may
+        // not move a load above a store to a buffer it cannot tell apart).
+        const int m = (threadIdx.x - 128) & (BM - 1);
+        const int cbeg = NCONV == 8 ? 4 * ((threadIdx.x - 128) >> 7) : 0;
+        constexpr int CPT = NCONV == 8 ? 4 : 8;   // output chunks per thread
         const int sw = m & 7;
         int64_t it = 0;
         bool ok = true;
@@ -526,48 +538,61 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
                 const uint8_t* stg = gbase + (stg0 - base) + (size_t)s * STG;
                 uint8_t* ophi = gbase + (op0 - base) + (size_t)j * 2 * OPA_BYTES;
                 uint8_t* oplo = ophi + OPA_BYTES;
-                if (KIND != 1) {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {  // output chunk c: k = 8c .. 8c+7
-                        float f[8];
-                        if (MODE == 0) {
-                            // box c/4 holds k = 32(c/4)..; row m, 16-byte chunk q at q ^ (m & 7)
-                            const uint8_t* rowp = stg + (c >> 2) * (BM * 128) + m * 128;
-                            const int q0 = (2 * c) & 7;
-                            const float4 v0 = *reinterpret_cast<const float4*>(rowp + ((q0 ^ sw) << 4));
-                            const float4 v1 = *reinterpret_cast<const float4*>(rowp + (((q0 + 1) ^ sw) << 4));
-                            f[0] = v0.x; f[1] = v0.y; f[2] = v0.z; f[3] = v0.w;
-                            f[4] = v1.x; f[5] = v1.y; f[6] = v1.z; f[7] = v1.w;
-                        } else {
-                            const float* col = reinterpret_cast<const float*>(stg) + m;  // [BK][128]
+                for (int g = 0; g < CPT; g += 4) {
+                    if (KIND != 1) {
+                        float f[4][8];   // output chunk c: k = 8c .. 8c+7
 #pragma unroll
-                            for (int i = 0; i < 8; ++i) f[i] = col[(8 * c + i) * BM];
+                        for (int cc = 0; cc < 4; ++cc) {
+                            const int c = cbeg + g + cc;
+                            if (MODE == 0) {
+                                // box c/4 holds k = 32(c/4)..; row m, 16-byte chunk q at q ^ (m & 7)
+                                const uint8_t* rowp = stg + (c >> 2) * (BM * 128) + m * 128;
+                                const int q0 = (2 * c) & 7;
+                                const float4 v0 = *reinterpret_cast<const float4*>(rowp + ((q0 ^ sw) << 4));
+                                const float4 v1 = *reinterpret_cast<const float4*>(rowp + (((q0 + 1) ^ sw) << 4));
+                                f[cc][0] = v0.x; f[cc][1] = v0.y; f[cc][2] = v0.z; f[cc][3] = v0.w;
+                                f[cc][4] = v1.x; f[cc][5] = v1.y; f[cc][6] = v1.z; f[cc][7] = v1.w;
+                            } else {
+                                const float* col = reinterpret_cast<const float*>(stg) + m;  // [BK][128]
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) f[cc][i] = col[(8 * c + i) * BM];
+                            }
                         }
-                        uint4 hi, lo;
-                        if (KIND == 2)
-                            split8_f16(f, a.tscale, hi, lo);
-                        else
-                            split8_bf16(f, hi, lo);
-                        const int pos = ((c ^ sw) << 4) + m * 128;
-                        *reinterpret_cast<uint4*>(ophi + pos) = hi;
-                        *reinterpret_cast<uint4*>(oplo + pos) = lo;
-                    }
-                } else {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {  // output chunk c: k = 4c .. 4c+3
-                        float4 v;
-                        if (MODE == 0) {
-                            v = *reinterpret_cast<const float4*>(stg + m * 128 + ((c ^ sw) << 4));
-                        } else {
-                            const float* col = reinterpret_cast<const float*>(stg) + m;
-                            v = make_float4(col[(4 * c) * BM], col[(4 * c + 1) * BM], col[(4 * c + 2) * BM],
-                                            col[(4 * c + 3) * BM]);
+                        for (int cc = 0; cc < 4; ++cc) {
+                            const int c = cbeg + g + cc;
+                            uint4 hi, lo;
+                            if (KIND == 2)
+                                split8_f16(f[cc], a.tscale, hi, lo);
+                            else
+                                split8_bf16(f[cc], hi, lo);
+                            const int pos = ((c ^ sw) << 4) + m * 128;
+                            *reinterpret_cast<uint4*>(ophi + pos) = hi;
+                            *reinterpret_cast<uint4*>(oplo + pos) = lo;
                         }
-                        float4 hi, lo;
-                        split4_tf32(v, hi, lo);
-                        const int pos = ((c ^ sw) << 4) + m * 128;
-                        *reinterpret_cast<float4*>(ophi + pos) = hi;
-                        *reinterpret_cast<float4*>(oplo + pos) = lo;
+                    } else {
+                        float4 v[4];     // output chunk c: k = 4c .. 4c+3
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) {
+                            const int c = cbeg + g + cc;
+                            if (MODE == 0) {
+                                v[cc] = *reinterpret_cast<const float4*>(stg + m * 128 + ((c ^ sw) << 4));
+                            } else {
+                                const float* col = reinterpret_cast<const float*>(stg) + m;
+                                v[cc] = make_float4(col[(4 * c) * BM], col[(4 * c + 1) * BM],
+                                                    col[(4 * c + 2) * BM], col[(4 * c + 3) * BM]);
+                            }
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) {
+                            const int c = cbeg + g + cc;
+                            float4 hi, lo;
+                            split4_tf32(v[cc], hi, lo);
+                            const int pos = ((c ^ sw) << 4) + m * 128;
+                            *reinterpret_cast<float4*>(ophi + pos) = hi;
+                            *reinterpret_cast<float4*>(oplo + pos) = lo;
+                        }
                     }
                 }
                 fence_proxy_async();
@@ -575,12 +600,12 @@ __global__ void __launch_bounds__(nthreads(EW), 1)
                 mbar_arrive(op_full(j));
             }
         }
-    } else if (warp >= 8) {
+    } else if (warp >= EPI0) {
         // ------------------------------------------------ epilogue (thread = TMEM lane = row)
         const int quad = warp & 3;             // TMEM lane quarter (warp id mod 4)
-        const int half = (warp - 8) >> 2;     // which alternate 16-column groups
+        const int half = (warp - EPI0) >> 2;  // which alternate 16-column groups
         constexpr int NHALF = NEPI / 4;
-        float* tb = reinterpret_cast<float*>(gbase + (epi0 - base)) + (warp - 8) * 32 * EPI_STRIDE;
+        float* tb = reinterpret_cast<float*>(gbase + (epi0 - base)) + (warp - EPI0) * 32 * EPI_STRIDE;
         // first-child pieces and their segment keys (-1: none), double-buffered by tile
         float* cpart = reinterpret_cast<float*>(gbase + (child0 - base));           // [2][4][2][128]
         long long* ckey = reinterpret_cast<long long*>(gbase + (child0 - base) + 2 * 4 * 2 * 128 * 4);
@@ -1034,7 +1059,7 @@ template <int MODE, int KIND, int CHILD, int EW>
 static cudaError_t launch(const TcPlan* pl, const TcPass& p1, const TcArgs& a, size_t smem, unsigned grid,
                           cudaStream_t st) {
     cudaFuncSetAttribute(k_ttm_tc<MODE, KIND, CHILD, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ttm_tc<MODE, KIND, CHILD, EW><<<grid, nthreads(EW), smem, st>>>(pl->tmT, pl->pass[0].tmBhi, pl->pass[0].tmBlo,
+    k_ttm_tc<MODE, KIND, CHILD, EW><<<grid, nthreads(EW, CHILD), smem, st>>>(pl->tmT, pl->pass[0].tmBhi, pl->pass[0].tmBlo,
                                                               p1.tmBhi, p1.tmBlo, a);
     return cudaGetLastError();
 }

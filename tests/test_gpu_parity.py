@@ -454,3 +454,64 @@ def test_f16x3_zero_tensor_and_zero_column(pkg):
     ref = np.tensordot(T32.astype(np.float64), A[1], axes=([1], [0]))
     assert relerr(X, ref) <= 1e-5
     ctx.close()
+
+
+# Parity at the laws of the large configurations, on sizes the oracle finishes in
+# seconds.  Large-rank order 3: 128^3 slice with rank-256 N(0,1) factors and 1e-2
+# noise, R = 256 (two column passes of the tensor-core TTM, blocked inverse).
+_C3LAW = {}
+
+
+def _c3law_oracle(route):
+    """Oracle results of the 128^3 large-rank law, computed once per route."""
+    if route not in _C3LAW:
+        Td, Tref, A0 = problem((128, 128, 128), 256, 20101205 + 2000, eta=1e-2, law="gaussian")
+        ref = co.cp_als(Tref, A0, 3, route=route)
+        M = [co.mttkrp(Tref, A0, n) for n in range(3)]
+        _C3LAW[route] = (Td, A0, M, ref, co.residual_direct(Tref, ref.A))
+    return _C3LAW[route]
+
+
+@pytest.mark.parametrize("route", ["dt", "msdt"])
+@pytest.mark.parametrize("prec", ["f16x3", "fp32"])
+def test_large_rank_gaussian_law(pkg, route, prec):
+    R = 256
+    Td, A0, M, ref, r_ref = _c3law_oracle(route)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    for n in range(3):
+        assert relerr(ctx.mttkrp(n).cpu().numpy(), M[n]) <= 1e-5, n
+    ctx.close()
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    (ctx.sweep_dt if route == "dt" else ctx.sweep_msdt)(3)
+    _, r = ctx.fit(exact=True)
+    assert abs(r - r_ref) <= FIT_TOL[prec]
+    got = np.array([t["resid"] for t in ctx.trace()])
+    assert np.abs(got - np.array(ref.resid)).max() <= 1e-5
+    if prec != "fp32":
+        assert ctx.stats()["ttm_tensor_core"] >= 1
+    ctx.close()
+
+
+def test_pp_collinear_law_follows_oracle(pkg):
+    """Alg. 2 (eps 0.1) on the pairwise-perturbation law: order 4, rank-30 factors of
+    pairwise cosine 0.9, 1e-3 noise (a 40^4 reduction of the 160^4 configuration).
+    For its first 20 sweeps the FP64 oracle's trajectory is stable under 1e-7
+    relative perturbations of T (residuals move by at most 2e-7), so the GPU must
+    take the same sweep kinds, the same operator builds, and stay within the fit
+    tolerance.  Later sweeps are chaotic in the oracle itself: an approximated
+    sweep drifts (its Eq. (residual) value goes to the clamp at zero), the regular
+    sweep after it raises the residual, and a 1e-7 perturbation of T changes the
+    kinds from sweep 32 on; they are not compared."""
+    dims, R, nsw = (40, 40, 40, 40), 30, 20
+    Td, Tref, A0 = problem(dims, R, 20101205 + 3000, eta=1e-3, law="collinear", C=0.9)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec="f16x3")
+    ctx.sweep_pp(nsw, eps=0.1)
+    ref = co.pp_cp_als(Tref, A0, nsw, eps=0.1)
+    tr = ctx.trace()
+    assert ["pp" if t["kind"] == "pp" else "als" for t in tr] == ref.kinds
+    assert sum(t["pp_init"] for t in tr) == ref.n_pp_init and ref.n_pp_init >= 3
+    got = np.array([t["resid"] for t in tr])
+    assert np.abs(got - np.array(ref.resid)).max() <= 1e-5
+    _, r = ctx.fit(exact=True)
+    assert abs(r - co.residual_direct(Tref, ref.A)) <= FIT_TOL["f16x3"]
+    ctx.close()
