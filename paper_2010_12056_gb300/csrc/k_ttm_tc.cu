@@ -8,8 +8,7 @@
 //               ring; the factor operand (stored [r][k], K-major, split in two
 //               parts) either once for the whole kernel (when all of K fits) or
 //               one chunk per k-step.
-//   warps 4..    converters (eight warps, each thread half of a tile row, or four
-//               warps of whole rows), thread = tile row: split every FP32 value into two
+//   warps 4-7   converters, thread = tile row: split every FP32 value into two
 //               parts in the canonical K-major 128-byte-swizzled layout (rows of
 //               128 B, 16-byte chunk c of row m at c ^ (m mod 8)):
 //                 bf16 family (BK = 64): hi = rn_bf16(x), lo = rn_bf16(x - hi)
@@ -58,11 +57,13 @@ constexpr int BM = 128;
 // 16-column groups) for passes of 128 columns, where the epilogue is the slowest
 // stage (measured on 128^4: R = 128 0.73 -> 0.81-0.87 of HBM; R <= 64 slower with
 // 8, whose extra warps take issue slots from the converters)
-// converter warps: eight (two per SM sub-partition, each half of a tile row's
-// k-chunk) when the register budget of 512 threads allows it, else four
-__host__ __device__ constexpr int conv_warps(int ew, int child) { return (child == 0 && ew == 4) ? 8 : 4; }
+// four converter warps (one per SM sub-partition; measured: eight are slower,
+// 0.290 vs 0.272 ms at 128^4 R = 64, their issue slots are the epilogue's)
+__host__ __device__ constexpr int conv_warps(int, int) { return 4; }
 __host__ __device__ constexpr int nthreads(int ew, int child) { return 128 + 32 * conv_warps(ew, child) + 32 * ew; }
-inline int epi_warps_for(int Rpad) { return Rpad >= 128 ? 8 : 4; }
+// (scaled fp16 parts also at 64 columns: their epilogue multiplies every value by
+// its column scale; measured 0.301 -> 0.281 ms at 128^4 R = 64, bf16 0.272 -> 0.277)
+inline int epi_warps_for(int Rpad, int kind) { return (Rpad >= 128 || (kind == 2 && Rpad >= 64)) ? 8 : 4; }
 constexpr int OPA_BYTES = BM * 128;        // one split part of a 128-row chunk: 16 KB
 constexpr int EPI_STRIDE = 20;             // floats per row of the epilogue transpose buffer
 constexpr int EPI_WARP_BYTES = 32 * EPI_STRIDE * 4;   // one epilogue warp's transpose buffer
@@ -303,14 +304,17 @@ struct Layout {
     uint32_t stg_bytes, op_bytes, bchunk_bytes;
 };
 
+// scaled fp16 parts: the per-column output scales of both passes in shared memory
+constexpr int CS_BYTES = 256 * 4;
+
 __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, int nk, int b_resident,
-                                               int BK, int ew, bool child = false, int ac_bytes = 0) {
+                                               int BK, int ew, int kind, bool child = false, int ac_bytes = 0) {
     const size_t stg = (size_t)BM * BK * 4;
     const size_t bchunk = 2 * (size_t)Rpad * 128;
     const size_t nb = b_resident ? (size_t)nk : (size_t)S_op;
     return 1024 + (size_t)S_stg * stg + (size_t)S_op * 2 * OPA_BYTES + nb * bchunk +
            (size_t)ew * EPI_WARP_BYTES +
-           (child ? CHILD_BYTES + (size_t)ac_bytes : 0) + BAR_BYTES;
+           (child ? CHILD_BYTES + (size_t)ac_bytes : 0) + (kind == 2 ? CS_BYTES : 0) + BAR_BYTES;
 }
 
 // ------------------------------------------------------------------ kernel
@@ -345,7 +349,8 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
     constexpr int EPI0 = 4 + NCONV;   // first epilogue warp (a multiple of 4: TMEM lane quarters)
     const uint32_t child0 = epi0 + NEPI * EPI_WARP_BYTES;
     const uint32_t ac0 = child0 + (CHILD ? CHILD_BYTES : 0);
-    const uint32_t bar0 = ac0 + (CHILD ? (uint32_t)a.ac_bytes : 0u);
+    const uint32_t cs0 = ac0 + (CHILD ? (uint32_t)a.ac_bytes : 0u);
+    const uint32_t bar0 = cs0 + (KIND == 2 ? (uint32_t)CS_BYTES : 0u);
     auto stg_full = [&](int s) { return bar0 + 8u * s; };
     auto stg_empty = [&](int s) { return bar0 + 8u * (MAX_STG + s); };
     auto op_full = [&](int j) { return bar0 + 8u * (2 * MAX_STG + j); };
@@ -386,6 +391,12 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                      "r"(a.tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (KIND == 2) {
+        // per-column output scales, read by the epilogue for every tile
+        float* sCs = reinterpret_cast<float*>(gbase + (cs0 - base));
+        const int n = 128 * (a.npass - 1) + a.Rpadp[a.npass - 1];
+        for (int i = threadIdx.x; i < n; i += nthreads(EW, CHILD)) sCs[i] = __ldg(a.colinv + i);
     }
     if (CHILD && a.ac_bytes > 0) {
         // the contracted factor, read by the epilogue for every tile
@@ -516,13 +527,13 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
         }
     } else if (warp >= 4 && warp < EPI0) {
         // ------------------------------------------------ converters (thread = tile row)
-        // NCONV = 8: warps 4-7 take output chunks 0-3 of their row, warps 8-11 chunks
-        // 4-7; NCONV = 4: every chunk.  Chunks are handled four at a time with all
-        // their shared-memory loads issued before the first store (the compiler may
-        // not move a load above a store to a buffer it cannot tell apart).
-        const int m = (threadIdx.x - 128) & (BM - 1);
-        const int cbeg = NCONV == 8 ? 4 * ((threadIdx.x - 128) >> 7) : 0;
-        constexpr int CPT = NCONV == 8 ? 4 : 8;   // output chunks per thread
+        // the 8 output chunks of a row are handled four at a time, with all their
+        // shared-memory loads issued before the first store (the compiler may not
+        // move a load above a store to a buffer it cannot tell apart; measured
+        // 0.290 -> 0.272 ms at 128^4 R = 64)
+        const int m = threadIdx.x - 128;
+        constexpr int cbeg = 0;
+        constexpr int CPT = 8;   // output chunks per thread
         const int sw = m & 7;
         int64_t it = 0;
         bool ok = true;
@@ -674,6 +685,12 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                 tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * a.set_cols);
             for (int c0 = 16 * half; c0 < Rpw; c0 += 16 * NHALF) {
                 float v[16];
+                // scaled fp16 parts: this lane's four output columns' scales, read
+                // before the accumulator loads so that their latency overlaps
+                float4 cs4 = make_float4(1.f, 1.f, 1.f, 1.f);
+                if (KIND == 2)
+                    cs4 = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(gbase + (cs0 - base)) +
+                                                           128 * pass + c0 + 4 * qq);
                 // corrections first (last accumulator), then the hi*hi partial sums;
                 // up to three accumulators per TMEM round trip
                 const uint32_t tcol = taddr + (uint32_t)c0;
@@ -703,15 +720,6 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] += w[i];
                 }
-                if (KIND == 2) {
-                    // undo the powers of two of T and of the factor's columns (exact)
-                    const float4* ci = reinterpret_cast<const float4*>(a.colinv + 128 * pass + c0);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 s4 = __ldg(ci + q);
-                        v[4 * q] *= s4.x; v[4 * q + 1] *= s4.y; v[4 * q + 2] *= s4.z; v[4 * q + 3] *= s4.w;
-                    }
-                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     *reinterpret_cast<float4*>(tb + lane * EPI_STRIDE + 4 * q) =
@@ -726,7 +734,11 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                     const int r = rr + 8 * i;
                     const int64_t g = g0 + r;
                     if (g < gend && col < Rw) {
-                        const float4 w = *reinterpret_cast<const float4*>(tb + r * EPI_STRIDE + 4 * q);
+                        float4 w = *reinterpret_cast<const float4*>(tb + r * EPI_STRIDE + 4 * q);
+                        if (KIND == 2) {
+                            // undo the powers of two of T and of the factor's columns (exact)
+                            w.x *= cs4.x; w.y *= cs4.y; w.z *= cs4.z; w.w *= cs4.w;
+                        }
                         float* dst = Xs + g * (int64_t)a.ldx + col;
                         if (((Rw | a.ldx) & 3) == 0) {
                             *reinterpret_cast<float4*>(dst) = w;
@@ -982,7 +994,7 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
         ps.b_resident = (pl->npass == 1 && (size_t)pl->nk * 2 * ps.Rpad * 128 <= 64 * 1024) ? 1 : 0;
         ps.S_stg = 0;
         for (int st = MAX_STG; st >= 2; --st)
-            if (layout_bytes(st, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK, epi_warps_for(ps.Rpad)) <= SMEM_LIMIT) {
+            if (layout_bytes(st, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK, epi_warps_for(ps.Rpad, kind), kind) <= SMEM_LIMIT) {
                 ps.S_stg = st;
                 break;
             }
@@ -1165,9 +1177,9 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     if (child) {
         auto fit = [&](int acb) {
             int st2 = p0.S_stg;
-            while (st2 > 2 && layout_bytes(st2, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, 4, true, acb) > SMEM_LIMIT)
+            while (st2 > 2 && layout_bytes(st2, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, 4, pl->kind, true, acb) > SMEM_LIMIT)
                 --st2;
-            return layout_bytes(st2, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, 4, true, acb) <= SMEM_LIMIT ? st2 : 0;
+            return layout_bytes(st2, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, 4, pl->kind, true, acb) <= SMEM_LIMIT ? st2 : 0;
         };
         const int acb = (child->sc * pl->R * 4 + 15) / 16 * 16;
         if (int st2 = fit(acb)) {
@@ -1219,8 +1231,8 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     a.colinv = pl->colinv;
     a.wait_limit = wait_limit > 0 ? wait_limit : DEFAULT_WAIT_LIMIT;
     // first-child epilogues use four warps; plain ones eight for wide passes
-    const int ew = child ? 4 : epi_warps_for(p0.Rpad);
-    const size_t smem = layout_bytes(S_stg, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, ew, child != nullptr, ac_bytes);
+    const int ew = child ? 4 : epi_warps_for(p0.Rpad, pl->kind);
+    const size_t smem = layout_bytes(S_stg, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, ew, pl->kind, child != nullptr, ac_bytes);
     const int64_t nwork = a.ntiles * a.nsk * a.npass;
     const unsigned grid = (unsigned)(nwork < num_sms ? nwork : num_sms);
     if (grid == 0) return cudaSuccess;

@@ -93,12 +93,14 @@ def test_singular_normal_equations_report_notspd(pkg, prec):
 
 
 def test_nan_factor_reports_enumeric(pkg):
+    """The NaN is put in the last factor: the first update of a sweep does not read
+    its own factor, so a NaN in factor 0 would be overwritten by finite values."""
     dims, R = (40, 36, 44), 6
     Td, _, A0 = problem(dims, R, 94)
     ctx = pkg.CPContext(Td, R, A0=A0, prec="f16x3")
-    bad = A0[0].copy()
+    bad = A0[2].copy()
     bad[3, 2] = np.nan
-    ctx.set_factor(0, bad)
+    ctx.set_factor(2, bad)
     with pytest.raises(pkg.CPError) as e:
         ctx.fit(exact=True)
     assert e.value.code == CP_ENUMERIC
