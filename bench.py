@@ -504,6 +504,9 @@ def main():
         # second child contracted on a side stream during the next update (6 blocks/SM)
         "msdt_lookahead": timed_sweeps("msdt", lookahead=6),
     }
+    if N >= 4:
+        # upper two levels combined (Sec. IV): level-2 roots straight from T, s^(N-2) R memory
+        schedules["msdt_levels2"] = timed_sweeps("msdt", msdt_levels=2)
 
     # ---------------------------------------------------------------- TTM roofline
     peaks, peak_kind = load_peaks()

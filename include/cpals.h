@@ -100,9 +100,11 @@ void cp_config_default(cp_config *cfg);
  *   stream   cudaStream_t (as void*) every later call is enqueued on.
  * Computes ||T||_F^2 and the Grams S(n) = A(n)^T A(n).  Sets dA(n) = A(n), so the
  * first PP test fails and the first sweep is a regular one (Alg. 2, line 2).
- * Returns CP_EINVAL on bad sizes, CP_ENOMEM if the workspace (about
- * prod(dims)/min(dims) * R * 4 bytes per tree level, plus PP operators on first
- * use) does not fit, CP_ECUDA on a CUDA failure.  *out is NULL on failure.
+ * Returns CP_EINVAL on bad sizes, CP_ENOMEM if the factor and normal-equation
+ * workspace does not fit, CP_ECUDA on a CUDA failure.  *out is NULL on failure.
+ * Tree intermediates (at most prod(dims)/min(dims) * R * 4 bytes per tree level)
+ * and PP operators are allocated on first use, so a sweep call can also return
+ * CP_ENOMEM; a schedule that never forms a level never allocates it.
  */
 cp_status cp_init(cp_ctx **out, int N, const int64_t *dims, int R, const void *T_dev,
                   int dtype, const double *A0_host, const cp_config *cfg, void *stream);
@@ -345,9 +347,20 @@ cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
  *                     the next call that synchronises reports CP_ETIMEOUT and the
  *                     context is poisoned.  A tiny value exists for tests of that
  *                     path (no GPU fault, no hang).
+ *   CP_OPT_MSDT_LEVELS (default 1) multi-sweep tree with its upper l levels
+ *                     combined (Sec. IV, the memory / cost trade-off), 1 <= l <= N-2:
+ *                     update t belongs to subtree t / (N-l), whose root contracts the
+ *                     l modes updated just before its first update t0 = (t/(N-l))(N-l),
+ *                     i.e. t0-1, ..., t0-l (mod N), and serves the next N-l updates.
+ *                     Intermediates need s^(N-l) R entries instead of s^(N-1) R; the
+ *                     first-level work becomes 2N/(N-l) s^N R per sweep.  For l = 2
+ *                     and adjacent modes the root is one tensor-core pass over T with
+ *                     the two factors' Khatri-Rao product.  The look-ahead applies to
+ *                     l = 1 only; results agree with l = 1 to FP32 rounding.
  * CP_EINVAL for an unknown option or value.  Takes effect at the next call.
  */
-enum { CP_OPT_FUSE_DT = 1, CP_OPT_LOOKAHEAD = 2, CP_OPT_FUSE_CHILD = 3, CP_OPT_WAIT_LIMIT = 4 };
+enum { CP_OPT_FUSE_DT = 1, CP_OPT_LOOKAHEAD = 2, CP_OPT_FUSE_CHILD = 3, CP_OPT_WAIT_LIMIT = 4,
+       CP_OPT_MSDT_LEVELS = 5 };
 cp_status cp_set_option(cp_ctx *ctx, int option, int value);
 
 /*

@@ -223,19 +223,49 @@ def dt_updates(T, A, ctr=None):
     yield from tree_updates(root, list(range(N)), A, ctr)
 
 
-def msdt_updates(T, A, n_updates, ctr=None):
+def contract_combined(T, A, modes, ctr=None):
+    """T contracted with the factors of several modes at once (the upper levels of a
+    tree combined, Sec. IV): one product of T with the Khatri-Rao product of those
+    factors, 2 s^N R flops; the result keeps the other modes and r."""
+    N = T.ndim
+    keep = [k for k in range(N) if k not in modes]
+    order = sorted(modes)
+    X = np.transpose(T, keep + order).reshape([T.shape[k] for k in keep] + [-1])
+    Y = X @ khatri_rao_rows([A[k] for k in order])
+    if ctr is not None:
+        ctr.edges.append(("T", tuple(keep)))
+        ctr.ttm += 1
+        ctr.ttm_flops += 2.0 * T.size * A[0].shape[1]
+        ctr.ttm_modes.append(tuple(order) if len(order) > 1 else order[0])
+    return Node(tuple(keep), Y, True)
+
+
+def msdt_updates(T, A, n_updates, ctr=None, levels=1):
     """Multi-sweep dimension tree (Sec. III, Fig. 2): yields (n, M^(n)) for n_updates updates.
 
-    Subtree j has root m_j = (N-1-j) mod N, built right after A[m_j] was last
-    updated, and serves the N-1 updates m_j+1, ..., m_j+N-1 (mod N).
+    levels = 1: subtree j has root m_j = (N-1-j) mod N, built right after A[m_j]
+    was last updated, and serves the N-1 updates m_j+1, ..., m_j+N-1 (mod N).
+
+    levels = l (1 <= l <= N-2, the upper l levels combined, Sec. IV): update t
+    (mode t mod N) belongs to subtree j = t // (N-l), whose root contracts, in one
+    pass over T, the l modes updated just before its first update t0 = j (N-l),
+    i.e. t0-1, ..., t0-l (mod N); it serves the N-l updates t0, ..., t0+N-l-1 with a
+    binary dimension tree over those leaves.  Auxiliary memory s^(N-l) R instead
+    of s^(N-1) R; first-level cost 2N/(N-l) s^N R per sweep.
     """
     N = T.ndim
+    if not 1 <= levels <= max(1, N - 2):
+        raise ValueError("levels must lie in 1..N-2")
     done = 0
     j = 0
     while done < n_updates:
-        m = (N - 1 - j) % N
-        root = contract(Node(tuple(range(N)), T, False), A, m, ctr)
-        leaves = [(m + 1 + i) % N for i in range(N - 1)]
+        t0 = j * (N - levels)
+        if levels == 1:
+            m = (N - 1 - j) % N
+            root = contract(Node(tuple(range(N)), T, False), A, m, ctr)
+        else:
+            root = contract_combined(T, A, [(t0 - 1 - i) % N for i in range(levels)], ctr)
+        leaves = [(t0 + i) % N for i in range(N - levels)]
         for item in tree_updates(root, leaves, A, ctr):
             yield item
             done += 1
@@ -264,11 +294,12 @@ def als_update(A, S, n, M):
     return G
 
 
-def cp_als(T, A0, n_sweeps, route="naive", delta=None):
+def cp_als(T, A0, n_sweeps, route="naive", delta=None, levels=1):
     """CP-ALS (Alg. 1) for a fixed sweep count (or until |r - r_old| <= delta).
 
-    route: "naive" (MTTKRP by definition), "dt" (Fig. 1a) or "msdt" (Fig. 2);
-    in exact arithmetic all three give the same factors.
+    route: "naive" (MTTKRP by definition), "dt" (Fig. 1a) or "msdt" (Fig. 2, with
+    `levels` upper levels combined, Sec. IV); in exact arithmetic all give the
+    same factors.
     """
     T = np.asarray(T, dtype=np.float64)
     N = T.ndim
@@ -280,7 +311,7 @@ def cp_als(T, A0, n_sweeps, route="naive", delta=None):
     r_old = 0.0
     r = 1.0
     if route == "msdt":
-        gen = msdt_updates(T, A, n_sweeps * N, ctr)
+        gen = msdt_updates(T, A, n_sweeps * N, ctr, levels)
     for sweep in range(n_sweeps):
         if route == "naive":
             items = ((n, None) for n in range(N))

@@ -121,6 +121,7 @@ struct cp_ctx {
     float* splitk_ws = nullptr;
     bool fuse_dt = true;
     bool fuse_child = false;
+    int msdt_levels = 1;       // upper levels of the multi-sweep tree combined (Sec. IV)
     long long wait_limit = 0;  // tensor-core TTM's bounded waits (cycles; 0: about 1 s)  // TTM epilogue forms the first child (multi-sweep tree)
     float* child_ws = nullptr;  // pieces of first-child segments that cross TTM tiles
     size_t child_ws_cap = 0;
@@ -348,6 +349,14 @@ Slot* find_node(cp_ctx* c, uint32_t mask) {
     return nullptr;
 }
 
+// Tree intermediates are allocated on first use: a schedule that never forms a
+// level (the fused standard tree, the multi-sweep tree with combined upper
+// levels) never holds its memory.
+cp_status slot_buf(cp_ctx* c, Slot& s) {
+    if (!s.buf && s.cap) CKST(dalloc(c, &s.buf, s.cap));
+    return CP_OK;
+}
+
 // The main stream waits for the look-ahead contraction in flight, if any.
 cp_status ahead_join(cp_ctx* c) {
     if (!c->ahead_pending) return CP_OK;
@@ -405,10 +414,12 @@ cp_status ensure_node(cp_ctx* c, const int* path, int d, float** out, bool fuse2
         return CP_OK;
     }
     Slot& s = c->slot[c->N - d];
+    CKST(slot_buf(c, s));
     s.valid = false;
     const int lo_m = d >= 2 ? std::min(path[0], path[1]) : -1;
     if (d == 2 && child && !find_node(c, 1u << path[0]) && child_fusable(c, path[0], path[1])) {
         Slot& root = c->slot[c->N - 1];
+        CKST(slot_buf(c, root));
         root.valid = false;
         CKST(launch_ttm_child(c, path[0], path[1], root.buf, s.buf));
         root.valid = true;
@@ -416,7 +427,7 @@ cp_status ensure_node(cp_ctx* c, const int* path, int d, float** out, bool fuse2
         for (int k = 0; k < c->N; ++k) root.ver[k] = c->ver[k];
     } else if (d == 1) {
         CKST(launch_ttm(c, path[0], s.buf));
-    } else if (d == 2 && fuse2 && c->fuse_dt && std::abs(path[0] - path[1]) == 1 && c->kr_plan[lo_m]) {
+    } else if (d == 2 && fuse2 && std::abs(path[0] - path[1]) == 1 && c->kr_plan[lo_m]) {
         CKST(launch_fused2(c, lo_m, s.buf));
     } else {
         float* parent = nullptr;
@@ -463,14 +474,20 @@ std::vector<int> dt_path(int N, int u, bool* fuse2 = nullptr) {
 }
 
 // MSDT (Sec. III): update t belongs to subtree j = t / (N-1) with root mode
-// m = (N-1-j) mod N serving leaves m+1, ..., m+N-1 (mod N).
-std::vector<int> msdt_path(int N, int64_t t, int* u_out) {
-    const int64_t j = t / (N - 1);
-    const int m = (int)(((N - 1 - j) % N + N) % N);
-    std::vector<int> leaves(N - 1), seq;
-    for (int i = 0; i < N - 1; ++i) leaves[i] = (m + 1 + i) % N;
-    const int u = leaves[(size_t)(t % (N - 1))];
-    seq.push_back(m);
+// m = (N-1-j) mod N serving leaves m+1, ..., m+N-1 (mod N).  With the upper
+// `levels` = l levels combined (Sec. IV: the memory / cost trade-off), subtree
+// j = t / (N-l) starts at update t0 = j (N-l); its root contracts the l modes
+// updated just before, t0-1, ..., t0-l (mod N), in one pass over T when l = 2 and
+// they are adjacent (Khatri-Rao operand), and serves leaves t0, ..., t0+N-l-1.
+// For l = 1 both descriptions give the same tree.
+std::vector<int> msdt_path(int N, int64_t t, int* u_out, int levels = 1) {
+    const int l = levels;
+    const int64_t j = t / (N - l);
+    const int64_t t0 = j * (N - l);
+    std::vector<int> leaves(N - l), seq;
+    for (int i = 0; i < N - l; ++i) leaves[i] = (int)((t0 + i) % N);
+    const int u = leaves[(size_t)(t - t0)];
+    for (int i = 0; i < l; ++i) seq.push_back((int)(((t0 - 1 - i) % N + N) % N));
     tree_path(leaves, u, seq);
     *u_out = u;
     return seq;
@@ -640,7 +657,7 @@ cp_status entry_check(cp_ctx* c) {
 // while b is updated.
 cp_status msdt_lookahead(cp_ctx* c, int64_t t) {
     const int N = c->N;
-    if (!c->lookahead || N < 4 || !c->ahead) return CP_OK;
+    if (!c->lookahead || N < 4 || !c->ahead || c->msdt_levels != 1) return CP_OK;
     if (t / (N - 1) != (t + 2) / (N - 1)) return CP_OK;
     int u1 = 0, u2 = 0;
     const std::vector<int> p1 = msdt_path(N, t + 1, &u1), p2 = msdt_path(N, t + 2, &u2);
@@ -652,8 +669,9 @@ cp_status msdt_lookahead(cp_ctx* c, int64_t t) {
     if (find_node(c, mask)) return CP_OK;
     Slot* parent = find_node(c, root);
     const int k = N - 2;
-    if (!parent || parent == &c->alt[N - 1] || !c->alt[k].buf || c->alt_busy[k] > t) return CP_OK;
+    if (!parent || parent == &c->alt[N - 1] || !c->alt[k].cap || c->alt_busy[k] > t) return CP_OK;
     Slot& s = c->alt[k];
+    CKST(slot_buf(c, s));
     s.valid = false;
     CKCUDA(c, cudaEventRecord(c->ev_x, c->st));
     CKCUDA(c, cudaStreamWaitEvent(c->ahead, c->ev_x, 0));
@@ -679,22 +697,25 @@ cp_status exact_sweep(cp_ctx* c, bool msdt, int k, bool keep_ahead = false) {
         bool fuse2 = false;
         const int64_t t = c->t_msdt;
         if (msdt) {
-            path = msdt_path(c->N, t, &u);
+            path = msdt_path(c->N, t, &u, c->msdt_levels);
             c->t_msdt++;
             if (c->ahead_pending && t >= c->ahead_target) CKST(ahead_join(c));
+            // combined levels: the root's two contracted modes in one pass over T
+            fuse2 = c->msdt_levels >= 2;
         } else {
             CKST(ahead_join(c));
             path = dt_path(c->N, u0, &fuse2);
+            fuse2 = fuse2 && c->fuse_dt;
         }
         if (!(c->chol_pending && c->chol_mode == u)) CKST(launch_chol(c, u, false, scal_slot(c, k, u)));
         float* M = nullptr;
-        CKST(mttkrp_leaf(c, path, &M, fuse2, msdt));
+        CKST(mttkrp_leaf(c, path, &M, fuse2, msdt && c->msdt_levels == 1));
         CKST(update_mode(c, u, M, false, scal_slot(c, k, u)));
         if (msdt && c->lookahead && u0 + 1 < c->N) {
             // the next update's factorisation goes first, so that its one-CTA inverse
             // finds an SM before the look-ahead contraction fills them
             int un = 0;
-            msdt_path(c->N, c->t_msdt, &un);
+            msdt_path(c->N, c->t_msdt, &un, c->msdt_levels);
             CKST(launch_chol(c, un, false, scal_slot(c, k, un)));
         }
         if (msdt) CKST(msdt_lookahead(c, t));
@@ -1253,12 +1274,8 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
     for (int k = 1; k < N; ++k) {
         int64_t cap = R;
         for (int i = 0; i < k; ++i) cap *= sd[i];
-        TRY(dalloc(c, &c->slot[k].buf, (size_t)cap));
-        c->slot[k].cap = (size_t)cap;
-        if (N >= 4 && k == N - 2) {  // look-ahead slot of the multi-sweep tree
-            TRY(dalloc(c, &c->alt[k].buf, (size_t)cap));
-            c->alt[k].cap = (size_t)cap;
-        }
+        c->slot[k].cap = (size_t)cap;           // allocated on first use
+        if (N >= 4 && k == N - 2) c->alt[k].cap = (size_t)cap;  // look-ahead slot of the multi-sweep tree
     }
     TRYC(cudaStreamCreateWithFlags(&c->ahead, cudaStreamNonBlocking));
     TRYC(cudaEventCreateWithFlags(&c->ev_x, cudaEventDisableTiming));
@@ -1389,6 +1406,7 @@ cp_status cp_mttkrp(cp_ctx* c, int mode, float* M_dev) {
     float* M = nullptr;
     bool fuse2 = false;
     std::vector<int> path = dt_path(c->N, mode, &fuse2);
+    fuse2 = fuse2 && c->fuse_dt;
     CKST(mttkrp_leaf(c, path, &M, fuse2));
     CKCUDA(c, cudaMemcpyAsync(M_dev, M, sizeof(float) * c->dims[mode] * c->R, cudaMemcpyDeviceToDevice, c->st));
     return CP_OK;
@@ -1459,6 +1477,11 @@ cp_status cp_set_option(cp_ctx* c, int option, int value) {
         case CP_OPT_WAIT_LIMIT:
             if (value < 0) return CP_EINVAL;
             c->wait_limit = value;
+            return CP_OK;
+        case CP_OPT_MSDT_LEVELS:
+            if (value < 1 || value > std::max(1, c->N - 2)) return CP_EINVAL;
+            CKST(ahead_join(c));
+            c->msdt_levels = value;
             return CP_OK;
         default: return CP_EINVAL;
     }

@@ -515,3 +515,33 @@ def test_pp_collinear_law_follows_oracle(pkg):
     _, r = ctx.fit(exact=True)
     assert abs(r - co.residual_direct(Tref, ref.A)) <= FIT_TOL["f16x3"]
     ctx.close()
+
+
+@pytest.mark.parametrize("dims,R,levels", [((24, 20, 22, 18), 8, 2), ((7, 6, 8, 5, 6), 3, 2),
+                                           ((7, 6, 8, 5, 6), 3, 3), ((6, 5, 6, 5, 6, 5), 3, 4)])
+@pytest.mark.parametrize("prec", ["f16x3", "fp32"])
+def test_msdt_combined_levels(pkg, dims, R, levels, prec):
+    """Multi-sweep tree with the upper l levels combined (Sec. IV): the same MTTKRPs
+    as every other tree, N first-level passes per N - l sweeps, and for l = 2 the
+    root is one tensor-core pass with the Khatri-Rao operand when its modes are
+    adjacent."""
+    N = len(dims)
+    Td, Tref, A0 = problem(dims, R, 42, eta=0.05)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    ctx.set_option("msdt_levels", levels)
+    nsw = 2 * (N - levels)
+    ctx.sweep_msdt(nsw)
+    ref = co.cp_als(Tref, A0, nsw, route="msdt", levels=levels)
+    got = np.array([t["resid"] for t in ctx.trace()])
+    assert np.abs(got - np.array(ref.resid)).max() <= 1e-5
+    _, r = ctx.fit(exact=True)
+    assert abs(r - co.residual_direct(Tref, ref.A)) <= FIT_TOL[prec]
+    st = ctx.stats()
+    assert st["ttm"] == ref.counters.ttm == 2 * N
+    if prec != "fp32" and levels == 2:
+        # roots (t0-1, t0-2): adjacent except when they wrap around mode 0
+        roots = [sorted(((j * (N - 2) - 1) % N, (j * (N - 2) - 2) % N)) for j in range(2 * N)]
+        assert st["ttm_fused"] == sum(1 for a, b in roots if b - a == 1)
+    with pytest.raises(pkg.CPError):
+        ctx.set_option("msdt_levels", N - 1)
+    ctx.close()

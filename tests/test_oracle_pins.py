@@ -161,6 +161,63 @@ def test_first_level_ttm_counts_table1():
         assert r_dt.counters.ttm_flops == pytest.approx(4 * s ** N * 2 * sweeps)
 
 
+@pytest.mark.parametrize("dims,levels", [((4, 5, 3, 6), 2), ((3, 4, 3, 4, 3), 2), ((3, 4, 3, 4, 3), 3),
+                                         ((3, 3, 2, 3, 3, 2), 4)])
+def test_combined_level_msdt_mttkrps_equal_definition(dims, levels):
+    """Multi-sweep tree with the upper `levels` levels combined (Sec. IV): every
+    MTTKRP equals the definition with the factors current at that moment."""
+    N = len(dims)
+    A = synth.uniform_factors(5, dims, 4)
+    T = synth.normal(6, 0, int(np.prod(dims))).reshape(dims)
+    n_upd = 2 * N * (N - levels)
+    count = 0
+    for n, M in co.msdt_updates(T, A, n_upd, levels=levels):
+        assert n == count % N                       # updates stay in mode order
+        ref = co.mttkrp(T, A, n)
+        assert np.abs(M - ref).max() <= 1e-12 * np.abs(ref).max()
+        A[n] = A[n] * 0.5 + 0.1 * synth.uniform(8, count, A[n].size).reshape(A[n].shape)
+        count += 1
+    assert count == n_upd
+
+
+@pytest.mark.parametrize("N,levels", [(4, 2), (5, 2), (5, 3), (6, 2), (6, 4)])
+def test_combined_level_msdt_costs(N, levels):
+    """Sec. IV: with the upper l levels combined, one pass over T per N - l updates
+    (2N/(N-l) s^N R flops per sweep, counted once per pass) and auxiliary memory of
+    s^(N-l) R: the largest intermediate the tree forms."""
+    s, R = 3, 2
+    dims = (s,) * N
+    T = synth.normal(9, 0, s ** N).reshape(dims)
+    A = synth.uniform_factors(10, dims, R)
+    ctr = co.Counters()
+    sweeps = N - levels                          # a whole number of subtrees
+    biggest = 0
+    for n, M in co.msdt_updates(T, A, sweeps * N, ctr, levels=levels):
+        pass
+    assert ctr.ttm == N
+    assert ctr.ttm_flops == pytest.approx(2 * N / (N - levels) * s ** N * R * sweeps)
+    # every first-level node keeps N - l modes
+    kept = [child for parent, child in ctr.edges if parent == "T"]
+    assert all(len(k) == N - levels for k in kept)
+    # each root contracts the l modes updated just before its subtree, all distinct
+    for j, modes in enumerate(ctr.ttm_modes):
+        t0 = j * (N - levels)
+        want = sorted((t0 - 1 - i) % N for i in range(levels))
+        assert sorted(modes if isinstance(modes, tuple) else (modes,)) == want
+    with pytest.raises(ValueError):
+        next(co.msdt_updates(T, A, 1, levels=N - 1))
+
+
+@pytest.mark.parametrize("dims,levels", [((5, 4, 6, 3), 2), ((3, 4, 3, 5, 3), 3)])
+def test_combined_level_msdt_trajectory_is_als(dims, levels):
+    T, F, A0 = synth.make_problem(41, dims, 3, eta=0.1)
+    a = co.cp_als(T, A0, 8, route="naive")
+    c = co.cp_als(T, A0, 8, route="msdt", levels=levels)
+    for n in range(len(dims)):
+        assert np.abs(a.A[n] - c.A[n]).max() < 1e-10 * np.abs(a.A[n]).max()
+    assert np.allclose(a.resid, c.resid, rtol=0, atol=1e-12)
+
+
 # ----------------------------------------------------------------------------- solve / residual
 
 
