@@ -86,7 +86,8 @@ void cp_config_default(cp_config *cfg);
  * cp_init - create a decomposition context (Alg. 1, line 2; Alg. 2, line 2).
  *   N        tensor order, 3 <= N <= 8
  *   dims     N mode sizes, each >= 1; host array, copied
- *   R        rank, 1 <= R <= 256
+ *   R        rank, 1 <= R <= 512 (the tensor-core TTM runs in column passes of
+ *            128, the normal equations' FP32 inverse in blocks of 128)
  *   T_dev    pointer to the tensor, C order, contiguous.  dtype 0: FP32 on the
  *            device, borrowed (must outlive the context, never written); dtype 1:
  *            FP64 on the device, converted once into a library-owned FP32 copy;

@@ -10,7 +10,7 @@
 #include "../../include/cpals.h"
 
 #define CP_MAXN 8
-#define CP_MAXR 256
+#define CP_MAXR 512
 #define CP_NSCAL 8  // per-update scalar slots, see SCAL_* below
 
 // Per-update scalar reductions written by the solve kernel (partials per block,

@@ -18,6 +18,8 @@
 //                 four orders of magnitude below the FP32 rounding of M itself.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "cpals_internal.h"
 
 namespace {
@@ -362,13 +364,14 @@ __global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(const float* __restrict__
     }
 }
 
-// ------------------------------------------------------------------ 128 < R <= 256
-// Gt = D Gamma D is inverted by blocks (n1 = 128, n2 = R - 128):
+// ------------------------------------------------------------------ 128 < R <= 512
+// Gt = D Gamma D is inverted by blocks, recursively (n1 = 128, n2 = n - 128):
 //   Gt = [[A, B], [B^T, C]],  S = C - B^T A^{-1} B (Schur complement, SPD),
 //   Gt^{-1} = [[A^{-1} + T2 T1^T, -T2], [-T2^T, S^{-1}]],  T1 = A^{-1} B,  T2 = T1 S^{-1},
-// with the two block inverses by the Gauss-Jordan kernel above (each scales its
-// own block) and four small FP32 GEMMs.  If a block pivot fails or the scaled
-// condition number exceeds 1e6, the FP64 factorisation runs instead.
+// with A^{-1} by the Gauss-Jordan kernel above (which scales its own block), S^{-1}
+// by the same construction on the n2 x n2 complement (a single Gauss-Jordan block
+// once n2 <= 128), and four small FP32 GEMMs per level.  If a block pivot fails or
+// the scaled condition number exceeds 1e6, the FP64 factorisation runs instead.
 
 // Gt = D G32 D (FP32, row stride R) and ||Gt||_inf; flags[0] = 0
 __global__ void __launch_bounds__(256) k_scale_big(const float* __restrict__ G32, int R, float* __restrict__ Gt,
@@ -490,25 +493,34 @@ __global__ void __launch_bounds__(256) k_gemm_small(int M, int N, int K, float a
         }
 }
 
-// assemble D Gt^{-1} D into Ginv, check the scaled condition number, choose the path
-__global__ void __launch_bounds__(256) k_schur_finish(int R, const float* __restrict__ B11,
-                                                      const float* __restrict__ T2, const float* __restrict__ Si,
-                                                      const float* __restrict__ dvec, float* __restrict__ Ginv,
-                                                      unsigned* __restrict__ flags, double* __restrict__ scal,
-                                                      int* __restrict__ mode) {
+// the off-diagonal blocks of one recursion level: dst_tr = -T2 (n1 x n2) and
+// dst_bl = -T2^T (n2 x n1), both with row stride ldd
+__global__ void __launch_bounds__(256) k_neg_blocks(const float* __restrict__ T2, int n1, int n2,
+                                                    float* __restrict__ dst_tr, float* __restrict__ dst_bl, int ldd) {
+    const int64_t n = (int64_t)n1 * n2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n2), j = (int)(e % n2);
+        const float v = -T2[e];
+        dst_tr[(size_t)i * ldd + j] = v;
+        dst_bl[(size_t)j * ldd + i] = v;
+    }
+}
+
+// Ginv = D W D from the assembled inverse W of Gt (row stride R), the scaled
+// condition number ||Gt||_inf ||W||_inf against 1e6, and the path decision
+__global__ void __launch_bounds__(256) k_inv_finish(int R, const float* __restrict__ Wi,
+                                                    const float* __restrict__ dvec, float* __restrict__ Ginv,
+                                                    unsigned* __restrict__ flags, double* __restrict__ scal,
+                                                    int* __restrict__ mode) {
     __shared__ float wsum[8];
     __shared__ unsigned imax_bits;
-    const int tid = threadIdx.x, n1 = 128, n2 = R - 128;
+    const int tid = threadIdx.x;
     if (tid == 0) imax_bits = 0u;
     __syncthreads();
     for (int r = blockIdx.x; r < R; r += gridDim.x) {
         float rs = 0.f;
         for (int c = tid; c < R; c += blockDim.x) {
-            float v;
-            if (r < n1 && c < n1) v = B11[(size_t)r * n1 + c];
-            else if (r < n1) v = -T2[(size_t)r * n2 + (c - n1)];
-            else if (c < n1) v = -T2[(size_t)c * n2 + (r - n1)];
-            else v = Si[(size_t)(r - n1) * n2 + (c - n1)];
+            const float v = Wi[(size_t)r * R + c];
             rs += fabsf(v);
             Ginv[(size_t)r * R + c] = v * (dvec[r] * dvec[c]);
         }
@@ -735,23 +747,26 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
         double prev = 0.0;
         bool conv = false;
         for (int itr = 0; itr < 30; ++itr) {
-            // r = m - x Gamma (FP64).  Eight partial sums per column, the thread's
-            // columns interleaved: 8 CT independent chains cover the FP64 FMA
-            // latency (64 cycles) with the few warps a row has.
+            // r = m - x Gamma (FP64).  NQ partial sums per column, the thread's
+            // columns interleaved: NQ CT independent chains cover the FP64 FMA
+            // latency (64 cycles) with the few warps a row has (eight for up to
+            // four columns per thread, four beyond: R > 256 keeps 32+ chains in
+            // about 130 registers)
             {
-                double ra[CT][8];
+                constexpr int NQ = CT <= 4 ? 8 : 4;
+                double ra[CT][NQ];
                 int jj[CT];
 #pragma unroll
                 for (int c = 0; c < CT; ++c) {
                     const int j = tid + SOLVE_THREADS * c;
                     jj[c] = j < R ? j : 0;  // idle columns read column 0 and are dropped
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) ra[c][q] = 0.0;
+                    for (int q = 0; q < NQ; ++q) ra[c][q] = 0.0;
                 }
                 int k = 0;
-                for (; k + 7 < R; k += 8) {
+                for (; k + NQ - 1 < R; k += NQ) {
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
+                    for (int q = 0; q < NQ; ++q) {
                         const double xk = xv[k + q];
                         const double* grow = Gm + (size_t)(k + q) * R;
 #pragma unroll
@@ -766,8 +781,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
                 for (int c = 0; c < CT; ++c) {
                     const int j = tid + SOLVE_THREADS * c;
                     if (j < R) {
-                        const double t = ((ra[c][0] + ra[c][1]) + (ra[c][2] + ra[c][3])) +
-                                         ((ra[c][4] + ra[c][5]) + (ra[c][6] + ra[c][7]));
+                        double t;
+                        if (NQ == 8)
+                            t = ((ra[c][0] + ra[c][1]) + (ra[c][2] + ra[c][3])) +
+                                ((ra[c][4 % NQ] + ra[c][5 % NQ]) + (ra[c][6 % NQ] + ra[c][7 % NQ]));
+                        else
+                            t = (ra[c][0] + ra[c][1]) + (ra[c][2 % NQ] + ra[c][3 % NQ]);
                         rv[j] = (float)(mj[c] - t);
                     }
                 }
@@ -951,9 +970,47 @@ cudaError_t launch_solve_mixed(const float* M, const double* W, const double* G,
 
 namespace cpk {
 
-size_t schur_ws_floats(int R) {
-    return R <= MIXED_MAXR ? 0 : (size_t)R * R + 6 * 128 * 128 + R + 4;
+// workspace of one recursion level of the blocked inverse for an n x n block
+static size_t inv_level_floats(int n) {
+    if (n <= MIXED_MAXR) return 0;
+    const size_t n1 = MIXED_MAXR, n2 = (size_t)n - n1;
+    return n1 * n1 + 2 * n1 * n2 + n2 * n2 + inv_level_floats((int)n2);   // Ai, T1, T2, S, deeper levels
 }
+
+size_t schur_ws_floats(int R) {
+    // Gt, the assembled inverse W, the levels' blocks, dvec, 4 flag words
+    return R <= MIXED_MAXR ? 0 : 2 * (size_t)R * R + inv_level_floats(R) + R + 4;
+}
+
+// W (row stride ldw) = inverse of the n x n SPD block G (row stride ldg), FP32, by
+// the recursive Schur construction above; ws holds inv_level_floats(n) floats.
+static void inv_blocked(const float* G, int ldg, int n, float* W, int ldw, float* ws, unsigned* flags,
+                        cudaStream_t st) {
+    if (n <= MIXED_MAXR) {
+        k_gj_block<16, 8, 4><<<1, 512, 0, st>>>(G, ldg, n, W, ldw, flags);
+        return;
+    }
+    const int n1 = MIXED_MAXR, n2 = n - n1;
+    float* Ai = ws;
+    float* T1 = Ai + (size_t)n1 * n1;
+    float* T2 = T1 + (size_t)n1 * n2;
+    float* S = T2 + (size_t)n1 * n2;
+    float* deeper = S + (size_t)n2 * n2;
+    auto grid = [](int M, int Nn) { return dim3((unsigned)((Nn + 31) / 32), (unsigned)((M + 31) / 32)); };
+    const float* B = G + n1;                       // n1 x n2, row stride ldg
+    const float* C = G + (size_t)n1 * ldg + n1;    // n2 x n2
+    k_gj_block<16, 8, 4><<<1, 512, 0, st>>>(G, ldg, n1, Ai, n1, flags);                        // A^{-1}
+    k_gemm_small<<<grid(n1, n2), 256, 0, st>>>(n1, n2, n1, 1.f, Ai, n1, 0, B, ldg, 0, 0.f, nullptr, 0, T1, n2);
+    k_gemm_small<<<grid(n2, n2), 256, 0, st>>>(n2, n2, n1, -1.f, B, ldg, 1, T1, n2, 0, 1.f, C, ldg, S, n2);
+    float* Wbr = W + (size_t)n1 * ldw + n1;
+    inv_blocked(S, n2, n2, Wbr, ldw, deeper, flags, st);                                         // S^{-1}
+    k_gemm_small<<<grid(n1, n2), 256, 0, st>>>(n1, n2, n2, 1.f, T1, n2, 0, Wbr, ldw, 0, 0.f, nullptr, 0, T2, n2);
+    k_gemm_small<<<grid(n1, n1), 256, 0, st>>>(n1, n1, n2, 1.f, T2, n2, 0, T1, n2, 1, 1.f, Ai, n1, W, ldw);
+    const int64_t ne = (int64_t)n1 * n2;
+    k_neg_blocks<<<(unsigned)std::min<int64_t>(1024, (ne + 255) / 256), 256, 0, st>>>(T2, n1, n2, W + n1,
+                                                                                   W + (size_t)n1 * ldw, ldw);
+}
+
 
 cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
                        double* Gamma, float* G32, float* Ginv, double* L64, double* invd64, double* W,
@@ -961,30 +1018,16 @@ cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int
     k_gamma_form<<<(R * R + 255) / 256, 256, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, G32, W);
     if (R > MIXED_MAXR) {
         if (!ws) return cudaErrorInvalidValue;
-        const int n1 = 128, n2 = R - 128;
         float* Gt = ws;
-        float* Ai = Gt + (size_t)R * R;
-        float* T1 = Ai + 128 * 128;
-        float* Sm = T1 + 128 * 128;
-        float* Si = Sm + 128 * 128;
-        float* T2 = Si + 128 * 128;
-        float* B11 = T2 + 128 * 128;
-        float* dvec = B11 + 128 * 128;
+        float* Wi = Gt + (size_t)R * R;
+        float* lev = Wi + (size_t)R * R;
+        float* dvec = lev + inv_level_floats(R);
         unsigned* flags = reinterpret_cast<unsigned*>(dvec + R);
         cudaError_t e = cudaMemsetAsync(flags, 0, 4 * sizeof(unsigned), st);
         if (e != cudaSuccess) return e;
-        auto grid = [](int M, int Nn) { return dim3((unsigned)((Nn + 31) / 32), (unsigned)((M + 31) / 32)); };
         k_scale_big<<<64, 256, 0, st>>>(G32, R, Gt, dvec, flags);
-        k_gj_block<16, 8, 4><<<1, 512, 0, st>>>(Gt, R, n1, Ai, n1, flags);
-        k_gemm_small<<<grid(n1, n2), 256, 0, st>>>(n1, n2, n1, 1.f, Ai, n1, 0, Gt + n1, R, 0, 0.f, nullptr, 0,
-                                                     T1, n2);
-        k_gemm_small<<<grid(n2, n2), 256, 0, st>>>(n2, n2, n1, -1.f, Gt + n1, R, 1, T1, n2, 0, 1.f,
-                                                     Gt + (size_t)n1 * R + n1, R, Sm, n2);
-        k_gj_block<16, 8, 4><<<1, 512, 0, st>>>(Sm, n2, n2, Si, n2, flags);
-        k_gemm_small<<<grid(n1, n2), 256, 0, st>>>(n1, n2, n2, 1.f, T1, n2, 0, Si, n2, 0, 0.f, nullptr, 0, T2,
-                                                     n2);
-        k_gemm_small<<<grid(n1, n1), 256, 0, st>>>(n1, n1, n2, 1.f, T2, n2, 0, T1, n2, 1, 1.f, Ai, n1, B11, n1);
-        k_schur_finish<<<64, 256, 0, st>>>(R, B11, T2, Si, dvec, Ginv, flags, scal, mode);
+        inv_blocked(Gt, R, R, Wi, R, lev, flags, st);
+        k_inv_finish<<<64, 256, 0, st>>>(R, Wi, dvec, Ginv, flags, scal, mode);
         k_chol_fp64_if<<<1, 1024, 0, st>>>(Gamma, R, L64, invd64, scal, mode);
         return cudaGetLastError();
     }
@@ -1013,6 +1056,10 @@ cudaError_t solve_mixed(const float* M, const double* W, const double* Gamma, co
         case 6: return launch_solve_mixed<6>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
         case 7: return launch_solve_mixed<7>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
         case 8: return launch_solve_mixed<8>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        case 9: case 10: return launch_solve_mixed<10>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        case 11: case 12: return launch_solve_mixed<12>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        case 13: case 14: return launch_solve_mixed<14>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        case 15: case 16: return launch_solve_mixed<16>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
         default: return cudaErrorInvalidValue;
     }
 }

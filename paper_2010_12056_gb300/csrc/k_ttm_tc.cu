@@ -92,8 +92,8 @@ struct TcArgs {
     // innermost, so a tile's second pass finds its T chunks in L2.  R / Rpad above
     // are the largest pass's (they size the shared-memory slots and TMEM sets).
     int npass;
-    int Rp[2], Rpadp[2];   // columns of pass p (written at column 128 p of X), padded
-    uint32_t idescp[2];    // MMA instruction descriptor of pass p (N = Rpadp[p])
+    int Rp[4], Rpadp[4];   // columns of pass p (written at column 128 p of X), padded
+    uint32_t idescp[4];    // MMA instruction descriptor of pass p (N = Rpadp[p])
     int set_cols;          // TMEM columns of one accumulator set
     uint32_t idesc;
     unsigned* dev_err;
@@ -305,7 +305,7 @@ struct Layout {
 };
 
 // scaled fp16 parts: the per-column output scales of both passes in shared memory
-constexpr int CS_BYTES = 256 * 4;
+constexpr int CS_BYTES = 512 * 4;
 
 __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, int nk, int b_resident,
                                                int BK, int ew, int kind, bool child = false, int ac_bytes = 0) {
@@ -330,7 +330,9 @@ template <int MODE, int KIND, int CHILD, int EW>
 __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
     k_ttm_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmBhi,
              const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmBhi1,
-             const __grid_constant__ CUtensorMap tmBlo1, const TcArgs a) {
+             const __grid_constant__ CUtensorMap tmBlo1, const __grid_constant__ CUtensorMap tmBhi2,
+             const __grid_constant__ CUtensorMap tmBlo2, const __grid_constant__ CUtensorMap tmBhi3,
+             const __grid_constant__ CUtensorMap tmBlo3, const TcArgs a) {
     constexpr int BK = KIND == 1 ? 32 : 64;
     constexpr uint32_t STG = BM * BK * 4;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -420,6 +422,14 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                 asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBhi1) : "memory");
                 asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBlo1) : "memory");
             }
+            if (a.npass > 2) {
+                asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBhi2) : "memory");
+                asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBlo2) : "memory");
+            }
+            if (a.npass > 3) {
+                asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBhi3) : "memory");
+                asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBlo3) : "memory");
+            }
             if (a.b_resident) {
                 mbar_expect_tx(b_full, (uint32_t)a.nk * bchunk);
                 for (int kc = 0; kc < a.nk; ++kc) {
@@ -435,8 +445,8 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                 const int64_t tile = w / ((int64_t)a.nsk * a.npass);
                 const int ks = (int)((w / a.npass) % a.nsk);
                 const int pass = (int)(w % a.npass);
-                const CUtensorMap* mhi = pass ? &tmBhi1 : &tmBhi;
-                const CUtensorMap* mlo = pass ? &tmBlo1 : &tmBlo;
+                const CUtensorMap* mhi = pass == 0 ? &tmBhi : pass == 1 ? &tmBhi1 : pass == 2 ? &tmBhi2 : &tmBhi3;
+                const CUtensorMap* mlo = pass == 0 ? &tmBlo : pass == 1 ? &tmBlo1 : pass == 2 ? &tmBlo2 : &tmBlo3;
                 const int kc0 = ks * a.nk / a.nsk, kc1 = (ks + 1) * a.nk / a.nsk;
                 for (int kc = kc0; kc < kc1 && ok; ++kc, ++it) {
                     const int s = (int)(it % S_stg);
@@ -936,7 +946,7 @@ namespace cpk {
 
 // R > 128 runs as column passes of at most 128 (one MMA N and one TMEM layout
 // that fit); pass p multiplies by factor rows 128 p .. and writes those columns.
-constexpr int MAX_PASS = 2, PASS_COLS = 128;
+constexpr int MAX_PASS = 4, PASS_COLS = 128;
 
 struct TcPass {
     CUtensorMap tmBhi, tmBlo;
@@ -1068,11 +1078,14 @@ int ttm_tc_splitk(const TcPlan* pl, int num_sms) {
 int64_t ttm_tc_rows(const TcPlan* pl) { return pl->PQ; }
 
 template <int MODE, int KIND, int CHILD, int EW>
-static cudaError_t launch(const TcPlan* pl, const TcPass& p1, const TcArgs& a, size_t smem, unsigned grid,
+static cudaError_t launch(const TcPlan* pl, const TcArgs& a, size_t smem, unsigned grid,
                           cudaStream_t st) {
     cudaFuncSetAttribute(k_ttm_tc<MODE, KIND, CHILD, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ttm_tc<MODE, KIND, CHILD, EW><<<grid, nthreads(EW, CHILD), smem, st>>>(pl->tmT, pl->pass[0].tmBhi, pl->pass[0].tmBlo,
-                                                              p1.tmBhi, p1.tmBlo, a);
+    // passes beyond npass repeat pass 0's maps (never read)
+    auto ps = [&](int q) -> const TcPass& { return pl->pass[q < pl->npass ? q : 0]; };
+    k_ttm_tc<MODE, KIND, CHILD, EW><<<grid, nthreads(EW, CHILD), smem, st>>>(
+        pl->tmT, ps(0).tmBhi, ps(0).tmBlo, ps(1).tmBhi, ps(1).tmBlo, ps(2).tmBhi, ps(2).tmBlo, ps(3).tmBhi,
+        ps(3).tmBlo, a);
     return cudaGetLastError();
 }
 
@@ -1211,7 +1224,7 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     // instruction-descriptor operand format: F16 = 0, BF16 = 1 (kind::f16); TF32 = 2 (kind::tf32)
     const uint32_t fmt = pl->kind == 0 ? 1u : (pl->kind == 1 ? 2u : 0u);
     a.npass = pl->npass;
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < MAX_PASS; ++q) {
         const TcPass& ps = pl->pass[q < pl->npass ? q : 0];
         a.Rp[q] = ps.R;
         a.Rpadp[q] = ps.Rpad;
@@ -1236,16 +1249,15 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     const int64_t nwork = a.ntiles * a.nsk * a.npass;
     const unsigned grid = (unsigned)(nwork < num_sms ? nwork : num_sms);
     if (grid == 0) return cudaSuccess;
-    const TcPass& p1 = pl->pass[pl->npass > 1 ? 1 : 0];
     cudaError_t e;
     const int ck = child ? (child->sc % 32 == 0 ? 1 : 2) : 0;
 #define CP_TTM_LAUNCH(C, W)                                                                               \
-    (pl->mode == 0 ? (pl->kind == 0   ? launch<0, 0, C, W>(pl, p1, a, smem, grid, st)                   \
-                      : pl->kind == 1 ? launch<0, 1, C, W>(pl, p1, a, smem, grid, st)                   \
-                                      : launch<0, 2, C, W>(pl, p1, a, smem, grid, st))                  \
-                   : (pl->kind == 0   ? launch<1, 0, C, W>(pl, p1, a, smem, grid, st)                   \
-                      : pl->kind == 1 ? launch<1, 1, C, W>(pl, p1, a, smem, grid, st)                   \
-                                      : launch<1, 2, C, W>(pl, p1, a, smem, grid, st)))
+    (pl->mode == 0 ? (pl->kind == 0   ? launch<0, 0, C, W>(pl, a, smem, grid, st)                   \
+                      : pl->kind == 1 ? launch<0, 1, C, W>(pl, a, smem, grid, st)                   \
+                                      : launch<0, 2, C, W>(pl, a, smem, grid, st))                  \
+                   : (pl->kind == 0   ? launch<1, 0, C, W>(pl, a, smem, grid, st)                   \
+                      : pl->kind == 1 ? launch<1, 1, C, W>(pl, a, smem, grid, st)                   \
+                                      : launch<1, 2, C, W>(pl, a, smem, grid, st)))
     if (ck == 1)
         e = CP_TTM_LAUNCH(1, 4);
     else if (ck == 2)

@@ -20,6 +20,7 @@
 namespace {
 
 constexpr int64_t NOALLOC_MAX_TILES = 65536;
+constexpr int NOALLOC_MAXR = 256;   // the rank limit this entry point documents
 
 // [0, MAX): per-tile sum of (t - t~)^2;  [MAX, 2 MAX): per-tile sum of t^2.
 // Every slot a call reads is written earlier in the same call, so nothing has
@@ -166,7 +167,7 @@ cudaError_t scratch_for_current_device(double** p) {
 
 extern "C" cp_status cp_resid_noalloc(int N, const int64_t* dims, int R, const float* T_dev,
                                       const float* const* A_dev, double* out_dev, void* stream) {
-    if (N < 3 || N > CP_MAXN || !dims || R < 1 || R > CP_MAXR || !T_dev || !A_dev || !out_dev)
+    if (N < 3 || N > CP_MAXN || !dims || R < 1 || R > NOALLOC_MAXR || !T_dev || !A_dev || !out_dev)
         return CP_EINVAL;
     Args a;
     a.T = T_dev;

@@ -41,7 +41,7 @@ def test_invalid_arguments_rejected_before_device_use(lib):
     fake = ctypes.c_void_p(16)          # never dereferenced: validation fails first
     assert lib.cp_init(ctypes.byref(h), 2, dims, 3, fake, 0, None, None, None) == 1  # N < 3
     assert lib.cp_init(ctypes.byref(h), 3, dims, 0, fake, 0, None, None, None) == 1  # R < 1
-    assert lib.cp_init(ctypes.byref(h), 3, dims, 257, fake, 0, None, None, None) == 1
+    assert lib.cp_init(ctypes.byref(h), 3, dims, 513, fake, 0, None, None, None) == 1
     assert lib.cp_init(ctypes.byref(h), 3, dims, 3, None, 0, None, None, None) == 1
     assert lib.cp_init(ctypes.byref(h), 3, dims, 3, fake, 3, None, None, None) == 1  # dtype
     bad = (ctypes.c_int64 * 3)(4, 0, 6)

@@ -550,3 +550,30 @@ def test_msdt_combined_levels(pkg, dims, R, levels, prec):
     with pytest.raises(pkg.CPError):
         ctx.set_option("msdt_levels", N - 1)
     ctx.close()
+
+
+@pytest.mark.parametrize("dims,R", [((180, 170, 160), 400), ((192, 176, 168), 512), ((200, 180, 190), 384),
+                                    ((100, 96, 104, 24), 300)])
+@pytest.mark.parametrize("prec", ["f16x3", "fp32"])
+def test_rank_up_to_512(pkg, dims, R, prec):
+    """R up to 512: the tensor-core TTM in three or four column passes of 128 and the
+    normal equations' FP32 inverse by recursive 128-blocks (three levels at R = 512)
+    with FP64 refinement; Gaussian factors keep the scaled Gamma's condition number
+    near 3e4, inside the FP32 inverse's range, so no FP64 fallback runs."""
+    Td, Tref, A0 = problem(dims, R, 43, eta=0.05, law="gaussian")
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    for n in range(len(dims)):
+        assert relerr(ctx.mttkrp(n).cpu().numpy(), co.mttkrp(Tref, A0, n)) <= 1e-5, n
+    ctx.close()
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    ctx.sweep_dt(2)
+    ref = co.cp_als(Tref, A0, 2, route="dt")
+    st = ctx.stats()
+    assert st["solves_fp64"] == 0
+    if prec != "fp32":
+        assert st["ttm_tensor_core"] >= 1
+    _, r = ctx.fit(exact=True)
+    assert abs(r - co.residual_direct(Tref, ref.A)) <= FIT_TOL[prec]
+    got = np.array([t["resid"] for t in ctx.trace()])
+    assert np.abs(got - np.array(ref.resid)).max() <= 1e-5
+    ctx.close()
