@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS) + ["policy"])
+    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS) + ["policy", "collinearity"])
     ap.add_argument("--prec", default="f16x3", choices=["fp32", "tf32", "bf16x3", "bf16", "tf32x3", "f16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -80,6 +80,12 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--policy-dims", default="256,256,256")
     ap.add_argument("--policy-law", default="collinear", choices=["collinear", "uniform"])
+    # collinearity study (--workload collinearity; Sec. V-A tensors with given collinearity)
+    ap.add_argument("--col-seeds", type=int, default=3, help="tensors per collinearity bin")
+    ap.add_argument("--col-size", type=int, default=1600)
+    ap.add_argument("--col-rank", type=int, default=400)
+    ap.add_argument("--col-bins", default="0,0.2,0.4,0.6,0.8,1.0")
+    ap.add_argument("--col-exact", default="dt,msdt", help="exact routes timed beside PP")
     ap.add_argument("--ttm-only", action="store_true",
                     help="time only one first-level TTM (cp_ttm, --ttm-mode) and exit")
     ap.add_argument("--ttm-mode", type=int, default=-1, help="mode of --ttm-only (default: the last)")
@@ -373,6 +379,80 @@ def run_policy(args):
     print(json.dumps(line), flush=True)
 
 
+def run_collinearity(args):
+    """The paper's collinearity study on one GPU (Sec. V-A, Fig. 4, Table 3): order-3
+    tensors s^3 = [[A, A, A]] from rank-R factors whose columns have pairwise cosine
+    C drawn uniformly from each bin [a, b) (no noise: CP rank at most R), U[0,1)
+    initial factors; PP-CP-ALS (Alg. 2) with tolerance 0.2 and exact sweeps, each
+    stopped when the relative residual changes by at most 1e-5 between sweeps or
+    after 300 sweeps (Sec. V-C).  Reports per bin the sweep counts of Table 3
+    (exact sweeps inside PP, PP initializations, approximated sweeps), the device
+    time to stop and the final direct fit of every method."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2010_12056_gb300 as pkg
+    import synth
+    s, R = args.col_size, args.col_rank
+    edges = [float(x) for x in args.col_bins.split(",")]
+    exact_routes = [x for x in args.col_exact.split(",") if x]
+    bins = []
+    for b in range(len(edges) - 1):
+        a, e = edges[b], edges[b + 1]
+        runs = []
+        for i in range(args.col_seeds):
+            seed = 20101205 + 9000 + 100 * b + i
+            g = np.random.default_rng(seed)
+            C = float(g.uniform(a, e))
+            C = min(C, 0.999)
+            T, _, A0 = synth.make_problem_device(seed, [s, s, s], R, law="collinear", C=C, eta=0.0)
+            torch.cuda.synchronize()
+            run = {"C": C, "seed": seed}
+            for route in exact_routes + ["pp"]:
+                ctx = pkg.CPContext(T, R, A0=A0, prec=args.prec, pp_eps=0.2, delta=1e-5, max_sweeps=300)
+                err = None
+                try:
+                    ctx.run(route)
+                except pkg.CPError as ex:
+                    err = str(ex)
+                tr = ctx.trace()
+                rec = {"sweeps": len(tr), "ms": sum(t["ms"] for t in tr), "error": err}
+                try:
+                    rec["fit_direct"] = ctx.fit(exact=True)[0]
+                except pkg.CPError as ex:
+                    rec["fit_direct"] = None
+                if route == "pp":
+                    rec["als"] = sum(1 for t in tr if t["kind"] != "pp")
+                    rec["pp_init"] = sum(t["pp_init"] for t in tr)
+                    rec["pp_approx"] = sum(1 for t in tr if t["kind"] == "pp")
+                run[route] = rec
+                ctx.close()
+            del T
+            torch.cuda.empty_cache()
+            runs.append(run)
+            print(json.dumps({"bin": [a, e], **run}), flush=True)
+
+        def mean(key, route):
+            v = [r[route][key] for r in runs if r[route].get(key) is not None]
+            return float(np.mean(v)) if v else None
+        summary = {"bin": [a, e], "tensors": len(runs),
+                   "num_als": mean("als", "pp"), "num_pp_init": mean("pp_init", "pp"),
+                   "num_pp_approx": mean("pp_approx", "pp"), "pp_ms": mean("ms", "pp"),
+                   "pp_fit": mean("fit_direct", "pp")}
+        for route in exact_routes:
+            summary[f"{route}_sweeps"] = mean("sweeps", route)
+            summary[f"{route}_ms"] = mean("ms", route)
+            summary[f"{route}_fit"] = mean("fit_direct", route)
+            sp = [r[route]["ms"] / r["pp"]["ms"] for r in runs if r["pp"]["ms"] > 0]
+            summary[f"speedup_pp_over_{route}_median"] = float(np.median(sp)) if sp else None
+        bins.append(summary)
+    print(json.dumps({"metric": "collinearity study: PP (eps 0.2) vs exact sweeps, time to stop",
+                      "config": {"dims": [s, s, s], "R": R, "eps": 0.2, "delta": 1e-5, "max_sweeps": 300,
+                                 "tensors_per_bin": args.col_seeds, "prec": args.prec, "noise": 0.0},
+                      "bins": bins}), flush=True)
+
+
 def run_ttm_only(args, wl):
     """Time cp_ttm of the last mode (the kernel the sweeps launch) on one workload."""
     import numpy as np
@@ -409,6 +489,10 @@ def main():
     if args.workload == "policy":
         if int(os.environ.get("RANK", "0")) == 0:
             run_policy(args)
+        return
+    if args.workload == "collinearity":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_collinearity(args)
         return
     wl = dict(WORKLOADS[args.workload])
     if args.dims or args.rank or args.law:

@@ -41,7 +41,7 @@ def init_theta(seed):
     return theta
 
 
-def collect(T, R, sweeps, prec="bf16x3", seed=1, follow=-1, min_gain=0.0):
+def collect(T, R, sweeps, prec="f16x3", seed=1, follow=-1, min_gain=0.0):
     """Probe `sweeps` consecutive states of one decomposition of T.
 
     Returns (X, y, recs): one sample per labelled choice (current operators when
@@ -102,7 +102,7 @@ def accuracy(pol, X, y):
     return float(np.mean((p >= 0.5) == (np.asarray(y) > 0.5)))
 
 
-def time_to_target(T, R, method, target_resid, max_sweeps, prec="bf16x3", seed=1, eps=0.1,
+def time_to_target(T, R, method, target_resid, max_sweeps, prec="f16x3", seed=1, eps=0.1,
                    policy=None, judge_every=5, A0=None):
     """Device milliseconds until the direct residual first drops to target_resid.
 
