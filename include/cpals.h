@@ -358,10 +358,17 @@ cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
  *                     and adjacent modes the root is one tensor-core pass over T with
  *                     the two factors' Khatri-Rao product.  The look-ahead applies to
  *                     l = 1 only; results agree with l = 1 to FP32 rounding.
+ *   CP_OPT_SOLVE_FP64 (default 0) 1: solve every update's normal equations with
+ *                     the FP64 LDL^T factorisation and FP64 substitution (Alg. 1,
+ *                     line 8, as a Cholesky-type solve in FP64) instead of the FP32
+ *                     inverse with FP64 refinement; slower, for inputs whose Gamma
+ *                     is too ill-conditioned for the refinement.  The library also
+ *                     falls back to it by itself per update when its a-posteriori
+ *                     check of the FP32 inverse fails (cp_stats.solves_fp64).
  * CP_EINVAL for an unknown option or value.  Takes effect at the next call.
  */
 enum { CP_OPT_FUSE_DT = 1, CP_OPT_LOOKAHEAD = 2, CP_OPT_FUSE_CHILD = 3, CP_OPT_WAIT_LIMIT = 4,
-       CP_OPT_MSDT_LEVELS = 5 };
+       CP_OPT_MSDT_LEVELS = 5, CP_OPT_SOLVE_FP64 = 6 };
 cp_status cp_set_option(cp_ctx *ctx, int option, int value);
 
 /*

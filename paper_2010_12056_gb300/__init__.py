@@ -66,7 +66,7 @@ class Stats(ctypes.Structure):
                 ("lookahead", ctypes.c_int64), ("ttm_child", ctypes.c_int64)]
 
 
-OPTIONS = {"fuse_dt": 1, "lookahead": 2, "fuse_child": 3, "wait_limit": 4, "msdt_levels": 5}
+OPTIONS = {"fuse_dt": 1, "lookahead": 2, "fuse_child": 3, "wait_limit": 4, "msdt_levels": 5, "solve_fp64": 6}
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int

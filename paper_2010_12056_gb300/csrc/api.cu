@@ -122,6 +122,7 @@ struct cp_ctx {
     bool fuse_dt = true;
     bool fuse_child = false;
     int msdt_levels = 1;       // upper levels of the multi-sweep tree combined (Sec. IV)
+    bool solve_fp64 = false;   // normal equations always by the FP64 factorisation
     long long wait_limit = 0;  // tensor-core TTM's bounded waits (cycles; 0: about 1 s)  // TTM epilogue forms the first child (multi-sweep tree)
     float* child_ws = nullptr;  // pieces of first-child segments that cross TTM tiles
     size_t child_ws_cap = 0;
@@ -519,7 +520,7 @@ cp_status launch_chol(cp_ctx* c, int u, bool pp, double* scal) {
     CKCUDA(c, cudaEventRecord(c->ev_ready, c->st));
     CKCUDA(c, cudaStreamWaitEvent(c->side, c->ev_ready, 0));
     LAUNCH(c, cpk::chol_mixed(c->d_Slist, c->d_dSlist, c->N, u, c->R, pp ? 1 : 0, c->Gamma, c->G32, c->Ginv,
-                              c->L, c->invd, c->W, scal, c->d_mode, c->schur_ws, c->side));
+                              c->L, c->invd, c->W, scal, c->d_mode, c->schur_ws, c->side, c->solve_fp64));
     CKCUDA(c, cudaEventRecord(c->ev_chol, c->side));
     c->chol_pending = true;
     c->chol_mode = u;
@@ -1362,6 +1363,14 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
                 for (int k = a + 2; k < N; ++k) Q *= dims[k];
                 c->kr_plan[a] = cpk::ttm_tc_plan(c->T, P, (int)(dims[a] * dims[a + 1]), Q, R, kind, c->kr_hi,
                                                  c->kr_lo, c->Rpad, c->kr_Kpad[a], tscale, c->kr_colinv);
+                cpk::ttm_tc_set_depth_bound(c->kr_plan[a], true);
+                // a contraction so long that even 64 K-slices leave deep accumulators
+                // (K = s_a s_b beyond about 65536 per hi*hi accumulator) is not fused:
+                // the tree then forms the level-1 node and contracts it by a multi-TTV
+                if (c->kr_plan[a] && cpk::ttm_tc_depth_slices(c->kr_plan[a]) > 64) {
+                    cpk::ttm_tc_plan_free(c->kr_plan[a]);
+                    c->kr_plan[a] = nullptr;
+                }
             }
         }
         // split-K workspace for contractions with few row tiles
@@ -1477,6 +1486,10 @@ cp_status cp_set_option(cp_ctx* c, int option, int value) {
         case CP_OPT_WAIT_LIMIT:
             if (value < 0) return CP_EINVAL;
             c->wait_limit = value;
+            return CP_OK;
+        case CP_OPT_SOLVE_FP64:
+            if (value != 0 && value != 1) return CP_EINVAL;
+            c->solve_fp64 = value != 0;
             return CP_OK;
         case CP_OPT_MSDT_LEVELS:
             if (value < 1 || value > std::max(1, c->N - 2)) return CP_EINVAL;

@@ -74,6 +74,10 @@ cudaError_t ttm_tc_run(const TcPlan* p, float* X, int prec, int num_sms, unsigne
                        cudaStream_t st, float* splitk_ws, const TcChild* child = nullptr,
                        long long wait_limit = 0);
 int ttm_tc_splitk(const TcPlan* p, int num_sms);
+// long contractions (the fused two-mode operand): split K so that no TMEM
+// accumulator sums more than 64 MMAs; depth_slices is the split that needs
+void ttm_tc_set_depth_bound(TcPlan* p, bool on);
+int ttm_tc_depth_slices(const TcPlan* p);
 int64_t ttm_tc_rows(const TcPlan* p);
 // Khatri-Rao operand of two adjacent modes a, a+1 for a fused two-mode contraction:
 // row k = i_a * s_b + i_b holds A_a[i_a][r] * A_b[i_b][r]; written transposed
@@ -132,9 +136,10 @@ struct SolveOut {
 // ([L | L^T], 2 R^2) and invd64 (*mode = 1);
 // solve_mixed then solves every row to FP64 accuracy (refinement or FP64
 // substitution).  Gamma and Ginv must have 16 spare bytes after R*R entries.
+// force64: skip the FP32 inverse and factor Gamma in FP64 (LDL^T) for this update.
 cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
                        double* Gamma, float* G32, float* Ginv, double* L64, double* invd64, double* W,
-                       double* scal, int* mode, float* ws, cudaStream_t st);
+                       double* scal, int* mode, float* ws, cudaStream_t st, bool force64 = false);
 // floats of the workspace chol_mixed needs for R > 128 (blocked inverse), else 0
 size_t schur_ws_floats(int R);
 cudaError_t solve_mixed(const float* M, const double* W, const double* Gamma, const float* Ginv,

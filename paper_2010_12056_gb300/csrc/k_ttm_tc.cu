@@ -963,6 +963,7 @@ struct TcPlan {
     int K, R, nk, S_op;
     float tscale = 1.f;              // fp16 parts: power of two applied to T
     const float* colinv = nullptr;   // fp16 parts: per-column output scale (Rpad floats)
+    bool depth_bound = false;        // split K so that no accumulator sums more than 64 MMAs
 };
 
 bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R) {
@@ -1065,14 +1066,43 @@ static int64_t plan_tiles(const TcPlan* pl) {
     return pl->mode == 1 ? pl->P * ((pl->Q + BM - 1) / BM) : (pl->PQ + BM - 1) / BM;
 }
 
+// hi*hi accumulators of one tile with three products per term (the corrections
+// take one more of the 256 TMEM columns a set may hold); single-product
+// precisions have one more, so the bound derived from this is conservative
+static int plan_nsplit(const TcPlan* pl) {
+    int nsplit = 256 / pl->pass[0].Rpad - 1;
+    if (nsplit > 4) nsplit = 4;
+    return nsplit < 1 ? 1 : nsplit;
+}
+
 int ttm_tc_splitk(const TcPlan* pl, int num_sms) {
     // split K when the row tiles alone cannot fill the GPU and K is long enough
     const int64_t nt = plan_tiles(pl);
-    if (pl->pass[0].b_resident || nt >= 2 * (int64_t)num_sms || pl->nk < 8) return 1;
-    int nsk = (int)((4 * (int64_t)num_sms + nt - 1) / nt);
-    if (nsk > pl->nk / 4) nsk = pl->nk / 4;
-    if (nsk > 16) nsk = 16;
+    int nsk = 1;
+    if (!pl->pass[0].b_resident && nt < 2 * (int64_t)num_sms && pl->nk >= 8) {
+        nsk = (int)((4 * (int64_t)num_sms + nt - 1) / nt);
+        if (nsk > pl->nk / 4) nsk = pl->nk / 4;
+        if (nsk > 16) nsk = 16;
+    }
+    if (pl->depth_bound) {
+        // the tensor core truncates its FP32 accumulation once per instruction
+        // (16 k): at most 64 instructions per accumulator keep that bias near 2^-19
+        // of the sum; longer contractions (the fused two-mode operand, K = s_a s_b)
+        // are split, and their slices added with round-to-nearest
+        const int64_t kslice = (int64_t)64 * 16 * plan_nsplit(pl);
+        const int64_t need = ((int64_t)pl->K + kslice - 1) / kslice;
+        if (need > nsk) nsk = (int)std::min<int64_t>(need, pl->nk);
+    }
     return nsk < 1 ? 1 : nsk;
+}
+
+int ttm_tc_depth_slices(const TcPlan* pl) {
+    const int64_t kslice = (int64_t)64 * 16 * plan_nsplit(pl);
+    return (int)(((int64_t)pl->K + kslice - 1) / kslice);
+}
+
+void ttm_tc_set_depth_bound(TcPlan* p, bool on) {
+    if (p) p->depth_bound = on;
 }
 
 int64_t ttm_tc_rows(const TcPlan* pl) { return pl->PQ; }

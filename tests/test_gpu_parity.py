@@ -577,3 +577,54 @@ def test_rank_up_to_512(pkg, dims, R, prec):
     got = np.array([t["resid"] for t in ctx.trace()])
     assert np.abs(got - np.array(ref.resid)).max() <= 1e-5
     ctx.close()
+
+
+@pytest.mark.parametrize("dims,R", [((40, 36, 44), 24), ((180, 170, 160), 400), ((100, 96, 104, 24), 300)])
+def test_fp64_normal_equations(pkg, dims, R):
+    """The FP64 factorisation path of the normal equations (LDL^T and FP64
+    substitution; the fallback of the FP32 inverse), forced for every update, for
+    R below and above 128: the sweeps follow the oracle to the fit tolerance."""
+    Td, Tref, A0 = problem(dims, R, 44, eta=0.05, law="gaussian")
+    ctx = pkg.CPContext(Td, R, A0=A0, prec="fp32")
+    ctx.set_option("solve_fp64", True)
+    ctx.sweep_dt(2)
+    ref = co.cp_als(Tref, A0, 2, route="dt")
+    assert ctx.stats()["solves_fp64"] == 2 * len(dims)
+    _, r = ctx.fit(exact=True)
+    assert abs(r - co.residual_direct(Tref, ref.A)) <= 1e-6
+    got = np.array([t["resid"] for t in ctx.trace()])
+    assert np.abs(got - np.array(ref.resid)).max() <= 1e-5
+    ctx.close()
+
+
+# Full-size workloads, in the launch configuration the benchmark times (device-
+# generated tensors of the benchmark's laws): MTTKRP rows and first-level TTM rows
+# sampled and computed one by one by their definition on the host.
+FULL = [("c2", (128, 128, 128, 128), 64, "uniform", 1e-3, None, 20101205 + 1000),
+        ("c3", (1024, 1024, 1024), 256, "gaussian", 1e-2, None, 20101205 + 2000),
+        ("c4", (160, 160, 160, 160), 100, "collinear", 1e-3, 0.9, 20101205 + 3000)]
+
+
+@pytest.mark.parametrize("name,dims,R,law,eta,C,seed", FULL, ids=[f[0] for f in FULL])
+def test_full_size_sampled_rows(pkg, name, dims, R, law, eta, C, seed):
+    T, _, A0 = synth.make_problem_device(seed, list(dims), R, law=law, eta=eta, C=C)
+    N = len(dims)
+    ctx = pkg.CPContext(T, R, A0=A0, prec="f16x3")
+    rng = np.random.default_rng(7)
+    for n in range(N):
+        M = ctx.mttkrp(n).cpu().numpy().astype(np.float64)
+        rows = sorted(set([0, dims[n] - 1] + list(rng.integers(0, dims[n], 4))))
+        others = [k for k in range(N) if k != n]
+        for x in rows:
+            sl = T.select(n, int(x)).double().cpu().numpy()     # the other modes, in order
+            ref = sl.reshape(-1) @ co.khatri_rao_rows([A0[k] for k in others])
+            assert relerr(M[x], ref) <= 1e-5, (name, n, x)
+    # first-level TTM of the last mode (the multi-sweep root), sampled rows of X
+    m = N - 1
+    X = ctx.ttm(m)
+    P = int(np.prod(dims[:-1]))
+    Xf = X.reshape(P, R)
+    for g in sorted(set([0, P - 1] + list(rng.integers(0, P, 6)))):
+        trow = T.reshape(P, dims[-1])[int(g)].double().cpu().numpy()
+        assert relerr(Xf[int(g)].double().cpu().numpy(), trow @ A0[m]) <= 1e-5, (name, g)
+    ctx.close()
