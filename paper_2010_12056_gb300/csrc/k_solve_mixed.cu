@@ -614,7 +614,7 @@ constexpr int SOLVE_THREADS = 64;
 
 // shared layout of the solve kernel (doubles unless noted)
 struct SolveSmem {
-    size_t G, Gi, m, x, r, part, red, total;
+    size_t G, Gi, m, x, r, part, red, pk, total;
 };
 __host__ __device__ inline SolveSmem solve_smem(int R) {
     // R > 128 solves in FP64 straight from global memory: no staged matrices
@@ -629,21 +629,23 @@ __host__ __device__ inline SolveSmem solve_smem(int R) {
     L.r = L.x + R;                             // R floats
     L.part = L.r + (R + 1) / 2 + 1;            // SOLVE_THREADS doubles
     L.red = L.part + SOLVE_THREADS;            // 2 * SOLVE_THREADS / 32 doubles
-    L.total = L.red + 16;
+    L.pk = L.red + 16;                         // k-split partials: 3 R doubles + 3 R floats
+    L.total = L.pk + 5 * (size_t)R;
     return L;
 }
 
-// One row x per block of 64 threads; in the refinement path thread t owns the
-// columns t + 64 c (c < CT) and computes every dot product of those columns by
-// itself (four partial sums, no reductions across threads).  Per iteration:
+// One row x per block of 64 KS threads; in the refinement path thread t of the
+// first 64 owns the columns t + 64 c (c < CT); each of the KS groups of 64 sums
+// its 1/KS share of every dot product of those columns, and the shares meet in
+// shared memory.  Per iteration:
 //   r = m - x Gamma   (FP64; Gamma staged in shared memory for R <= 128, else read from L2)
 //   d = r G32         (FP32; r is small, so FP32 carries it to full accuracy)
 //   x += d
 // and two barriers.  It stops once the error left after the step, estimated as
 // rho ||d||_inf with rho the contraction seen between steps, is below
 // 2^-36 ||x||_inf: far below the FP32 error of the MTTKRP that forms m.
-template <int RT>
-__global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
+template <int RT, int KS>
+__global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
     const float* __restrict__ M, const double* __restrict__ W, const double* __restrict__ G,
     const float* __restrict__ Ginv, const double* __restrict__ L64, const double* __restrict__ invd64,
     const int* __restrict__ mode, cpk::SolveOut o, int s, int R, double* __restrict__ scal,
@@ -660,6 +662,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
     double* part = sm + lay.part;
     double* red = sm + lay.red;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // KS groups of 64 threads: group q sums its 1/KS share of every dot product of
+    // the refinement; group 0 owns the columns (tcol + 64 c) and everything else
+    const int q = tid / SOLVE_THREADS, tcol = tid % SOLVE_THREADS;
+    double* pk = sm + lay.pk;                                      // (KS-1) x R FP64 partials
+    float* pkf = reinterpret_cast<float*>(sm + lay.pk + 3 * (size_t)R);  // (KS-1) x R FP32 partials
+    const int kq = (R + KS - 1) / KS, k0 = q * kq, k1 = min(R, k0 + kq);
     const int x = blockIdx.x;
     const int path = *mode;
     const int RR = R * R;
@@ -669,7 +677,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
     double xj[CT], mj[CT], aold[CT];
 #pragma unroll
     for (int c = 0; c < CT; ++c) {
-        const int j = tid + SOLVE_THREADS * c;
+        const int j = tcol + SOLVE_THREADS * c;
         xj[c] = 0.0;
         aold[c] = (j < R) ? o.A64[(size_t)x * R + j] : 0.0;
         mj[c] = (j < R) ? (double)M[(size_t)x * R + j] : 0.0;
@@ -701,15 +709,15 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
         }
 #pragma unroll
         for (int c = 0; c < CT; ++c) {
-            const int j = tid + SOLVE_THREADS * c;
-            if (j < R) xv[j] = aold[c];  // for the V term
+            const int j = tcol + SOLVE_THREADS * c;
+            if (q == 0 && j < R) xv[j] = aold[c];  // for the V term
         }
         __syncthreads();
-        if (W) {
+        if (W && q == 0) {
             // V(x,:) = A_old(x,:) W (Eq. V_nij), FP64
 #pragma unroll
             for (int c = 0; c < CT; ++c) {
-                const int j = tid + SOLVE_THREADS * c;
+                const int j = tcol + SOLVE_THREADS * c;
                 if (j >= R) continue;
                 double v0 = 0.0, v1 = 0.0;
                 int q = 0;
@@ -725,8 +733,8 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
         }
 #pragma unroll
         for (int c = 0; c < CT; ++c) {
-            const int j = tid + SOLVE_THREADS * c;
-            if (j < R) rv[j] = (float)mj[c];
+            const int j = tcol + SOLVE_THREADS * c;
+            if (q == 0 && j < R) rv[j] = (float)mj[c];
         }
         // bounded wait for the staged matrices (about 1 s)
         if (staged) {
@@ -751,23 +759,40 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
             }
         }
         __syncthreads();
-        // d = rv G32 for the owned columns (FP32, four partial sums)
+        // d = rv G32 for the owned columns (FP32, four partial sums over this
+        // group's k share; the groups' shares meet in shared memory)
         auto apply_ginv = [&](float* d) {
 #pragma unroll
             for (int c = 0; c < CT; ++c) {
-                const int j = tid + SOLVE_THREADS * c;
+                const int j = tcol + SOLVE_THREADS * c;
                 float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
                 if (j < R) {
-                    int k = 0;
-                    for (; k + 3 < R; k += 4) {
+                    int k = k0;
+                    for (; k + 3 < k1; k += 4) {
                         a0 = fmaf(rv[k], Gim[k * R + j], a0);
                         a1 = fmaf(rv[k + 1], Gim[(k + 1) * R + j], a1);
                         a2 = fmaf(rv[k + 2], Gim[(k + 2) * R + j], a2);
                         a3 = fmaf(rv[k + 3], Gim[(k + 3) * R + j], a3);
                     }
-                    for (; k < R; ++k) a0 = fmaf(rv[k], Gim[k * R + j], a0);
+                    for (; k < k1; ++k) a0 = fmaf(rv[k], Gim[k * R + j], a0);
                 }
                 d[c] = (a0 + a1) + (a2 + a3);
+            }
+            if (KS > 1) {
+                if (q > 0)
+#pragma unroll
+                    for (int c = 0; c < CT; ++c) {
+                        const int j = tcol + SOLVE_THREADS * c;
+                        if (j < R) pkf[(size_t)(q - 1) * R + j] = d[c];
+                    }
+                __syncthreads();
+                if (q == 0)
+#pragma unroll
+                    for (int c = 0; c < CT; ++c) {
+                        const int j = tcol + SOLVE_THREADS * c;
+                        if (j < R)
+                            for (int g = 1; g < KS; ++g) d[c] += pkf[(size_t)(g - 1) * R + j];
+                    }
             }
         };
         float d0[CT];
@@ -775,9 +800,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
         float dmx = 0.f, xmx = 0.f;
 #pragma unroll
         for (int c = 0; c < CT; ++c) {
-            const int j = tid + SOLVE_THREADS * c;
+            const int j = tcol + SOLVE_THREADS * c;
             xj[c] = (double)d0[c];
-            if (j < R) xv[j] = xj[c];
+            if (q == 0 && j < R) xv[j] = xj[c];
         }
         __syncthreads();
         double prev = 0.0;
@@ -794,13 +819,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
                 int jj[CT];
 #pragma unroll
                 for (int c = 0; c < CT; ++c) {
-                    const int j = tid + SOLVE_THREADS * c;
+                    const int j = tcol + SOLVE_THREADS * c;
                     jj[c] = j < R ? j : 0;  // idle columns read column 0 and are dropped
 #pragma unroll
                     for (int q = 0; q < NQ; ++q) ra[c][q] = 0.0;
                 }
-                int k = 0;
-                for (; k + NQ - 1 < R; k += NQ) {
+                int k = k0;
+                for (; k + NQ - 1 < k1; k += NQ) {
 #pragma unroll
                     for (int q = 0; q < NQ; ++q) {
                         const double xk = xv[k + q];
@@ -809,45 +834,62 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
                         for (int c = 0; c < CT; ++c) ra[c][q] = fma(xk, grow[jj[c]], ra[c][q]);
                     }
                 }
-                for (; k < R; ++k) {
+                for (; k < k1; ++k) {
 #pragma unroll
                     for (int c = 0; c < CT; ++c) ra[c][0] = fma(xv[k], Gm[(size_t)k * R + jj[c]], ra[c][0]);
                 }
+                double tt[CT];
 #pragma unroll
                 for (int c = 0; c < CT; ++c) {
-                    const int j = tid + SOLVE_THREADS * c;
-                    if (j < R) {
-                        double t;
-                        if (NQ == 8)
-                            t = ((ra[c][0] + ra[c][1]) + (ra[c][2] + ra[c][3])) +
+                    if (NQ == 8)
+                        tt[c] = ((ra[c][0] + ra[c][1]) + (ra[c][2] + ra[c][3])) +
                                 ((ra[c][4 % NQ] + ra[c][5 % NQ]) + (ra[c][6 % NQ] + ra[c][7 % NQ]));
-                        else
-                            t = (ra[c][0] + ra[c][1]) + (ra[c][2 % NQ] + ra[c][3 % NQ]);
-                        rv[j] = (float)(mj[c] - t);
-                    }
+                    else
+                        tt[c] = (ra[c][0] + ra[c][1]) + (ra[c][2 % NQ] + ra[c][3 % NQ]);
                 }
+                if (KS > 1) {
+                    if (q > 0)
+#pragma unroll
+                        for (int c = 0; c < CT; ++c) {
+                            const int j = tcol + SOLVE_THREADS * c;
+                            if (j < R) pk[(size_t)(q - 1) * R + j] = tt[c];
+                        }
+                    __syncthreads();
+                }
+                if (q == 0)
+#pragma unroll
+                    for (int c = 0; c < CT; ++c) {
+                        const int j = tcol + SOLVE_THREADS * c;
+                        if (j < R) {
+                            double t = tt[c];
+                            for (int g = 1; g < KS; ++g) t += pk[(size_t)(g - 1) * R + j];
+                            rv[j] = (float)(mj[c] - t);
+                        }
+                    }
             }
             __syncthreads();
             float dd[CT];
             apply_ginv(dd);
             dmx = 0.f;
             xmx = 0.f;
+            if (q == 0) {
 #pragma unroll
-            for (int c = 0; c < CT; ++c) {
-                const int j = tid + SOLVE_THREADS * c;
-                xj[c] += (double)dd[c];
-                dmx = fmaxf(dmx, fabsf(dd[c]));
-                xmx = fmaxf(xmx, fabsf((float)xj[c]));
-                if (j < R) xv[j] = xj[c];
-            }
+                for (int c = 0; c < CT; ++c) {
+                    const int j = tcol + SOLVE_THREADS * c;
+                    xj[c] += (double)dd[c];
+                    dmx = fmaxf(dmx, fabsf(dd[c]));
+                    xmx = fmaxf(xmx, fabsf((float)xj[c]));
+                    if (j < R) xv[j] = xj[c];
+                }
 #pragma unroll
-            for (int o2 = 16; o2; o2 >>= 1) {
-                dmx = fmaxf(dmx, __shfl_xor_sync(FULL, dmx, o2));
-                xmx = fmaxf(xmx, __shfl_xor_sync(FULL, xmx, o2));
-            }
-            if (lane == 0) {
-                red[warp] = dmx;
-                red[2 + warp] = xmx;
+                for (int o2 = 16; o2; o2 >>= 1) {
+                    dmx = fmaxf(dmx, __shfl_xor_sync(FULL, dmx, o2));
+                    xmx = fmaxf(xmx, __shfl_xor_sync(FULL, xmx, o2));
+                }
+                if (lane == 0) {
+                    red[warp] = dmx;
+                    red[2 + warp] = xmx;
+                }
             }
             __syncthreads();  // also publishes xv for the next residual
             const double dmax = fmax(red[0], red[1]), xmax = fmax(red[2], red[3]);
@@ -960,21 +1002,23 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_mixed(
         sc[SCAL_MA] += mj * av;
         sc[SCAL_M2] += mj * mj;
     };
-    if (path == 0) {
+    if (q == 0) {
+        if (path == 0) {
 #pragma unroll
-        for (int c = 0; c < CT; ++c) {
-            const int j = tid + SOLVE_THREADS * c;
-            if (j < R) emit(j, xj[c], mj[c], aold[c]);
+            for (int c = 0; c < CT; ++c) {
+                const int j = tcol + SOLVE_THREADS * c;
+                if (j < R) emit(j, xj[c], mj[c], aold[c]);
+            }
+        } else {
+            // the FP64 path covers any R: every thread takes columns tid, tid + 64, ...
+            for (int j = tcol; j < R; j += SOLVE_THREADS) emit(j, xv[j], mv[j], o.A64[(size_t)x * R + j]);
         }
-    } else {
-        // the FP64 path covers any R: every thread takes columns tid, tid + 64, ...
-        for (int j = tid; j < R; j += SOLVE_THREADS) emit(j, xv[j], mv[j], o.A64[(size_t)x * R + j]);
     }
     // block reduction of the 8 scalars: warp sums, then warp 0
 #pragma unroll
     for (int i = 0; i < CP_NSCAL; ++i) sc[i] = warp_sum_d(sc[i]);
     __syncthreads();
-    if (lane == 0)
+    if (lane == 0 && q == 0)
 #pragma unroll
         for (int i = 0; i < CP_NSCAL; ++i) part[warp * CP_NSCAL + i] = sc[i];
     __syncthreads();
@@ -990,15 +1034,20 @@ cudaError_t launch_solve_mixed(const float* M, const double* W, const double* G,
                                const double* L64, const double* invd64, const int* mode,
                                const cpk::SolveOut& o, int s, int R, double* scal, double* scal_part,
                                unsigned* dev_err, cudaStream_t st) {
+    // groups of 64 threads per row that split the refinement's dot products: a
+    // row's work is a chain of dependent FP64 FMAs (64-cycle latency) with one
+    // block per SM, so for small R more threads per row shorten the chains
+    // (R <= 64: four groups, R <= 128: two)
+    constexpr int KS = RT <= 2 ? 4 : (RT <= 4 ? 2 : 1);
     const size_t smem = solve_smem(R).total * sizeof(double) + 64;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_solve_mixed<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_solve_mixed<RT, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(solve_smem(MIXED_MAXR).total * sizeof(double) + 64));
         attr = true;
     }
-    k_solve_mixed<RT><<<(unsigned)s, SOLVE_THREADS, smem, st>>>(M, W, G, Ginv, L64, invd64, mode, o, s, R,
-                                                               scal, scal_part, dev_err);
+    k_solve_mixed<RT, KS><<<(unsigned)s, SOLVE_THREADS * KS, smem, st>>>(M, W, G, Ginv, L64, invd64, mode, o, s, R,
+                                                                         scal, scal_part, dev_err);
     return cudaGetLastError();
 }
 
