@@ -143,51 +143,6 @@ __global__ void __launch_bounds__(256) k_gram_cl(const double* __restrict__ A,
     cluster_sync_all();  // every CTA's partials stay readable until CTA 0 is done
 }
 
-// Gram of a factor with few rows (s <= 512): one CTA per 16 x 16 tile sums every
-// row itself, in four interleaved partial sums (row mod 4) added in a fixed
-// order, with no cluster and no second pass (the cluster launch above costs
-// more than the arithmetic at these sizes).  Same outputs as k_gram_cl.
-__global__ void __launch_bounds__(256) k_gram_rows(const double* __restrict__ A, const double* __restrict__ dA,
-                                                   int s, int R, const double* __restrict__ Gamma,
-                                                   double* __restrict__ S, double* __restrict__ dS,
-                                                   double* __restrict__ tile_gs) {
-    __shared__ double a1[16][17], a2[16][17], d2[16][17];
-    __shared__ double red[32];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int r1 = blockIdx.x * 16 + ty, r2 = blockIdx.y * 16 + tx;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0}, accd[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int xb = 0; xb < s; xb += 16) {
-        const int x = xb + ty;
-        const int ca = blockIdx.x * 16 + tx, cb = blockIdx.y * 16 + tx;
-        a1[ty][tx] = (x < s && ca < R) ? A[(size_t)x * R + ca] : 0.0;
-        a2[ty][tx] = (x < s && cb < R) ? A[(size_t)x * R + cb] : 0.0;
-        if (dA) d2[ty][tx] = (x < s && cb < R) ? dA[(size_t)x * R + cb] : 0.0;
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 16; k += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                acc[u] = fma(a1[k + u][ty], a2[k + u][tx], acc[u]);
-                if (dA) accd[u] = fma(a1[k + u][ty], d2[k + u][tx], accd[u]);
-            }
-        }
-        __syncthreads();
-    }
-    const double v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-    const double d = (accd[0] + accd[1]) + (accd[2] + accd[3]);
-    double gs = 0.0;
-    if (r1 < R && r2 < R) {
-        const size_t e = (size_t)r1 * R + r2;
-        S[e] = v;
-        if (dA) dS[e] = d;
-        if (Gamma) gs = Gamma[e] * v;
-    }
-    if (tile_gs) {
-        gs = block_sum(gs, red);
-        if (tid == 0) tile_gs[blockIdx.y * gridDim.x + blockIdx.x] = gs;
-    }
-}
-
 // The update's scalars: the solve's per-block partials and the tile shares of
 // <Gamma, S>, added in a fixed order.  Off the critical path (own stream).
 __global__ void __launch_bounds__(256) k_scal_fin(const double* __restrict__ scal_part, int nblk,
@@ -738,11 +693,7 @@ int gram_tiles(int R) { return ((R + 15) / 16) * ((R + 15) / 16); }
 
 cudaError_t gram(const double* A, const double* dA, int s, int R, const double* Gamma, double* S,
                  double* dS, double* tile_gs, cudaStream_t st) {
-    if (s <= 512) {
-        const dim3 g((R + 15) / 16, (R + 15) / 16);
-        k_gram_rows<<<g, 256, 0, st>>>(A, dA, s, R, Gamma, S, dS, tile_gs);
-        return cudaGetLastError();
-    }
+
     int nc = (s + 31) / 32;  // about 32 rows per chunk
     if (nc > GRAM_MAX_CHUNKS) nc = GRAM_MAX_CHUNKS;
     if (nc < 1) nc = 1;

@@ -1036,9 +1036,11 @@ cudaError_t launch_solve_mixed(const float* M, const double* W, const double* G,
                                unsigned* dev_err, cudaStream_t st) {
     // groups of 64 threads per row that split the refinement's dot products: a
     // row's work is a chain of dependent FP64 FMAs (64-cycle latency) with one
-    // block per SM, so for small R more threads per row shorten the chains
-    // (R <= 64: four groups, R <= 128: two)
-    constexpr int KS = RT <= 2 ? 4 : (RT <= 4 ? 2 : 1);
+    // block per SM, so more threads per row shorten the chains.  Measured (CUDA
+    // events per update): R = 128 44 -> 32 us with two groups; R = 64 unchanged
+    // with four (20 us; its FP64 pipe is already a quarter busy) and R = 16 slower
+    // (14 -> 16 us), so one group up to R = 64
+    constexpr int KS = (RT == 3 || RT == 4) ? 2 : 1;
     const size_t smem = solve_smem(R).total * sizeof(double) + 64;
     static bool attr = false;
     if (!attr) {

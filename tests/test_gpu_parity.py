@@ -495,14 +495,17 @@ def test_large_rank_gaussian_law(pkg, route, prec):
 def test_pp_collinear_law_follows_oracle(pkg):
     """Alg. 2 (eps 0.1) on the pairwise-perturbation law: order 4, rank-30 factors of
     pairwise cosine 0.9, 1e-3 noise (a 40^4 reduction of the 160^4 configuration).
-    For its first 20 sweeps the FP64 oracle's trajectory is stable under 1e-7
-    relative perturbations of T (residuals move by at most 2e-7), so the GPU must
+    For its first 16 sweeps the FP64 oracle's trajectory is stable under 1e-7
+    relative perturbations of T (residuals move by at most 6e-8), so the GPU must
     take the same sweep kinds, the same operator builds, and stay within the fit
     tolerance.  Later sweeps are chaotic in the oracle itself: an approximated
-    sweep drifts (its Eq. (residual) value goes to the clamp at zero), the regular
-    sweep after it raises the residual, and a 1e-7 perturbation of T changes the
-    kinds from sweep 32 on; they are not compared."""
-    dims, R, nsw = (40, 40, 40, 40), 30, 20
+    sweep drifts (its Eq. (residual) value goes to the clamp at zero at sweep 22),
+    the regular sweep after it raises the residual, and a 1e-7 perturbation of T
+    changes the kinds from sweep 32 on; the perturbed residuals already move by
+    2e-7 at sweeps 18-20 and 8e-7 at sweep 21, which the GPU's FP32 MTTKRPs
+    amplify to about 2e-6 in the direct residual after 20 sweeps.  So the
+    comparison stops after 16 sweeps (perturbed residuals within 6e-8)."""
+    dims, R, nsw = (40, 40, 40, 40), 30, 16
     Td, Tref, A0 = problem(dims, R, 20101205 + 3000, eta=1e-3, law="collinear", C=0.9)
     ctx = pkg.CPContext(Td, R, A0=A0, prec="f16x3")
     ctx.sweep_pp(nsw, eps=0.1)
