@@ -83,7 +83,7 @@ typedef struct {
 void cp_config_default(cp_config *cfg);
 
 /*
- * cp_init - create a decomposition context (Alg. 1, line 2; Alg. 2, line 2).
+ * cp_init - create a decomposition context (Alg. 1 and Alg. 2, set-up).
  *   N        tensor order, 3 <= N <= 8
  *   dims     N mode sizes, each >= 1; host array, copied
  *   R        rank, 1 <= R <= 512 (the tensor-core TTM runs in column passes of
@@ -100,7 +100,7 @@ void cp_config_default(cp_config *cfg);
  *   cfg      NULL for defaults; copied.
  *   stream   cudaStream_t (as void*) every later call is enqueued on.
  * Computes ||T||_F^2 and the Grams S(n) = A(n)^T A(n).  Sets dA(n) = A(n), so the
- * first PP test fails and the first sweep is a regular one (Alg. 2, line 2).
+ * first PP test fails and the first sweep is a regular one (Alg. 2 starts from dA = A).
  * Returns CP_EINVAL on bad sizes, CP_ENOMEM if the factor and normal-equation
  * workspace does not fit, CP_ECUDA on a CUDA failure.  *out is NULL on failure.
  * Tree intermediates (at most prod(dims)/min(dims) * R * 4 bytes per tree level)
@@ -360,7 +360,7 @@ cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
  *                     l = 1 only; results agree with l = 1 to FP32 rounding.
  *   CP_OPT_SOLVE_FP64 (default 0) 1: solve every update's normal equations with
  *                     the FP64 LDL^T factorisation and FP64 substitution (Alg. 1,
- *                     line 8, as a Cholesky-type solve in FP64) instead of the FP32
+ *                     solve step, as a Cholesky-type solve in FP64) instead of the FP32
  *                     inverse with FP64 refinement; slower, for inputs whose Gamma
  *                     is too ill-conditioned for the refinement.  The library also
  *                     falls back to it by itself per update when its a-posteriori

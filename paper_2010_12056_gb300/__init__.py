@@ -306,8 +306,9 @@ class CPContext:
                 "label_cur": r.label_cur, "label_new": r.label_new, "followed": r.followed}
 
     def set_option(self, option, value):
-        """cp_set_option: option in OPTIONS ('fuse_dt', 'lookahead', 'fuse_child'); value a
-        bool, or for 'lookahead' the blocks per SM of the look-ahead contraction (1..8)."""
+        """cp_set_option: option a key of OPTIONS; value a bool, or for 'lookahead' the
+        blocks per SM of the look-ahead contraction (1..8), for 'wait_limit' cycles, for
+        'msdt_levels' the combined upper levels."""
         v = int(value) if not isinstance(value, bool) else (1 if value else 0)
         if option == "lookahead" and value is True:
             v = 3

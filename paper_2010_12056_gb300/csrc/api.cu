@@ -513,7 +513,7 @@ cp_status grow_hist(cp_ctx* c, int nsweeps) {
     return CP_OK;
 }
 
-// Hadamard chain and factorisation of Gamma(u) (Alg. 1 line 6) on the side
+// Hadamard chain and factorisation of Gamma(u) (Alg. 1, the Hadamard product of the Grams) on the side
 // stream: Gamma(u) needs only the Grams of the other modes, so it is enqueued
 // before the MTTKRP of update u and runs concurrently with it.
 cp_status launch_chol(cp_ctx* c, int u, bool pp, double* scal) {
@@ -527,7 +527,7 @@ cp_status launch_chol(cp_ctx* c, int u, bool pp, double* scal) {
     return CP_OK;
 }
 
-// One factor update (Alg. 1 lines 6-9; in PP mode Alg. 2 lines 10-12 with V).
+// One factor update (Alg. 1: Gamma, MTTKRP, solve, Gram; in PP mode Alg. 2's approximated update with V).
 // launch_chol(u) must have been called for this update.
 cp_status update_mode(cp_ctx* c, int u, const float* M, bool pp, double* scal) {
     const int R = c->R, s = (int)c->dims[u];
@@ -1190,6 +1190,24 @@ void cp_config_default(cp_config* cfg) {
     cfg->seed = 20101205ull;
 }
 
+// tensor-core TTM plan of every mode's first-level contraction T x_m A(m)
+// (NULL where the shape needs the SIMT kernel)
+static void make_mode_plans(cp_ctx* c) {
+    const bool bf = uses_bf16(c), hf = c->cfg.prec == CP_F16X3;
+    const int kind = bf ? 0 : (hf ? 2 : 1);
+    const float tscale = ldexpf(1.f, c->eT);
+    for (int m = 0; m < c->N; ++m) {
+        cpk::ttm_tc_plan_free(c->tc_plan[m]);
+        int64_t P, Q;
+        contract_dims(c, 0u, m, &P, &Q);
+        const void* hi = (bf || hf) ? (const void*)c->bhi[m] : (const void*)c->bt32[m];
+        const void* lo = (bf || hf) ? (const void*)c->blo[m]
+                                    : (const void*)(c->bt32[m] + (size_t)c->Rpad * c->Kpad[m]);
+        c->tc_plan[m] = cpk::ttm_tc_plan(c->T, P, (int)c->dims[m], Q, c->R, kind, hi, lo, c->Rpad, c->Kpad[m],
+                                         tscale, c->colinv[m]);
+    }
+}
+
 cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T_dev, int dtype,
                   const double* A0_host, const cp_config* cfg, void* stream) {
     if (!out) return CP_EINVAL;
@@ -1215,7 +1233,7 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
         c->dims[i] = dims[i];
         c->Kpad[i] = (int)((dims[i] + 63) / 64 * 64);
         c->smax = std::max<int>(c->smax, (int)dims[i]);
-        c->dA_rel[i] = 1.0;  // Alg. 2 line 2: dA <- A
+        c->dA_rel[i] = 1.0;  // Alg. 2 starts from dA = A
     }
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1309,7 +1327,7 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
     TRYC(cudaMemsetAsync(c->dev_err, 0, sizeof(unsigned), c->st));
     TRY(grow_hist(c, 8));
 
-    // initial factors (Alg. 1 line 2)
+    // initial factors (Alg. 1)
     std::vector<double> h;
     for (int i = 0; i < N; ++i) {
         const size_t sR = (size_t)dims[i] * R;
@@ -1331,15 +1349,7 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
         const bool bf = uses_bf16(c), hf = c->cfg.prec == CP_F16X3;
         const int kind = bf ? 0 : (hf ? 2 : 1);
         const float tscale = ldexpf(1.f, c->eT);
-        for (int m = 0; m < N; ++m) {
-            int64_t P, Q;
-            contract_dims(c, 0u, m, &P, &Q);
-            const void* hi = (bf || hf) ? (const void*)c->bhi[m] : (const void*)c->bt32[m];
-            const void* lo = (bf || hf) ? (const void*)c->blo[m]
-                                        : (const void*)(c->bt32[m] + (size_t)c->Rpad * c->Kpad[m]);
-            c->tc_plan[m] = cpk::ttm_tc_plan(c->T, P, (int)dims[m], Q, R, kind, hi, lo, c->Rpad, c->Kpad[m],
-                                             tscale, c->colinv[m]);
-        }
+        make_mode_plans(c);
         // fused two-mode contractions of adjacent pairs (standard tree, N >= 3)
         size_t kr_elems = 0;
         for (int a = 0; a + 1 < N; ++a) {
@@ -1463,7 +1473,7 @@ static cp_status sweeps_exact(cp_ctx* c, int nsweeps, bool msdt) {
         CKCUDA(c, cudaEventRecord(c->events[k + 1], c->st));
     }
     CKST(harvest(c, nsweeps, kinds.data(), nullptr, 0));
-    // regular sweeps: dA(i) = this sweep's change (Alg. 2 line 14)
+    // regular sweeps: dA(i) = this sweep's change (Alg. 2, after a regular sweep)
     return CP_OK;
 }
 

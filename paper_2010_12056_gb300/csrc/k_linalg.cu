@@ -1,5 +1,5 @@
-// Dense side kernels of the factor updates and the residual (Alg. 1 lines 8-9;
-// Alg. 2 lines 10-12; Eq. ds, Eq. residual, Eq. residual-def): the Grams
+// Dense side kernels of the factor updates and the residual (Alg. 1 solve and Gram;
+// Alg. 2 approximated update; Eq. ds, Eq. residual, Eq. residual-def): the Grams
 // S(n) = A^T A and dS(n) = A^T dA in FP64 (thread-block clusters), the update's
 // scalar terms, the operand copies of a factor for the tensor-core TTM (bf16 /
 // tf32 / scaled fp16 parts), norms and maxima, the direct residual, the PP

@@ -1,5 +1,5 @@
-// Normal equations of one factor update, A(n) Gamma(n) = M(n) (Alg. 1 line 8,
-// Alg. 2 line 11), solved to FP64 accuracy with FP32 factorisation plus FP64
+// Normal equations of one factor update, A(n) Gamma(n) = M(n) (Alg. 1 and
+// Alg. 2, the solve step), solved to FP64 accuracy with FP32 factorisation plus FP64
 // iterative refinement (Wilkinson; Moler, JACM 1967; Carson and Higham, SISC 2018).
 //
 // On this GPU an FP64 FMA has a 64-cycle dependent latency and 1/70 of the FP32
@@ -11,7 +11,7 @@
 //                 Gauss-Jordan elimination; if the scaled condition number is
 //                 above 1e6 or a pivot is not positive, an FP64 LDL^T of Gamma
 //                 instead, and the solve kernel substitutes in FP64.
-//   k_solve_mixed (one 64-thread block per row) m = M(x,:) [+ A_old(x,:) W];
+//   k_solve_mixed (one block of 64 or 128 threads per row) m = M(x,:) [+ A_old(x,:) W];
 //                 x0 = m G32;  repeat  r = m - x Gamma (FP64),  d = r G32,  x += d
 //                 until the estimated remaining error ||d||_inf * rho is below
 //                 2^-36 ||x||_inf (rho = contraction seen between iterations),

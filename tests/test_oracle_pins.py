@@ -432,7 +432,7 @@ def _grow(A0, factor):
 
 def test_pp_control_follows_alg2_on_a_script(monkeypatch):
     """Alg. 2's regime logic, sweep by sweep, on scripted relative changes (eps 0.1):
-      0  dA = A (line 2): regular                      step 0.5  -> change 0.333
+      0  dA = A (start): regular                        step 0.5  -> change 0.333
       1  0.333 >= eps: regular                         step 0.05 -> change 0.048
       2  0.048 < eps: build operators (A_p = A), PP    step 0.04 -> A - A_p 0.038
       3  0.038 < eps: stay in PP                       step 0.04 -> 0.075
@@ -448,7 +448,7 @@ def test_pp_control_follows_alg2_on_a_script(monkeypatch):
     assert res.kinds == ["als", "als", "pp", "pp", "pp", "als", "pp", "als", "als", "pp"]
     assert len(res.kinds) == len(res.resid) == len(steps)
     assert res.n_pp_init == 3 == len(builds)
-    # each build starts from the factors of that moment (A_p = A, Alg. 2 line 6)
+    # each build starts from the factors of that moment (A_p = A, Alg. 2's operator build)
     for b, k in zip(builds, (2, 6, 9)):
         g = float(np.prod([1.0 + x for x in steps[:k]]))
         for n in range(3):
@@ -461,7 +461,7 @@ def test_pp_control_follows_alg2_on_a_script(monkeypatch):
 
 def test_pp_control_reentry_uses_the_regular_sweeps_change(monkeypatch):
     """After leaving PP, the entry test uses the change made by the regular sweep
-    (Alg. 2 line 14), not A - A_p of the old operators: here the accumulated
+    (Alg. 2, after a regular sweep), not A - A_p of the old operators: here the accumulated
     A - A_p (0.3 after the regular sweep) would keep it out, the sweep's own change
     (0.01) lets it back in with new operators."""
     steps = [0.5, 0.05, 0.09, 0.09, 0.01, 0.01]
