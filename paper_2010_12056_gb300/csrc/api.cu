@@ -71,6 +71,10 @@ struct cp_ctx {
     double* Ap64[CP_MAXN] = {0};
     float* dA32[CP_MAXN] = {0};
     double* dA64[CP_MAXN] = {0};
+    // R <= 128: the factor and its change as float pairs (hi + lo = the FP64
+    // value), written by the row solve for the double-float Gram
+    float2* A2[CP_MAXN] = {0};
+    float2* dA2[CP_MAXN] = {0};
     int ver[CP_MAXN] = {0};
     double** d_Slist = nullptr;
     double** d_dSlist = nullptr;
@@ -78,6 +82,8 @@ struct cp_ctx {
     double *Gamma = nullptr, *L = nullptr, *invd = nullptr, *W = nullptr;
     float* Ginv = nullptr;      // FP32 Gamma^{-1} for iterative refinement
     float* G32 = nullptr;       // FP32 copy of Gamma (input of the inverse)
+    float* G2 = nullptr;        // Gamma as float pairs (hi, lo): the double-float refinement
+    float* W2 = nullptr;        // PP's W as float pairs
     float* schur_ws = nullptr;  // blocked inverse workspace (R > 128)
     cudaStream_t side = nullptr;            // normal-equation factorisation runs here,
     cudaEvent_t ev_ready = nullptr, ev_chol = nullptr;  // overlapped with the MTTKRP
@@ -283,6 +289,11 @@ cp_status ensure_f16(cp_ctx* c, int mode) {
     return CP_OK;
 }
 
+// SMs for a persistent tensor-core TTM: one fewer while the one-CTA
+// factorisation of the side stream is in flight, so that no TTM CTA waits for its
+// SM (the tiles are assigned statically; a late CTA would delay the whole TTM)
+int tc_sms(const cp_ctx* c) { return c->chol_pending && c->num_sms > 1 ? c->num_sms - 1 : c->num_sms; }
+
 cp_status launch_ttm(cp_ctx* c, int mode, float* X) {
     int64_t P, Q;
     contract_dims(c, 0u, mode, &P, &Q);
@@ -290,7 +301,7 @@ cp_status launch_ttm(cp_ctx* c, int mode, float* X) {
     const int prec = c->cfg.prec;
     if (prec != CP_FP32_SIMT && c->tc_plan[mode]) {
         CKST(ensure_f16(c, mode));
-        LAUNCH(c, cpk::ttm_tc_run(c->tc_plan[mode], X, prec, c->num_sms, c->dev_err, c->st, c->splitk_ws, nullptr,
+        LAUNCH(c, cpk::ttm_tc_run(c->tc_plan[mode], X, prec, tc_sms(c), c->dev_err, c->st, c->splitk_ws, nullptr,
                                   c->wait_limit));
         if (c->splitk_ws && cpk::ttm_tc_splitk(c->tc_plan[mode], c->num_sms) > 1) c->stats.launches++;  // partial-sum kernel
         c->stats.ttm_tensor_core++;
@@ -324,7 +335,7 @@ cp_status launch_fused2(cp_ctx* c, int a, float* X) {
     const int R = c->R, sa = (int)c->dims[a], sb = (int)c->dims[a + 1];
     LAUNCH(c, cpk::kr_operand(c->A64[a], c->A64[a + 1], sa, sb, R, c->kr_Kpad[a], kind, c->kr_hi, c->kr_lo,
                               c->st, c->eT, c->kr_scale, c->kr_colinv));
-    LAUNCH(c, cpk::ttm_tc_run(c->kr_plan[a], X, c->cfg.prec, c->num_sms, c->dev_err, c->st, c->splitk_ws, nullptr,
+    LAUNCH(c, cpk::ttm_tc_run(c->kr_plan[a], X, c->cfg.prec, tc_sms(c), c->dev_err, c->st, c->splitk_ws, nullptr,
                               c->wait_limit));
     if (c->splitk_ws && cpk::ttm_tc_splitk(c->kr_plan[a], c->num_sms) > 1) c->stats.launches++;  // partial-sum kernel
     const double rows = (double)c->numel / ((double)sa * sb);
@@ -519,8 +530,9 @@ cp_status grow_hist(cp_ctx* c, int nsweeps) {
 cp_status launch_chol(cp_ctx* c, int u, bool pp, double* scal) {
     CKCUDA(c, cudaEventRecord(c->ev_ready, c->st));
     CKCUDA(c, cudaStreamWaitEvent(c->side, c->ev_ready, 0));
-    LAUNCH(c, cpk::chol_mixed(c->d_Slist, c->d_dSlist, c->N, u, c->R, pp ? 1 : 0, c->Gamma, c->G32, c->Ginv,
-                              c->L, c->invd, c->W, scal, c->d_mode, c->schur_ws, c->side, c->solve_fp64));
+    LAUNCH(c, cpk::chol_mixed(c->d_Slist, c->d_dSlist, c->N, u, c->R, pp ? 1 : 0, c->Gamma, c->G32, c->G2,
+                              c->Ginv, c->L, c->invd, c->W, c->W2, scal, c->d_mode, c->schur_ws, c->side,
+                              c->solve_fp64));
     CKCUDA(c, cudaEventRecord(c->ev_chol, c->side));
     c->chol_pending = true;
     c->chol_mode = u;
@@ -545,13 +557,20 @@ cp_status update_mode(cp_ctx* c, int u, const float* M, bool pp, double* scal) {
     o.Ap = pp ? c->Ap64[u] : nullptr;
     o.dA32 = pp ? c->dA32[u] : nullptr;
     o.dA64 = pp ? c->dA64[u] : nullptr;
+    o.A2 = c->A2[u];
+    o.dA2 = pp ? c->dA2[u] : nullptr;
     int nblk = 0;
     double* sp = c->scal_part + (size_t)u * c->smax * CP_NSCAL;
     double* tg = c->tile_gs + (size_t)u * c->ntiles;
     CKCUDA(c, cudaStreamWaitEvent(c->st, c->ev_scal[u], 0));  // sp / tg of mode u are free
-    LAUNCH(c, cpk::solve_mixed(M, pp ? c->W : nullptr, c->Gamma, c->Ginv, c->L, c->invd, c->d_mode, o, s, R, scal,
+    LAUNCH(c, cpk::solve_mixed(M, pp ? c->W : nullptr, pp ? c->W2 : nullptr, c->Gamma, c->G2, c->Ginv, c->L,
+                               c->invd, c->d_mode, o, s, R, scal,
                                sp, &nblk, c->dev_err, c->st));
-    LAUNCH(c, cpk::gram(c->A64[u], pp ? c->dA64[u] : nullptr, s, R, c->Gamma, c->S[u], c->dS[u], tg, c->st));
+    if (c->A2[u])
+        LAUNCH(c, cpk::gram_df(c->A2[u], pp ? c->dA2[u] : nullptr, s, R, reinterpret_cast<const float2*>(c->G2),
+                               c->S[u], c->dS[u], tg, c->st));
+    else
+        LAUNCH(c, cpk::gram(c->A64[u], pp ? c->dA64[u] : nullptr, s, R, c->Gamma, c->S[u], c->dS[u], tg, c->st));
     CKCUDA(c, cudaEventRecord(c->ev_g, c->st));
     CKCUDA(c, cudaStreamWaitEvent(c->aux, c->ev_g, 0));
     LAUNCH(c, cpk::scal_fin(sp, nblk, tg, c->ntiles, scal, c->aux));
@@ -902,13 +921,15 @@ cp_status pp_sweep(cp_ctx* c, int k) {
     return CP_OK;
 }
 
+cp_status regram(cp_ctx* c, int i, bool pp);
+
 cp_status init_grams(cp_ctx* c) {
     for (int n = 0; n < c->N; ++n) {
         const int s = (int)c->dims[n];
         LAUNCH(c, cpk::factor_copies(c->A64[n], c->A32[n], uses_bf16(c) ? c->bhi[n] : nullptr,
                                      uses_bf16(c) ? c->blo[n] : nullptr, uses_tf32(c) ? c->bt32[n] : nullptr, s,
                                      c->R, c->Rpad, c->Kpad[n], c->st));
-        LAUNCH(c, cpk::gram(c->A64[n], nullptr, s, c->R, nullptr, c->S[n], nullptr, nullptr, c->st));
+        CKST(regram(c, n, false));
     }
     return CP_OK;
 }
@@ -938,10 +959,20 @@ cp_status direct_resid(cp_ctx* c, double* r) {
     return CP_OK;
 }
 
-// S(i) (and dS(i) when `pp`) from the factors now in A64 (and dA64)
+// S(i) (and dS(i) when `pp`) from the factors now in A64 (and dA64).  For R <= 128
+// through the float pairs the row solve also writes, so that a Gram formed here
+// equals the one an update forms from the same factor.
 cp_status regram(cp_ctx* c, int i, bool pp) {
     const int s = (int)c->dims[i];
-    LAUNCH(c, cpk::gram(c->A64[i], pp ? c->dA64[i] : nullptr, s, c->R, nullptr, c->S[i], c->dS[i], nullptr, c->st));
+    if (c->A2[i]) {
+        LAUNCH(c, cpk::split_pairs(c->A64[i], c->A2[i], (int64_t)s * c->R, c->st));
+        if (pp) LAUNCH(c, cpk::split_pairs(c->dA64[i], c->dA2[i], (int64_t)s * c->R, c->st));
+        LAUNCH(c, cpk::gram_df(c->A2[i], pp ? c->dA2[i] : nullptr, s, c->R, nullptr, c->S[i], c->dS[i], nullptr,
+                               c->st));
+    } else {
+        LAUNCH(c, cpk::gram(c->A64[i], pp ? c->dA64[i] : nullptr, s, c->R, nullptr, c->S[i], c->dS[i], nullptr,
+                            c->st));
+    }
     return CP_OK;
 }
 
@@ -1158,8 +1189,12 @@ void free_all(cp_ctx* c) {
         c->kr_plan[i] = nullptr;
     }
     F(c->kr_hi); F(c->kr_lo); F(c->kr_scale); F(c->kr_colinv); F(c->splitk_ws); F(c->child_ws);
-    for (int i = 0; i < CP_MAXN; ++i) F(c->colinv[i]);
-    F(c->Ginv); F(c->G32); F(c->schur_ws); F(c->d_mode);
+    for (int i = 0; i < CP_MAXN; ++i) {
+        F(c->colinv[i]);
+        F(c->A2[i]);
+        F(c->dA2[i]);
+    }
+    F(c->Ginv); F(c->G32); F(c->G2); F(c->W2); F(c->schur_ws); F(c->d_mode);
     if (c->side) { cudaStreamSynchronize(c->side); cudaStreamDestroy(c->side); c->side = nullptr; }
     if (c->ev_ready) { cudaEventDestroy(c->ev_ready); c->ev_ready = nullptr; }
     if (c->ev_chol) { cudaEventDestroy(c->ev_chol); c->ev_chol = nullptr; }
@@ -1274,6 +1309,10 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
         const size_t sR = (size_t)dims[i] * R;
         TRY(dalloc(c, &c->A64[i], sR));
         TRY(dalloc(c, &c->A32[i], sR));
+        if (R <= 128) {
+            TRY(dalloc(c, &c->A2[i], sR));
+            TRY(dalloc(c, &c->dA2[i], sR));
+        }
         TRY(dalloc(c, &c->S[i], RR));
         TRY(dalloc(c, &c->dS[i], RR));
         TRYC(cudaMemsetAsync(c->dS[i], 0, sizeof(double) * RR, c->st));
@@ -1306,6 +1345,8 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
     TRY(dalloc(c, &c->Gamma, RR + 2));
     TRY(dalloc(c, &c->Ginv, RR + 4));
     TRY(dalloc(c, &c->G32, RR + 4));
+    TRY(dalloc(c, &c->G2, 2 * RR + 4));
+    TRY(dalloc(c, &c->W2, 2 * RR + 4));
     if (cpk::schur_ws_floats(R)) TRY(dalloc(c, &c->schur_ws, cpk::schur_ws_floats(R)));
     TRYC(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     TRYC(cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming));
@@ -1850,8 +1891,7 @@ cp_status cp_set_factor(cp_ctx* c, int mode, const double* A_host) {
     const bool pp = c->pp_valid;
     if (pp)
         LAUNCH(c, cpk::pp_delta(c->A64[mode], c->Ap64[mode], c->dA32[mode], c->dA64[mode], (int64_t)s * c->R, c->st));
-    LAUNCH(c, cpk::gram(c->A64[mode], pp ? c->dA64[mode] : nullptr, s, c->R, nullptr, c->S[mode], c->dS[mode],
-                        nullptr, c->st));
+    CKST(regram(c, mode, pp));
     CKCUDA(c, cudaStreamSynchronize(c->st));
     c->ver[mode] = ++c->vclock;
     c->have_last = false;

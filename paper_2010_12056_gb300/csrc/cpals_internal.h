@@ -129,23 +129,26 @@ struct SolveOut {
     const double* Ap;   // PP base factor (NULL outside PP)
     float* dA32;        // A_new - A_p (or - A_old outside PP), FP32
     double* dA64;       // same in FP64
+    float2* A2;         // A_new as float pairs (hi, lo) for gram_df (NULL: not written)
+    float2* dA2;        // dA as float pairs (NULL: not written)
 };
 // Mixed-precision normal-equation solve (k_solve_mixed.cu): chol_mixed forms
-// Gamma (FP64, written to Gamma), PP's W, and either Ginv ~ Gamma^{-1} in FP32
-// from the diagonally scaled matrix (*mode = 0) or the FP64 factor L64
-// ([L | L^T], 2 R^2) and invd64 (*mode = 1);
+// Gamma (FP64, written to Gamma; its FP32 copy G32 and float pairs hi, lo in
+// G2), PP's W (FP64 and pairs W2), and either Ginv ~ Gamma^{-1} in FP32 from the
+// diagonally scaled matrix (*mode = 0) or the FP64 factor L64 ([L | L^T], 2 R^2)
+// and invd64 (*mode = 1);
 // solve_mixed then solves every row to FP64 accuracy (refinement or FP64
-// substitution).  Gamma and Ginv must have 16 spare bytes after R*R entries.
+// substitution).  Gamma, G2 and Ginv must have 16 spare bytes after their R*R entries.
 // force64: skip the FP32 inverse and factor Gamma in FP64 (LDL^T) for this update.
 cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
-                       double* Gamma, float* G32, float* Ginv, double* L64, double* invd64, double* W,
-                       double* scal, int* mode, float* ws, cudaStream_t st, bool force64 = false);
+                       double* Gamma, float* G32, float* G2, float* Ginv, double* L64, double* invd64, double* W,
+                       float* W2, double* scal, int* mode, float* ws, cudaStream_t st, bool force64 = false);
 // floats of the workspace chol_mixed needs for R > 128 (blocked inverse), else 0
 size_t schur_ws_floats(int R);
-cudaError_t solve_mixed(const float* M, const double* W, const double* Gamma, const float* Ginv,
-                        const double* L64, const double* invd64, const int* mode, const SolveOut& o,
-                        int s, int R, double* scal, double* scal_part, int* nblk, unsigned* dev_err,
-                        cudaStream_t st);
+cudaError_t solve_mixed(const float* M, const double* W, const float* W2, const double* Gamma, const float* G2,
+                        const float* Ginv, const double* L64, const double* invd64, const int* mode,
+                        const SolveOut& o, int s, int R, double* scal, double* scal_part, int* nblk,
+                        unsigned* dev_err, cudaStream_t st);
 
 // S = A^T A (and dS = A^T dA when dA != NULL), one cluster launch over row
 // chunks; with Gamma and tile_gs (gram_tiles(R) doubles) also the tile shares of
@@ -154,6 +157,12 @@ cudaError_t solve_mixed(const float* M, const double* W, const double* Gamma, co
 int gram_tiles(int R);
 cudaError_t gram(const double* A, const double* dA, int s, int R, const double* Gamma, double* S,
                  double* dS, double* tile_gs, cudaStream_t st);
+// Same from the float-pair copies the solve writes (A2, dA2 = hi + lo of the FP64
+// values), in double-float arithmetic; Gamma for <Gamma, S> as float pairs (G2).
+cudaError_t gram_df(const float2* A2, const float2* dA2, int s, int R, const float2* G2, double* S,
+                    double* dS, double* tile_gs, cudaStream_t st);
+// y[i] = float pair (hi, lo) of x[i] (hi = x rounded to float, lo = the rest rounded)
+cudaError_t split_pairs(const double* x, float2* y, int64_t n, cudaStream_t st);
 cudaError_t scal_fin(const double* scal_part, int nblk, const double* tile_gs, int ntiles, double* scal_out,
                      cudaStream_t st);
 

@@ -10,6 +10,7 @@
 #include <cuda_fp16.h>
 
 #include "cpals_internal.h"
+#include "df_arith.h"
 
 namespace {
 
@@ -141,6 +142,102 @@ __global__ void __launch_bounds__(256) k_gram_cl(const double* __restrict__ A,
         }
     }
     cluster_sync_all();  // every CTA's partials stay readable until CTA 0 is done
+}
+
+__device__ __forceinline__ float2 ld_cluster_f2(const float2* local, unsigned rank) {
+    uint32_t la = (uint32_t)__cvta_generic_to_shared(local), ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(rank));
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(ra) : "memory");
+    return v;
+}
+
+// The same Gram from the float-pair copy of the factor (hi + lo = its FP64 value,
+// written by the row solve): the products in double-float arithmetic on the FP32
+// pipe (exact leading products, about 2^-44 relative), the chunk partials added
+// in chunk order by CTA 0 of the cluster, FP64 only for the stored entries.
+// <Gamma, S> per tile from Gamma's float pairs, also in double-float.
+__global__ void __launch_bounds__(256) k_gram_df(const float2* __restrict__ A, const float2* __restrict__ dA,
+                                                 int s, int R, int rows_per, const float2* __restrict__ G2,
+                                                 double* __restrict__ S, double* __restrict__ dS,
+                                                 double* __restrict__ tile_gs) {
+    __shared__ float2 a1[16][17], a2[16][17], d2[16][17];
+    __shared__ float2 ps[256], pd[256];
+    __shared__ float2 red[8];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31, warp = tid >> 5;
+    const int r1 = blockIdx.x * 16 + ty, r2 = blockIdx.y * 16 + tx;
+    const int c = blockIdx.z, nc = gridDim.z;
+    const int x0 = c * rows_per, x1 = min(s, x0 + rows_per);
+    const float2 z = make_float2(0.f, 0.f);
+    float sh = 0.f, sl = 0.f, dh = 0.f, dl = 0.f;
+    for (int xb = x0; xb < x1; xb += 16) {
+        const int x = xb + ty;
+        const int ca = blockIdx.x * 16 + tx, cb = blockIdx.y * 16 + tx;
+        a1[ty][tx] = (x < x1 && ca < R) ? A[(size_t)x * R + ca] : z;
+        a2[ty][tx] = (x < x1 && cb < R) ? A[(size_t)x * R + cb] : z;
+        if (dA) d2[ty][tx] = (x < x1 && cb < R) ? dA[(size_t)x * R + cb] : z;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float2 u = a1[k][ty], v = a2[k][tx];
+            cpdf::fma_acc(u.x, u.y, v.x, v.y, sh, sl);
+            if (dA) {
+                const float2 w = d2[k][tx];
+                cpdf::fma_acc(u.x, u.y, w.x, w.y, dh, dl);
+            }
+        }
+        __syncthreads();
+    }
+    ps[tid] = make_float2(sh, sl);
+    pd[tid] = make_float2(dh, dl);
+    cluster_sync_all();
+    if (c == 0) {
+        // cluster dims (1, 1, nc): the rank of a CTA in its cluster is blockIdx.z
+        float2 pv[GRAM_MAX_CHUNKS], pq[GRAM_MAX_CHUNKS];
+#pragma unroll
+        for (int q = 0; q < GRAM_MAX_CHUNKS; ++q) {
+            pv[q] = q < nc ? ld_cluster_f2(&ps[tid], (unsigned)q) : z;
+            pq[q] = (q < nc && dA) ? ld_cluster_f2(&pd[tid], (unsigned)q) : z;
+        }
+        float vh = pv[0].x, vl = pv[0].y, wh = pq[0].x, wl = pq[0].y;
+#pragma unroll
+        for (int q = 1; q < GRAM_MAX_CHUNKS; ++q) {
+            cpdf::add(vh, vl, pv[q].x, pv[q].y);
+            if (dA) cpdf::add(wh, wl, pq[q].x, pq[q].y);
+        }
+        float gh = 0.f, gl = 0.f;
+        if (r1 < R && r2 < R) {
+            const size_t e = (size_t)r1 * R + r2;
+            S[e] = (double)vh + (double)vl;
+            if (dA) dS[e] = (double)wh + (double)wl;
+            if (G2) {
+                const float2 g = G2[e];
+                cpdf::fma_acc(g.x, g.y, vh, vl, gh, gl);
+            }
+        }
+        if (tile_gs) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const float bh = __shfl_xor_sync(0xffffffffu, gh, o), bl = __shfl_xor_sync(0xffffffffu, gl, o);
+                cpdf::add(gh, gl, bh, bl);
+            }
+            if (lane == 0) red[warp] = make_float2(gh, gl);
+            __syncthreads();
+            if (tid == 0) {
+                float h = red[0].x, l = red[0].y;
+                for (int w = 1; w < 8; ++w) cpdf::add(h, l, red[w].x, red[w].y);
+                tile_gs[blockIdx.y * gridDim.x + blockIdx.x] = (double)h + (double)l;
+            }
+        }
+    }
+    cluster_sync_all();  // every CTA's partials stay readable until CTA 0 is done
+}
+
+// y = float pairs (hi, lo) of x, the same rounding the row solve uses
+__global__ void __launch_bounds__(256) k_split_pairs(const double* __restrict__ x, float2* __restrict__ y,
+                                                     int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = cpdf::split(x[i]);
 }
 
 // The update's scalars: the solve's per-block partials and the tile shares of
@@ -712,6 +809,36 @@ cudaError_t gram(const double* A, const double* dA, int s, int R, const double* 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_gram_cl, A, dA, s, R, rows_per, Gamma, S, dS, tile_gs);
+}
+
+cudaError_t split_pairs(const double* x, float2* y, int64_t n, cudaStream_t st) {
+    int64_t want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want > 4096 ? 4096 : (want < 1 ? 1 : want));
+    k_split_pairs<<<blocks, 256, 0, st>>>(x, y, n);
+    return cudaGetLastError();
+}
+
+cudaError_t gram_df(const float2* A2, const float2* dA2, int s, int R, const float2* G2, double* S,
+                    double* dS, double* tile_gs, cudaStream_t st) {
+    // about 32 rows per chunk, at most GRAM_MAX_CHUNKS chunks (one cluster)
+    int nc = (s + 31) / 32;
+    if (nc > GRAM_MAX_CHUNKS) nc = GRAM_MAX_CHUNKS;
+    if (nc < 1) nc = 1;
+    const int rows_per = (s + nc - 1) / nc;
+    nc = (s + rows_per - 1) / rows_per;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((R + 15) / 16, (R + 15) / 16, nc);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = nc;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_gram_df, A2, dA2, s, R, rows_per, G2, S, dS, tile_gs);
 }
 
 cudaError_t scal_fin(const double* scal_part, int nblk, const double* tile_gs, int ntiles, double* scal_out,

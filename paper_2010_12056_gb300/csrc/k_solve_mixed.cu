@@ -11,16 +11,20 @@
 //                 Gauss-Jordan elimination; if the scaled condition number is
 //                 above 1e6 or a pivot is not positive, an FP64 LDL^T of Gamma
 //                 instead, and the solve kernel substitutes in FP64.
-//   k_solve_mixed (one block of 64 or 128 threads per row) m = M(x,:) [+ A_old(x,:) W];
-//                 x0 = m G32;  repeat  r = m - x Gamma (FP64),  d = r G32,  x += d
+//   k_solve_mixed (one block per row) m = M(x,:) [+ A_old(x,:) W];
+//                 x0 = m G32;  repeat  r = m - x Gamma,  d = r G32,  x += d
 //                 until the estimated remaining error ||d||_inf * rho is below
 //                 2^-36 ||x||_inf (rho = contraction seen between iterations),
 //                 four orders of magnitude below the FP32 rounding of M itself.
+//                 For R <= 128 the residual (and V) is formed in double-float
+//                 arithmetic on the FP32 pipe (about 2^-44 relative), with x and
+//                 Gamma held as pairs of floats; above, in FP64.
 #include <cuda_bf16.h>
 
 #include <algorithm>
 
 #include "cpals_internal.h"
+#include "df_arith.h"
 
 namespace {
 
@@ -30,11 +34,6 @@ constexpr int MIXED_MAXR = 128;
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_max_d(double v) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
     return v;
 }
 __device__ double block_sum_d(double v, double* sh) {
@@ -152,8 +151,8 @@ __device__ __forceinline__ double gamma_entry(const double* const* Sp, const dou
 __global__ void __launch_bounds__(256) k_gamma_form(double* const* __restrict__ S_list,
                                                     double* const* __restrict__ dS_list, int N,
                                                     int n, int R, int pp, double* __restrict__ G,
-                                                    float* __restrict__ G32,
-                                                    double* __restrict__ W) {
+                                                    float* __restrict__ G32, float* __restrict__ G2,
+                                                    double* __restrict__ W, float* __restrict__ W2) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= R * R) return;
     const double* Sp[CP_MAXN];
@@ -165,8 +164,17 @@ __global__ void __launch_bounds__(256) k_gamma_form(double* const* __restrict__ 
     double w = 0.0;
     const double g = gamma_entry(Sp, dSp, N, n, pp, (size_t)e, &w);
     G[e] = g;
-    G32[e] = (float)g;
-    if (pp) W[e] = w;
+    const float gh = (float)g;
+    G32[e] = gh;
+    // float pairs (hi, lo) for the double-float refinement of the row solve
+    G2[2 * e] = gh;
+    G2[2 * e + 1] = (float)(g - (double)gh);
+    if (pp) {
+        W[e] = w;
+        const float wh = (float)w;
+        W2[2 * e] = wh;
+        W2[2 * e + 1] = (float)(w - (double)wh);
+    }
 }
 
 // R <= 128: explicit inverse of the diagonally scaled matrix
@@ -634,38 +642,83 @@ __host__ __device__ inline SolveSmem solve_smem(int R) {
     return L;
 }
 
-// One row x per block of 64 KS threads; in the refinement path thread t of the
-// first 64 owns the columns t + 64 c (c < CT); each of the KS groups of 64 sums
-// its 1/KS share of every dot product of those columns, and the shares meet in
-// shared memory.  Per iteration:
-//   r = m - x Gamma   (FP64; Gamma staged in shared memory for R <= 128, else read from L2)
+using cpdf::fast_two_sum;
+using cpdf::two_sum;
+__device__ __forceinline__ void df_fma(float vh, float vl, float2 p, float& ah, float& al) {
+    cpdf::fma_acc(vh, vl, p.x, p.y, ah, al);
+}
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) { cpdf::add(ah, al, bh, bl); }
+
+// h[c] + l[c] = sum_{k0 <= k < k1} (vh[k] + vl[k]) P[k][jj[c]]  (two chains per column)
+template <int CT>
+__device__ __forceinline__ void df_dot(const float* vh, const float* vl, const float2* __restrict__ P, int R,
+                                       int k0, int k1, const int (&jj)[CT], float (&h)[CT], float (&l)[CT]) {
+    float h2[CT], l2[CT];
+#pragma unroll
+    for (int c = 0; c < CT; ++c) h[c] = l[c] = h2[c] = l2[c] = 0.f;
+    int k = k0;
+    for (; k + 1 < k1; k += 2) {
+        const float a0 = vh[k], b0 = vl[k], a1 = vh[k + 1], b1 = vl[k + 1];
+        const float2* p0 = P + (size_t)k * R;
+        const float2* p1 = p0 + R;
+#pragma unroll
+        for (int c = 0; c < CT; ++c) {
+            df_fma(a0, b0, p0[jj[c]], h[c], l[c]);
+            df_fma(a1, b1, p1[jj[c]], h2[c], l2[c]);
+        }
+    }
+    if (k < k1) {
+        const float2* p0 = P + (size_t)k * R;
+#pragma unroll
+        for (int c = 0; c < CT; ++c) df_fma(vh[k], vl[k], p0[jj[c]], h[c], l[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < CT; ++c) df_add(h[c], l[c], h2[c], l2[c]);
+}
+
+// One row x per block of KS groups of 64 threads; thread t of a group owns the
+// columns t + 64 c (c < CT), each group sums its 1/KS share of every dot product
+// of those columns, and the shares meet in shared memory.  Per refinement step:
+//   r = m - x Gamma   R <= 128: in double-float arithmetic on the FP32 pipe, x =
+//                     xh + xl and Gamma = Gh + Gl (staged as float pairs), exact
+//                     leading products, about 2^-44 relative accuracy;
+//                     R > 128: FP64, Gamma read from L2
 //   d = r G32         (FP32; r is small, so FP32 carries it to full accuracy)
 //   x += d
-// and two barriers.  It stops once the error left after the step, estimated as
-// rho ||d||_inf with rho the contraction seen between steps, is below
-// 2^-36 ||x||_inf: far below the FP32 error of the MTTKRP that forms m.
+// GB300's FP64 pipe retires about 1.6 FMAs per cycle per SM, so an FP64 residual
+// of a 64-column row took about 5 us per step; the double-float one needs a
+// tenth of the issue slots of the FP32 pipe.  The iteration stops once the error
+// left after the step, estimated as rho ||d||_inf with rho the contraction seen
+// between steps, is below 2^-36 ||x||_inf: far below the FP32 error of the
+// MTTKRP that forms m.
 template <int RT, int KS>
 __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
-    const float* __restrict__ M, const double* __restrict__ W, const double* __restrict__ G,
-    const float* __restrict__ Ginv, const double* __restrict__ L64, const double* __restrict__ invd64,
-    const int* __restrict__ mode, cpk::SolveOut o, int s, int R, double* __restrict__ scal,
-    double* __restrict__ scal_part, unsigned* __restrict__ dev_err) {
-    constexpr int CT = (RT + 1) / 2;  // columns per thread in the refinement path
+    const float* __restrict__ M, const double* __restrict__ W, const float2* __restrict__ W2,
+    const double* __restrict__ G, const float2* __restrict__ G2, const float* __restrict__ Ginv,
+    const double* __restrict__ L64, const double* __restrict__ invd64, const int* __restrict__ mode,
+    cpk::SolveOut o, int s, int R, double* __restrict__ scal, double* __restrict__ scal_part,
+    unsigned* __restrict__ dev_err) {
+    constexpr bool DF = RT <= 4;       // R <= 128: staged matrices, double-float refinement
+    constexpr int CT = (RT + 1) / 2;   // columns per thread in the refinement path
     extern __shared__ __align__(16) double sm[];
     __shared__ __align__(8) uint64_t bar;
     const SolveSmem lay = solve_smem(R);
     double* sG = sm + lay.G;
+    const float2* sG2 = reinterpret_cast<const float2*>(sm + lay.G);
     float* sGi = reinterpret_cast<float*>(sm + lay.Gi);
     double* mv = sm + lay.m;
     double* xv = sm + lay.x;
+    float* xh_s = reinterpret_cast<float*>(sm + lay.x);   // double-float x: hi then lo
+    float* xl_s = xh_s + R;
     float* rv = reinterpret_cast<float*>(sm + lay.r);
     double* part = sm + lay.part;
-    double* red = sm + lay.red;
+    float* redf = reinterpret_cast<float*>(sm + lay.red);   // warp maxima of the step and of x
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // KS groups of 64 threads: group q sums its 1/KS share of every dot product of
     // the refinement; group 0 owns the columns (tcol + 64 c) and everything else
     const int q = tid / SOLVE_THREADS, tcol = tid % SOLVE_THREADS;
     double* pk = sm + lay.pk;                                      // (KS-1) x R FP64 partials
+    float2* pk2 = reinterpret_cast<float2*>(sm + lay.pk);          // (KS-1) x R double-float partials
     float* pkf = reinterpret_cast<float*>(sm + lay.pk + 3 * (size_t)R);  // (KS-1) x R FP32 partials
     const int kq = (R + KS - 1) / KS, k0 = q * kq, k1 = min(R, k0 + kq);
     const int x = blockIdx.x;
@@ -675,23 +728,29 @@ __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
 #pragma unroll
     for (int i = 0; i < CP_NSCAL; ++i) sc[i] = 0.0;
     double xj[CT], mj[CT], aold[CT];
+    float mh[CT], ml[CT], xh[CT], xl[CT];
+    int jj[CT];
 #pragma unroll
     for (int c = 0; c < CT; ++c) {
         const int j = tcol + SOLVE_THREADS * c;
+        jj[c] = j < R ? j : 0;  // idle columns read column 0 and are dropped
         xj[c] = 0.0;
+        xh[c] = xl[c] = 0.f;
         aold[c] = (j < R) ? o.A64[(size_t)x * R + j] : 0.0;
-        mj[c] = (j < R) ? (double)M[(size_t)x * R + j] : 0.0;
+        mh[c] = (j < R) ? M[(size_t)x * R + j] : 0.f;
+        ml[c] = 0.f;
+        mj[c] = 0.0;
+        if constexpr (!DF) mj[c] = (double)mh[c];
     }
+    float fv2 = 0.f;   // double-float path: ||V||^2 of this thread's columns
 
     if (path == 0) {
-        // R <= 128: stage Gamma and G32 with two bulk copies (sizes rounded up to
-        // 16 bytes; the sources have 16 spare bytes).  Larger R reads both from L2.
-        const bool staged = R <= MIXED_MAXR;
-        const double* Gm = staged ? sG : G;
-        const float* Gim = staged ? sGi : Ginv;
+        // R <= 128: stage Gamma (as float pairs, or FP64 above) and G32 with two
+        // bulk copies (sizes rounded up to 16 bytes; the sources have 16 spare bytes)
+        const float* Gim = DF ? sGi : Ginv;
         const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
         const uint32_t bytesG = (uint32_t)((RR * 8 + 15) & ~15), bytesGi = (uint32_t)((RR * 4 + 15) & ~15);
-        if (tid == 0 && staged) {
+        if (DF && tid == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytesG + bytesGi)
@@ -699,7 +758,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                     (uint32_t)__cvta_generic_to_shared(sG)),
-                "l"(G), "r"(bytesG), "r"(b)
+                "l"(G2), "r"(bytesG), "r"(b)
                 : "memory");
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -707,37 +766,86 @@ __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
                 "l"(Ginv), "r"(bytesGi), "r"(b)
                 : "memory");
         }
+        __syncthreads();  // the barrier is initialised before any thread waits on it
+        if (W) {
+            // V(x,:) = A_old(x,:) W (Eq. V_nij), added to m
+            if constexpr (DF) {
 #pragma unroll
-        for (int c = 0; c < CT; ++c) {
-            const int j = tcol + SOLVE_THREADS * c;
-            if (q == 0 && j < R) xv[j] = aold[c];  // for the V term
-        }
-        __syncthreads();
-        if (W && q == 0) {
-            // V(x,:) = A_old(x,:) W (Eq. V_nij), FP64
-#pragma unroll
-            for (int c = 0; c < CT; ++c) {
-                const int j = tcol + SOLVE_THREADS * c;
-                if (j >= R) continue;
-                double v0 = 0.0, v1 = 0.0;
-                int q = 0;
-                for (; q + 1 < R; q += 2) {
-                    v0 = fma(xv[q], W[(size_t)q * R + j], v0);
-                    v1 = fma(xv[q + 1], W[(size_t)(q + 1) * R + j], v1);
+                for (int c = 0; c < CT; ++c) {
+                    const int j = tcol + SOLVE_THREADS * c;
+                    if (q == 0 && j < R) {
+                        const float ah = (float)aold[c];
+                        xh_s[j] = ah;
+                        xl_s[j] = (float)(aold[c] - (double)ah);
+                    }
                 }
-                if (q < R) v0 = fma(xv[q], W[(size_t)q * R + j], v0);
-                const double v = v0 + v1;
-                mj[c] += v;
-                sc[SCAL_V2] += v * v;
+                __syncthreads();
+                float vh[CT], vl[CT];
+                df_dot<CT>(xh_s, xl_s, W2, R, k0, k1, jj, vh, vl);
+                if (KS > 1) {
+                    if (q > 0)
+#pragma unroll
+                        for (int c = 0; c < CT; ++c) {
+                            const int j = tcol + SOLVE_THREADS * c;
+                            if (j < R) pk2[(size_t)(q - 1) * R + j] = make_float2(vh[c], vl[c]);
+                        }
+                    __syncthreads();
+                    if (q == 0)
+#pragma unroll
+                        for (int c = 0; c < CT; ++c) {
+                            const int j = tcol + SOLVE_THREADS * c;
+                            if (j < R)
+                                for (int g = 1; g < KS; ++g) {
+                                    const float2 t = pk2[(size_t)(g - 1) * R + j];
+                                    df_add(vh[c], vl[c], t.x, t.y);
+                                }
+                        }
+                }
+                if (q == 0)
+#pragma unroll
+                    for (int c = 0; c < CT; ++c) {
+                        const int j = tcol + SOLVE_THREADS * c;
+                        if (j >= R) continue;
+                        const float vf = __fadd_rn(vh[c], vl[c]);
+                        fv2 = fmaf(vf, vf, fv2);
+                        float sh, sl;
+                        two_sum(mh[c], vh[c], sh, sl);
+                        sl = __fadd_rn(sl, vl[c]);
+                        fast_two_sum(sh, sl, mh[c], ml[c]);
+                    }
+            } else {
+#pragma unroll
+                for (int c = 0; c < CT; ++c) {
+                    const int j = tcol + SOLVE_THREADS * c;
+                    if (q == 0 && j < R) xv[j] = aold[c];
+                }
+                __syncthreads();
+                if (q == 0) {
+#pragma unroll
+                    for (int c = 0; c < CT; ++c) {
+                        const int j = tcol + SOLVE_THREADS * c;
+                        if (j >= R) continue;
+                        double v0 = 0.0, v1 = 0.0;
+                        int k = 0;
+                        for (; k + 1 < R; k += 2) {
+                            v0 = fma(xv[k], W[(size_t)k * R + j], v0);
+                            v1 = fma(xv[k + 1], W[(size_t)(k + 1) * R + j], v1);
+                        }
+                        if (k < R) v0 = fma(xv[k], W[(size_t)k * R + j], v0);
+                        const double v = v0 + v1;
+                        mj[c] += v;
+                        sc[SCAL_V2] += v * v;
+                    }
+                }
             }
         }
 #pragma unroll
         for (int c = 0; c < CT; ++c) {
             const int j = tcol + SOLVE_THREADS * c;
-            if (q == 0 && j < R) rv[j] = (float)mj[c];
+            if (q == 0 && j < R) rv[j] = DF ? __fadd_rn(mh[c], ml[c]) : (float)mj[c];
         }
         // bounded wait for the staged matrices (about 1 s)
-        if (staged) {
+        if (DF) {
             const long long t0 = clock64();
             uint32_t ok = 0;
             int give_up = 0;
@@ -801,42 +909,72 @@ __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
 #pragma unroll
         for (int c = 0; c < CT; ++c) {
             const int j = tcol + SOLVE_THREADS * c;
-            xj[c] = (double)d0[c];
-            if (q == 0 && j < R) xv[j] = xj[c];
+            if constexpr (!DF) xj[c] = (double)d0[c];
+            xh[c] = d0[c];
+            xl[c] = 0.f;
+            if (q == 0 && j < R) {
+                if (DF) {
+                    xh_s[j] = d0[c];
+                    xl_s[j] = 0.f;
+                } else {
+                    xv[j] = xj[c];
+                }
+            }
         }
         __syncthreads();
-        double prev = 0.0;
+        float prev = 0.f;
         bool conv = false;
         for (int itr = 0; itr < 30; ++itr) {
-            // r = m - x Gamma (FP64).  NQ partial sums per column, the thread's
-            // columns interleaved: NQ CT independent chains cover the FP64 FMA
-            // latency (64 cycles) with the few warps a row has (eight for up to
-            // four columns per thread, four beyond: R > 256 keeps 32+ chains in
-            // about 130 registers)
-            {
+            if constexpr (DF) {
+                // r = m - x Gamma in double-float arithmetic
+                float th[CT], tl[CT];
+                df_dot<CT>(xh_s, xl_s, sG2, R, k0, k1, jj, th, tl);
+                if (KS > 1) {
+                    if (q > 0)
+#pragma unroll
+                        for (int c = 0; c < CT; ++c) {
+                            const int j = tcol + SOLVE_THREADS * c;
+                            if (j < R) pk2[(size_t)(q - 1) * R + j] = make_float2(th[c], tl[c]);
+                        }
+                    __syncthreads();
+                }
+                if (q == 0)
+#pragma unroll
+                    for (int c = 0; c < CT; ++c) {
+                        const int j = tcol + SOLVE_THREADS * c;
+                        if (j < R) {
+                            for (int g = 1; g < KS; ++g) {
+                                const float2 t = pk2[(size_t)(g - 1) * R + j];
+                                df_add(th[c], tl[c], t.x, t.y);
+                            }
+                            // m - S: the leading difference is exact when the two
+                            // are close (Sterbenz), so r keeps its own 24 bits
+                            rv[j] = __fadd_rn(__fsub_rn(mh[c], th[c]), __fsub_rn(ml[c], tl[c]));
+                        }
+                    }
+            } else {
+                // r = m - x Gamma (FP64).  NQ partial sums per column, the thread's
+                // columns interleaved: NQ CT independent chains cover the FP64 FMA
+                // latency (64 cycles) with the few warps a row has
                 constexpr int NQ = CT <= 4 ? 8 : 4;
                 double ra[CT][NQ];
-                int jj[CT];
 #pragma unroll
-                for (int c = 0; c < CT; ++c) {
-                    const int j = tcol + SOLVE_THREADS * c;
-                    jj[c] = j < R ? j : 0;  // idle columns read column 0 and are dropped
+                for (int c = 0; c < CT; ++c)
 #pragma unroll
-                    for (int q = 0; q < NQ; ++q) ra[c][q] = 0.0;
-                }
+                    for (int u = 0; u < NQ; ++u) ra[c][u] = 0.0;
                 int k = k0;
                 for (; k + NQ - 1 < k1; k += NQ) {
 #pragma unroll
-                    for (int q = 0; q < NQ; ++q) {
-                        const double xk = xv[k + q];
-                        const double* grow = Gm + (size_t)(k + q) * R;
+                    for (int u = 0; u < NQ; ++u) {
+                        const double xk = xv[k + u];
+                        const double* grow = G + (size_t)(k + u) * R;
 #pragma unroll
-                        for (int c = 0; c < CT; ++c) ra[c][q] = fma(xk, grow[jj[c]], ra[c][q]);
+                        for (int c = 0; c < CT; ++c) ra[c][u] = fma(xk, grow[jj[c]], ra[c][u]);
                     }
                 }
                 for (; k < k1; ++k) {
 #pragma unroll
-                    for (int c = 0; c < CT; ++c) ra[c][0] = fma(xv[k], Gm[(size_t)k * R + jj[c]], ra[c][0]);
+                    for (int c = 0; c < CT; ++c) ra[c][0] = fma(xv[k], G[(size_t)k * R + jj[c]], ra[c][0]);
                 }
                 double tt[CT];
 #pragma unroll
@@ -876,10 +1014,21 @@ __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
 #pragma unroll
                 for (int c = 0; c < CT; ++c) {
                     const int j = tcol + SOLVE_THREADS * c;
-                    xj[c] += (double)dd[c];
                     dmx = fmaxf(dmx, fabsf(dd[c]));
-                    xmx = fmaxf(xmx, fabsf((float)xj[c]));
-                    if (j < R) xv[j] = xj[c];
+                    if (DF) {
+                        float s1, e1;
+                        two_sum(xh[c], dd[c], s1, e1);
+                        fast_two_sum(s1, __fadd_rn(e1, xl[c]), xh[c], xl[c]);
+                        xmx = fmaxf(xmx, fabsf(xh[c]));
+                        if (j < R) {
+                            xh_s[j] = xh[c];
+                            xl_s[j] = xl[c];
+                        }
+                    } else {
+                        xj[c] += (double)dd[c];
+                        xmx = fmaxf(xmx, fabsf((float)xj[c]));
+                        if (j < R) xv[j] = xj[c];
+                    }
                 }
 #pragma unroll
                 for (int o2 = 16; o2; o2 >>= 1) {
@@ -887,20 +1036,108 @@ __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
                     xmx = fmaxf(xmx, __shfl_xor_sync(FULL, xmx, o2));
                 }
                 if (lane == 0) {
-                    red[warp] = dmx;
-                    red[2 + warp] = xmx;
+                    redf[warp] = dmx;
+                    redf[2 + warp] = xmx;
                 }
             }
-            __syncthreads();  // also publishes xv for the next residual
-            const double dmax = fmax(red[0], red[1]), xmax = fmax(red[2], red[3]);
+            __syncthreads();  // also publishes x for the next residual
+            // in FP32: every thread evaluates the test, and each FP64 instruction
+            // of a warp holds this GPU's FP64 pipe for tens of cycles
+            const float dmax = fmaxf(redf[0], redf[1]), xmax = fmaxf(redf[2], redf[3]);
             // remaining error after this step is about rho * dmax, rho = dmax / prev
-            const double rho = (itr > 0 && prev > 0.0) ? dmax / prev : 1.0;
-            conv = rho * dmax <= 0x1.0p-36 * xmax || dmax == 0.0;
+            const float rho = (itr > 0 && prev > 0.f) ? __fdiv_rn(dmax, prev) : 1.f;
+            conv = rho * dmax <= 0x1.0p-36f * xmax || dmax == 0.f;
             prev = dmax;
             if (conv) break;
-            __syncthreads();  // red[] is rewritten by the next step
+            __syncthreads();  // redf[] is rewritten by the next step
         }
         if (tid == 0 && !conv) scal[SCAL_FLAGS] = 3.0;
+        if constexpr (DF) {
+            // outputs and scalar partials with FP64 only for what is stored in FP64:
+            // the norms that steer the PP regime in FP32, <m, x> (Eq. residual, a
+            // difference of nearly equal terms) in double-float
+            float fs[5] = {0.f, 0.f, 0.f, 0.f, fv2};   // ||A||^2, ||dA_step||^2, ||A - A_p||^2, ||m||^2, ||V||^2
+            float mah = 0.f, mal = 0.f;
+            if (q == 0) {
+#pragma unroll
+                for (int c = 0; c < CT; ++c) {
+                    const int j = tcol + SOLVE_THREADS * c;
+                    if (j >= R) continue;
+                    const size_t e = (size_t)x * R + j;
+                    const double av = (double)xh[c] + (double)xl[c];
+                    // every copy derives from the stored FP64 value, as after a restore
+                    const float af = (float)av;
+                    o.A64[e] = av;
+                    if (o.A32) o.A32[e] = af;
+                    if (o.bhi) {
+                        uint16_t hi, lo;
+                        bf16_split(af, hi, lo);
+                        o.bhi[(size_t)j * o.Kpad + x] = hi;
+                        o.blo[(size_t)j * o.Kpad + x] = lo;
+                    }
+                    if (o.bt32) {
+                        const float h = tf32_rna(af);
+                        const size_t f = (size_t)j * o.Kpad + x;
+                        o.bt32[f] = h;
+                        o.bt32[(size_t)o.Rpad * o.Kpad + f] = tf32_rna(af - h);
+                    }
+                    // the pair of the stored FP64 value, so that a Gram formed later
+                    // from A64 (after a restore) sees the same pairs
+                    if (o.A2) o.A2[e] = cpdf::split(av);
+                    const double d = av - (o.Ap ? o.Ap[e] : aold[c]);
+                    const float df = (float)d;
+                    if (o.dA32) o.dA32[e] = df;
+                    if (o.dA64) o.dA64[e] = d;
+                    if (o.dA2) o.dA2[e] = cpdf::split(d);
+                    const float step = o.Ap ? (float)(av - aold[c]) : df;
+                    const float mf = __fadd_rn(mh[c], ml[c]);
+                    fs[0] = fmaf(af, af, fs[0]);
+                    fs[1] = fmaf(step, step, fs[1]);
+                    if (o.Ap) fs[2] = fmaf(df, df, fs[2]);
+                    fs[3] = fmaf(mf, mf, fs[3]);
+                    // <m, x>: exact leading product, double-float sum
+                    const float pm = __fmul_rn(mh[c], xh[c]);
+                    float pe = __fmaf_rn(mh[c], xh[c], -pm);
+                    pe = __fmaf_rn(mh[c], xl[c], __fmaf_rn(ml[c], xh[c], pe));
+                    float s1, t1;
+                    two_sum(mah, pm, s1, t1);
+                    mah = s1;
+                    mal = __fadd_rn(mal, __fadd_rn(t1, pe));
+                }
+#pragma unroll
+                for (int o2 = 16; o2; o2 >>= 1) {
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) fs[i] += __shfl_xor_sync(FULL, fs[i], o2);
+                    const float bh = __shfl_xor_sync(FULL, mah, o2), bl = __shfl_xor_sync(FULL, mal, o2);
+                    df_add(mah, mal, bh, bl);
+                }
+                if (lane == 0) {
+                    float* pf = reinterpret_cast<float*>(part) + warp * 8;
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) pf[i] = fs[i];
+                    pf[5] = mah;
+                    pf[6] = mal;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                // the two warps of group 0
+                const float* p0 = reinterpret_cast<const float*>(part);
+                const float* p1 = p0 + 8;
+                float h = p0[5], l = p0[6];
+                df_add(h, l, p1[5], p1[6]);
+                double* out = scal_part + (size_t)blockIdx.x * CP_NSCAL;
+                out[SCAL_A2] = (double)p0[0] + (double)p1[0];
+                out[SCAL_STEP2] = (double)p0[1] + (double)p1[1];
+                out[SCAL_DAP2] = (double)p0[2] + (double)p1[2];
+                out[SCAL_MA] = (double)h + (double)l;
+                out[SCAL_GS] = 0.0;
+                out[SCAL_M2] = (double)p0[3] + (double)p1[3];
+                out[SCAL_V2] = (double)p0[4] + (double)p1[4];
+                out[SCAL_FLAGS] = 0.0;
+            }
+            return;
+        }
     } else {
         // FP64 substitution with the fallback factor: warp 0, lane l owns l + 32 t
         if (warp == 0) {
@@ -992,10 +1229,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
             o.bt32[f] = h;
             o.bt32[(size_t)o.Rpad * o.Kpad + f] = tf32_rna(af - h);
         }
+        if (o.A2) o.A2[e] = cpdf::split(av);
         const double base = o.Ap ? o.Ap[e] : ao;
         const double d = av - base;
         if (o.dA32) o.dA32[e] = (float)d;
         if (o.dA64) o.dA64[e] = d;
+        if (o.dA2) o.dA2[e] = cpdf::split(d);
         sc[SCAL_A2] += av * av;
         sc[SCAL_STEP2] += (av - ao) * (av - ao);
         if (o.Ap) sc[SCAL_DAP2] += d * d;
@@ -1014,13 +1253,26 @@ __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
             for (int j = tcol; j < R; j += SOLVE_THREADS) emit(j, xv[j], mv[j], o.A64[(size_t)x * R + j]);
         }
     }
-    // block reduction of the 8 scalars: warp sums, then warp 0
+    // block reduction of the 8 scalars.  Warp sums by a transposing butterfly:
+    // after the exchanges at distance 16, 8 and 4, lane l holds scalar
+    // 4 b4 + 2 b3 + b2 (bits of l) summed over 8 lanes, and two more exchanges
+    // finish it: 9 FP64 additions per lane instead of 40
+    double v4[4], v2[2], v1;
+    {
+        const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
 #pragma unroll
-    for (int i = 0; i < CP_NSCAL; ++i) sc[i] = warp_sum_d(sc[i]);
+        for (int i = 0; i < 4; ++i)
+            v4[i] = (u16 ? sc[4 + i] : sc[i]) + __shfl_xor_sync(FULL, u16 ? sc[i] : sc[4 + i], 16);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+            v2[i] = (u8 ? v4[2 + i] : v4[i]) + __shfl_xor_sync(FULL, u8 ? v4[i] : v4[2 + i], 8);
+        v1 = (u4 ? v2[1] : v2[0]) + __shfl_xor_sync(FULL, u4 ? v2[0] : v2[1], 4);
+        v1 += __shfl_xor_sync(FULL, v1, 2);
+        v1 += __shfl_xor_sync(FULL, v1, 1);
+    }
+    const int sidx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     __syncthreads();
-    if (lane == 0 && q == 0)
-#pragma unroll
-        for (int i = 0; i < CP_NSCAL; ++i) part[warp * CP_NSCAL + i] = sc[i];
+    if (q == 0 && (lane & 3) == 0) part[warp * CP_NSCAL + sidx] = v1;
     __syncthreads();
     if (tid < CP_NSCAL) {
         double v = 0.0;
@@ -1030,17 +1282,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
 }
 
 template <int RT>
-cudaError_t launch_solve_mixed(const float* M, const double* W, const double* G, const float* Ginv,
-                               const double* L64, const double* invd64, const int* mode,
-                               const cpk::SolveOut& o, int s, int R, double* scal, double* scal_part,
-                               unsigned* dev_err, cudaStream_t st) {
-    // groups of 64 threads per row that split the refinement's dot products: a
-    // row's work is a chain of dependent FP64 FMAs (64-cycle latency) with one
-    // block per SM, so more threads per row shorten the chains.  Measured (CUDA
-    // events per update): R = 128 44 -> 32 us with two groups; R = 64 unchanged
-    // with four (20 us; its FP64 pipe is already a quarter busy) and R = 16 slower
-    // (14 -> 16 us), so one group up to R = 64
-    constexpr int KS = (RT == 3 || RT == 4) ? 2 : 1;
+cudaError_t launch_solve_mixed(const float* M, const double* W, const float2* W2, const double* G,
+                               const float2* G2, const float* Ginv, const double* L64, const double* invd64,
+                               const int* mode, const cpk::SolveOut& o, int s, int R, double* scal,
+                               double* scal_part, unsigned* dev_err, cudaStream_t st) {
+    // groups of 64 threads per row that split the refinement's dot products.
+    // R <= 128 (double-float residual on the FP32 pipe): four groups, so that
+    // every SM sub-partition issues; R > 128 (FP64 residual from L2): one group
+    constexpr int KS = RT <= 4 ? 4 : 1;
     const size_t smem = solve_smem(R).total * sizeof(double) + 64;
     static bool attr = false;
     if (!attr) {
@@ -1048,8 +1297,8 @@ cudaError_t launch_solve_mixed(const float* M, const double* W, const double* G,
                              (int)(solve_smem(MIXED_MAXR).total * sizeof(double) + 64));
         attr = true;
     }
-    k_solve_mixed<RT, KS><<<(unsigned)s, SOLVE_THREADS * KS, smem, st>>>(M, W, G, Ginv, L64, invd64, mode, o, s, R,
-                                                                         scal, scal_part, dev_err);
+    k_solve_mixed<RT, KS><<<(unsigned)s, SOLVE_THREADS * KS, smem, st>>>(M, W, W2, G, G2, Ginv, L64, invd64,
+                                                                         mode, o, s, R, scal, scal_part, dev_err);
     return cudaGetLastError();
 }
 
@@ -1065,9 +1314,9 @@ size_t schur_ws_floats(int R) {
 }
 
 cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
-                       double* Gamma, float* G32, float* Ginv, double* L64, double* invd64, double* W,
-                       double* scal, int* mode, float* ws, cudaStream_t st, bool force64) {
-    k_gamma_form<<<(R * R + 255) / 256, 256, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, G32, W);
+                       double* Gamma, float* G32, float* G2, float* Ginv, double* L64, double* invd64, double* W,
+                       float* W2, double* scal, int* mode, float* ws, cudaStream_t st, bool force64) {
+    k_gamma_form<<<(R * R + 255) / 256, 256, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, G32, G2, W, W2);
     if (force64) {
         k_choose_fp64<<<1, 32, 0, st>>>(mode);
         k_chol_fp64_if<<<1, 1024, 0, st>>>(Gamma, R, L64, invd64, scal, mode);
@@ -1119,26 +1368,30 @@ cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int
     return cudaGetLastError();
 }
 
-cudaError_t solve_mixed(const float* M, const double* W, const double* Gamma, const float* Ginv,
-                        const double* L64, const double* invd64, const int* mode, const SolveOut& o,
-                        int s, int R, double* scal, double* scal_part, int* nblk, unsigned* dev_err,
-                        cudaStream_t st) {
+cudaError_t solve_mixed(const float* M, const double* W, const float* W2, const double* Gamma, const float* G2,
+                        const float* Ginv, const double* L64, const double* invd64, const int* mode,
+                        const SolveOut& o, int s, int R, double* scal, double* scal_part, int* nblk,
+                        unsigned* dev_err, cudaStream_t st) {
     *nblk = s;
+    const float2* w2 = reinterpret_cast<const float2*>(W2);
+    const float2* g2 = reinterpret_cast<const float2*>(G2);
+#define CP_SOLVE(RT) launch_solve_mixed<RT>(M, W, w2, Gamma, g2, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st)
     switch ((R + 31) / 32) {
-        case 1: return launch_solve_mixed<1>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
-        case 2: return launch_solve_mixed<2>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
-        case 3: return launch_solve_mixed<3>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
-        case 4: return launch_solve_mixed<4>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
-        case 5: return launch_solve_mixed<5>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
-        case 6: return launch_solve_mixed<6>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
-        case 7: return launch_solve_mixed<7>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
-        case 8: return launch_solve_mixed<8>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
-        case 9: case 10: return launch_solve_mixed<10>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
-        case 11: case 12: return launch_solve_mixed<12>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
-        case 13: case 14: return launch_solve_mixed<14>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
-        case 15: case 16: return launch_solve_mixed<16>(M, W, Gamma, Ginv, L64, invd64, mode, o, s, R, scal, scal_part, dev_err, st);
+        case 1: return CP_SOLVE(1);
+        case 2: return CP_SOLVE(2);
+        case 3: return CP_SOLVE(3);
+        case 4: return CP_SOLVE(4);
+        case 5: return CP_SOLVE(5);
+        case 6: return CP_SOLVE(6);
+        case 7: return CP_SOLVE(7);
+        case 8: return CP_SOLVE(8);
+        case 9: case 10: return CP_SOLVE(10);
+        case 11: case 12: return CP_SOLVE(12);
+        case 13: case 14: return CP_SOLVE(14);
+        case 15: case 16: return CP_SOLVE(16);
         default: return cudaErrorInvalidValue;
     }
+#undef CP_SOLVE
 }
 
 }  // namespace cpk
