@@ -75,6 +75,10 @@ struct cp_ctx {
     // value), written by the row solve for the double-float Gram
     float2* A2[CP_MAXN] = {0};
     float2* dA2[CP_MAXN] = {0};
+    float2* S2[CP_MAXN] = {0};      // the Grams as float pairs (R <= 128)
+    float2* dS2[CP_MAXN] = {0};
+    float2** d_S2list = nullptr;
+    float2** d_dS2list = nullptr;
     int ver[CP_MAXN] = {0};
     double** d_Slist = nullptr;
     double** d_dSlist = nullptr;
@@ -530,9 +534,9 @@ cp_status grow_hist(cp_ctx* c, int nsweeps) {
 cp_status launch_chol(cp_ctx* c, int u, bool pp, double* scal) {
     CKCUDA(c, cudaEventRecord(c->ev_ready, c->st));
     CKCUDA(c, cudaStreamWaitEvent(c->side, c->ev_ready, 0));
-    LAUNCH(c, cpk::chol_mixed(c->d_Slist, c->d_dSlist, c->N, u, c->R, pp ? 1 : 0, c->Gamma, c->G32, c->G2,
-                              c->Ginv, c->L, c->invd, c->W, c->W2, scal, c->d_mode, c->schur_ws, c->side,
-                              c->solve_fp64));
+    LAUNCH(c, cpk::chol_mixed(c->d_Slist, c->d_dSlist, c->d_S2list, c->d_dS2list, c->N, u, c->R, pp ? 1 : 0,
+                              c->Gamma, c->G32, c->G2, c->Ginv, c->L, c->invd, c->W, c->W2, scal, c->d_mode,
+                              c->schur_ws, c->side, c->solve_fp64));
     CKCUDA(c, cudaEventRecord(c->ev_chol, c->side));
     c->chol_pending = true;
     c->chol_mode = u;
@@ -568,7 +572,7 @@ cp_status update_mode(cp_ctx* c, int u, const float* M, bool pp, double* scal) {
                                sp, &nblk, c->dev_err, c->st));
     if (c->A2[u])
         LAUNCH(c, cpk::gram_df(c->A2[u], pp ? c->dA2[u] : nullptr, s, R, reinterpret_cast<const float2*>(c->G2),
-                               c->S[u], c->dS[u], tg, c->st));
+                               c->S[u], c->dS[u], c->S2[u], c->dS2[u], tg, c->st));
     else
         LAUNCH(c, cpk::gram(c->A64[u], pp ? c->dA64[u] : nullptr, s, R, c->Gamma, c->S[u], c->dS[u], tg, c->st));
     CKCUDA(c, cudaEventRecord(c->ev_g, c->st));
@@ -840,6 +844,7 @@ cp_status pp_init_impl(cp_ctx* c) {
         CKCUDA(c, cudaMemsetAsync(c->dA32[i], 0, sizeof(float) * c->dims[i] * R, c->st));
         CKCUDA(c, cudaMemsetAsync(c->dA64[i], 0, sizeof(double) * c->dims[i] * R, c->st));
         CKCUDA(c, cudaMemsetAsync(c->dS[i], 0, sizeof(double) * R * R, c->st));
+        if (c->dS2[i]) CKCUDA(c, cudaMemsetAsync(c->dS2[i], 0, sizeof(float2) * R * R, c->st));
     }
     // pairs ordered by their contraction sequence so shared ancestors stay cached
     struct PP { std::vector<int> seq; int a, b; };
@@ -967,8 +972,8 @@ cp_status regram(cp_ctx* c, int i, bool pp) {
     if (c->A2[i]) {
         LAUNCH(c, cpk::split_pairs(c->A64[i], c->A2[i], (int64_t)s * c->R, c->st));
         if (pp) LAUNCH(c, cpk::split_pairs(c->dA64[i], c->dA2[i], (int64_t)s * c->R, c->st));
-        LAUNCH(c, cpk::gram_df(c->A2[i], pp ? c->dA2[i] : nullptr, s, c->R, nullptr, c->S[i], c->dS[i], nullptr,
-                               c->st));
+        LAUNCH(c, cpk::gram_df(c->A2[i], pp ? c->dA2[i] : nullptr, s, c->R, nullptr, c->S[i], c->dS[i], c->S2[i],
+                               c->dS2[i], nullptr, c->st));
     } else {
         LAUNCH(c, cpk::gram(c->A64[i], pp ? c->dA64[i] : nullptr, s, c->R, nullptr, c->S[i], c->dS[i], nullptr,
                             c->st));
@@ -1193,7 +1198,10 @@ void free_all(cp_ctx* c) {
         F(c->colinv[i]);
         F(c->A2[i]);
         F(c->dA2[i]);
+        F(c->S2[i]);
+        F(c->dS2[i]);
     }
+    F(c->d_S2list); F(c->d_dS2list);
     F(c->Ginv); F(c->G32); F(c->G2); F(c->W2); F(c->schur_ws); F(c->d_mode);
     if (c->side) { cudaStreamSynchronize(c->side); cudaStreamDestroy(c->side); c->side = nullptr; }
     if (c->ev_ready) { cudaEventDestroy(c->ev_ready); c->ev_ready = nullptr; }
@@ -1312,6 +1320,9 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
         if (R <= 128) {
             TRY(dalloc(c, &c->A2[i], sR));
             TRY(dalloc(c, &c->dA2[i], sR));
+            TRY(dalloc(c, &c->S2[i], RR));
+            TRY(dalloc(c, &c->dS2[i], RR));
+            TRYC(cudaMemsetAsync(c->dS2[i], 0, sizeof(float2) * RR, c->st));
         }
         TRY(dalloc(c, &c->S[i], RR));
         TRY(dalloc(c, &c->dS[i], RR));
@@ -1342,6 +1353,12 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
     TRY(dalloc(c, &c->d_dSlist, N));
     TRYC(cudaMemcpyAsync(c->d_Slist, c->S, sizeof(double*) * N, cudaMemcpyHostToDevice, c->st));
     TRYC(cudaMemcpyAsync(c->d_dSlist, c->dS, sizeof(double*) * N, cudaMemcpyHostToDevice, c->st));
+    if (R <= 128) {
+        TRY(dalloc(c, &c->d_S2list, N));
+        TRY(dalloc(c, &c->d_dS2list, N));
+        TRYC(cudaMemcpyAsync(c->d_S2list, c->S2, sizeof(float2*) * N, cudaMemcpyHostToDevice, c->st));
+        TRYC(cudaMemcpyAsync(c->d_dS2list, c->dS2, sizeof(float2*) * N, cudaMemcpyHostToDevice, c->st));
+    }
     TRY(dalloc(c, &c->Gamma, RR + 2));
     TRY(dalloc(c, &c->Ginv, RR + 4));
     TRY(dalloc(c, &c->G32, RR + 4));

@@ -140,9 +140,13 @@ struct SolveOut {
 // solve_mixed then solves every row to FP64 accuracy (refinement or FP64
 // substitution).  Gamma, G2 and Ginv must have 16 spare bytes after their R*R entries.
 // force64: skip the FP32 inverse and factor Gamma in FP64 (LDL^T) for this update.
-cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
-                       double* Gamma, float* G32, float* G2, float* Ginv, double* L64, double* invd64, double* W,
-                       float* W2, double* scal, int* mode, float* ws, cudaStream_t st, bool force64 = false);
+// S2_list / dS2_list (device arrays of N pointers, R <= 128): the Grams as float
+// pairs, from which Gamma and W are formed in double-float arithmetic (else from
+// the FP64 Grams); an exact sweep's update then forms Gamma inside the inverse.
+cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, const float2* const* S2_list,
+                       const float2* const* dS2_list, int N, int n, int R, int pp, double* Gamma, float* G32,
+                       float* G2, float* Ginv, double* L64, double* invd64, double* W, float* W2, double* scal,
+                       int* mode, float* ws, cudaStream_t st, bool force64 = false);
 // floats of the workspace chol_mixed needs for R > 128 (blocked inverse), else 0
 size_t schur_ws_floats(int R);
 cudaError_t solve_mixed(const float* M, const double* W, const float* W2, const double* Gamma, const float* G2,
@@ -158,9 +162,10 @@ int gram_tiles(int R);
 cudaError_t gram(const double* A, const double* dA, int s, int R, const double* Gamma, double* S,
                  double* dS, double* tile_gs, cudaStream_t st);
 // Same from the float-pair copies the solve writes (A2, dA2 = hi + lo of the FP64
-// values), in double-float arithmetic; Gamma for <Gamma, S> as float pairs (G2).
+// values), in double-float arithmetic; Gamma for <Gamma, S> as float pairs (G2);
+// S and dS also written as float pairs (S2, dS2).
 cudaError_t gram_df(const float2* A2, const float2* dA2, int s, int R, const float2* G2, double* S,
-                    double* dS, double* tile_gs, cudaStream_t st);
+                    double* dS, float2* S2, float2* dS2, double* tile_gs, cudaStream_t st);
 // y[i] = float pair (hi, lo) of x[i] (hi = x rounded to float, lo = the rest rounded)
 cudaError_t split_pairs(const double* x, float2* y, int64_t n, cudaStream_t st);
 cudaError_t scal_fin(const double* scal_part, int nblk, const double* tile_gs, int ntiles, double* scal_out,

@@ -40,6 +40,15 @@ __device__ __forceinline__ void add(float& ah, float& al, float bh, float bl) {
     t = __fadd_rn(t, __fadd_rn(al, bl));
     fast_two_sum(s, t, ah, al);
 }
+// (ah, al) * (bh, bl): exact leading product, cross terms in FP32, renormalised
+__device__ __forceinline__ float2 mul(float2 a, float2 b) {
+    const float m = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -m);
+    e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));
+    float h, l;
+    fast_two_sum(m, e, h, l);
+    return make_float2(h, l);
+}
 // a double as a float pair
 __device__ __forceinline__ float2 split(double v) {
     const float h = (float)v;

@@ -160,6 +160,7 @@ __device__ __forceinline__ float2 ld_cluster_f2(const float2* local, unsigned ra
 __global__ void __launch_bounds__(256) k_gram_df(const float2* __restrict__ A, const float2* __restrict__ dA,
                                                  int s, int R, int rows_per, const float2* __restrict__ G2,
                                                  double* __restrict__ S, double* __restrict__ dS,
+                                                 float2* __restrict__ S2, float2* __restrict__ dS2,
                                                  double* __restrict__ tile_gs) {
     __shared__ float2 a1[16][17], a2[16][17], d2[16][17];
     __shared__ float2 ps[256], pd[256];
@@ -209,7 +210,11 @@ __global__ void __launch_bounds__(256) k_gram_df(const float2* __restrict__ A, c
         if (r1 < R && r2 < R) {
             const size_t e = (size_t)r1 * R + r2;
             S[e] = (double)vh + (double)vl;
-            if (dA) dS[e] = (double)wh + (double)wl;
+            S2[e] = make_float2(vh, vl);
+            if (dA) {
+                dS[e] = (double)wh + (double)wl;
+                dS2[e] = make_float2(wh, wl);
+            }
             if (G2) {
                 const float2 g = G2[e];
                 cpdf::fma_acc(g.x, g.y, vh, vl, gh, gl);
@@ -819,7 +824,7 @@ cudaError_t split_pairs(const double* x, float2* y, int64_t n, cudaStream_t st) 
 }
 
 cudaError_t gram_df(const float2* A2, const float2* dA2, int s, int R, const float2* G2, double* S,
-                    double* dS, double* tile_gs, cudaStream_t st) {
+                    double* dS, float2* S2, float2* dS2, double* tile_gs, cudaStream_t st) {
     // about 32 rows per chunk, at most GRAM_MAX_CHUNKS chunks (one cluster)
     int nc = (s + 31) / 32;
     if (nc > GRAM_MAX_CHUNKS) nc = GRAM_MAX_CHUNKS;
@@ -838,7 +843,7 @@ cudaError_t gram_df(const float2* A2, const float2* dA2, int s, int R, const flo
     attr[0].val.clusterDim.z = nc;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_gram_df, A2, dA2, s, R, rows_per, G2, S, dS, tile_gs);
+    return cudaLaunchKernelEx(&cfg, k_gram_df, A2, dA2, s, R, rows_per, G2, S, dS, S2, dS2, tile_gs);
 }
 
 cudaError_t scal_fin(const double* scal_part, int nblk, const double* tile_gs, int ntiles, double* scal_out,

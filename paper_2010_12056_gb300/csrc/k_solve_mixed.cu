@@ -146,15 +146,60 @@ __device__ __forceinline__ double gamma_entry(const double* const* Sp, const dou
     return g;
 }
 
+// The same from the Grams' float pairs (R <= 128), in double-float arithmetic:
+// the one formula for Gamma that every path of an update uses, so that a kernel
+// that forms it (k_gamma_form, or the Gauss-Jordan kernel of an exact sweep)
+// gives the same pairs.
+__device__ __forceinline__ float2 gamma_entry_df(const float2* const* S2, const float2* const* dS2, int N, int n,
+                                                 int pp, size_t e, float2* w_out) {
+    float2 g = make_float2(1.f, 0.f);
+    bool first = true;
+    for (int m = 0; m < N; ++m) {
+        if (m == n) continue;
+        g = first ? S2[m][e] : cpdf::mul(g, S2[m][e]);
+        first = false;
+    }
+    if (pp) {
+        float ah = 0.f, al = 0.f;
+        for (int a = 0; a < N; ++a) {
+            if (a == n) continue;
+            for (int b = a + 1; b < N; ++b) {
+                if (b == n) continue;
+                float2 t = cpdf::mul(dS2[a][e], dS2[b][e]);
+                for (int m = 0; m < N; ++m)
+                    if (m != a && m != b && m != n) t = cpdf::mul(t, S2[m][e]);
+                cpdf::add(ah, al, t.x, t.y);
+            }
+        }
+        *w_out = make_float2(ah, al);
+    }
+    return g;
+}
+
 // Gamma (FP64), its FP32 copy and PP's W, one entry per thread over many
 // blocks: FP64 throughput per SM is low, so this work is spread over the GPU.
 __global__ void __launch_bounds__(256) k_gamma_form(double* const* __restrict__ S_list,
                                                     double* const* __restrict__ dS_list, int N,
                                                     int n, int R, int pp, double* __restrict__ G,
                                                     float* __restrict__ G32, float* __restrict__ G2,
-                                                    double* __restrict__ W, float* __restrict__ W2) {
+                                                    double* __restrict__ W, float* __restrict__ W2,
+                                                    const float2* const* __restrict__ S2_list,
+                                                    const float2* const* __restrict__ dS2_list) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= R * R) return;
+    if (S2_list) {
+        // R <= 128: from the Grams' float pairs
+        float2 w = make_float2(0.f, 0.f);
+        const float2 g = gamma_entry_df(S2_list, dS2_list, N, n, pp, (size_t)e, &w);
+        G[e] = (double)g.x + (double)g.y;
+        G32[e] = g.x;
+        reinterpret_cast<float2*>(G2)[e] = g;
+        if (pp) {
+            W[e] = (double)w.x + (double)w.y;
+            reinterpret_cast<float2*>(W2)[e] = w;
+        }
+        return;
+    }
     const double* Sp[CP_MAXN];
     const double* dSp[CP_MAXN];
     for (int k = 0; k < N; ++k) {
@@ -272,13 +317,15 @@ __device__ __forceinline__ bool gj_steps(float (&a)[IR][JC], int n, float (*prow
 }
 
 template <int TY, int IR, int JC>
-__global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(const float* __restrict__ G32, int R,
-                                                       const double* __restrict__ G,
+__global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(float* __restrict__ G32, int R,
+                                                       double* __restrict__ G,
                                                        float* __restrict__ Ginv,
                                                        double* __restrict__ L64,
                                                        double* __restrict__ invd64,
                                                        double* __restrict__ scal,
-                                                       int* __restrict__ mode) {
+                                                       int* __restrict__ mode,
+                                                       const float2* const* __restrict__ S2_list,
+                                                       int N, int n, float2* __restrict__ G2) {
     constexpr int NT = 32 * TY, RMAX = TY * IR;
     static_assert(RMAX <= MIXED_MAXR && 32 * JC <= MIXED_MAXR && IR % JC == 0 && IR % 4 == 0,
                   "tile shape");
@@ -297,26 +344,76 @@ __global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(const float* __restrict__
         imax_bits = 0u;
     }
     __syncthreads();
-    for (int r = tid; r < MIXED_MAXR; r += NT) {
-        float d = 0.f;
-        if (r < R) {
-            const float g = __ldg(G32 + (size_t)r * R + r);
-            d = (g > 0.f && isfinite(g)) ? rsqrtf(g) : 0.f;
-            if (!(d > 0.f)) sfail = 1;
+    // S2_list: an exact sweep's update with R <= 128 forms Gamma here from the
+    // Grams' float pairs (the product order of k_gamma_form, so the same pairs),
+    // writing its pairs and FP32 copy; its FP64 copy only if the FP64
+    // factorisation is needed.  The thread's entries of each Gram are loaded at
+    // once (IR rows x JC columns), one round of loads per Gram.
+    float a[IR][JC];
+    if (S2_list) {
+        float2 acc[IR][JC];
+        bool first = true;
+        for (int m = 0; m < N; ++m) {
+            if (m == n) continue;
+            const float2* Sm = S2_list[m];
+            float2 v[IR][JC];
+#pragma unroll
+            for (int i = 0; i < IR; ++i)
+#pragma unroll
+                for (int j = 0; j < JC; ++j) {
+                    const int r = r0 + i, c = c0 + j;
+                    v[i][j] = (r < R && c < R) ? Sm[(size_t)r * R + c] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+            for (int i = 0; i < IR; ++i)
+#pragma unroll
+                for (int j = 0; j < JC; ++j) acc[i][j] = first ? v[i][j] : cpdf::mul(acc[i][j], v[i][j]);
+            first = false;
         }
-        dsc[r] = d;
+#pragma unroll
+        for (int i = 0; i < IR; ++i)
+#pragma unroll
+            for (int j = 0; j < JC; ++j) {
+                const int r = r0 + i, c = c0 + j;
+                a[i][j] = acc[i][j].x;
+                if (r < R && c < R) {
+                    const size_t e = (size_t)r * R + c;
+                    G2[e] = acc[i][j];
+                    G32[e] = acc[i][j].x;
+                    if (r == c) {
+                        const float g = acc[i][j].x;
+                        const float d = (g > 0.f && isfinite(g)) ? rsqrtf(g) : 0.f;
+                        if (!(d > 0.f)) sfail = 1;
+                        dsc[r] = d;
+                    }
+                }
+            }
+    } else {
+        for (int r = tid; r < MIXED_MAXR; r += NT) {
+            float d = 0.f;
+            if (r < R) {
+                const float g = G32[(size_t)r * R + r];
+                d = (g > 0.f && isfinite(g)) ? rsqrtf(g) : 0.f;
+                if (!(d > 0.f)) sfail = 1;
+            }
+            dsc[r] = d;
+        }
+#pragma unroll
+        for (int i = 0; i < IR; ++i)
+#pragma unroll
+            for (int j = 0; j < JC; ++j) {
+                const int r = r0 + i, c = c0 + j;
+                a[i][j] = (r < R && c < R) ? G32[(size_t)r * R + c] : 0.f;
+            }
     }
     __syncthreads();
-    float a[IR][JC];
 #pragma unroll
-    for (int i = 0; i < IR; ++i) {
-        const int r = r0 + i;
+    for (int i = 0; i < IR; ++i)
 #pragma unroll
         for (int j = 0; j < JC; ++j) {
-            const int c = c0 + j;
-            a[i][j] = (r < R && c < R) ? __ldg(G32 + (size_t)r * R + c) * (dsc[r] * dsc[c]) : 0.f;
+            const int r = r0 + i, c = c0 + j;
+            a[i][j] = (r < R && c < R) ? a[i][j] * (dsc[r] * dsc[c]) : 0.f;
         }
-    }
     // ||Gt||_inf: a warp holds whole rows
 #pragma unroll
     for (int i = 0; i < IR; ++i) {
@@ -344,6 +441,13 @@ __global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(const float* __restrict__
         use64 = !(kappa <= 1e6f);
     }
     if (use64) {
+        if (S2_list) {
+            // the FP64 copy of Gamma for the FP64 factorisation (its pairs, written
+            // above by this CTA, are visible after the barrier)
+            __syncthreads();
+            for (int e = tid; e < R * R; e += NT) G[e] = (double)G2[e].x + (double)G2[e].y;
+            __syncthreads();
+        }
         double tr = 0.0;
         for (int j = tid; j < R; j += NT) tr += G[(size_t)j * R + j];
         tr = block_sum_d(tr, red);
@@ -1313,10 +1417,25 @@ size_t schur_ws_floats(int R) {
                            : 4 * (size_t)R * R + 2 * (size_t)R * MIXED_MAXR + (size_t)MIXED_MAXR * MIXED_MAXR + R + 4;
 }
 
-cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int n, int R, int pp,
-                       double* Gamma, float* G32, float* G2, float* Ginv, double* L64, double* invd64, double* W,
-                       float* W2, double* scal, int* mode, float* ws, cudaStream_t st, bool force64) {
-    k_gamma_form<<<(R * R + 255) / 256, 256, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, G32, G2, W, W2);
+cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, const float2* const* S2_list,
+                       const float2* const* dS2_list, int N, int n, int R, int pp, double* Gamma, float* G32,
+                       float* G2, float* Ginv, double* L64, double* invd64, double* W, float* W2, double* scal,
+                       int* mode, float* ws, cudaStream_t st, bool force64) {
+    float2* g2 = reinterpret_cast<float2*>(G2);
+    if (R <= MIXED_MAXR && S2_list && !pp && !force64) {
+        // exact sweep: Gamma formed inside the one-CTA inverse (one launch, so
+        // that the inverse takes its SM before the update's contraction fills the GPU)
+        if (R <= 32)
+            k_gj_inv<8, 4, 1><<<1, 256, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode, S2_list, N, n, g2);
+        else if (R <= 64)
+            k_gj_inv<16, 4, 2><<<1, 512, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode, S2_list, N, n, g2);
+        else
+            k_gj_inv<16, 8, 4><<<1, 512, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode, S2_list, N, n, g2);
+        return cudaGetLastError();
+    }
+    k_gamma_form<<<(R * R + 255) / 256, 256, 0, st>>>(S_list, dS_list, N, n, R, pp, Gamma, G32, G2, W, W2,
+                                                      R <= MIXED_MAXR ? S2_list : nullptr,
+                                                      R <= MIXED_MAXR ? dS2_list : nullptr);
     if (force64) {
         k_choose_fp64<<<1, 32, 0, st>>>(mode);
         k_chol_fp64_if<<<1, 1024, 0, st>>>(Gamma, R, L64, invd64, scal, mode);
@@ -1360,11 +1479,11 @@ cudaError_t chol_mixed(double* const* S_list, double* const* dS_list, int N, int
     // (warps, rows per thread, columns per thread): TY x IR >= R, 32 JC >= R.
     // Sixteen warps hide the latency of each step's dependent chain.
     if (R <= 32)
-        k_gj_inv<8, 4, 1><<<1, 256, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
+        k_gj_inv<8, 4, 1><<<1, 256, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode, nullptr, N, n, g2);
     else if (R <= 64)
-        k_gj_inv<16, 4, 2><<<1, 512, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
+        k_gj_inv<16, 4, 2><<<1, 512, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode, nullptr, N, n, g2);
     else
-        k_gj_inv<16, 8, 4><<<1, 512, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode);
+        k_gj_inv<16, 8, 4><<<1, 512, 0, st>>>(G32, R, Gamma, Ginv, L64, invd64, scal, mode, nullptr, N, n, g2);
     return cudaGetLastError();
 }
 
