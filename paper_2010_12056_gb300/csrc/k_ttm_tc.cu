@@ -64,7 +64,6 @@ __host__ __device__ constexpr int nthreads(int ew, int child) { return 128 + 32 
 // (scaled fp16 parts also at 64 columns: their epilogue multiplies every value by
 // its column scale; measured 0.301 -> 0.281 ms at 128^4 R = 64, bf16 0.272 -> 0.277)
 inline int epi_warps_for(int Rpad, int kind) { return (Rpad >= 128 || (kind == 2 && Rpad >= 64)) ? 8 : 4; }
-constexpr int OPA_BYTES = BM * 128;        // one split part of a 128-row chunk: 16 KB
 constexpr int EPI_STRIDE = 20;             // floats per row of the epilogue transpose buffer
 constexpr int EPI_WARP_BYTES = 32 * EPI_STRIDE * 4;   // one epilogue warp's transpose buffer
 constexpr int BAR_BYTES = 512;
@@ -95,6 +94,7 @@ struct TcArgs {
     int Rp[4], Rpadp[4];   // columns of pass p (written at column 128 p of X), padded
     uint32_t idescp[4];    // MMA instruction descriptor of pass p (N = Rpadp[p])
     int set_cols;          // TMEM columns of one accumulator set
+    int nsets;             // accumulator sets (2: the epilogue overlaps the next tile; 1: wide passes)
     uint32_t idesc;
     unsigned* dev_err;
     // first child (NULL Yc: off): Yc[(g / sc)][r] += X[g][r] Ac[g % sc][r].  Pieces:
@@ -209,6 +209,16 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;             // 128-byte swizzle
     return d;
 }
+// K-major, 64-byte swizzle (rows of 64 B: 32 16-bit k), 8-row groups 512 B apart
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512u >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;             // descriptor version
+    d |= (uint64_t)4 << 61;             // 64-byte swizzle
+    return d;
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];
     asm volatile(
@@ -308,11 +318,14 @@ struct Layout {
 constexpr int CS_BYTES = 512 * 4;
 
 __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, int nk, int b_resident,
-                                               int BK, int ew, int kind, bool child = false, int ac_bytes = 0) {
+                                               int BK, int ew, int kind, bool child = false, int ac_bytes = 0,
+                                               bool wide = false) {
+    // operand rows: 128 bytes (64 16-bit or 32 tf32 k), or 64 bytes in wide mode
+    const size_t rowb = wide ? 64 : 128;
     const size_t stg = (size_t)BM * BK * 4;
-    const size_t bchunk = 2 * (size_t)Rpad * 128;
+    const size_t bchunk = 2 * (size_t)Rpad * rowb;
     const size_t nb = b_resident ? (size_t)nk : (size_t)S_op;
-    return 1024 + (size_t)S_stg * stg + (size_t)S_op * 2 * OPA_BYTES + nb * bchunk +
+    return 1024 + (size_t)S_stg * stg + (size_t)S_op * 2 * BM * rowb + nb * bchunk +
            (size_t)ew * EPI_WARP_BYTES +
            (child ? CHILD_BYTES + (size_t)ac_bytes : 0) + (kind == 2 ? CS_BYTES : 0) + BAR_BYTES;
 }
@@ -326,24 +339,33 @@ __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, in
 // CHILD: 0 plain; 1 the epilogue also forms the first child (a.Yc) for sc a
 // multiple of 32; 2 for other sc.  Separate instantiations keep each kernel's
 // code, registers and shared memory to what it runs.
-template <int MODE, int KIND, int CHILD, int EW>
+// WIDE (16-bit parts, R > 128): column passes of up to 256 (one MMA N = 256, so T
+// is split once per tile and read once), 32-k chunks in the 64-byte swizzle so that
+// three operand stages fit, and one TMEM accumulator set (hi*hi and corrections,
+// 2 x 256 columns): the epilogue does not overlap the next tile's MMAs.
+template <int MODE, int KIND, int CHILD, int EW, int WIDE = 0>
 __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
     k_ttm_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmBhi,
              const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmBhi1,
              const __grid_constant__ CUtensorMap tmBlo1, const __grid_constant__ CUtensorMap tmBhi2,
              const __grid_constant__ CUtensorMap tmBlo2, const __grid_constant__ CUtensorMap tmBhi3,
              const __grid_constant__ CUtensorMap tmBlo3, const TcArgs a) {
-    constexpr int BK = KIND == 1 ? 32 : 64;
+    static_assert(!WIDE || (KIND != 1 && CHILD == 0), "wide passes use 16-bit parts and no first child");
+    constexpr int BK = (KIND == 1 || WIDE) ? 32 : 64;
     constexpr uint32_t STG = BM * BK * 4;
+    constexpr uint32_t ROWB = WIDE ? 64u : 128u;     // bytes of one operand row (k-chunk)
+    constexpr uint32_t OPA = BM * ROWB;               // one split part of a 128-row chunk
+    constexpr int KSTEPS = ROWB / 32;                 // MMAs of K = 16 (32 bytes) per chunk
+    constexpr int PW = WIDE ? 256 : 128;              // columns per pass
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* gbase = smem_raw + (base - raw);
     const int S_stg = a.S_stg, S_op = a.S_op;
-    const uint32_t bchunk = 2u * (uint32_t)a.Rpad * 128u;   // hi + lo of one k-chunk
+    const uint32_t bchunk = 2u * (uint32_t)a.Rpad * ROWB;   // hi + lo of one k-chunk
     const uint32_t stg0 = base;
     const uint32_t op0 = stg0 + (uint32_t)S_stg * STG;
-    const uint32_t b0 = op0 + (uint32_t)S_op * 2u * OPA_BYTES;
+    const uint32_t b0 = op0 + (uint32_t)S_op * 2u * OPA;
     const uint32_t epi0 = b0 + (uint32_t)(a.b_resident ? a.nk : S_op) * bchunk;
     static_assert(EW == 4 || (EW == 8 && CHILD == 0), "first-child epilogues use four warps");
     constexpr int NEPI = EW;
@@ -397,7 +419,7 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
     if (KIND == 2) {
         // per-column output scales, read by the epilogue for every tile
         float* sCs = reinterpret_cast<float*>(gbase + (cs0 - base));
-        const int n = 128 * (a.npass - 1) + a.Rpadp[a.npass - 1];
+        const int n = PW * (a.npass - 1) + a.Rpadp[a.npass - 1];
         for (int i = threadIdx.x; i < n; i += nthreads(EW, CHILD)) sCs[i] = __ldg(a.colinv + i);
     }
     if (CHILD && a.ac_bytes > 0) {
@@ -410,7 +432,7 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const uint32_t bpart = (uint32_t)a.Rpad * 128u;
+    const uint32_t bpart = (uint32_t)a.Rpad * ROWB;
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -470,7 +492,7 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                         if (!(ok = mbar_wait(op_empty(j), (uj & 1u) ^ 1u, abort_flag, a.wait_limit))) break;
                         // this pass's operand rows only (a smaller last pass leaves the
                         // rest of the slot unused)
-                        mbar_expect_tx(op_full(j), 2u * (uint32_t)a.Rpadp[pass] * 128u);
+                        mbar_expect_tx(op_full(j), 2u * (uint32_t)a.Rpadp[pass] * ROWB);
                         const uint32_t bdst = b0 + (uint32_t)j * bchunk;
                         tma_load_2d(bdst, mhi, kc * BK, 0, op_full(j));
                         tma_load_2d(bdst + bpart, mlo, kc * BK, 0, op_full(j));
@@ -498,8 +520,8 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                 const int pass = (int)(w % a.npass);
                 const uint32_t idesc = a.idescp[pass];
                 const int kc0 = ks * a.nk / a.nsk, kc1 = (ks + 1) * a.nk / a.nsk;
-                const int buf = lt & 1;
-                const uint32_t ub = (uint32_t)(lt >> 1);
+                const int buf = lt % a.nsets;
+                const uint32_t ub = (uint32_t)(lt / a.nsets);
                 if (!(ok = mbar_wait(acc_empty(buf), (ub & 1u) ^ 1u, abort_flag, a.wait_limit))) break;
                 tc_fence_after();
                 const uint32_t dt = tmem_base + (uint32_t)(buf * a.set_cols);
@@ -510,17 +532,18 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                     const int j = (int)(it % S_op);
                     if (!(ok = mbar_wait(op_full(j), (uint32_t)((it / S_op) & 1), abort_flag, a.wait_limit))) break;
                     tc_fence_after();
-                    const uint32_t ahi = op0 + (uint32_t)j * 2u * OPA_BYTES, alo = ahi + OPA_BYTES;
+                    const uint32_t ahi = op0 + (uint32_t)j * 2u * OPA, alo = ahi + OPA;
                     const uint32_t bhi = b0 + (uint32_t)(a.b_resident ? kc : j) * bchunk, blo = bhi + bpart;
+                    auto desc = [](uint32_t addr) { return WIDE ? sw64_desc(addr) : sw128_desc(addr); };
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {  // 4 k-steps of 32 bytes per 128-byte row
+                    for (int kk = 0; kk < KSTEPS; ++kk) {  // k-steps of 32 bytes per operand row
                         const uint32_t off = (uint32_t)kk * 32u;
                         const uint32_t accm = (rc >= a.nsplit || kk > 0) ? 1u : 0u;
-                        tc_mma<KIND>(dmain, sw128_desc(ahi + off), sw128_desc(bhi + off), idesc, accm);
+                        tc_mma<KIND>(dmain, desc(ahi + off), desc(bhi + off), idesc, accm);
                         if (a.x3) {
                             const uint32_t accc = (rc > 0 || kk > 0) ? 1u : 0u;
-                            tc_mma<KIND>(dcorr, sw128_desc(ahi + off), sw128_desc(blo + off), idesc, accc);
-                            tc_mma<KIND>(dcorr, sw128_desc(alo + off), sw128_desc(bhi + off), idesc, 1u);
+                            tc_mma<KIND>(dcorr, desc(ahi + off), desc(blo + off), idesc, accc);
+                            tc_mma<KIND>(dcorr, desc(alo + off), desc(bhi + off), idesc, 1u);
                         }
                     }
                     tc_commit(op_empty(j));
@@ -543,7 +566,7 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
         // 0.290 -> 0.272 ms at 128^4 R = 64)
         const int m = threadIdx.x - 128;
         constexpr int cbeg = 0;
-        constexpr int CPT = 8;   // output chunks per thread
+        constexpr int CPT = WIDE ? 4 : 8;   // output chunks per thread
         const int sw = m & 7;
         int64_t it = 0;
         bool ok = true;
@@ -557,8 +580,8 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                 if (!(ok = mbar_wait(stg_full(s), (uint32_t)((it / S_stg) & 1), abort_flag, a.wait_limit))) break;
                 if (!(ok = mbar_wait(op_empty(j), (uint32_t)(((it / S_op) & 1) ^ 1), abort_flag, a.wait_limit))) break;
                 const uint8_t* stg = gbase + (stg0 - base) + (size_t)s * STG;
-                uint8_t* ophi = gbase + (op0 - base) + (size_t)j * 2 * OPA_BYTES;
-                uint8_t* oplo = ophi + OPA_BYTES;
+                uint8_t* ophi = gbase + (op0 - base) + (size_t)j * 2 * OPA;
+                uint8_t* oplo = ophi + OPA;
 #pragma unroll
                 for (int g = 0; g < CPT; g += 4) {
                     if (KIND != 1) {
@@ -588,7 +611,9 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                                 split8_f16(f[cc], a.tscale, hi, lo);
                             else
                                 split8_bf16(f[cc], hi, lo);
-                            const int pos = ((c ^ sw) << 4) + m * 128;
+                            // 16-byte chunk c of row m: 128-byte rows, chunk at c ^ (m mod 8);
+                            // wide: 64-byte rows, chunk at c ^ ((m / 2) mod 4)
+                            const int pos = WIDE ? ((c ^ ((m >> 1) & 3)) << 4) + m * 64 : ((c ^ sw) << 4) + m * 128;
                             *reinterpret_cast<uint4*>(ophi + pos) = hi;
                             *reinterpret_cast<uint4*>(oplo + pos) = lo;
                         }
@@ -643,9 +668,9 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
             const int64_t tile = w / ((int64_t)a.nsk * a.npass);
             const int pass = (int)(w % a.npass);
             const int Rw = a.Rp[pass], Rpw = a.Rpadp[pass];
-            float* Xs = a.X + (int64_t)((w / a.npass) % a.nsk) * a.slice + 128 * pass;
-            const int buf = lt & 1;
-            if (!(ok = mbar_wait(acc_full(buf), (uint32_t)((lt >> 1) & 1), abort_flag, a.wait_limit))) break;
+            float* Xs = a.X + (int64_t)((w / a.npass) % a.nsk) * a.slice + PW * pass;
+            const int buf = lt % a.nsets;
+            if (!(ok = mbar_wait(acc_full(buf), (uint32_t)((lt / a.nsets) & 1), abort_flag, a.wait_limit))) break;
             tc_fence_after();
             int64_t g0;       // global row of this warp's first row
             int64_t gend;     // rows g0 + r < gend belong to this tile
@@ -700,7 +725,7 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                 float4 cs4 = make_float4(1.f, 1.f, 1.f, 1.f);
                 if (KIND == 2)
                     cs4 = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(gbase + (cs0 - base)) +
-                                                           128 * pass + c0 + 4 * qq);
+                                                           PW * pass + c0 + 4 * qq);
                 // corrections first (last accumulator), then the hi*hi partial sums;
                 // up to three accumulators per TMEM round trip
                 const uint32_t tcol = taddr + (uint32_t)c0;
@@ -944,9 +969,10 @@ EncodeTiledFn encoder() {
 
 namespace cpk {
 
-// R > 128 runs as column passes of at most 128 (one MMA N and one TMEM layout
-// that fit); pass p multiplies by factor rows 128 p .. and writes those columns.
-constexpr int MAX_PASS = 4, PASS_COLS = 128;
+// R > 128 runs as column passes: of at most 256 for the 16-bit parts (wide
+// kernel: one MMA N = 256, one TMEM accumulator set), of at most 128 for tf32
+// parts; pass p multiplies by factor rows (pass width) p .. and writes those columns.
+constexpr int MAX_PASS = 4, PASS_COLS = 128, PASS_COLS_WIDE = 256;
 
 struct TcPass {
     CUtensorMap tmBhi, tmBlo;
@@ -964,6 +990,7 @@ struct TcPlan {
     float tscale = 1.f;              // fp16 parts: power of two applied to T
     const float* colinv = nullptr;   // fp16 parts: per-column output scale (Rpad floats)
     bool depth_bound = false;        // split K so that no accumulator sums more than 64 MMAs
+    bool wide = false;               // R > 128 with 16-bit parts: the wide kernel
 };
 
 bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R) {
@@ -981,8 +1008,12 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
     if (kind == 2 && (!colinv || ((uintptr_t)colinv & 15))) return nullptr;
     EncodeTiledFn enc = encoder();
     if (!enc) return nullptr;
-    const int BK = kind == 1 ? 32 : 64;
+    const bool wide = kind != 1 && R > PASS_COLS;
+    const int BK = (kind == 1 || wide) ? 32 : 64;
+    const int pcols = wide ? PASS_COLS_WIDE : PASS_COLS;
+    const size_t rowb = wide ? 64 : 128;
     TcPlan* pl = new TcPlan();
+    pl->wide = wide;
     pl->kind = kind;
     pl->P = P;
     pl->Q = Q;
@@ -990,8 +1021,8 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
     pl->K = K;
     pl->R = R;
     pl->nk = (K + BK - 1) / BK;
-    pl->S_op = 2;
-    pl->npass = (R + PASS_COLS - 1) / PASS_COLS;
+    pl->S_op = wide ? 3 : 2;   // wide: 32-k chunks, a deeper operand ring
+    pl->npass = (R + pcols - 1) / pcols;
     pl->tscale = tscale;
     pl->colinv = colinv;
     const int esz = kind == 1 ? 4 : 2;
@@ -999,13 +1030,14 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
     const cuuint32_t es[3] = {1, 1, 1};
     for (int q = 0; q < pl->npass; ++q) {
         TcPass& ps = pl->pass[q];
-        ps.R = std::min(PASS_COLS, R - q * PASS_COLS);
+        ps.R = std::min(pcols, R - q * pcols);
         ps.Rpad = pl->npass == 1 ? Rpad : (ps.R + 15) / 16 * 16;
         // with two passes the operand slots are refilled per work item
-        ps.b_resident = (pl->npass == 1 && (size_t)pl->nk * 2 * ps.Rpad * 128 <= 64 * 1024) ? 1 : 0;
+        ps.b_resident = (pl->npass == 1 && (size_t)pl->nk * 2 * ps.Rpad * rowb <= 64 * 1024) ? 1 : 0;
         ps.S_stg = 0;
         for (int st = MAX_STG; st >= 2; --st)
-            if (layout_bytes(st, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK, epi_warps_for(ps.Rpad, kind), kind) <= SMEM_LIMIT) {
+            if (layout_bytes(st, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK, epi_warps_for(ps.Rpad, kind), kind,
+                             false, 0, wide) <= SMEM_LIMIT) {
                 ps.S_stg = st;
                 break;
             }
@@ -1013,16 +1045,17 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
             delete pl;
             return nullptr;
         }
-        // rows 128 q .. 128 q + Rpad_q - 1 of the [Rpad][Kpad] operand copies
-        const size_t off = (size_t)q * PASS_COLS * Kpad * esz;
+        // rows pcols q .. pcols q + Rpad_q - 1 of the [Rpad][Kpad] operand copies
+        const size_t off = (size_t)q * pcols * Kpad * esz;
+        const CUtensorMapSwizzle bsw = wide ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
         const cuuint64_t bd[2] = {(cuuint64_t)Kpad, (cuuint64_t)ps.Rpad};
         const cuuint64_t bs[1] = {(cuuint64_t)Kpad * esz};
         const cuuint32_t bb[2] = {(cuuint32_t)BK, (cuuint32_t)ps.Rpad};
         CUresult r2 = enc(&ps.tmBhi, bt, 2, (void*)((const char*)bhi + off), bd, bs, bb, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, bsw,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         CUresult r3 = enc(&ps.tmBlo, bt, 2, (void*)((const char*)blo + off), bd, bs, bb, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, bsw,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r2 != CUDA_SUCCESS || r3 != CUDA_SUCCESS) {
             delete pl;
@@ -1107,13 +1140,14 @@ void ttm_tc_set_depth_bound(TcPlan* p, bool on) {
 
 int64_t ttm_tc_rows(const TcPlan* pl) { return pl->PQ; }
 
-template <int MODE, int KIND, int CHILD, int EW>
+template <int MODE, int KIND, int CHILD, int EW, int WIDE = 0>
 static cudaError_t launch(const TcPlan* pl, const TcArgs& a, size_t smem, unsigned grid,
                           cudaStream_t st) {
-    cudaFuncSetAttribute(k_ttm_tc<MODE, KIND, CHILD, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_ttm_tc<MODE, KIND, CHILD, EW, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     // passes beyond npass repeat pass 0's maps (never read)
     auto ps = [&](int q) -> const TcPass& { return pl->pass[q < pl->npass ? q : 0]; };
-    k_ttm_tc<MODE, KIND, CHILD, EW><<<grid, nthreads(EW, CHILD), smem, st>>>(
+    k_ttm_tc<MODE, KIND, CHILD, EW, WIDE><<<grid, nthreads(EW, CHILD), smem, st>>>(
         pl->tmT, ps(0).tmBhi, ps(0).tmBlo, ps(1).tmBhi, ps(1).tmBlo, ps(2).tmBhi, ps(2).tmBlo, ps(3).tmBhi,
         ps(3).tmBlo, a);
     return cudaGetLastError();
@@ -1143,7 +1177,7 @@ __global__ void k_splitk_sum(const float* __restrict__ ws, int nsk, int64_t n, f
 bool ttm_tc_child_ok(const TcPlan* pl, int sc) {
     // one column pass, rows = one run of X's row index (last mode, or first mode
     // with nothing before it), and the contracted mode innermost in that index
-    if (!pl || pl->npass != 1 || sc < 1) return false;
+    if (!pl || pl->npass != 1 || pl->wide || sc < 1) return false;
     if (!(pl->mode == 0 || pl->P == 1)) return false;
     return pl->PQ % sc == 0;
 }
@@ -1200,7 +1234,7 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     if ((pl->kind == 0 && !bf) || (pl->kind == 1 && !tf) || (pl->kind == 2 && !hf)) return cudaErrorInvalidValue;
     if (((uintptr_t)X & 15) && (pl->R & 3) == 0) return cudaErrorMisalignedAddress;
     const int nsk = splitk_ws ? ttm_tc_splitk(pl, num_sms) : 1;
-    const int BK = pl->kind == 1 ? 32 : 64;
+    const int BK = (pl->kind == 1 || pl->wide) ? 32 : 64;
     const TcPass& p0 = pl->pass[0];  // the widest pass: it sizes the slots and TMEM sets
     TcArgs a;
     a.X = nsk > 1 ? splitk_ws : X;
@@ -1239,8 +1273,9 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     a.b_resident = p0.b_resident;
     a.x3 = (prec == CP_BF16X3 || prec == CP_TF32X3 || prec == CP_F16X3) ? 1 : 0;
     // accumulators per tile: nsplit for hi*hi (by k-chunk) + 1 for the corrections;
-    // two sets must fit the 512 TMEM columns
-    const int per_set = 256 / p0.Rpad;
+    // two sets must fit the 512 TMEM columns (one set in the wide kernel)
+    a.nsets = pl->wide ? 1 : 2;
+    const int per_set = (512 / a.nsets) / p0.Rpad;
     int nsplit = per_set - a.x3;
     if (nsplit > 4) nsplit = 4;
     if (nsplit > pl->nk) nsplit = pl->nk;
@@ -1249,7 +1284,7 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     a.nacc = nsplit + a.x3;
     a.set_cols = a.nacc * p0.Rpad;
     int cols = 32;
-    while (cols < 2 * a.set_cols) cols *= 2;
+    while (cols < a.nsets * a.set_cols) cols *= 2;
     a.tmem_cols = cols;
     // instruction-descriptor operand format: F16 = 0, BF16 = 1 (kind::f16); TF32 = 2 (kind::tf32)
     const uint32_t fmt = pl->kind == 0 ? 1u : (pl->kind == 1 ? 2u : 0u);
@@ -1275,7 +1310,8 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
     a.wait_limit = wait_limit > 0 ? wait_limit : DEFAULT_WAIT_LIMIT;
     // first-child epilogues use four warps; plain ones eight for wide passes
     const int ew = child ? 4 : epi_warps_for(p0.Rpad, pl->kind);
-    const size_t smem = layout_bytes(S_stg, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, ew, pl->kind, child != nullptr, ac_bytes);
+    const size_t smem = layout_bytes(S_stg, pl->S_op, p0.Rpad, pl->nk, p0.b_resident, BK, ew, pl->kind, child != nullptr,
+                                     ac_bytes, pl->wide);
     const int64_t nwork = a.ntiles * a.nsk * a.npass;
     const unsigned grid = (unsigned)(nwork < num_sms ? nwork : num_sms);
     if (grid == 0) return cudaSuccess;
@@ -1288,7 +1324,12 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
                    : (pl->kind == 0   ? launch<1, 0, C, W>(pl, a, smem, grid, st)                   \
                       : pl->kind == 1 ? launch<1, 1, C, W>(pl, a, smem, grid, st)                   \
                                       : launch<1, 2, C, W>(pl, a, smem, grid, st)))
-    if (ck == 1)
+    if (pl->wide)
+        e = pl->mode == 0 ? (pl->kind == 0 ? launch<0, 0, 0, 8, 1>(pl, a, smem, grid, st)
+                                           : launch<0, 2, 0, 8, 1>(pl, a, smem, grid, st))
+                          : (pl->kind == 0 ? launch<1, 0, 0, 8, 1>(pl, a, smem, grid, st)
+                                           : launch<1, 2, 0, 8, 1>(pl, a, smem, grid, st));
+    else if (ck == 1)
         e = CP_TTM_LAUNCH(1, 4);
     else if (ck == 2)
         e = CP_TTM_LAUNCH(2, 4);
