@@ -49,7 +49,7 @@ WORKLOADS = {
     # singular normal equations, so this stand-in draws N(0,1) factors
     "chem": dict(dims=(4520, 280, 280), R=256, law="gaussian", eta=1e-3, seed=20101205 + 8000,
                  desc="order-3 FP32 4520x280x280 (density-fitting tensor shape), rank-256 N(0,1) factors "
-                      "+ 1e-3 noise (the paper's ranks 300-1000 exceed the library's 256)"),
+                      "+ 1e-3 noise (the paper uses ranks 300-1000)"),
 }
 STANDINS = ("coil", "timelapse", "chem")
 METRIC = "ALS sweep/s (MSDT) on 1 GPU, order-4 128^4 R=64"
@@ -57,7 +57,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # DRAM bytes per launch of the last-mode TTM on 128^4 R=64 from ncu captures of
 # the current kernel, by precision (profiles/ttm_tc_*_c2.md); a precision whose
 # kernel changed since its capture has no entry (traffic null)
-TRAFFIC_C2 = {"f16x3": 1.073848e9 + 0.501321e9}
+TRAFFIC_C2 = {"f16x3": 1.073861e9 + 0.501550e9}
 FIT_SWEEPS = 20     # the fit check: direct residual after this many MSDT sweeps from A0
 FIT_TOL = 1e-6
 
