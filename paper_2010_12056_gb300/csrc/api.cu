@@ -951,12 +951,16 @@ cp_status direct_resid(cp_ctx* c, double* r) {
         a.dims[i] = c->dims[i];
     }
     c->stats.launches += 2;
-    int nb = cpk::resid_direct_partials(a, c->red_part, 4096, c->st);
+    // tensor cores where the shape allows it, else the FP32 SIMT kernel
+    int nb = cpk::resid_tc_partials(a, c->red_part, 4096, c->num_sms, c->dev_err, c->wait_limit, c->st);
+    if (nb < 0) CKCUDA(c, cudaGetLastError());
+    if (nb == 0) nb = cpk::resid_direct_partials(a, c->red_part, 4096, c->st);
     CKCUDA(c, cudaGetLastError());
     CKCUDA(c, cpk::sum_partials(c->red_part, nb, c->d_red_out, c->st));
     double s2 = 0.0;
     CKCUDA(c, cudaMemcpyAsync(&s2, c->d_red_out, sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CKCUDA(c, cudaStreamSynchronize(c->st));
+    CKST(check_dev_err(c));
     // a NaN must not be clamped away with the rounding-level negatives
     if (!std::isfinite(s2)) return fail(c, CP_ENUMERIC, "non-finite residual");
     *r = sqrt(s2 > 0 ? s2 : 0.0) / sqrt(c->normT2);

@@ -183,6 +183,12 @@ struct ResidArgs {
     int N, R;
 };
 int resid_direct_partials(const ResidArgs& a, double* partials, int max_blocks, cudaStream_t st);
+// The same on the tensor cores (k_resid_tc.cu; tf32x3 model values, double-float
+// sums): R <= 64, last mode a multiple of 4 and at most num_sms column blocks of
+// 128.  Returns the number of partials written, 0 if the shape is not supported
+// (nothing launched), -1 on a launch error.
+int resid_tc_partials(const ResidArgs& a, double* partials, int max_blocks, int num_sms, unsigned* dev_err,
+                      long long wait_limit, cudaStream_t st);
 
 // PP: dA = A - A_p (FP64 and FP32); out = Mt + A W (the V term of Eq. ppupdate)
 cudaError_t pp_delta(const double* A, const double* Ap, float* d32, double* d64, int64_t n,

@@ -129,6 +129,43 @@ def test_direct_residual(pkg):
     ctx.close()
 
 
+@pytest.mark.parametrize("dims,R", [((40, 36, 132), 7), ((20, 16, 24, 128), 16), ((9, 10, 11, 12, 8), 33),
+                                    ((64, 64, 256), 64), ((300, 200, 64), 50), ((50, 60, 40), 1)])
+def test_direct_residual_tensor_cores(pkg, dims, R):
+    """Eq. residual-def on the tensor cores (last mode a multiple of 4, R <= 64):
+    ragged row tiles and column blocks, orders 3-5, R not a multiple of 4 or 32;
+    against the FP64 oracle and against the FP32 SIMT kernel of cp_resid_noalloc."""
+    Td, Tref, A0 = problem(dims, R, 41, eta=0.05)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec="fp32")
+    ctx.sweep_msdt(2)
+    _, r = ctx.fit(exact=True)
+    A = ctx.factors()
+    r_ref = co.residual_direct(Tref, A)
+    assert abs(r - r_ref) <= 1e-6
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    pkg.resid_noalloc(Td, [torch.from_numpy(a.astype(np.float32)).cuda() for a in A], out)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    assert abs(float(np.sqrt(o[0] / o[1])) - r) <= 1e-7
+    ctx.close()
+
+
+@pytest.mark.parametrize("R", [16, 64])
+def test_direct_residual_tensor_cores_many_tiles(pkg, R):
+    """Several row tiles per CTA and two column blocks (256^3: 512 row tiles on
+    76 CTAs per block), so every ring of the kernel wraps around: the residual
+    equals the oracle's and repeated calls give the same bits."""
+    dims = (256, 256, 256)
+    T, _, A0 = synth.make_problem_device(20103205, dims, R, law="uniform", eta=1e-3, device="cuda")
+    ctx = pkg.CPContext(T, R, A0=A0, prec="f16x3")
+    ctx.sweep_msdt(2)
+    rs = [ctx.fit(exact=True)[1] for _ in range(4)]
+    assert len(set(rs)) == 1
+    r_ref = co.residual_direct(T.cpu().numpy().astype(np.float64), ctx.factors())
+    assert abs(rs[0] - r_ref) <= 1e-6
+    ctx.close()
+
+
 def _pp_case(pkg, dims, R, seed, t, cp_tensor=False, only=None):
     Ap = synth.uniform_factors(seed, dims, R)
     D = synth.gaussian_factors(seed + 1, dims, R)
