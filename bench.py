@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--ttm-only", action="store_true",
                     help="time only one first-level TTM (cp_ttm, --ttm-mode) and exit")
     ap.add_argument("--ttm-mode", type=int, default=-1, help="mode of --ttm-only (default: the last)")
+    ap.add_argument("--no-presplit", action="store_true",
+                    help="R > 128: split T inside the TTM instead of reading its stored 16-bit parts")
     ap.add_argument("--dims", default=None, help="override the workload's mode sizes, e.g. 512,512,512")
     ap.add_argument("--rank", type=int, default=None, help="override the workload's rank")
     ap.add_argument("--law", default=None, choices=["uniform", "gaussian", "collinear"])
@@ -464,6 +466,8 @@ def run_ttm_only(args, wl):
     numel = int(np.prod(dims))
     T, _, A0 = make_inputs(wl, "cuda")
     ctx = pkg.CPContext(T, R, A0=A0, prec=args.prec)
+    if args.no_presplit:
+        ctx.set_option("ttm_presplit", False)
     mode = args.ttm_mode if args.ttm_mode >= 0 else len(dims) - 1
     X = torch.empty(numel // dims[mode] * R, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -480,7 +484,8 @@ def run_ttm_only(args, wl):
     print(json.dumps({"metric": "first-level TTM time", "value": ms, "unit": "ms", "workload": wl["desc"],
                       "prec": args.prec, "mode": mode, "tflops_algorithmic": 2.0 * numel * R / (ms / 1e3) / 1e12,
                       "gbs_algorithmic": (4.0 * numel + 4.0 * numel // dims[mode] * R) / (ms / 1e3) / 1e9,
-                      "tensor_core_launches": st["ttm_tensor_core"]}), flush=True)
+                      "tensor_core_launches": st["ttm_tensor_core"],
+                      "stored_parts_launches": st["ttm_stored_parts"]}), flush=True)
     ctx.close()
 
 

@@ -321,6 +321,8 @@ typedef struct {
                                with the next update (cp_set_option)           */
     int64_t ttm_child;      /* first-level TTMs whose epilogue also produced
                                the first child node (cp_set_option)           */
+    int64_t ttm_stored_parts;/* first-level TTMs that read T's stored 16-bit
+                               parts (CP_OPT_TTM_PRESPLIT)                    */
 } cp_stats;
 cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
 
@@ -365,10 +367,17 @@ cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
  *                     is too ill-conditioned for the refinement.  The library also
  *                     falls back to it by itself per update when its a-posteriori
  *                     check of the FP32 inverse fails (cp_stats.solves_fp64).
+ *   CP_OPT_TTM_PRESPLIT (default 1) R > 128 with CP_F16X3 / CP_BF16X3: keep T's
+ *                     two 16-bit parts per mode in device memory, the contracted
+ *                     mode innermost (2 x 2 bytes per entry and mode, written at
+ *                     cp_init and cp_load_tensor), so that the first-level TTM
+ *                     loads its operand with TMA instead of converting T; a mode
+ *                     whose copy does not fit converts T as with 0.  Results are
+ *                     bit-identical to 0.
  * CP_EINVAL for an unknown option or value.  Takes effect at the next call.
  */
 enum { CP_OPT_FUSE_DT = 1, CP_OPT_LOOKAHEAD = 2, CP_OPT_FUSE_CHILD = 3, CP_OPT_WAIT_LIMIT = 4,
-       CP_OPT_MSDT_LEVELS = 5, CP_OPT_SOLVE_FP64 = 6 };
+       CP_OPT_MSDT_LEVELS = 5, CP_OPT_SOLVE_FP64 = 6, CP_OPT_TTM_PRESPLIT = 7 };
 cp_status cp_set_option(cp_ctx *ctx, int option, int value);
 
 /*

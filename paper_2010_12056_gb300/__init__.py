@@ -63,10 +63,12 @@ class Stats(ctypes.Structure):
                 ("ttm_bytes", ctypes.c_double), ("mttv_bytes", ctypes.c_double),
                 ("ttm_tensor_core", ctypes.c_int64), ("ttm_fused", ctypes.c_int64),
                 ("solves_fp64", ctypes.c_int64), ("rollbacks", ctypes.c_int64),
-                ("lookahead", ctypes.c_int64), ("ttm_child", ctypes.c_int64)]
+                ("lookahead", ctypes.c_int64), ("ttm_child", ctypes.c_int64),
+                ("ttm_stored_parts", ctypes.c_int64)]
 
 
-OPTIONS = {"fuse_dt": 1, "lookahead": 2, "fuse_child": 3, "wait_limit": 4, "msdt_levels": 5, "solve_fp64": 6}
+OPTIONS = {"fuse_dt": 1, "lookahead": 2, "fuse_child": 3, "wait_limit": 4, "msdt_levels": 5, "solve_fp64": 6,
+           "ttm_presplit": 7}
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int

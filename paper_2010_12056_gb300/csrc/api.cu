@@ -66,6 +66,11 @@ struct cp_ctx {
     float* colinv[CP_MAXN] = {0};
     int f16_ver[CP_MAXN] = {-1, -1, -1, -1, -1, -1, -1, -1};
     int eT = 0;                     // f16x3: T is multiplied by 2^eT before its split
+    // R > 128, f16x3 / bf16x3: T's 16-bit parts per mode, contracted mode
+    // innermost ([P][Q][K]), read by that mode's first-level TTM instead of T
+    uint16_t* Tp_hi[CP_MAXN] = {0};
+    uint16_t* Tp_lo[CP_MAXN] = {0};
+    bool presplit = true;
     double* S[CP_MAXN] = {0};
     double* dS[CP_MAXN] = {0};
     double* Ap64[CP_MAXN] = {0};
@@ -309,6 +314,7 @@ cp_status launch_ttm(cp_ctx* c, int mode, float* X) {
                                   c->wait_limit));
         if (c->splitk_ws && cpk::ttm_tc_splitk(c->tc_plan[mode], c->num_sms) > 1) c->stats.launches++;  // partial-sum kernel
         c->stats.ttm_tensor_core++;
+        if (cpk::ttm_tc_stored_parts(c->tc_plan[mode])) c->stats.ttm_stored_parts++;
     } else {
         LAUNCH(c, cpk::ttm_simt(c->T, c->A32[mode], X, P, K, Q, c->R, c->st));
     }
@@ -1200,6 +1206,8 @@ void free_all(cp_ctx* c) {
     F(c->kr_hi); F(c->kr_lo); F(c->kr_scale); F(c->kr_colinv); F(c->splitk_ws); F(c->child_ws);
     for (int i = 0; i < CP_MAXN; ++i) {
         F(c->colinv[i]);
+        F(c->Tp_hi[i]);
+        F(c->Tp_lo[i]);
         F(c->A2[i]);
         F(c->dA2[i]);
         F(c->S2[i]);
@@ -1251,8 +1259,51 @@ static void make_mode_plans(cp_ctx* c) {
         const void* lo = (bf || hf) ? (const void*)c->blo[m]
                                     : (const void*)(c->bt32[m] + (size_t)c->Rpad * c->Kpad[m]);
         c->tc_plan[m] = cpk::ttm_tc_plan(c->T, P, (int)c->dims[m], Q, c->R, kind, hi, lo, c->Rpad, c->Kpad[m],
-                                         tscale, c->colinv[m]);
+                                         tscale, c->colinv[m], c->Tp_hi[m], c->Tp_lo[m]);
     }
+}
+
+// T's stored 16-bit parts (one copy per mode whose TTM takes R > 128 columns):
+// allocated where memory allows (a mode without them converts T in its TTM),
+// refilled whenever T or its f16x3 scale changes
+static bool presplit_wanted(const cp_ctx* c, int m) {
+    return c->presplit && c->R > 128 && (c->cfg.prec == CP_F16X3 || c->cfg.prec == CP_BF16X3) &&
+           c->dims[m] % 8 == 0 && c->numel <= ((int64_t)1 << 31);
+}
+
+static void free_presplit(cp_ctx* c) {
+    for (int m = 0; m < CP_MAXN; ++m) {
+        if (c->Tp_hi[m]) cudaFree(c->Tp_hi[m]);
+        if (c->Tp_lo[m]) cudaFree(c->Tp_lo[m]);
+        c->Tp_hi[m] = c->Tp_lo[m] = nullptr;
+    }
+}
+
+static cp_status fill_presplit(cp_ctx* c) {
+    const int kind = c->cfg.prec == CP_F16X3 ? 2 : 0;
+    const float tscale = ldexpf(1.f, c->eT);
+    for (int m = 0; m < c->N; ++m) {
+        if (!c->Tp_hi[m]) continue;
+        int64_t P, Q;
+        contract_dims(c, 0u, m, &P, &Q);
+        LAUNCH(c, cpk::ttm_presplit(c->T, P, (int)c->dims[m], Q, kind, tscale, c->Tp_hi[m], c->Tp_lo[m],
+                                    c->num_sms, c->st));
+        c->stats.launches++;
+    }
+    return CP_OK;
+}
+
+static cp_status alloc_presplit(cp_ctx* c) {
+    for (int m = 0; m < c->N; ++m) {
+        if (!presplit_wanted(c, m) || c->Tp_hi[m]) continue;
+        const size_t bytes = sizeof(uint16_t) * (size_t)c->numel;
+        if (cudaMalloc(&c->Tp_hi[m], bytes) != cudaSuccess || cudaMalloc(&c->Tp_lo[m], bytes) != cudaSuccess) {
+            (void)cudaGetLastError();  // out of memory: this mode converts T in its TTM
+            if (c->Tp_hi[m]) cudaFree(c->Tp_hi[m]);
+            c->Tp_hi[m] = c->Tp_lo[m] = nullptr;
+        }
+    }
+    return fill_presplit(c);
 }
 
 cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T_dev, int dtype,
@@ -1411,6 +1462,7 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
         const bool bf = uses_bf16(c), hf = c->cfg.prec == CP_F16X3;
         const int kind = bf ? 0 : (hf ? 2 : 1);
         const float tscale = ldexpf(1.f, c->eT);
+        TRY(alloc_presplit(c));
         make_mode_plans(c);
         // fused two-mode contractions of adjacent pairs (standard tree, N >= 3)
         size_t kr_elems = 0;
@@ -1517,6 +1569,7 @@ cp_status cp_load_tensor(cp_ctx* c, const float* T, int on_host) {
     c->have_last = false;
     CKST(tensor_norm(c));
     if (c->cfg.prec == CP_F16X3) CKST(tensor_exponent(c));
+    CKST(fill_presplit(c));
     return CP_OK;
 }
 
@@ -1562,6 +1615,16 @@ cp_status cp_set_option(cp_ctx* c, int option, int value) {
         case CP_OPT_SOLVE_FP64:
             if (value != 0 && value != 1) return CP_EINVAL;
             c->solve_fp64 = value != 0;
+            return CP_OK;
+        case CP_OPT_TTM_PRESPLIT:
+            if (value != 0 && value != 1) return CP_EINVAL;
+            if (c->presplit == (value != 0)) return CP_OK;
+            CKST(ahead_join(c));
+            CKCUDA(c, cudaStreamSynchronize(c->st));
+            c->presplit = value != 0;
+            if (c->presplit) CKST(alloc_presplit(c));
+            else free_presplit(c);
+            if (c->cfg.prec != CP_FP32_SIMT) make_mode_plans(c);
             return CP_OK;
         case CP_OPT_MSDT_LEVELS:
             if (value < 1 || value > std::max(1, c->N - 2)) return CP_EINVAL;

@@ -49,8 +49,16 @@ bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R);
 // kind 2: fp16 parts of the scaled factor (uint16 [Rpad][Kpad]); T is multiplied
 // by tscale (a power of two) before its split and column c of the result by
 // colinv[c] (device, Rpad floats, 16-byte aligned).
+// pre_hi / pre_lo: T's 16-bit parts stored with the contracted mode innermost
+// ([P][Q][K], from ttm_presplit with the same kind and tscale): for R > 128 the
+// kernel then loads its A operand directly (no converter warps).
 TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind, const void* bhi,
-                    const void* blo, int Rpad, int Kpad, float tscale = 1.f, const float* colinv = nullptr);
+                    const void* blo, int Rpad, int Kpad, float tscale = 1.f, const float* colinv = nullptr,
+                    const void* pre_hi = nullptr, const void* pre_lo = nullptr);
+// T viewed as [P][K][Q] -> its 16-bit parts [P][Q][K] (kind 2: fp16 of T tscale; kind 0: bf16),
+// split exactly as the kernel's converter warps split it
+cudaError_t ttm_presplit(const float* T, int64_t P, int K, int64_t Q, int kind, float tscale, uint16_t* hi,
+                         uint16_t* lo, int num_sms, cudaStream_t st);
 int ttm_tc_kind(const TcPlan* p);
 void ttm_tc_set_tscale(TcPlan* p, float tscale);
 void ttm_tc_plan_free(TcPlan* p);
@@ -74,6 +82,8 @@ cudaError_t ttm_tc_run(const TcPlan* p, float* X, int prec, int num_sms, unsigne
                        cudaStream_t st, float* splitk_ws, const TcChild* child = nullptr,
                        long long wait_limit = 0);
 int ttm_tc_splitk(const TcPlan* p, int num_sms);
+// the plan reads T's stored 16-bit parts
+bool ttm_tc_stored_parts(const TcPlan* p);
 // long contractions (the fused two-mode operand): split K so that no TMEM
 // accumulator sums more than 64 MMAs; depth_slices is the split that needs
 void ttm_tc_set_depth_bound(TcPlan* p, bool on);

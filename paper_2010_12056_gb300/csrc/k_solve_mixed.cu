@@ -793,8 +793,9 @@ __device__ __forceinline__ void df_dot(const float* vh, const float* vl, const f
 // of a 64-column row took about 5 us per step; the double-float one needs a
 // tenth of the issue slots of the FP32 pipe.  The iteration stops once the error
 // left after the step, estimated as rho ||d||_inf with rho the contraction seen
-// between steps, is below 2^-36 ||x||_inf: far below the FP32 error of the
-// MTTKRP that forms m.
+// between steps, is below 2^-36 ||x||_inf (far below the FP32 error of the
+// MTTKRP that forms m), or once the steps stop contracting at the residual's
+// rounding floor, if that floor is below 2^-20 ||x||_inf.
 template <int RT, int KS>
 __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
     const float* __restrict__ M, const double* __restrict__ W, const float2* __restrict__ W2,
@@ -1151,6 +1152,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
             // remaining error after this step is about rho * dmax, rho = dmax / prev
             const float rho = (itr > 0 && prev > 0.f) ? __fdiv_rn(dmax, prev) : 1.f;
             conv = rho * dmax <= 0x1.0p-36f * xmax || dmax == 0.f;
+            // The residual's own rounding (about 2^-44 cond(Gamma) relative in
+            // double-float, 2^-53 cond in FP64) is a floor the steps cannot go
+            // below: once they stop contracting there, x is as accurate as this
+            // residual can make it.  The floor is accepted up to 2^-20 ||x||: it is
+            // above 2^-36 only for cond >= 2^8, and then the FP32-rounded m alone
+            // moves the exact solution by about 2^-24 cond >= 2^-16.
+            conv = conv || ((itr >= 2 && rho >= 0.5f) || itr == 29) && dmax <= 0x1.0p-20f * xmax;
             prev = dmax;
             if (conv) break;
             __syncthreads();  // redf[] is rewritten by the next step

@@ -184,14 +184,20 @@ __host__ __device__ inline size_t layout_bytes(int S_stg, int S_op, int Rpad, in
 // is split once per tile and read once), 32-k chunks in the 64-byte swizzle so that
 // three operand stages fit, and one TMEM accumulator set (hi*hi and corrections,
 // 2 x 256 columns): the epilogue does not overlap the next tile's MMAs.
-template <int MODE, int KIND, int CHILD, int EW, int WIDE = 0>
+// PRE (wide only): T was stored once as fp16 / bf16 parts with the contracted mode
+// innermost ([rows][K], rows = the kept modes in order): the TMA loads the A
+// operand directly (two 2-D maps, hi and lo), with no staging ring and no
+// converter warps; rows are the flattened kept modes (MODE 0 addressing).
+template <int MODE, int KIND, int CHILD, int EW, int WIDE = 0, int PRE = 0>
 __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
     k_ttm_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmBhi,
              const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmBhi1,
              const __grid_constant__ CUtensorMap tmBlo1, const __grid_constant__ CUtensorMap tmBhi2,
              const __grid_constant__ CUtensorMap tmBlo2, const __grid_constant__ CUtensorMap tmBhi3,
-             const __grid_constant__ CUtensorMap tmBlo3, const TcArgs a) {
+             const __grid_constant__ CUtensorMap tmBlo3, const __grid_constant__ CUtensorMap tmTlo,
+             const TcArgs a) {
     static_assert(!WIDE || (KIND != 1 && CHILD == 0), "wide passes use 16-bit parts and no first child");
+    static_assert(!PRE || (WIDE && MODE == 0), "stored parts: wide passes, flattened rows");
     constexpr int BK = (KIND == 1 || WIDE) ? 32 : 64;
     constexpr uint32_t STG = BM * BK * 4;
     constexpr uint32_t ROWB = WIDE ? 64u : 128u;     // bytes of one operand row (k-chunk)
@@ -236,7 +242,9 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
             mbar_init(stg_empty(s), 32 * NCONV);
         }
         for (int j = 0; j < S_op; ++j) {
-            mbar_init(op_full(j), a.b_resident ? 32 * NCONV : 32 * NCONV + 1);
+            // converted A (NCONV warps) and the factor chunk (one expect_tx), or with
+            // stored parts both by the producer's one expect_tx
+            mbar_init(op_full(j), PRE ? 1 : (a.b_resident ? 32 * NCONV : 32 * NCONV + 1));
             mbar_init(op_empty(j), 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -280,6 +288,7 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmT) : "memory");
+            if (PRE) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmTlo) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBhi) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmBlo) : "memory");
             if (a.npass > 1) {
@@ -312,6 +321,25 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                 const CUtensorMap* mhi = pass == 0 ? &tmBhi : pass == 1 ? &tmBhi1 : pass == 2 ? &tmBhi2 : &tmBhi3;
                 const CUtensorMap* mlo = pass == 0 ? &tmBlo : pass == 1 ? &tmBlo1 : pass == 2 ? &tmBlo2 : &tmBlo3;
                 const int kc0 = ks * a.nk / a.nsk, kc1 = (ks + 1) * a.nk / a.nsk;
+                if (PRE) {
+                    // the A chunk's hi and lo parts and the factor chunk into one stage
+                    for (int kc = kc0; kc < kc1 && ok; ++kc, ++it) {
+                        const int j = (int)(it % S_op);
+                        const uint32_t uj = (uint32_t)(it / S_op);
+                        if (!(ok = mbar_wait(op_empty(j), (uj & 1u) ^ 1u, abort_flag, a.wait_limit))) break;
+                        const uint32_t bbytes = a.b_resident ? 0u : 2u * (uint32_t)a.Rpadp[pass] * ROWB;
+                        mbar_expect_tx(op_full(j), 2u * OPA + bbytes);
+                        const uint32_t adst = op0 + (uint32_t)j * 2u * OPA;
+                        tma_load_2d(adst, &tmT, kc * BK, (int)(tile * BM), op_full(j));
+                        tma_load_2d(adst + OPA, &tmTlo, kc * BK, (int)(tile * BM), op_full(j));
+                        if (!a.b_resident) {
+                            const uint32_t bdst = b0 + (uint32_t)j * bchunk;
+                            tma_load_2d(bdst, mhi, kc * BK, 0, op_full(j));
+                            tma_load_2d(bdst + bpart, mlo, kc * BK, 0, op_full(j));
+                        }
+                    }
+                    continue;
+                }
                 for (int kc = kc0; kc < kc1 && ok; ++kc, ++it) {
                     const int s = (int)(it % S_stg);
                     const uint32_t us = (uint32_t)(it / S_stg);
@@ -344,8 +372,13 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
             if (!ok) {
                 // drain: wait (bounded) for the copies issued into the last stages
                 volatile int never = 0;
-                for (int64_t k = (it > S_stg ? it - S_stg : 0); k <= it; ++k)
-                    mbar_wait(stg_full((int)(k % S_stg)), (uint32_t)((k / S_stg) & 1), &never, DRAIN_LIMIT);
+                if (PRE) {
+                    for (int64_t k = (it > S_op ? it - S_op : 0); k < it; ++k)
+                        mbar_wait(op_full((int)(k % S_op)), (uint32_t)((k / S_op) & 1), &never, DRAIN_LIMIT);
+                } else {
+                    for (int64_t k = (it > S_stg ? it - S_stg : 0); k <= it; ++k)
+                        mbar_wait(stg_full((int)(k % S_stg)), (uint32_t)((k / S_stg) & 1), &never, DRAIN_LIMIT);
+                }
                 if (a.b_resident) mbar_wait(b_full, 0u, &never, DRAIN_LIMIT);
             }
         }
@@ -400,7 +433,7 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                 mbar_wait(drain_bar, 0u, &never, DRAIN_LIMIT);
             }
         }
-    } else if (warp >= 4 && warp < EPI0) {
+    } else if (!PRE && warp >= 4 && warp < EPI0) {
         // ------------------------------------------------ converters (thread = tile row)
         // the 8 output chunks of a row are handled four at a time, with all their
         // shared-memory loads issued before the first store (the compiler may not
@@ -801,6 +834,7 @@ struct TcPass {
 
 struct TcPlan {
     CUtensorMap tmT;
+    CUtensorMap tmTlo;   // stored parts: the lo map (tmT holds the hi map)
     TcPass pass[MAX_PASS];
     int npass;
     int mode;   // kernel MODE
@@ -811,6 +845,7 @@ struct TcPlan {
     const float* colinv = nullptr;   // fp16 parts: per-column output scale (Rpad floats)
     bool depth_bound = false;        // split K so that no accumulator sums more than 64 MMAs
     bool wide = false;               // R > 128 with 16-bit parts: the wide kernel
+    bool pre = false;                // the A operand from T's stored 16-bit parts
 };
 
 bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R) {
@@ -823,17 +858,22 @@ bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R) {
 }
 
 TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind, const void* bhi,
-                    const void* blo, int Rpad, int Kpad, float tscale, const float* colinv) {
+                    const void* blo, int Rpad, int Kpad, float tscale, const float* colinv, const void* pre_hi,
+                    const void* pre_lo) {
     if (!ttm_tc_supported(P, K, Q, R) || ((uintptr_t)T & 15)) return nullptr;
     if (kind == 2 && (!colinv || ((uintptr_t)colinv & 15))) return nullptr;
     EncodeTiledFn enc = encoder();
     if (!enc) return nullptr;
     const bool wide = kind != 1 && R > PASS_COLS;
+    // stored parts: rows of K 16-bit values must be 16-byte aligned for the TMA
+    const bool pre = wide && pre_hi && pre_lo && K % 8 == 0 && P * Q <= ((int64_t)1 << 31) &&
+                     (((uintptr_t)pre_hi | (uintptr_t)pre_lo) & 15) == 0;
     const int BK = (kind == 1 || wide) ? 32 : 64;
     const int pcols = wide ? PASS_COLS_WIDE : PASS_COLS;
     const size_t rowb = wide ? 64 : 128;
     TcPlan* pl = new TcPlan();
     pl->wide = wide;
+    pl->pre = pre;
     pl->kind = kind;
     pl->P = P;
     pl->Q = Q;
@@ -841,7 +881,7 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
     pl->K = K;
     pl->R = R;
     pl->nk = (K + BK - 1) / BK;
-    pl->S_op = wide ? 3 : 2;   // wide: 32-k chunks, a deeper operand ring
+    pl->S_op = pre ? 4 : (wide ? 3 : 2);   // wide: 32-k chunks, a deeper operand ring
     pl->npass = (R + pcols - 1) / pcols;
     pl->tscale = tscale;
     pl->colinv = colinv;
@@ -855,13 +895,19 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
         // with two passes the operand slots are refilled per work item
         ps.b_resident = (pl->npass == 1 && (size_t)pl->nk * 2 * ps.Rpad * rowb <= 64 * 1024) ? 1 : 0;
         ps.S_stg = 0;
-        for (int st = MAX_STG; st >= 2; --st)
-            if (layout_bytes(st, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK, epi_warps_for(ps.Rpad, kind), kind,
-                             false, 0, wide) <= SMEM_LIMIT) {
-                ps.S_stg = st;
-                break;
-            }
-        if (ps.S_stg == 0) {
+        bool fits = false;
+        if (pre) {
+            // no staging ring
+            fits = layout_bytes(0, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK, 8, kind, false, 0, true) <= SMEM_LIMIT;
+        } else {
+            for (int st = MAX_STG; st >= 2 && !fits; --st)
+                if (layout_bytes(st, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK, epi_warps_for(ps.Rpad, kind), kind,
+                                 false, 0, wide) <= SMEM_LIMIT) {
+                    ps.S_stg = st;
+                    fits = true;
+                }
+        }
+        if (!fits) {
             delete pl;
             return nullptr;
         }
@@ -883,7 +929,19 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
         }
     }
     CUresult r1;
-    if (Q == 1) {
+    if (pre) {
+        // rows = the kept modes flattened, K contiguous: the last-mode addressing
+        pl->mode = 0;
+        const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)(P * Q)};
+        const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+        const cuuint32_t box[2] = {32, BM};
+        const CUtensorMapDataType pt = kind == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+        r1 = enc(&pl->tmT, pt, 2, (void*)pre_hi, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                 CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r1 == CUDA_SUCCESS)
+            r1 = enc(&pl->tmTlo, pt, 2, (void*)pre_lo, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else if (Q == 1) {
         pl->mode = 0;
         const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)P};
         const cuuint64_t strides[1] = {(cuuint64_t)K * 4};
@@ -928,6 +986,8 @@ static int plan_nsplit(const TcPlan* pl) {
     return nsplit < 1 ? 1 : nsplit;
 }
 
+bool ttm_tc_stored_parts(const TcPlan* pl) { return pl && pl->pre; }
+
 int ttm_tc_splitk(const TcPlan* pl, int num_sms) {
     // split K when the row tiles alone cannot fill the GPU and K is long enough
     const int64_t nt = plan_tiles(pl);
@@ -960,16 +1020,17 @@ void ttm_tc_set_depth_bound(TcPlan* p, bool on) {
 
 int64_t ttm_tc_rows(const TcPlan* pl) { return pl->PQ; }
 
-template <int MODE, int KIND, int CHILD, int EW, int WIDE = 0>
+template <int MODE, int KIND, int CHILD, int EW, int WIDE = 0, int PRE = 0>
 static cudaError_t launch(const TcPlan* pl, const TcArgs& a, size_t smem, unsigned grid,
                           cudaStream_t st) {
-    cudaFuncSetAttribute(k_ttm_tc<MODE, KIND, CHILD, EW, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_ttm_tc<MODE, KIND, CHILD, EW, WIDE, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     // passes beyond npass repeat pass 0's maps (never read)
     auto ps = [&](int q) -> const TcPass& { return pl->pass[q < pl->npass ? q : 0]; };
-    k_ttm_tc<MODE, KIND, CHILD, EW, WIDE><<<grid, nthreads(EW, CHILD), smem, st>>>(
+    // tmTlo is read only with stored parts (PRE)
+    k_ttm_tc<MODE, KIND, CHILD, EW, WIDE, PRE><<<grid, nthreads(EW, CHILD), smem, st>>>(
         pl->tmT, ps(0).tmBhi, ps(0).tmBlo, ps(1).tmBhi, ps(1).tmBlo, ps(2).tmBhi, ps(2).tmBlo, ps(3).tmBhi,
-        ps(3).tmBlo, a);
+        ps(3).tmBlo, PRE ? pl->tmTlo : pl->tmT, a);
     return cudaGetLastError();
 }
 
@@ -993,6 +1054,84 @@ __global__ void k_splitk_sum(const float* __restrict__ ws, int nsk, int64_t n, f
     }
 }
 }  // namespace
+
+namespace {
+// one value's 16-bit parts, as the converter warps split it: fp16 of y = x tscale
+// (KIND 2) or bf16 of x (KIND 0); hi = rn(y), lo = rn(y - hi)
+template <int KIND>
+__device__ __forceinline__ void split_one(float x, float tscale, uint16_t& h, uint16_t& l) {
+    if (KIND == 2) {
+        const float y = x * tscale;
+        const __half hh = __float2half_rn(y);
+        h = __half_as_ushort(hh);
+        l = __half_as_ushort(__float2half_rn(y - __half2float(hh)));
+    } else {
+        const __nv_bfloat16 hb = __float2bfloat16_rn(x);
+        h = __bfloat16_as_ushort(hb);
+        l = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hb)));
+    }
+}
+// T viewed as [P][K][Q] -> parts [P][Q][K] (the contracted mode innermost), in
+// 32 x 32 tiles through shared memory; Q == 1 needs no transpose
+template <int KIND>
+__global__ void __launch_bounds__(256) k_presplit(const float* __restrict__ T, int64_t P, int K, int64_t Q,
+                                                  float tscale, uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
+    __shared__ float tile[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t q0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * 32;
+    for (int64_t p = blockIdx.z; p < P; p += gridDim.z) {
+        const float* Tp = T + (size_t)p * K * Q;
+        for (int i = ty; i < 32; i += 8) {
+            const int k = k0 + i;
+            const int64_t q = q0 + tx;
+            tile[i][tx] = (k < K && q < Q) ? Tp[(size_t)k * Q + q] : 0.f;
+        }
+        __syncthreads();
+        for (int i = ty; i < 32; i += 8) {
+            const int64_t q = q0 + i;
+            const int k = k0 + tx;
+            if (q < Q && k < K) {
+                uint16_t h, l;
+                split_one<KIND>(tile[tx][i], tscale, h, l);
+                const size_t o = ((size_t)p * Q + q) * K + k;
+                hi[o] = h;
+                lo[o] = l;
+            }
+        }
+        __syncthreads();
+    }
+}
+template <int KIND>
+__global__ void __launch_bounds__(256) k_presplit_flat(const float* __restrict__ T, int64_t n, float tscale,
+                                                       uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint16_t h, l;
+        split_one<KIND>(T[i], tscale, h, l);
+        hi[i] = h;
+        lo[i] = l;
+    }
+}
+}  // namespace
+
+cudaError_t ttm_presplit(const float* T, int64_t P, int K, int64_t Q, int kind, float tscale, uint16_t* hi,
+                         uint16_t* lo, int num_sms, cudaStream_t st) {
+    if (kind != 0 && kind != 2) return cudaErrorInvalidValue;
+    if (Q == 1) {
+        const int64_t n = P * (int64_t)K;
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > 16 * (int64_t)num_sms) blocks = 16 * (int64_t)num_sms;
+        if (kind == 2) k_presplit_flat<2><<<(unsigned)blocks, 256, 0, st>>>(T, n, tscale, hi, lo);
+        else k_presplit_flat<0><<<(unsigned)blocks, 256, 0, st>>>(T, n, tscale, hi, lo);
+    } else {
+        const int64_t gx = (Q + 31) / 32;
+        if (gx > 0x7fffffff) return cudaErrorInvalidValue;
+        const dim3 grid((unsigned)gx, (unsigned)((K + 31) / 32), (unsigned)(P < 65535 ? P : 65535));
+        if (kind == 2) k_presplit<2><<<grid, 256, 0, st>>>(T, P, K, Q, tscale, hi, lo);
+        else k_presplit<0><<<grid, 256, 0, st>>>(T, P, K, Q, tscale, hi, lo);
+    }
+    return cudaGetLastError();
+}
 
 bool ttm_tc_child_ok(const TcPlan* pl, int sc) {
     // one column pass, rows = one run of X's row index (last mode, or first mode
@@ -1144,7 +1283,9 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
                    : (pl->kind == 0   ? launch<1, 0, C, W>(pl, a, smem, grid, st)                   \
                       : pl->kind == 1 ? launch<1, 1, C, W>(pl, a, smem, grid, st)                   \
                                       : launch<1, 2, C, W>(pl, a, smem, grid, st)))
-    if (pl->wide)
+    if (pl->pre)
+        e = pl->kind == 0 ? launch<0, 0, 0, 8, 1, 1>(pl, a, smem, grid, st) : launch<0, 2, 0, 8, 1, 1>(pl, a, smem, grid, st);
+    else if (pl->wide)
         e = pl->mode == 0 ? (pl->kind == 0 ? launch<0, 0, 0, 8, 1>(pl, a, smem, grid, st)
                                            : launch<0, 2, 0, 8, 1>(pl, a, smem, grid, st))
                           : (pl->kind == 0 ? launch<1, 0, 0, 8, 1>(pl, a, smem, grid, st)

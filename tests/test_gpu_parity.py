@@ -327,6 +327,46 @@ def test_mixed_solve_no_fallback_on_well_conditioned(pkg):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_mixed_solve_ill_conditioned_gamma(pkg, prec):
+    """Rank-32 factors of pairwise cosine 0.95: from the first update on, the
+    diagonally scaled Gamma of modes 0 and 1 has a condition number of 3e2-2e3 and
+    that of mode 2 about 2e6 (oracle), so double-float refinement reaches its
+    rounding floor (about 2^-44 cond) before 2^-36 and must stop there instead of
+    reporting a failed solve.  The solve is isolated by running the same MTTKRPs with
+    every update solved by the FP64 factorisation: the direct residuals agree to the
+    fit tolerance (1.8e-7 measured for FP32, the mixed solve the lower).  The factors
+    themselves are ill-determined here (cond(Gamma) up to 2e6): the two solves'
+    factors differ by 9e-3 relative for f16x3, held to 5e-2.  Against the oracle the
+    MTTKRP's rounding dominates on this problem: the collinear factors' large
+    alternating coefficients cancel in M (FP32 MTTKRPs in numpy end 1.5e-5 away from
+    the FP64 residual, the GPU's FP32 path 1.3e-6), so the direct residual is held to
+    1e-5 there; the trace's Eq. (residual) values, which subtract 2 <M, A>, move by
+    up to 2.5e-5 for f16x3 and are only required to be finite."""
+    dims, R = (64, 60, 56), 32
+    Td, Tref, A0 = problem(dims, R, 46, eta=1e-3, law="collinear", C=0.95)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    ctx.sweep_msdt(4)
+    _, r = ctx.fit(exact=True)
+    A = [ctx.get_factor(n) for n in range(3)]
+    got = np.array([t["resid"] for t in ctx.trace()])
+    ctx.close()
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    ctx.set_option("solve_fp64", True)
+    ctx.sweep_msdt(4)
+    assert ctx.stats()["solves_fp64"] == 12
+    _, r64 = ctx.fit(exact=True)
+    fe = max(relerr(A[n], ctx.get_factor(n)) for n in range(3))
+    ctx.close()
+    ref = co.cp_als(Tref, A0, 4, route="msdt")
+    ro = co.residual_direct(Tref, ref.A)
+    msg = "mixed %.6e fp64-solve %.6e oracle %.6e factors %.2e" % (r, r64, ro, fe)
+    assert abs(r - r64) <= FIT_TOL[prec], msg
+    assert fe <= 5e-2, msg
+    assert abs(r - ro) <= 1e-5, msg
+    assert np.all(np.isfinite(got)), msg
+
+
 @pytest.mark.parametrize("route", ["dt", "msdt"])
 def test_run_stops_like_alg1(pkg, route):
     """cp_run: sweeps until |r - r_old| <= delta (Alg. 1), like the oracle's loop."""
@@ -589,6 +629,39 @@ def test_msdt_combined_levels(pkg, dims, R, levels, prec):
         assert st["ttm_fused"] == sum(1 for a, b in roots if b - a == 1 and fusable(a))
     with pytest.raises(pkg.CPError):
         ctx.set_option("msdt_levels", N - 1)
+    ctx.close()
+
+
+@pytest.mark.parametrize("dims,R", [((40, 48, 36), 200), ((72, 24, 136), 256), ((16, 40, 56, 12), 144),
+                                    ((56, 37, 64), 300), ((300, 8, 8), 129)])
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+def test_ttm_stored_parts(pkg, dims, R, prec):
+    """R > 128: the first-level TTM reading T's stored 16-bit parts (contracted mode
+    innermost, written by the split kernel) equals, bit for bit, the TTM that splits T
+    inside the kernel, for every mode (last, middle and first; K a multiple of 8 or
+    not, which keeps the in-kernel split), and matches the contraction of the oracle's
+    inputs.  After cp_load_tensor the parts follow the new tensor."""
+    Td, Tref, A0 = problem(dims, R, 47)
+    ctx = pkg.CPContext(Td, R, A0=A0, prec=prec)
+    got = [ctx.ttm(m).cpu().numpy() for m in range(len(dims))]
+    st = ctx.stats()
+    want = sum(1 for m in range(len(dims)) if dims[m] % 8 == 0)
+    assert st["ttm_stored_parts"] == want and st["ttm_tensor_core"] == len(dims)
+    ctx.set_option("ttm_presplit", False)
+    for m in range(len(dims)):
+        plain = ctx.ttm(m).cpu().numpy()
+        assert np.array_equal(got[m], plain), m
+        ref = np.tensordot(Tref, A0[m], axes=([m], [0]))
+        assert relerr(got[m], ref) <= 1e-5, m
+    assert ctx.stats()["ttm_stored_parts"] == want
+    ctx.set_option("ttm_presplit", True)
+    Td2, Tref2, _ = problem(dims, R, 48)
+    Td.copy_(Td2)          # the context borrows Td: change it in place
+    ctx.load_tensor()
+    for m in range(len(dims)):
+        ref = np.tensordot(Tref2, A0[m], axes=([m], [0]))
+        assert relerr(ctx.ttm(m).cpu().numpy(), ref) <= 1e-5, m
+    assert ctx.stats()["ttm_stored_parts"] == 2 * want
     ctx.close()
 
 
