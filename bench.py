@@ -89,8 +89,9 @@ def parse():
     ap.add_argument("--ttm-only", action="store_true",
                     help="time only one first-level TTM (cp_ttm, --ttm-mode) and exit")
     ap.add_argument("--ttm-mode", type=int, default=-1, help="mode of --ttm-only (default: the last)")
-    ap.add_argument("--no-presplit", action="store_true",
-                    help="R > 128: split T inside the TTM instead of reading its stored 16-bit parts")
+    ap.add_argument("--presplit", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="R > 128: T's stored 16-bit parts (cp_set_option CP_OPT_TTM_PRESPLIT; "
+                         "0 off, 1 256-column passes, 2 128-column passes; -1 the library's default)")
     ap.add_argument("--dims", default=None, help="override the workload's mode sizes, e.g. 512,512,512")
     ap.add_argument("--rank", type=int, default=None, help="override the workload's rank")
     ap.add_argument("--law", default=None, choices=["uniform", "gaussian", "collinear"])
@@ -466,8 +467,8 @@ def run_ttm_only(args, wl):
     numel = int(np.prod(dims))
     T, _, A0 = make_inputs(wl, "cuda")
     ctx = pkg.CPContext(T, R, A0=A0, prec=args.prec)
-    if args.no_presplit:
-        ctx.set_option("ttm_presplit", False)
+    if args.presplit >= 0:
+        ctx.set_option("ttm_presplit", args.presplit)
     mode = args.ttm_mode if args.ttm_mode >= 0 else len(dims) - 1
     X = torch.empty(numel // dims[mode] * R, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):

@@ -372,8 +372,11 @@ cp_status cp_get_stats(cp_ctx *ctx, cp_stats *st);
  *                     mode innermost (2 x 2 bytes per entry and mode, written at
  *                     cp_init and cp_load_tensor), so that the first-level TTM
  *                     loads its operand with TMA instead of converting T; a mode
- *                     whose copy does not fit converts T as with 0.  Results are
- *                     bit-identical to 0.
+ *                     whose copy does not fit, or whose size is not a multiple
+ *                     of 8, converts T as with 0.  1: column passes of up to 256
+ *                     (results bit-identical to 0); 2: passes of 128 with two
+ *                     accumulator sets (results equal to FP32 rounding; faster
+ *                     only for small tensors).
  * CP_EINVAL for an unknown option or value.  Takes effect at the next call.
  */
 enum { CP_OPT_FUSE_DT = 1, CP_OPT_LOOKAHEAD = 2, CP_OPT_FUSE_CHILD = 3, CP_OPT_WAIT_LIMIT = 4,

@@ -70,7 +70,7 @@ struct cp_ctx {
     // innermost ([P][Q][K]), read by that mode's first-level TTM instead of T
     uint16_t* Tp_hi[CP_MAXN] = {0};
     uint16_t* Tp_lo[CP_MAXN] = {0};
-    bool presplit = true;
+    int presplit = 1;   // 0 off, 1 on (256-column passes), 2 on with 128-column passes
     double* S[CP_MAXN] = {0};
     double* dS[CP_MAXN] = {0};
     double* Ap64[CP_MAXN] = {0};
@@ -1259,7 +1259,7 @@ static void make_mode_plans(cp_ctx* c) {
         const void* lo = (bf || hf) ? (const void*)c->blo[m]
                                     : (const void*)(c->bt32[m] + (size_t)c->Rpad * c->Kpad[m]);
         c->tc_plan[m] = cpk::ttm_tc_plan(c->T, P, (int)c->dims[m], Q, c->R, kind, hi, lo, c->Rpad, c->Kpad[m],
-                                         tscale, c->colinv[m], c->Tp_hi[m], c->Tp_lo[m]);
+                                         tscale, c->colinv[m], c->Tp_hi[m], c->Tp_lo[m], c->presplit == 2);
     }
 }
 
@@ -1617,11 +1617,11 @@ cp_status cp_set_option(cp_ctx* c, int option, int value) {
             c->solve_fp64 = value != 0;
             return CP_OK;
         case CP_OPT_TTM_PRESPLIT:
-            if (value != 0 && value != 1) return CP_EINVAL;
-            if (c->presplit == (value != 0)) return CP_OK;
+            if (value < 0 || value > 2) return CP_EINVAL;
+            if (c->presplit == value) return CP_OK;
             CKST(ahead_join(c));
             CKCUDA(c, cudaStreamSynchronize(c->st));
-            c->presplit = value != 0;
+            c->presplit = value;
             if (c->presplit) CKST(alloc_presplit(c));
             else free_presplit(c);
             if (c->cfg.prec != CP_FP32_SIMT) make_mode_plans(c);

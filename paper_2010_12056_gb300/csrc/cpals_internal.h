@@ -54,7 +54,7 @@ bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R);
 // kernel then loads its A operand directly (no converter warps).
 TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind, const void* bhi,
                     const void* blo, int Rpad, int Kpad, float tscale = 1.f, const float* colinv = nullptr,
-                    const void* pre_hi = nullptr, const void* pre_lo = nullptr);
+                    const void* pre_hi = nullptr, const void* pre_lo = nullptr, bool pre_narrow = false);
 // T viewed as [P][K][Q] -> its 16-bit parts [P][Q][K] (kind 2: fp16 of T tscale; kind 0: bf16),
 // split exactly as the kernel's converter warps split it
 cudaError_t ttm_presplit(const float* T, int64_t P, int K, int64_t Q, int kind, float tscale, uint16_t* hi,

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
              const __grid_constant__ CUtensorMap tmBlo3, const __grid_constant__ CUtensorMap tmTlo,
              const TcArgs a) {
     static_assert(!WIDE || (KIND != 1 && CHILD == 0), "wide passes use 16-bit parts and no first child");
-    static_assert(!PRE || (WIDE && MODE == 0), "stored parts: wide passes, flattened rows");
+    static_assert(!PRE || MODE == 0, "stored parts: flattened rows");
     constexpr int BK = (KIND == 1 || WIDE) ? 32 : 64;
     constexpr uint32_t STG = BM * BK * 4;
     constexpr uint32_t ROWB = WIDE ? 64u : 128u;     // bytes of one operand row (k-chunk)
@@ -859,15 +859,18 @@ bool ttm_tc_supported(int64_t P, int K, int64_t Q, int R) {
 
 TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind, const void* bhi,
                     const void* blo, int Rpad, int Kpad, float tscale, const float* colinv, const void* pre_hi,
-                    const void* pre_lo) {
+                    const void* pre_lo, bool pre_narrow) {
     if (!ttm_tc_supported(P, K, Q, R) || ((uintptr_t)T & 15)) return nullptr;
     if (kind == 2 && (!colinv || ((uintptr_t)colinv & 15))) return nullptr;
     EncodeTiledFn enc = encoder();
     if (!enc) return nullptr;
-    const bool wide = kind != 1 && R > PASS_COLS;
     // stored parts: rows of K 16-bit values must be 16-byte aligned for the TMA
-    const bool pre = wide && pre_hi && pre_lo && K % 8 == 0 && P * Q <= ((int64_t)1 << 31) &&
-                     (((uintptr_t)pre_hi | (uintptr_t)pre_lo) & 15) == 0;
+    const bool pre = kind != 1 && R > PASS_COLS && pre_hi && pre_lo && K % 8 == 0 &&
+                     P * Q <= ((int64_t)1 << 31) && (((uintptr_t)pre_hi | (uintptr_t)pre_lo) & 15) == 0;
+    // R > 128 with 16-bit parts: one pass of up to 256 columns (one accumulator
+    // set), or with stored parts on request passes of 128 with two sets (the
+    // epilogue overlaps the next work item; A is read once per pass)
+    const bool wide = kind != 1 && R > PASS_COLS && !(pre && pre_narrow);
     const int BK = (kind == 1 || wide) ? 32 : 64;
     const int pcols = wide ? PASS_COLS_WIDE : PASS_COLS;
     const size_t rowb = wide ? 64 : 128;
@@ -881,7 +884,7 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
     pl->K = K;
     pl->R = R;
     pl->nk = (K + BK - 1) / BK;
-    pl->S_op = pre ? 4 : (wide ? 3 : 2);   // wide: 32-k chunks, a deeper operand ring
+    pl->S_op = pre ? (wide ? 4 : 3) : (wide ? 3 : 2);   // wide: 32-k chunks, a deeper operand ring
     pl->npass = (R + pcols - 1) / pcols;
     pl->tscale = tscale;
     pl->colinv = colinv;
@@ -898,7 +901,7 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
         bool fits = false;
         if (pre) {
             // no staging ring
-            fits = layout_bytes(0, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK, 8, kind, false, 0, true) <= SMEM_LIMIT;
+            fits = layout_bytes(0, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK, 8, kind, false, 0, wide) <= SMEM_LIMIT;
         } else {
             for (int st = MAX_STG; st >= 2 && !fits; --st)
                 if (layout_bytes(st, pl->S_op, ps.Rpad, pl->nk, ps.b_resident, BK, epi_warps_for(ps.Rpad, kind), kind,
@@ -934,13 +937,15 @@ TcPlan* ttm_tc_plan(const float* T, int64_t P, int K, int64_t Q, int R, int kind
         pl->mode = 0;
         const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)(P * Q)};
         const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-        const cuuint32_t box[2] = {32, BM};
+        // one operand row per tile row: BK 16-bit values (64 bytes wide, 128 narrow)
+        const cuuint32_t box[2] = {(cuuint32_t)BK, BM};
+        const CUtensorMapSwizzle asw = wide ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
         const CUtensorMapDataType pt = kind == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-        r1 = enc(&pl->tmT, pt, 2, (void*)pre_hi, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                 CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        r1 = enc(&pl->tmT, pt, 2, (void*)pre_hi, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, asw,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r1 == CUDA_SUCCESS)
-            r1 = enc(&pl->tmTlo, pt, 2, (void*)pre_lo, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            r1 = enc(&pl->tmTlo, pt, 2, (void*)pre_lo, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, asw,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else if (Q == 1) {
         pl->mode = 0;
         const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)P};
@@ -1283,8 +1288,10 @@ cudaError_t ttm_tc_run(const TcPlan* pl, float* X, int prec, int num_sms, unsign
                    : (pl->kind == 0   ? launch<1, 0, C, W>(pl, a, smem, grid, st)                   \
                       : pl->kind == 1 ? launch<1, 1, C, W>(pl, a, smem, grid, st)                   \
                                       : launch<1, 2, C, W>(pl, a, smem, grid, st)))
-    if (pl->pre)
+    if (pl->pre && pl->wide)
         e = pl->kind == 0 ? launch<0, 0, 0, 8, 1, 1>(pl, a, smem, grid, st) : launch<0, 2, 0, 8, 1, 1>(pl, a, smem, grid, st);
+    else if (pl->pre)
+        e = pl->kind == 0 ? launch<0, 0, 0, 8, 0, 1>(pl, a, smem, grid, st) : launch<0, 2, 0, 8, 0, 1>(pl, a, smem, grid, st);
     else if (pl->wide)
         e = pl->mode == 0 ? (pl->kind == 0 ? launch<0, 0, 0, 8, 1>(pl, a, smem, grid, st)
                                            : launch<0, 2, 0, 8, 1>(pl, a, smem, grid, st))
