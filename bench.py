@@ -57,7 +57,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # DRAM bytes per launch of the last-mode TTM on 128^4 R=64 from ncu captures of
 # the current kernel, by precision (profiles/ttm_tc_*_c2.md); a precision whose
 # kernel changed since its capture has no entry (traffic null)
-TRAFFIC_C2 = {"f16x3": 1.073861e9 + 0.501550e9}
+TRAFFIC_C2 = {"f16x3": 1.073848e9 + 0.500767e9}
 FIT_SWEEPS = 20     # the fit check: direct residual after this many MSDT sweeps from A0
 FIT_TOL = 1e-6
 

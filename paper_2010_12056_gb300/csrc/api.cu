@@ -104,7 +104,8 @@ struct cp_ctx {
     double* scal_part = nullptr;   // per mode: the solve's per-block scalars
     // the update's scalars are reduced on their own stream, off the critical path
     cudaStream_t aux = nullptr;
-    cudaEvent_t ev_g = nullptr, ev_a = nullptr, ev_scal[CP_MAXN] = {0};
+    cudaEvent_t ev_g = nullptr, ev_scal[CP_MAXN] = {0};
+    int aux_last = -1;   // mode whose scalars the aux stream finished last (ev_scal)
     double* scal_hist = nullptr;   // [cap][N][CP_NSCAL]
     int scal_hist_cap = 0;
     double* red_part = nullptr;
@@ -585,7 +586,7 @@ cp_status update_mode(cp_ctx* c, int u, const float* M, bool pp, double* scal) {
     CKCUDA(c, cudaStreamWaitEvent(c->aux, c->ev_g, 0));
     LAUNCH(c, cpk::scal_fin(sp, nblk, tg, c->ntiles, scal, c->aux));
     CKCUDA(c, cudaEventRecord(c->ev_scal[u], c->aux));
-    CKCUDA(c, cudaEventRecord(c->ev_a, c->aux));
+    c->aux_last = u;
     c->ver[u] = ++c->vclock;
     return CP_OK;
 }
@@ -603,7 +604,7 @@ cp_status check_dev_err(cp_ctx* c) {
 cp_status harvest(cp_ctx* c, int k, const int* kinds, const int* inits, int first_event) {
     std::vector<double>& h = c->last_hist;
     h.assign((size_t)k * c->N * CP_NSCAL, 0.0);
-    CKCUDA(c, cudaStreamWaitEvent(c->st, c->ev_a, 0));
+    if (c->aux_last >= 0) CKCUDA(c, cudaStreamWaitEvent(c->st, c->ev_scal[c->aux_last], 0));  // the last scalars
     CKCUDA(c, cudaMemcpyAsync(h.data(), c->scal_hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CKST(check_dev_err(c));
     for (int i = 0; i < k; ++i) {
@@ -1221,7 +1222,7 @@ void free_all(cp_ctx* c) {
     F(c->Mt); F(c->d_Slist); F(c->d_dSlist); F(c->Gamma); F(c->L); F(c->invd); F(c->W);
     if (c->aux) { cudaStreamSynchronize(c->aux); cudaStreamDestroy(c->aux); c->aux = nullptr; }
     F(c->tile_gs); F(c->scal_part);
-    for (cudaEvent_t* e : {&c->ev_g, &c->ev_a})
+    for (cudaEvent_t* e : {&c->ev_g})
         if (*e) { cudaEventDestroy(*e); *e = nullptr; }
     for (int i = 0; i < CP_MAXN; ++i)
         if (c->ev_scal[i]) { cudaEventDestroy(c->ev_scal[i]); c->ev_scal[i] = nullptr; } F(c->scal_hist); F(c->red_part); F(c->d_red_out); F(c->dev_err);
@@ -1432,7 +1433,6 @@ cp_status cp_init(cp_ctx** out, int N, const int64_t* dims, int R, const void* T
     TRY(dalloc(c, &c->scal_part, (size_t)N * c->smax * CP_NSCAL));
     TRYC(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
     TRYC(cudaEventCreateWithFlags(&c->ev_g, cudaEventDisableTiming));
-    TRYC(cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming));
     for (int i = 0; i < N; ++i) TRYC(cudaEventCreateWithFlags(&c->ev_scal[i], cudaEventDisableTiming));
     TRY(dalloc(c, &c->red_part, 4096));
     TRY(dalloc(c, &c->d_red_out, 16));

@@ -11,6 +11,7 @@
 
 #include "cpals_internal.h"
 #include "df_arith.h"
+#include "pdl.h"
 
 namespace {
 
@@ -165,6 +166,8 @@ __global__ void __launch_bounds__(256) k_gram_df(const float2* __restrict__ A, c
     __shared__ float2 a1[16][17], a2[16][17], d2[16][17];
     __shared__ float2 ps[256], pd[256];
     __shared__ float2 red[8];
+    pdl::wait();
+    pdl::trigger();
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31, warp = tid >> 5;
     const int r1 = blockIdx.x * 16 + ty, r2 = blockIdx.y * 16 + tx;
     const int c = blockIdx.z, nc = gridDim.z;
@@ -607,6 +610,8 @@ __global__ void __launch_bounds__(1024) k_f16_operand(const float* __restrict__ 
     __shared__ float red[32][33];
     __shared__ uint16_t th[32][33], tl[32][33];
     __shared__ float scl[32];
+    pdl::wait();
+    pdl::trigger();
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int c = blockIdx.x * 32 + tx;
     float m = 0.f;
@@ -764,7 +769,9 @@ cudaError_t kr_operand(const double* Aa, const double* Ab, int sa, int sb, int R
 
 cudaError_t f16_operand(const float* A32, int s, int R, int Rpad, int Kpad, int eT, uint16_t* hi, uint16_t* lo,
                         float* colinv, cudaStream_t st) {
-    k_f16_operand<<<(unsigned)((R + 31) / 32), 1024, 0, st>>>(A32, s, R, Rpad, Kpad, eT, hi, lo, colinv);
+    cudaError_t e = pdl::launch(k_f16_operand, (unsigned)((R + 31) / 32), 1024, 0, st, A32, s, R, Rpad, Kpad, eT,
+                                hi, lo, colinv);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -836,13 +843,14 @@ cudaError_t gram_df(const float2* A2, const float2* dA2, int s, int R, const flo
     cfg.blockDim = dim3(256, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 1;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = nc;
+    pdl::set_attr(attr[1]);
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, k_gram_df, A2, dA2, s, R, rows_per, G2, S, dS, S2, dS2, tile_gs);
 }
 

@@ -6,6 +6,7 @@
 // contiguous along (q, r) for every k; the factor is tiny and stays in L1/L2.
 // The kernel is bandwidth-bound: one pass over X, 2 flops per element read.
 #include "cpals_internal.h"
+#include "pdl.h"
 
 namespace {
 
@@ -33,6 +34,8 @@ __global__ void __launch_bounds__(256) k_mttv(const float* __restrict__ X,
                                               float* __restrict__ Y, int64_t P, int K, int64_t Q,
                                               int R, int TX, int KS) {
     extern __shared__ float4 red[];  // TX * KS
+    pdl::wait();
+    pdl::trigger();
     const int RV = R / VEC;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int64_t nout = P * Q * RV;
@@ -110,17 +113,18 @@ cudaError_t mttv(const float* X, const float* A, float* Y, int64_t P, int K, int
     if (stride) nchunks = (int64_t)max_blocks_per_sm * num_sms;
     const unsigned nblk = (unsigned)nchunks;
     const size_t smem = sizeof(float4) * 256;
-#define CP_MTTV_LAUNCH(V)                                                                    \
-    (stride ? k_mttv<V, 16, true><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS)      \
-            : k_mttv<V, 16, false><<<nblk, 256, smem, st>>>(X, A, Y, P, K, Q, R, TX, KS))
+#define CP_MTTV_LAUNCH(V)                                                                               \
+    (stride ? pdl::launch(k_mttv<V, 16, true>, nblk, 256, smem, st, X, A, Y, P, K, Q, R, TX, KS)        \
+            : pdl::launch(k_mttv<V, 16, false>, nblk, 256, smem, st, X, A, Y, P, K, Q, R, TX, KS))
+    cudaError_t e;
     if (VEC == 4)
-        CP_MTTV_LAUNCH(4);
+        e = CP_MTTV_LAUNCH(4);
     else if (VEC == 2)
-        CP_MTTV_LAUNCH(2);
+        e = CP_MTTV_LAUNCH(2);
     else
-        CP_MTTV_LAUNCH(1);
+        e = CP_MTTV_LAUNCH(1);
 #undef CP_MTTV_LAUNCH
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace cpk

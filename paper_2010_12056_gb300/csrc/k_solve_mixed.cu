@@ -25,6 +25,7 @@
 
 #include "cpals_internal.h"
 #include "df_arith.h"
+#include "pdl.h"
 
 namespace {
 
@@ -827,6 +828,8 @@ __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
     float* pkf = reinterpret_cast<float*>(sm + lay.pk + 3 * (size_t)R);  // (KS-1) x R FP32 partials
     const int kq = (R + KS - 1) / KS, k0 = q * kq, k1 = min(R, k0 + kq);
     const int x = blockIdx.x;
+    pdl::wait();
+    pdl::trigger();
     const int path = *mode;
     const int RR = R * R;
     double sc[CP_NSCAL];
@@ -1409,9 +1412,8 @@ cudaError_t launch_solve_mixed(const float* M, const double* W, const float2* W2
                              (int)(solve_smem(MIXED_MAXR).total * sizeof(double) + 64));
         attr = true;
     }
-    k_solve_mixed<RT, KS><<<(unsigned)s, SOLVE_THREADS * KS, smem, st>>>(M, W, W2, G, G2, Ginv, L64, invd64,
-                                                                         mode, o, s, R, scal, scal_part, dev_err);
-    return cudaGetLastError();
+    return pdl::launch(k_solve_mixed<RT, KS>, (unsigned)s, SOLVE_THREADS * KS, smem, st, M, W, W2, G, G2, Ginv, L64,
+                       invd64, mode, o, s, R, scal, scal_part, dev_err);
 }
 
 }  // namespace

@@ -43,12 +43,14 @@
 //               that cross tiles added by a second kernel in a fixed order.
 // Every mbarrier wait is bounded; on expiry the CTA sets DEVERR_TIMEOUT, drains
 // what it issued (bounded), frees TMEM and exits.
+#include <atomic>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "cpals_internal.h"
 #include "tc_ptx.h"
+#include "pdl.h"
 
 namespace {
 
@@ -266,6 +268,11 @@ __global__ void __launch_bounds__(nthreads(EW, CHILD), 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // everything above touched only this CTA's shared memory and TMEM: the kernel
+    // before this one on the stream may still be running until here.  No early
+    // signal to the next kernel: its blocks (a multi-TTV of many blocks) would
+    // take the SM this grid leaves to the next update's normal-equation inverse.
+    pdl::wait();
     if (KIND == 2) {
         // per-column output scales, read by the epilogue for every tile
         float* sCs = reinterpret_cast<float*>(gbase + (cs0 - base));
@@ -1028,15 +1035,25 @@ int64_t ttm_tc_rows(const TcPlan* pl) { return pl->PQ; }
 template <int MODE, int KIND, int CHILD, int EW, int WIDE = 0, int PRE = 0>
 static cudaError_t launch(const TcPlan* pl, const TcArgs& a, size_t smem, unsigned grid,
                           cudaStream_t st) {
-    cudaFuncSetAttribute(k_ttm_tc<MODE, KIND, CHILD, EW, WIDE, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    // the shared-memory limit once per device (every layout stays below it)
+    static std::atomic<unsigned> set_on{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned bit = 1u << (dev & 31);
+    if (!(set_on.load() & bit)) {
+        e = cudaFuncSetAttribute(k_ttm_tc<MODE, KIND, CHILD, EW, WIDE, PRE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+        if (e != cudaSuccess) return e;
+        set_on.fetch_or(bit);
+    }
+    if (smem > SMEM_LIMIT) return cudaErrorInvalidValue;
     // passes beyond npass repeat pass 0's maps (never read)
     auto ps = [&](int q) -> const TcPass& { return pl->pass[q < pl->npass ? q : 0]; };
     // tmTlo is read only with stored parts (PRE)
-    k_ttm_tc<MODE, KIND, CHILD, EW, WIDE, PRE><<<grid, nthreads(EW, CHILD), smem, st>>>(
-        pl->tmT, ps(0).tmBhi, ps(0).tmBlo, ps(1).tmBhi, ps(1).tmBlo, ps(2).tmBhi, ps(2).tmBlo, ps(3).tmBhi,
-        ps(3).tmBlo, PRE ? pl->tmTlo : pl->tmT, a);
-    return cudaGetLastError();
+    return pdl::launch(k_ttm_tc<MODE, KIND, CHILD, EW, WIDE, PRE>, grid, nthreads(EW, CHILD), smem, st, pl->tmT,
+                       ps(0).tmBhi, ps(0).tmBlo, ps(1).tmBhi, ps(1).tmBlo, ps(2).tmBhi, ps(2).tmBlo, ps(3).tmBhi,
+                       ps(3).tmBlo, PRE ? pl->tmTlo : pl->tmT, a);
 }
 
 namespace {
