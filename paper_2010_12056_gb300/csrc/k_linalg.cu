@@ -1,11 +1,12 @@
 // Dense side kernels of the factor updates and the residual (Alg. 1 solve and Gram;
 // Alg. 2 approximated update; Eq. ds, Eq. residual, Eq. residual-def): the Grams
-// S(n) = A^T A and dS(n) = A^T dA in FP64 (thread-block clusters), the update's
+// S(n) = A^T A and dS(n) = A^T dA (thread-block clusters; from the factor's float
+// pairs in double-float arithmetic for R <= 128, FP64 above), the update's
 // scalar terms, the operand copies of a factor for the tensor-core TTM (bf16 /
-// tf32 / scaled fp16 parts), norms and maxima, the direct residual, the PP
-// first-order terms (Eq. U_ni) and the Khatri-Rao operand of the fused
-// standard-tree contraction.  The normal equations themselves (Hadamard chain,
-// FP32 inverse with FP64 refinement) are in k_solve_mixed.cu.
+// tf32 / scaled fp16 parts), norms and maxima, the direct residual on the CUDA
+// cores, the PP first-order terms (Eq. U_ni) and the Khatri-Rao operand of the
+// fused standard-tree contraction.  The normal equations themselves (Hadamard
+// chain, FP32 inverse with iterative refinement) are in k_solve_mixed.cu.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
