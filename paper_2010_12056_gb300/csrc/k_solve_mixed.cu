@@ -8,8 +8,7 @@
 // parallel across the R entries of a row:
 //   k_gamma_form  Gamma = *_{k != n} S(k) and PP's W in FP64 (many blocks)
 //   k_gj_inv      (one CTA) the FP32 inverse of the diagonally scaled Gamma by
-//                 Gauss-Jordan elimination, in blocks of one warp's rows (one
-//                 barrier per block); if the scaled condition number is
+//                 Gauss-Jordan elimination; if the scaled condition number is
 //                 above 1e6 or a pivot is not positive, an FP64 LDL^T of Gamma
 //                 instead, and the solve kernel substitutes in FP64.
 //   k_solve_mixed (one block per row) m = M(x,:) [+ A_old(x,:) W];
@@ -318,104 +317,6 @@ __device__ __forceinline__ bool gj_steps(float (&a)[IR][JC], int n, float (*prow
     return !bad;
 }
 
-// Block form of the same elimination, IR pivots at a time: the pivots of block
-// K = kb .. kb + IR - 1 are the rows of one warp.  That warp eliminates them
-// among its own rows (pivot values and pivot-column entries by warp shuffles,
-// no block barrier), which gives those rows their final values
-// [P | P Gt_K,rest] (P = the inverse of the pivot block); it publishes them (U),
-// every thread publishes its entries of the pivot columns as they were before
-// the block, and after one barrier each row i outside K takes
-//     a_ij <- [j not in K] a_ij - sum_t a_i,kb+t u_t,j,
-// which is what the IR scalar steps give in exact arithmetic (rows outside K
-// change only through rows of K).  Two buffer sets: one barrier per block
-// instead of one per pivot.  Returns false (every thread) if a pivot is not
-// positive.  Ends with a barrier.
-template <int TY, int IR, int JC>
-__device__ __forceinline__ bool gj_block_steps(float (&a)[IR][JC], int n, float (*ub)[IR][MIXED_MAXR],
-                                               float (*pb)[MIXED_MAXR][IR], int* sbad) {
-    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    const int r0 = ty * IR, c0 = tx * JC;
-    if (tid == 0) *sbad = 0;
-    __syncthreads();
-    int par = 0;
-    for (int kb = 0; kb < n; kb += IR, par ^= 1) {
-        const bool own = ty == kb / IR;
-        // the pivot columns' entries before this block (columns kb .. kb + IR - 1
-        // belong to lanes kb / JC .. (kb + IR - 1) / JC)
-#pragma unroll
-        for (int j = 0; j < JC; ++j) {
-            const int c = c0 + j;
-            if (c >= kb && c < kb + IR)
-#pragma unroll
-                for (int i = 0; i < IR; ++i) pb[par][r0 + i][c - kb] = a[i][j];
-        }
-        if (own) {
-            bool bad = false;
-#pragma unroll
-            for (int kk = 0; kk < IR; ++kk) {
-                const int k = kb + kk;
-                if (k >= n) break;
-                // kb is a multiple of IR and IR of JC: column k sits in register
-                // slot kk % JC of lane k / JC
-                const int jk = kk % JC;
-                const int src = k / JC;
-                const float p = __shfl_sync(FULL, a[kk][jk], src);
-                if (!(p > 0.f) || !isfinite(p)) {
-                    bad = true;
-                    break;
-                }
-                const float inv = __frcp_rn(p);
-                float f[IR];
-#pragma unroll
-                for (int i = 0; i < IR; ++i) f[i] = __shfl_sync(FULL, a[i][jk], src) * inv;
-                const bool kcol = tx == src;
-                float rp[JC];
-#pragma unroll
-                for (int j = 0; j < JC; ++j) rp[j] = a[kk][j];
-                if (kcol) rp[jk] = 1.f;
-#pragma unroll
-                for (int i = 0; i < IR; ++i) {
-                    if (i == kk) {
-#pragma unroll
-                        for (int j = 0; j < JC; ++j) a[i][j] = rp[j] * inv;
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < JC; ++j) {
-                            const float g = fmaf(-f[i], rp[j], a[i][j]);
-                            a[i][j] = (j == jk && kcol) ? -f[i] : g;
-                        }
-                    }
-                }
-            }
-            if (bad && tx == 0) *sbad = 1;   // the warp agrees: every lane saw the same pivot
-#pragma unroll
-            for (int i = 0; i < IR; ++i)
-#pragma unroll
-                for (int j = 0; j < JC; ++j) ub[par][i][c0 + j] = a[i][j];
-        }
-        __syncthreads();
-        if (*sbad) return false;
-        if (!own) {
-#pragma unroll
-            for (int i = 0; i < IR; ++i) {
-                float pk[IR];
-#pragma unroll
-                for (int t = 0; t < IR; ++t) pk[t] = pb[par][r0 + i][t];
-#pragma unroll
-                for (int j = 0; j < JC; ++j) {
-                    const int c = c0 + j;
-                    float acc = (c >= kb && c < kb + IR) ? 0.f : a[i][j];
-#pragma unroll
-                    for (int t = 0; t < IR; ++t) acc = fmaf(-pk[t], ub[par][t][c], acc);
-                    a[i][j] = acc;
-                }
-            }
-        }
-    }
-    __syncthreads();
-    return true;
-}
-
 template <int TY, int IR, int JC>
 __global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(float* __restrict__ G32, int R,
                                                        double* __restrict__ G,
@@ -431,11 +332,11 @@ __global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(float* __restrict__ G32, 
                   "tile shape");
     __shared__ double red[32];
     __shared__ double sinv[CP_MAXR], srs[CP_MAXR];
+    __shared__ __align__(16) float prow[2][MIXED_MAXR];
+    __shared__ __align__(16) float pcol[2][MIXED_MAXR];
     __shared__ float dsc[MIXED_MAXR];
-    __shared__ int sfail, sbad;
+    __shared__ int sfail;
     __shared__ unsigned gmax_bits, imax_bits;
-    __shared__ float ublk[2][IR][MIXED_MAXR];   // the pivot block's rows (block elimination)
-    __shared__ float pblk[2][MIXED_MAXR][IR];   // the pivot columns before the block
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const int r0 = ty * IR, c0 = tx * JC;
     if (tid == 0) {
@@ -525,7 +426,7 @@ __global__ void __launch_bounds__(32 * TY, 1) k_gj_inv(float* __restrict__ G32, 
         if (tx == 0 && r0 + i < R) atomicMax(&gmax_bits, __float_as_uint(rs));
     }
     bool use64 = sfail != 0;
-    if (!use64) use64 = !gj_block_steps<TY, IR, JC>(a, R, ublk, pblk, &sbad);
+    if (!use64) use64 = !gj_steps<TY, IR, JC>(a, R, prow, pcol);
     if (!use64) {
 #pragma unroll
         for (int i = 0; i < IR; ++i) {
@@ -1256,11 +1157,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS * KS, 1) k_solve_mixed(
             conv = rho * dmax <= 0x1.0p-36f * xmax || dmax == 0.f;
             // The residual's own rounding (about 2^-44 cond(Gamma) relative in
             // double-float, 2^-53 cond in FP64) is a floor the steps cannot go
-            // below: once they stop contracting there, x is as accurate as this
+            // below: once they stop contracting there (rho >= 0.9; a slower but
+            // real contraction goes on to 2^-36), x is as accurate as this
             // residual can make it.  The floor is accepted up to 2^-20 ||x||: it is
             // above 2^-36 only for cond >= 2^8, and then the FP32-rounded m alone
             // moves the exact solution by about 2^-24 cond >= 2^-16.
-            conv = conv || ((itr >= 2 && rho >= 0.5f) || itr == 29) && dmax <= 0x1.0p-20f * xmax;
+            conv = conv || ((itr >= 2 && rho >= 0.9f) || itr == 29) && dmax <= 0x1.0p-20f * xmax;
             prev = dmax;
             if (conv) break;
             __syncthreads();  // redf[] is rewritten by the next step
