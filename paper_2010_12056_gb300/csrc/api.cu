@@ -1268,8 +1268,13 @@ static void make_mode_plans(cp_ctx* c) {
 // allocated where memory allows (a mode without them converts T in its TTM),
 // refilled whenever T or its f16x3 scale changes
 static bool presplit_wanted(const cp_ctx* c, int m) {
-    return c->presplit && c->R > 128 && (c->cfg.prec == CP_F16X3 || c->cfg.prec == CP_BF16X3) &&
-           c->dims[m] % 8 == 0 && c->numel <= ((int64_t)1 << 31);
+    if (!(c->presplit && c->R > 128 && (c->cfg.prec == CP_F16X3 || c->cfg.prec == CP_BF16X3) &&
+          c->dims[m] % 8 == 0 && c->numel <= ((int64_t)1 << 31)))
+        return false;
+    // only for a mode whose first-level TTM runs on the tensor cores at all
+    int64_t P, Q;
+    contract_dims(c, 0u, m, &P, &Q);
+    return cpk::ttm_tc_supported(P, (int)c->dims[m], Q, c->R);
 }
 
 static void free_presplit(cp_ctx* c) {
