@@ -1303,10 +1303,15 @@ static cp_status alloc_presplit(cp_ctx* c) {
     for (int m = 0; m < c->N; ++m) {
         if (!presplit_wanted(c, m) || c->Tp_hi[m]) continue;
         const size_t bytes = sizeof(uint16_t) * (size_t)c->numel;
-        if (cudaMalloc(&c->Tp_hi[m], bytes) != cudaSuccess || cudaMalloc(&c->Tp_lo[m], bytes) != cudaSuccess) {
-            (void)cudaGetLastError();  // out of memory: this mode converts T in its TTM
-            if (c->Tp_hi[m]) cudaFree(c->Tp_hi[m]);
-            c->Tp_hi[m] = c->Tp_lo[m] = nullptr;
+        void* hi = nullptr;
+        void* lo = nullptr;
+        if (cudaMalloc(&hi, bytes) == cudaSuccess && cudaMalloc(&lo, bytes) == cudaSuccess) {
+            c->Tp_hi[m] = static_cast<uint16_t*>(hi);
+            c->Tp_lo[m] = static_cast<uint16_t*>(lo);
+        } else {
+            // out of memory (not a sticky error): this mode splits T in its TTM
+            (void)cudaGetLastError();
+            if (hi) cudaFree(hi);
         }
     }
     return fill_presplit(c);
